@@ -1,0 +1,485 @@
+"""Benchmark of the permute-scale-add hot path (TTC, arXiv 1607.01249, Eq. 1).
+
+Default workload (`sweep`): one step = every case of the 2D..6D sweep of
+single transposes with 2^26 elements per tensor (N = 2..6, 8 seeded perms per
+N, FP32 and FP64, alpha = 1.7, beta in {0, 0.4}) = 160 transposes through the
+C ABI, inputs resident in HBM.  Metric: effective HBM bandwidth (decimal GB/s)
+counting n*(s_A + s_B) bytes for beta = 0 and n*(s_A + 2 s_B) otherwise.
+
+Other workloads (`--workload`): single4d, packing, batch, serving.
+
+--impl reference times the CPU oracle (plain C, FP64 arithmetic) on the host
+cores on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank runs the same workload on its own GPU
+(replicas, no data exchange); the step time is the max over ranks and the
+value is the bytes of all ranks over that time.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1607_01249_gb300 import inputs  # noqa: E402
+
+METRIC = "effective HBM GB/s (frac of ~8 TB/s); served transposes/s + p99 vs per-call"
+KERNEL_SOURCES = ["paper_1607_01249_gb300/csrc/kernels.cu", "paper_1607_01249_gb300/csrc/kernels.cuh"]
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for s in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, s), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(f"{workload}:{kernel}")
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for i, nm in enumerate(names):
+                if s[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------- workloads --
+
+def sweep_problems():
+    return inputs.sweep_cases()
+
+
+def workload_problems(name: str):
+    if name == "sweep":
+        return sweep_problems()
+    if name == "single4d":
+        return [inputs.single_4d()]
+    if name == "packing":
+        return inputs.packing_cases()
+    raise ValueError(name)
+
+
+def storage_torch(dt):
+    import torch
+    return {"f32": torch.float32, "f64": torch.float64, "bf16": torch.int16, "e4m3": torch.uint8}[dt]
+
+
+class DeviceSet:
+    """Device buffers for a list of problems: two alternating A/B sets per
+    dtype pair so that consecutive transposes never re-read the same input."""
+
+    def __init__(self, probs, seed=0):
+        import torch
+        self.bufs = {}
+        need = {}
+        for p in probs:
+            key = (p.dtype_in, p.dtype_out)
+            a, b = need.get(key, (0, 0))
+            need[key] = (max(a, p.vol_a), max(b, p.vol_b))
+        g = torch.Generator(device="cuda")
+        g.manual_seed(seed)
+        for (di, do), (va, vb) in need.items():
+            sets = []
+            for j in range(2):
+                A = self._rand(di, va, g)
+                B = self._rand(do, vb, g)
+                sets.append((A, B))
+            self.bufs[(di, do)] = sets
+
+    @staticmethod
+    def _rand(dt, n, g):
+        import torch
+        if dt in ("f32", "f64"):
+            t = torch.empty(n, dtype=storage_torch(dt), device="cuda")
+            t.uniform_(-1.0, 1.0, generator=g)
+            return t
+        x = torch.empty(n, dtype=torch.float32, device="cuda").uniform_(-1.0, 1.0, generator=g)
+        if dt == "bf16":
+            return (x.view(torch.int32) >> 16).to(torch.int16)
+        return torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda", generator=g)
+
+    def get(self, p, i):
+        return self.bufs[(p.dtype_in, p.dtype_out)][i % 2]
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_1607_01249_gb300 import build as ttc_build
+    from paper_1607_01249_gb300 import ttc
+
+    ttc_build.build()
+    ttc.lib()
+    dev = rank % max(torch.cuda.device_count(), 1)
+    torch.cuda.set_device(dev)
+    probs = workload_problems(args.workload)
+    plans = [ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta, p.outer_a, p.outer_b)
+             for p in probs]
+    if args.autotune:
+        for pl in plans:
+            pl.autotune(max_candidates=args.autotune)
+    bufs = DeviceSet(probs)
+    stream = torch.cuda.current_stream()
+    bytes_step = sum(p.algorithmic_bytes() for p in probs)
+
+    def step(events=None):
+        for i, (p, pl) in enumerate(zip(probs, plans)):
+            A, B = bufs.get(p, i)
+            if events is not None:
+                events[i][0].record(stream)
+            pl.execute(A, B, stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(max(args.warmup, 3) if args.warmup >= 0 else 3):
+        step()
+    torch.cuda.synchronize()
+
+    # per-launch durations (CUDA events on the launching stream), one extra pass
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in probs]
+    step(ev)
+    torch.cuda.synchronize()
+    per_case_ms = [a.elapsed_time(b) for a, b in ev]
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev) if rank == 0 else None
+    if clk:
+        clk.start()
+    l0 = ttc.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = ttc.launch_count() - l0
+    clocks = clk.stop() if clk else None
+    ms_total = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        tdist.barrier()
+    ms_step = ms_total / args.steps
+    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+
+    # dominant kernel: group launches by variant
+    by_var = {}
+    for p, pl, ms in zip(probs, plans, per_case_ms):
+        v = pl.info()["variant"]
+        d = by_var.setdefault(v, {"ms": 0.0, "bytes": 0, "launches": 0})
+        d["ms"] += ms
+        d["bytes"] += p.algorithmic_bytes()
+        d["launches"] += 1
+    dom = max(by_var, key=lambda k: by_var[k]["ms"])
+    peak, peak_kind = measured_peaks()
+    kname = {"tile": "tile_kernel", "copy": "copy_kernel"}.get(dom, dom)
+    achieved = by_var[dom]["bytes"] / (by_var[dom]["ms"] * 1e-3) / 1e9
+    tr = ncu_traffic(kname, args.workload)
+    case_gbs = [p.algorithmic_bytes() / (ms * 1e-3) / 1e9 for p, ms in zip(probs, per_case_ms)]
+    big = [g for p, g in zip(probs, case_gbs) if p.n * inputs.DTYPE_BYTES[p.dtype_in] >= (256 << 20)]
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, probs, plans, bufs, stream, world)
+
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.workload == "sweep" else "+".join(sorted({p.dtype_in for p in probs})),
+        "data": "synthetic (seeded uniform[-1,1], torch Philox on the device)",
+        "config": {"workload": workload_desc(args.workload, probs), "transposes_per_step": len(probs),
+                   "algorithmic_bytes_per_step": bytes_step, "l2": "inputs > L2 (256-512 MiB per tensor), "
+                   "two alternating buffer sets" if args.workload == "sweep" else "see workload",
+                   "parallelism": f"replicas x{world}", "autotune": bool(args.autotune)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "kernel": kname, "launches": by_var[dom]["launches"],
+                     "traffic": (tr["bytes_per_launch"] if tr else None),
+                     "traffic_note": (tr.get("note") if tr else "no ncu capture of the current kernel source")},
+        "per_variant": {k: {"GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1), "launches": v["launches"],
+                            "ms": round(v["ms"], 3)} for k, v in by_var.items()},
+        "cases": {"min_GBs": round(min(case_gbs), 1), "median_GBs": round(float(np.median(case_gbs)), 1),
+                  "max_GBs": round(max(case_gbs), 1),
+                  "frac_ge_256MiB_at_80pct_of_8TBs": (round(sum(g >= 6400 for g in big) / len(big), 3)
+                                                      if big else None)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    return out
+
+
+def workload_desc(name, probs):
+    if name == "sweep":
+        return ("single transposes, N=2..6 x 8 seeded perms, 2^26 elems/tensor (+-1%), f32+f64, "
+                "alpha=1.7, beta in {0,0.4}")
+    if name == "single4d":
+        return "4D f32 (32,40,24,36) perm (2,0,3,1) alpha=1 beta=0"
+    if name == "packing":
+        return "GEMM packing 4096x2048 of 8192^2 f32 -> 256x128 panels, and (48,64,40,56) in (64,80,48,64) perm (1,3,0,2); -> bf16 / e4m3+scale"
+    return name
+
+
+def run_e2e(args, probs, plans, bufs, stream, world):
+    """Same metric with host (pinned) inputs: every step copies A (and B when
+    beta != 0) host->device, runs the plan, and copies B back."""
+    import torch
+    host = {}
+    for key, sets in bufs.bufs.items():
+        A, B = sets[0]
+        host[key] = (torch.empty(A.numel(), dtype=A.dtype, pin_memory=True),
+                     torch.empty(B.numel(), dtype=B.dtype, pin_memory=True))
+        host[key][0].copy_(A.cpu())
+        host[key][1].copy_(B.cpu())
+    h2d = d2h = 0
+    for p in probs:
+        ea, eb = torch.empty(0, dtype=storage_torch(p.dtype_in)).element_size(), \
+            torch.empty(0, dtype=storage_torch(p.dtype_out)).element_size()
+        h2d += p.vol_a * ea + (p.vol_b * eb if p.beta != 0 else 0)
+        d2h += p.vol_b * eb
+
+    def step():
+        for i, (p, pl) in enumerate(zip(probs, plans)):
+            A, B = bufs.get(p, i)
+            hA, hB = host[(p.dtype_in, p.dtype_out)]
+            A[:p.vol_a].copy_(hA[:p.vol_a], non_blocking=True)
+            if p.beta != 0:
+                B[:p.vol_b].copy_(hB[:p.vol_b], non_blocking=True)
+            pl.execute(A, B, stream)
+            hB[:p.vol_b].copy_(B[:p.vol_b], non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1) / steps
+    if world > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    bytes_step = sum(p.algorithmic_bytes() for p in probs)
+    return {"value": round(world * bytes_step / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3),
+            "wall_s": round(wall, 3), "steps": steps}
+
+
+# ------------------------------------------------------ CPU oracle timing --
+
+def oracle_slabs(p, A, B, threads):
+    """Run the oracle on `threads` slabs of the problem (split along A's last
+    index; each slab is itself a valid sub-tensor problem) in parallel threads
+    (ctypes releases the GIL)."""
+    import oracle
+    N = len(p.sizes)
+    last = p.sizes[-1]
+    oA = list(p.outer_a or p.sizes)
+    sB = p.sizes_b
+    oB = list(p.outer_b or sB)
+    strideA = int(np.prod(oA[:-1], dtype=np.int64))
+    posB = p.perm.index(N - 1)
+    strideB = int(np.prod(oB[:posB], dtype=np.int64))
+    ODT = {"f32": oracle.F32, "f64": oracle.F64, "bf16": oracle.BF16, "e4m3": oracle.E4M3}
+    chunks = np.array_split(np.arange(last), min(threads, last))
+
+    def work(ch):
+        if len(ch) == 0:
+            return
+        s0 = int(ch[0])
+        sizes = list(p.sizes[:-1]) + [len(ch)]
+        subA = A[s0 * strideA:]
+        subB = B[s0 * strideB:]
+        oracle.permute(p.perm, sizes, subA, subB, p.alpha, p.beta, ODT[p.dtype_in], ODT[p.dtype_out],
+                       oA, oB)
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(work, chunks))
+
+
+def cpu_baseline(budget_s: float, probs, threads: int, max_cases: int = 3):
+    """Time the oracle as it stands on a bounded sample: the first few cases of
+    the workload, full size, until budget_s is spent."""
+    import oracle
+    oracle.build()
+    done_bytes, t_total, names = 0, 0.0, []
+    t_start = time.perf_counter()
+    for p in probs[:max_cases]:
+        A = inputs.tensor_for(p.dtype_in, p.vol_a, 1)
+        B = inputs.tensor_for(p.dtype_out, p.vol_b, 2)
+        t0 = time.perf_counter()
+        oracle_slabs(p, A, B, threads)
+        dt = time.perf_counter() - t0
+        t_total += dt
+        done_bytes += p.algorithmic_bytes()
+        names.append(f"{p.tag}/{p.dtype_in}/b{p.beta}")
+        if time.perf_counter() - t_start > budget_s:
+            break
+    return {"value": round(done_bytes / t_total / 1e9, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(names)} full-size cases of the workload ({', '.join(names)}), "
+                      f"{t_total:.1f} s of oracle time on {threads} threads (slabs along the last index)"}
+
+
+def run_reference(args, rank, world):
+    probs = workload_problems(args.workload)
+    threads = os.cpu_count() or 1
+    import oracle
+    oracle.build()
+    # warm-up steps: small
+    per_step = []
+    for s in range(args.warmup + args.steps):
+        p = probs[(s * 7) % len(probs)]
+        A = inputs.tensor_for(p.dtype_in, p.vol_a, 1)
+        B = inputs.tensor_for(p.dtype_out, p.vol_b, 2)
+        t0 = time.perf_counter()
+        oracle_slabs(p, A, B, threads)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            per_step.append((p.algorithmic_bytes(), dt))
+    tot_b = sum(b for b, _ in per_step)
+    tot_t = sum(t for _, t in per_step)
+    value = tot_b / tot_t / 1e9
+    sample = (f"each step = one full-size case of the workload (rotating), oracle on {threads} host threads")
+    return {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * tot_t / len(per_step), 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (oracle arithmetic)",
+            "data": "synthetic (seeded uniform[-1,1])", "impl": "reference",
+            "config": {"workload": workload_desc(args.workload, probs), "parallelism": "host threads"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "single4d", "packing"])
+    ap.add_argument("--autotune", type=int, default=0, help="time up to this many candidates per plan first")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+        tdist.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu and world == 1:
+            out["cpu_baseline"] = cpu_baseline(args.cpu_budget, workload_problems(args.workload),
+                                               os.cpu_count() or 1)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

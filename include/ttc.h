@@ -1,0 +1,197 @@
+/*
+ * ttc.h -- C ABI of libttc: GB300-native tensor permute-scale-add.
+ *
+ * The operation (Springer, Sankaran, Bientinesi, "TTC: A Tensor Transposition
+ * Compiler for Multiple Architectures", arXiv 1607.01249, section 1, Eq. 1):
+ *
+ *     B[Pi(i0,...,iN-1)] <- alpha * A[i0,...,iN-1] + beta * B[Pi(i0,...,iN-1)]
+ *
+ * Conventions (all fixed by the paper unless marked "reading"):
+ *  - Layout: column-major (section 1, footnote 2): index 0 has stride 1 and
+ *    indices are stored left to right.
+ *  - Permutation: perm[d] is the index of A that becomes index d of B
+ *    (section 2.1, Fig. 2b/2c: perm=2,1,0 on A(i0,i1,i2) gives B(i2,i1,i0);
+ *    Fig. 3: perm=0,2,1 on A(m1,m2,k) gives B(m1,k,m2)).  B's size along d is
+ *    sizes[perm[d]].
+ *  - Outer sizes ("multiple leading dimensions", section 2.1, Table 1
+ *    --lda/--ldb, Fig. 2): each index of A (and of B) may live in a larger
+ *    extent, so A and/or B can be sub-tensors of larger tensors.  The stride of
+ *    index k is the product of the outer sizes of indices 0..k-1.  NULL means
+ *    the tensor is dense (outer = sizes).  outer_sizes_B is given in B's own
+ *    index order (reading: the paper does not say).
+ *  - Precision (reading): the compute type is FP64 when A or B is FP64, else
+ *    FP32.  alpha and beta are rounded once to it.  FP32 compute evaluates
+ *    r = fmaf(beta, b, fl32(alpha*a)), FP64 compute r = fma(beta, b,
+ *    fl64(alpha*a)); r is rounded once (round-to-nearest-even) to B's type.
+ *    beta == 0: B is not read.  alpha == 1 and beta == 0 with equal types: a
+ *    bit copy.  Mixed types follow the paper's mixed-precision transpositions
+ *    (section 2.1, --dataType=sd/ds).
+ *  - FP8 E4M3 output (OCP E4M3, max 448, saturating): code =
+ *    RNE_satfinite(fl32(fl32(alpha*a) / scale)); scale is either supplied by
+ *    the caller (ttc_plan_set_fp8_scale) or computed on the device as
+ *    fl32(amax/448), amax = max |fl32(alpha*a)| over the sub-tensor (NaN
+ *    ignored; scale = 1 if amax is 0, infinite, or amax/448 underflows).  Only
+ *    beta == 0 is supported with FP8 output.
+ *
+ * Streams: every call that takes a ttc_stream_t enqueues work on that CUDA
+ * stream (a cudaStream_t; NULL = the legacy default stream) and returns
+ * without synchronising, unless stated otherwise.  Pointers named d_* or
+ * A/B in execute calls are device pointers on the current device.
+ *
+ * Errors: every call returns a ttc_status; nothing aborts.  ttc_last_error()
+ * gives a human-readable detail for the calling thread's last failure.
+ */
+#ifndef TTC_H_
+#define TTC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (same underlying type), named here so that this header does
+ * not need the CUDA headers. */
+typedef struct CUstream_st* ttc_stream_t;
+
+typedef enum {
+    TTC_F32 = 0,       /* IEEE binary32 ("s" in the paper's --dataType) */
+    TTC_F64 = 1,       /* IEEE binary64 ("d") */
+    TTC_BF16 = 2,      /* bfloat16 (output of a fused downcast, or input) */
+    TTC_FP8_E4M3 = 3   /* OCP FP8 E4M3 (output only, with a per-tensor scale) */
+} ttc_dtype;
+
+typedef enum {
+    TTC_OK = 0,
+    TTC_ERR_INVALID_PERM = 1,      /* perm is not a permutation of 0..ndim-1, or ndim out of range */
+    TTC_ERR_INVALID_SIZE = 2,      /* a size is negative, or the problem is too large */
+    TTC_ERR_INVALID_OUTER = 3,     /* an outer size is smaller than its size */
+    TTC_ERR_UNSUPPORTED_DTYPE = 4, /* dtype pair (or FP8 with beta != 0) not supported */
+    TTC_ERR_ALIAS = 5,             /* the byte ranges of A and B overlap (Eq. 1 is out of place) */
+    TTC_ERR_ALIGN = 6,             /* a pointer is not aligned to its element size */
+    TTC_ERR_OOM = 7,               /* host or device allocation failed */
+    TTC_ERR_CUDA = 8,              /* a CUDA runtime call failed (see ttc_last_error) */
+    TTC_ERR_TIMEOUT = 9,           /* a bounded wait gave up */
+    TTC_ERR_BUDGET = 10,           /* a request exceeds the server's memory budget */
+    TTC_ERR_INVALID_ARG = 11,      /* NULL handle/pointer or bad argument */
+    TTC_ERR_NOT_READY = 12         /* polled work has not finished yet */
+} ttc_status;
+
+#define TTC_MAX_DIM 16
+
+typedef struct ttc_plan_s* ttc_plan_t;
+
+/*
+ * ttc_plan -- describe one permute-scale-add (Eq. 1; section 2.1 Table 1:
+ * --perm, --size, --dataType, --beta, --lda, --ldb) and prepare it: validate,
+ * drop size-1 indices, merge neighbouring indices into super-indices where
+ * the memory layout allows it (section 2.1 stage 1, footnote 5), and choose a
+ * kernel schedule (tile extents, vector widths, order of the flat grid).
+ *
+ *  out            receives the plan handle (owned by the caller; free with
+ *                 ttc_plan_destroy).
+ *  ndim           1..TTC_MAX_DIM.
+ *  perm[ndim]     B index d is A index perm[d].
+ *  sizes[ndim]    extents of A's indices (>= 0; any 0 makes the plan a no-op).
+ *  outer_sizes_A  NULL or ndim outer extents of A (in A's index order).
+ *  outer_sizes_B  NULL or ndim outer extents of B (in B's index order).
+ *  dtype_in/out   types of A and B.  Supported pairs: f32->{f32,f64,bf16,e4m3},
+ *                 f64->{f64,f32}, bf16->{bf16,f32,e4m3}.
+ *  alpha, beta    the scalars of Eq. 1 (rounded once to the compute type).
+ *
+ * Host-only: no CUDA call is made; device resources are created on the first
+ * execution on each device.  Thread-safe.
+ */
+ttc_status ttc_plan(ttc_plan_t* out, int ndim, const int* perm, const int64_t* sizes,
+                    const int64_t* outer_sizes_A, const int64_t* outer_sizes_B,
+                    ttc_dtype dtype_in, ttc_dtype dtype_out, double alpha, double beta);
+
+/*
+ * ttc_execute -- run the plan: B <- alpha*A + beta*B under the permutation
+ * (Eq. 1), asynchronously on `stream`.
+ *  A   device pointer to element (0,...,0) of A (of its sub-tensor when outer
+ *      sizes are given); must be aligned to the size of dtype_in.
+ *  B   device pointer to element (0,...,0) of B; aligned to dtype_out.  Only
+ *      elements of the sub-tensor are read or written.
+ * Returns TTC_ERR_ALIAS if the byte ranges spanned by A and B overlap.  The
+ * caller owns A, B and the stream; A and B must stay valid until the work on
+ * `stream` has completed.  A size-0 plan returns TTC_OK without launching.
+ * Launch errors are reported as TTC_ERR_CUDA.  Concurrent executions of one
+ * plan on different streams are allowed except for FP8 plans that compute
+ * their scale (they share the plan's amax scratch word).
+ */
+ttc_status ttc_execute(ttc_plan_t plan, const void* A, void* B, ttc_stream_t stream);
+
+/* Release the plan and its device resources (waits for nothing: the caller
+ * must not destroy a plan while work that uses it is still queued). */
+ttc_status ttc_plan_destroy(ttc_plan_t plan);
+
+/*
+ * FP8 scale control (fused downcast; the per-tensor scale is this library's
+ * addition to the paper's mixed-precision transpositions).
+ *  ttc_plan_set_fp8_scale: d_scale = device pointer to one float read by
+ *    every later execution (the caller keeps it alive), or NULL to compute the
+ *    scale from amax on each execution (the default).
+ *  ttc_plan_get_fp8_scale: enqueue on `stream` a copy of the scale used by the
+ *    plan's most recent execution into d_scale_out (device pointer to one
+ *    float).  Only valid after an execution on the current device.
+ */
+ttc_status ttc_plan_set_fp8_scale(ttc_plan_t plan, const float* d_scale);
+ttc_status ttc_plan_get_fp8_scale(ttc_plan_t plan, float* d_scale_out, ttc_stream_t stream);
+
+/* What the planner made of the problem (for tests and tooling). */
+typedef enum { TTC_VARIANT_EMPTY = 0, TTC_VARIANT_COPY = 1, TTC_VARIANT_TILE = 2 } ttc_variant;
+
+typedef struct {
+    int ndim;                      /* canonical number of indices after dropping/merging */
+    int perm[TTC_MAX_DIM];         /* canonical permutation */
+    int64_t sizes[TTC_MAX_DIM];    /* canonical sizes (A order) */
+    int64_t stride_A[TTC_MAX_DIM]; /* element strides of the canonical indices in A */
+    int64_t stride_B[TTC_MAX_DIM]; /* element strides of the canonical indices in B (A order) */
+    int64_t n;                     /* number of elements transposed */
+    int64_t algorithmic_bytes;     /* n*(sA+sB) for beta == 0, n*(sA+2sB) otherwise */
+    int variant;                   /* ttc_variant */
+    int tile_c, tile_a, tile_b;    /* tile extents: common inner run, A-side run, B-side run */
+    int64_t ntiles;                /* tiles (or rows for the copy variant) of one execution */
+    int vec_in, vec_out;           /* vector widths (elements) the schedule uses when aligned */
+    int candidate;                 /* index of the schedule in the plan's candidate list */
+    int ncandidates;               /* number of candidate schedules the planner kept */
+} ttc_plan_info;
+
+ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info);
+
+/*
+ * Autotuner (replaces the paper's candidate search of section 2.1 stages 2-6
+ * and 2.2-2.3): time up to max_candidates of the plan's candidate schedules
+ * (tile extents, vector widths, order of the flat grid) on the current device
+ * and keep the fastest.  Timing uses temporary device buffers that the call
+ * allocates and frees itself (the caller's tensors are not touched), on
+ * `stream`; the call synchronises that stream.  The choice is remembered in a
+ * process-wide cache keyed by the canonical problem and device, so later plans
+ * of the same problem start from it.  best_ms (may be NULL) receives the
+ * winning time per execution in milliseconds.
+ */
+ttc_status ttc_plan_autotune(ttc_plan_t plan, int max_candidates, ttc_stream_t stream,
+                             float* best_ms);
+
+/* Select candidate schedule `index` (0 = the planner's first choice). */
+ttc_status ttc_plan_select_candidate(ttc_plan_t plan, int index);
+
+/* Save / load the autotune cache as a text file (one line per entry). */
+ttc_status ttc_tune_cache_save(const char* path);
+ttc_status ttc_tune_cache_load(const char* path);
+
+/* Human-readable name of a status, and detail of the calling thread's last
+ * failure (valid until its next call into the library). */
+const char* ttc_status_string(ttc_status status);
+const char* ttc_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads).  Used by benchmarks to report launch counts. */
+int64_t ttc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTC_H_ */

@@ -79,8 +79,19 @@ def _ptr(x: np.ndarray):
     return ctypes.c_void_p(x.ctypes.data)
 
 
-def _check_buf(x: np.ndarray, dt: int, outer, name: str):
-    need = int(np.prod([int(v) for v in outer], dtype=np.int64)) if len(outer) else 1
+def _span(sizes, outer) -> int:
+    """1 + the largest element offset of a column-major (sub-)tensor."""
+    if any(int(s) == 0 for s in sizes):
+        return 0
+    span, stride = 1, 1
+    for s, o in zip(sizes, outer):
+        span += (int(s) - 1) * stride
+        stride *= int(o)
+    return span
+
+
+def _check_buf(x: np.ndarray, dt: int, sizes, outer, name: str):
+    need = _span(sizes, outer)
     if x.dtype != NP_DTYPE[dt] or not x.flags.c_contiguous or x.size < need:
         raise ValueError(f"{name}: need a contiguous {NP_DTYPE[dt].__name__} buffer of >= {need}")
 
@@ -96,9 +107,9 @@ def dims(perm, sizes, outerA=None, outerB=None):
 def permute(perm, sizes, A, B, alpha=1.0, beta=0.0, dtA=F32, dtB=F32, outerA=None,
             outerB=None, fp8_scale=1.0):
     """B <- alpha*A + beta*B under perm (in place on the numpy buffer B)."""
-    n, oA, _, oB = dims(perm, sizes, outerA, outerB)
-    _check_buf(A, dtA, oA, "A")
-    _check_buf(B, dtB, oB, "B")
+    n, oA, sB, oB = dims(perm, sizes, outerA, outerB)
+    _check_buf(A, dtA, sizes, oA, "A")
+    _check_buf(B, dtB, sB, oB, "B")
     rc = lib().oracle_permute(n, (ctypes.c_int * n)(*perm), _i64(sizes), _i64(outerA),
                               _i64(outerB), dtA, dtB, float(alpha), float(beta), _ptr(A),
                               _ptr(B), float(fp8_scale))
@@ -110,10 +121,10 @@ def permute(perm, sizes, A, B, alpha=1.0, beta=0.0, dtA=F32, dtB=F32, outerA=Non
 def permute_exact(perm, sizes, A, B, alpha=1.0, beta=0.0, dtA=F32, dtB=F32, outerA=None,
                   outerB=None):
     """Exact value (rounded once to double) and tolerance scale, in B's layout."""
-    n, oA, _, oB = dims(perm, sizes, outerA, outerB)
-    _check_buf(A, dtA, oA, "A")
-    _check_buf(B, dtB, oB, "B")
-    vol = int(np.prod(oB, dtype=np.int64))
+    n, oA, sB, oB = dims(perm, sizes, outerA, outerB)
+    _check_buf(A, dtA, sizes, oA, "A")
+    _check_buf(B, dtB, sB, oB, "B")
+    vol = B.size
     R = np.full(vol, np.nan)
     S = np.full(vol, np.nan)
     rc = lib().oracle_permute_exact(n, (ctypes.c_int * n)(*perm), _i64(sizes), _i64(outerA),
@@ -128,7 +139,7 @@ def fp8_scale(sizes, A, alpha=1.0, dtA=F32, outerA=None):
     """(scale, amax) of the FP8 E4M3 output for A's sub-tensor."""
     n = len(sizes)
     oA = list(outerA) if outerA is not None else list(sizes)
-    _check_buf(A, dtA, oA, "A")
+    _check_buf(A, dtA, sizes, oA, "A")
     amax = ctypes.c_float(0)
     s = lib().oracle_fp8_scale(n, _i64(sizes), _i64(outerA), dtA, float(alpha), _ptr(A),
                                ctypes.byref(amax))

@@ -1,0 +1,20 @@
+// launch.h -- host entry points of the kernels (implemented in kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ttc_internal.h"
+
+namespace ttc {
+
+bool pair_supported(int din, int dout);
+int copy_vec_width(int din, int dout);
+cudaError_t launch_tile(int din, int dout, const void* A, void* B, const TileParams& p, int smem,
+                        cudaStream_t s, int grid_override);
+cudaError_t launch_copy(int din, int dout, int vec, const void* A, void* B, const RowParams& p,
+                        cudaStream_t s);
+cudaError_t launch_amax(int din, const void* A, const RowParams& p, float alpha_f, uint32_t* amax_bits,
+                        cudaStream_t s);
+int64_t launch_count();
+
+}  // namespace ttc

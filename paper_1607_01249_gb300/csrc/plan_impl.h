@@ -1,0 +1,57 @@
+// plan_impl.h -- the plan object behind the opaque ttc_plan_t handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ttc.h"
+#include "planner.h"
+#include "ttc_internal.h"
+
+namespace ttc {
+
+// Device-side resources of a plan on one device: a small scratch area (FP8
+// amax word and scale) and the cross-offset tables of the selected schedule.
+struct DevRes {
+  void* base = nullptr;
+  size_t bytes = 0;
+  uint32_t* amax = nullptr;
+  float* scale = nullptr;
+  int32_t* tables = nullptr;
+  int sel = -1;          // candidate the parameters below were built for
+  TileParams tp;
+  RowParams rp;
+  int smem = 0;
+};
+
+}  // namespace ttc
+
+struct ttc_plan_s {
+  std::mutex mu;
+  // the problem as given (for the schedule checker)
+  int ndim = 0;
+  int perm0[ttc::kMaxDim] = {};
+  int64_t sizes0[ttc::kMaxDim] = {}, outerA0[ttc::kMaxDim] = {}, outerB0[ttc::kMaxDim] = {};
+  int din = 0, dout = 0;
+  double alpha = 1.0, beta = 0.0;
+  ttc::Canon canon;
+  std::vector<ttc::Candidate> cands;
+  int sel = 0;
+  bool user_selected = false;
+  const float* user_scale = nullptr;
+  ttc::RowParams amax_rows;
+  std::map<int, ttc::DevRes> dev;
+};
+
+namespace ttc {
+ttc_status fail(ttc_status s, const std::string& msg);
+ttc_status cuda_fail(cudaError_t e, const char* where);
+ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s, int grid_override);
+ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out);
+Epilogue make_epilogue(const ttc_plan_s* p, const DevRes* r);
+std::string plan_key(const ttc_plan_s* p, int dev);
+}  // namespace ttc

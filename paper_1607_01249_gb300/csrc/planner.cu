@@ -1,0 +1,534 @@
+// planner.cu -- validation, canonicalisation (index merging) and candidate
+// schedules of one permute-scale-add.  Host code only.
+//
+// Canonicalisation follows section 2.1 stage 1: neighbouring indices are
+// merged into a "super index" whose size is the product of their sizes
+// (footnote 5: only when ld(i_m) = size(i_m)).  Reading taken here: two
+// indices i_m, i_m+1 of A merge when they are also neighbours, in the same
+// order, in B, and both memory layouts are dense across them (the stride of
+// i_m+1 is the stride of i_m times its size, in A and in B).  Indices of size 1
+// are dropped first; neither step changes which element goes where.
+//
+// Candidate schedules replace TTC's candidate list (section 2.1 stages 2-3,
+// section 2.2: blockings b_A, b_B and loop orders; section 2.3 heuristics).
+// Here a candidate is a tile shape (which indices form the A-side and B-side
+// runs of the tile and how the last of each is cut into blocks) plus the
+// order of the flat grid of tiles; a cost model in the spirit of section 2.3
+// ranks them (long contiguous runs on both sides = sector efficiency, little
+// remainder, enough work per tile), and the autotuner times the best few.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <numeric>
+#include <set>
+#include <sstream>
+
+#include "../../include/ttc.h"
+#include "planner.h"
+
+namespace ttc {
+
+namespace {
+
+bool mul_overflows(int64_t a, int64_t b) {
+  if (a == 0 || b == 0) return false;
+  return a > INT64_MAX / b;
+}
+
+// Cost-model constants of one GB300 (only ratios matter for ranking).
+constexpr double kHbmBytesPerS = 6.8e12;
+constexpr double kLaneInstrPerS = 152.0 * 4 * 32 * 1.9e9;
+
+}  // namespace
+
+double sector_efficiency(double bytes, int elem) {
+  if (bytes <= 0) return 1.0;
+  // a run of `bytes` starting at a random multiple of `elem` inside a sector
+  // touches on average (bytes + 32 - elem) / 32 sectors
+  const double sectors = std::max(1.0, (bytes + 32.0 - elem) / 32.0);
+  return std::min(1.0, bytes / (32.0 * sectors));
+}
+
+std::string Candidate::describe() const {
+  std::ostringstream o;
+  if (variant == VAR_EMPTY) return "empty";
+  if (variant == VAR_COPY) {
+    o << "copy chunk=" << chunk << " vec=" << vec;
+  } else {
+    o << "tile c=" << has_c << " ga=[";
+    for (size_t i = 0; i < ga.size(); ++i) o << (i ? "," : "") << ga[i];
+    o << "]/" << ta << " gb=[";
+    for (size_t i = 0; i < gb.size(); ++i) o << (i ? "," : "") << gb[i];
+    o << "]/" << tb << " order=[";
+    for (size_t i = 0; i < order.size(); ++i) o << (i ? "," : "") << order[i];
+    o << "]";
+  }
+  o << " est_us=" << est_s * 1e6 << " segA=" << seg_a << " segB=" << seg_b;
+  return o.str();
+}
+
+int canonicalize(int ndim, const int* perm, const int64_t* sizes, const int64_t* outerA,
+                 const int64_t* outerB, Canon* c, std::string* err) {
+  *c = Canon();
+  if (!perm || !sizes) {
+    *err = "perm and sizes must not be NULL";
+    return TTC_ERR_INVALID_ARG;
+  }
+  if (ndim < 1 || ndim > kMaxDim) {
+    *err = "ndim must be in 1..16";
+    return TTC_ERR_INVALID_PERM;
+  }
+  bool seen[kMaxDim] = {};
+  for (int d = 0; d < ndim; ++d) {
+    if (perm[d] < 0 || perm[d] >= ndim || seen[perm[d]]) {
+      *err = "perm is not a permutation of 0..ndim-1";
+      return TTC_ERR_INVALID_PERM;
+    }
+    seen[perm[d]] = true;
+  }
+  int64_t oA[kMaxDim], oB[kMaxDim];
+  for (int k = 0; k < ndim; ++k) {
+    if (sizes[k] < 0) {
+      *err = "negative size";
+      return TTC_ERR_INVALID_SIZE;
+    }
+    oA[k] = outerA ? outerA[k] : sizes[k];
+    if (oA[k] < sizes[k]) {
+      *err = "outer size of A smaller than the size";
+      return TTC_ERR_INVALID_OUTER;
+    }
+  }
+  for (int d = 0; d < ndim; ++d) {
+    oB[d] = outerB ? outerB[d] : sizes[perm[d]];
+    if (oB[d] < sizes[perm[d]]) {
+      *err = "outer size of B smaller than the size";
+      return TTC_ERR_INVALID_OUTER;
+    }
+  }
+  // strides (column-major, footnote 2) and element count
+  int64_t stA[kMaxDim], stB[kMaxDim];
+  int64_t acc = 1;
+  for (int k = 0; k < ndim; ++k) {
+    stA[k] = acc;
+    if (mul_overflows(acc, std::max<int64_t>(oA[k], 1))) {
+      *err = "A is too large";
+      return TTC_ERR_INVALID_SIZE;
+    }
+    acc *= std::max<int64_t>(oA[k], 1);
+  }
+  acc = 1;
+  for (int d = 0; d < ndim; ++d) {
+    stB[d] = acc;
+    if (mul_overflows(acc, std::max<int64_t>(oB[d], 1))) {
+      *err = "B is too large";
+      return TTC_ERR_INVALID_SIZE;
+    }
+    acc *= std::max<int64_t>(oB[d], 1);
+  }
+  int64_t n = 1;
+  for (int k = 0; k < ndim; ++k) {
+    if (mul_overflows(n, sizes[k])) {
+      *err = "too many elements";
+      return TTC_ERR_INVALID_SIZE;
+    }
+    n *= sizes[k];
+  }
+  c->n = n;
+  if (n == 0) return TTC_OK;
+  int posB[kMaxDim];
+  for (int d = 0; d < ndim; ++d) posB[perm[d]] = d;
+
+  struct Ix {
+    int64_t s, sa, sb;
+    int bpos;
+  };
+  std::vector<Ix> L;
+  for (int k = 0; k < ndim; ++k)
+    if (sizes[k] > 1) L.push_back({sizes[k], stA[k], stB[posB[k]], posB[k]});
+  if (L.empty()) L.push_back({1, 1, 1, 0});
+
+  // merge neighbours (A order) that are neighbours in the same order in B and
+  // dense across the pair in both tensors
+  for (bool merged = true; merged && L.size() > 1;) {
+    merged = false;
+    std::vector<int> rank(L.size());
+    std::vector<int> byb(L.size());
+    std::iota(byb.begin(), byb.end(), 0);
+    std::sort(byb.begin(), byb.end(), [&](int x, int y) { return L[x].bpos < L[y].bpos; });
+    for (size_t r = 0; r < byb.size(); ++r) rank[byb[r]] = int(r);
+    for (size_t i = 0; i + 1 < L.size(); ++i) {
+      if (rank[i + 1] == rank[i] + 1 && L[i + 1].sa == L[i].sa * L[i].s &&
+          L[i + 1].sb == L[i].sb * L[i].s) {
+        L[i].s *= L[i + 1].s;
+        L.erase(L.begin() + i + 1);
+        merged = true;
+        break;
+      }
+    }
+  }
+  c->N = int(L.size());
+  std::vector<int> byb(L.size());
+  std::iota(byb.begin(), byb.end(), 0);
+  std::sort(byb.begin(), byb.end(), [&](int x, int y) { return L[x].bpos < L[y].bpos; });
+  c->spanA = 1;
+  c->spanB = 1;
+  for (int k = 0; k < c->N; ++k) {
+    c->s[k] = L[k].s;
+    c->sa[k] = L[k].sa;
+    c->sb[k] = L[k].sb;
+    c->perm[k] = byb[k];
+    c->spanA += (L[k].s - 1) * L[k].sa;
+    c->spanB += (L[k].s - 1) * L[k].sb;
+  }
+  return TTC_OK;
+}
+
+namespace {
+
+// Block extents considered for a cut index of size s (section 2.2 uses
+// b in {w, 2w, 3w, 4w}; here: powers of two, balanced splits, and the
+// divisors of s, which leave no remainder -- section 2.3's blocking heuristic).
+std::vector<int> cut_options(int64_t s, int64_t cap) {
+  std::set<int64_t> o;
+  if (s <= cap) o.insert(s);
+  for (int64_t p = 2; p < s && p <= cap; p *= 2) o.insert(p);
+  for (int64_t j = 2; j <= 16; ++j) {
+    int64_t t = (s + j - 1) / j;
+    if (t >= 2 && t < s && t <= cap) o.insert(t);
+  }
+  for (int64_t d = 2; d * d <= s && d <= 4096; ++d) {
+    if (s % d == 0) {
+      if (d <= cap) o.insert(d);
+      if (s / d <= cap && s / d < s) o.insert(s / d);
+    }
+  }
+  return std::vector<int>(o.begin(), o.end());
+}
+
+int stage_bytes(int din) { return din == DT_F64 ? 8 : 4; }
+
+// shared-memory pitch (elements) of one lb row; see ttc_internal.h
+int pick_pitch(int U, int LC, int LB, int din, int smem_cap) {
+  const int banks = din == DT_F64 ? 16 : 32;
+  int P;
+  if (LC <= 1) P = U | 1;
+  else P = U + (((LC - U) % banks) + banks) % banks;
+  if (int64_t(P) * LB * stage_bytes(din) > smem_cap) P = (LC <= 1) ? (U | 1) : U;
+  if (int64_t(P) * LB * stage_bytes(din) > smem_cap) P = U;
+  return P;
+}
+
+struct TileShape {
+  int has_c;
+  std::vector<int> ga, gb;
+  int ta, tb;
+};
+
+// extents of every canonical index inside the tile (1 if not in it)
+void tile_extents(const Canon& c, const TileShape& t, int64_t* ext) {
+  for (int k = 0; k < c.N; ++k) ext[k] = 1;
+  if (t.has_c) ext[0] = c.s[0];
+  for (size_t i = 0; i < t.ga.size(); ++i) ext[t.ga[i]] = (i + 1 == t.ga.size()) ? t.ta : c.s[t.ga[i]];
+  for (size_t i = 0; i < t.gb.size(); ++i) ext[t.gb[i]] = (i + 1 == t.gb.size()) ? t.tb : c.s[t.gb[i]];
+}
+
+// contiguous run (elements) of the tile in memory order of one tensor
+double run_length(const Canon& c, const int64_t* ext, const int* order, const int64_t* st) {
+  double seg = 1;
+  if (st[order[0]] != 1) return 1;
+  for (int i = 0; i < c.N; ++i) {
+    const int k = order[i];
+    if (ext[k] == 1) break;
+    seg *= double(ext[k]);
+    if (ext[k] < c.s[k]) break;
+    if (i + 1 < c.N && st[order[i + 1]] != st[k] * c.s[k]) break;
+  }
+  return seg;
+}
+
+std::vector<int> grid_order(const Canon& c, const int64_t* ext, int mode) {
+  std::vector<int> g;
+  for (int k = 0; k < c.N; ++k)
+    if (ext[k] < c.s[k]) g.push_back(k);
+  auto key = [&](int k) -> double {
+    const double a = double(ext[k]) * double(c.sa[k]), b = double(ext[k]) * double(c.sb[k]);
+    if (mode == 1) return a;
+    if (mode == 2) return b;
+    return std::min(a, b) + 1e-9 * std::max(a, b);
+  };
+  std::stable_sort(g.begin(), g.end(), [&](int x, int y) { return key(x) < key(y); });
+  return g;
+}
+
+}  // namespace
+
+std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double beta, int max_keep) {
+  std::vector<Candidate> out;
+  if (c.N == 0) {
+    out.push_back(Candidate());
+    return out;
+  }
+  const int esA = dtype_size(din), esB = dtype_size(dout);
+  const bool bnz = beta != 0.0;
+  const double n = double(c.n);
+  int orderA[kMaxDim], orderB[kMaxDim];
+  for (int k = 0; k < c.N; ++k) {
+    orderA[k] = k;
+    orderB[k] = c.perm[k];
+  }
+
+  // ---- streaming copy (perm keeps index 0)
+  if (c.perm[0] == 0) {
+    Candidate k;
+    k.variant = VAR_COPY;
+    const int64_t len = c.s[0];
+    k.chunk = len <= 16384 ? len : 8192;
+    const int w = 16 / std::max(esA, esB);
+    bool vec_ok = c.sa[0] == 1 && c.sb[0] == 1 && len % w == 0;
+    for (int i = 1; i < c.N; ++i) vec_ok = vec_ok && c.sa[i] % w == 0 && c.sb[i] % w == 0;
+    k.vec = vec_ok ? w : 1;
+    const double nitems = double(c.n / len) * double((len + k.chunk - 1) / k.chunk);
+    if (nitems >= 2147483647.0) k.variant = VAR_EMPTY;   // marked unusable below
+    const double ra = c.sa[0] == 1 ? double(len) : 1.0, rb = c.sb[0] == 1 ? double(len) : 1.0;
+    k.seg_a = ra;
+    k.seg_b = rb;
+    const double mem = (n * esA / sector_efficiency(ra * esA, esA) +
+                        n * esB * (bnz ? 2 : 1) / sector_efficiency(rb * esB, esB)) / kHbmBytesPerS;
+    const double rows = n / double(len);
+    const double lanes_per_row = std::ceil(double(len) / (32.0 * k.vec)) * 32.0;
+    const double issue = (rows * lanes_per_row * 10.0 + rows * 32.0 * (8.0 * c.N)) / kLaneInstrPerS;
+    k.est_s = std::max(mem, issue) + 0.2 * std::min(mem, issue) + 2e-6;
+    if (k.variant == VAR_COPY) out.push_back(k);
+  }
+
+  // ---- staged tile
+  const bool hc = c.perm[0] == 0;
+  const int c0 = hc ? 1 : 0;
+  const int64_t LC = hc ? c.s[0] : 1;
+  const int Vmax = kTileVmax;
+  std::vector<Candidate> tiles;
+  if (!(hc && c.N == 1) && LC * 2 <= Vmax) {
+    // A-group index list: A order from c0, dense, never B's first index after C
+    std::vector<int> ka;
+    for (int k = c0; k < c.N; ++k) {
+      if (k == c.perm[c0]) break;
+      if (k > 0 && c.sa[k] != c.sa[k - 1] * c.s[k - 1]) break;
+      ka.push_back(k);
+    }
+    for (size_t nA = 0; nA <= ka.size(); ++nA) {
+      int64_t fullA = 1;
+      bool too_big = false;
+      for (size_t i = 0; i + 1 < nA; ++i) {
+        fullA *= c.s[ka[i]];
+        if (LC * fullA * 2 > Vmax) too_big = true;
+      }
+      if (too_big) break;
+      std::vector<int> topts = nA ? cut_options(c.s[ka[nA - 1]], Vmax / (2 * LC * fullA)) : std::vector<int>{1};
+      for (int ta : topts) {
+        const int64_t LA = fullA * ta;
+        if (LC * LA * 2 > Vmax) continue;
+        std::vector<int> ga(ka.begin(), ka.begin() + nA);
+        std::set<int> inA(ga.begin(), ga.end());
+        std::vector<int> kb;
+        for (int d = c0; d < c.N; ++d) {
+          const int m = c.perm[d];
+          if (inA.count(m)) break;
+          if (d > 0 && c.sb[m] != c.sb[c.perm[d - 1]] * c.s[c.perm[d - 1]]) break;
+          kb.push_back(m);
+        }
+        for (size_t nB = 0; nB <= kb.size(); ++nB) {
+          int64_t fullB = 1;
+          bool big = false;
+          for (size_t i = 0; i + 1 < nB; ++i) {
+            fullB *= c.s[kb[i]];
+            if (LC * LA * fullB > Vmax) big = true;
+          }
+          if (big) break;
+          std::vector<int> tbopts = nB ? cut_options(c.s[kb[nB - 1]], Vmax / (LC * LA * fullB)) : std::vector<int>{1};
+          for (int tb : tbopts) {
+            const int64_t LB = fullB * tb;
+            const int64_t V = LC * LA * LB;
+            if (V > Vmax || (LA == 1 && LB == 1)) continue;
+            TileShape sh{hc ? 1 : 0, ga, std::vector<int>(kb.begin(), kb.begin() + nB), int(ta), int(tb)};
+            if (sh.ga.empty()) sh.ta = 1;
+            if (sh.gb.empty()) sh.tb = 1;
+            int64_t ext[kMaxDim];
+            tile_extents(c, sh, ext);
+            double ntiles = 1;
+            for (int k = 0; k < c.N; ++k) ntiles *= std::ceil(double(c.s[k]) / double(ext[k]));
+            if (ntiles >= 2147483647.0) continue;
+            {
+              // in-tile offsets must fit in 32 bits
+              double maxA = double(LC * LA - 1) * double(c.sa[0]), maxB = double(LC * LB - 1) * double(c.sb[c.perm[0]]);
+              for (int m : sh.gb) maxA += double(ext[m] - 1) * double(c.sa[m]);
+              for (int m : sh.ga) maxB += double(ext[m] - 1) * double(c.sb[m]);
+              for (int m : sh.gb) maxA = std::max(maxA, double(c.sa[m]));
+              for (int m : sh.ga) maxB = std::max(maxB, double(c.sb[m]));
+              if (maxA >= 2147483647.0 || maxB >= 2147483647.0) continue;
+            }
+            if ((!sh.ga.empty() && c.s[sh.ga.back()] >= (int64_t(1) << 30)) ||
+                (!sh.gb.empty() && c.s[sh.gb.back()] >= (int64_t(1) << 30)))
+              continue;
+            const double ra = run_length(c, ext, orderA, c.sa), rb = run_length(c, ext, orderB, c.sb);
+            const double mem = (n * esA / sector_efficiency(ra * esA, esA) +
+                                n * esB * (bnz ? 2 : 1) / sector_efficiency(rb * esB, esB)) / kHbmBytesPerS;
+            const double per_slot = 26.0 + (sh.ga.size() > 1 ? 3 : 0) + (sh.gb.size() > 1 ? 3 : 0) + (bnz ? 6 : 0);
+            const double issue = ntiles * kTileK * kThreads * per_slot / kLaneInstrPerS;
+            const double over = ntiles * kThreads * (60.0 + 10.0 * c.N) / kLaneInstrPerS;
+            Candidate k;
+            k.variant = VAR_TILE;
+            k.has_c = sh.has_c;
+            k.ga = sh.ga;
+            k.ta = sh.ta;
+            k.gb = sh.gb;
+            k.tb = sh.tb;
+            k.order = grid_order(c, ext, 0);
+            k.seg_a = ra;
+            k.seg_b = rb;
+            k.est_s = std::max(mem, issue) + 0.25 * std::min(mem, issue) + over + 3e-6;
+            tiles.push_back(k);
+          }
+        }
+      }
+    }
+  }
+  std::stable_sort(tiles.begin(), tiles.end(),
+                   [](const Candidate& a, const Candidate& b) { return a.est_s < b.est_s; });
+  // keep the best few shapes, each also with the A-major and B-major grid orders
+  std::vector<Candidate> keep;
+  for (const auto& t : tiles) {
+    if (int(keep.size()) >= max_keep) break;
+    keep.push_back(t);
+  }
+  const size_t nshape = keep.size();
+  for (size_t i = 0; i < nshape && i < 3; ++i) {
+    int64_t ext[kMaxDim];
+    TileShape sh{keep[i].has_c, keep[i].ga, keep[i].gb, keep[i].ta, keep[i].tb};
+    tile_extents(c, sh, ext);
+    for (int mode = 1; mode <= 2; ++mode) {
+      Candidate k = keep[i];
+      k.order = grid_order(c, ext, mode);
+      if (k.order != keep[i].order) {
+        k.est_s *= 1.01;
+        keep.push_back(k);
+      }
+    }
+  }
+  out.insert(out.end(), keep.begin(), keep.end());
+  std::stable_sort(out.begin(), out.end(),
+                   [](const Candidate& a, const Candidate& b) { return a.est_s < b.est_s; });
+  if (int(out.size()) > max_keep) out.resize(max_keep);
+  return out;
+}
+
+void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* p,
+                       std::vector<int32_t>* tabA, std::vector<int32_t>* tabB, int* smem_bytes) {
+  *p = TileParams();
+  int64_t ext[kMaxDim];
+  {
+    TileShape sh{k.has_c, k.ga, k.gb, k.ta, k.tb};
+    tile_extents(c, sh, ext);
+  }
+  const int LC = k.has_c ? int(c.s[0]) : 1;
+  int LA = 1, LB = 1, fullA = 1, fullB = 1;
+  for (size_t i = 0; i < k.ga.size(); ++i) {
+    LA *= int(ext[k.ga[i]]);
+    if (i + 1 < k.ga.size()) fullA *= int(ext[k.ga[i]]);
+  }
+  for (size_t i = 0; i < k.gb.size(); ++i) {
+    LB *= int(ext[k.gb[i]]);
+    if (i + 1 < k.gb.size()) fullB *= int(ext[k.gb[i]]);
+  }
+  p->LC = LC;
+  p->LA = LA;
+  p->LB = LB;
+  p->U = LC * LA;
+  p->W = LC * LB;
+  p->V = LC * LA * LB;
+  p->fullA = fullA;
+  p->fullB = fullB;
+  p->saU = int32_t(c.sa[0]);
+  p->sbV = int32_t(c.sb[c.perm[0]]);
+  // cross offsets: A offset of GB's coordinates (lb), B offset of GA's coordinates (la)
+  tabA->clear();
+  tabB->clear();
+  if (k.gb.size() <= 1) {
+    p->crossA_lin = k.gb.empty() ? 0 : int32_t(c.sa[k.gb[0]]);
+  } else {
+    p->crossA_tab = 1;
+    tabA->resize(LB);
+    for (int lb = 0; lb < LB; ++lb) {
+      int64_t r = lb, off = 0;
+      for (int m : k.gb) {
+        off += (r % ext[m]) * c.sa[m];
+        r /= ext[m];
+      }
+      (*tabA)[lb] = int32_t(off);
+    }
+  }
+  if (k.ga.size() <= 1) {
+    p->crossB_lin = k.ga.empty() ? 0 : int32_t(c.sb[k.ga[0]]);
+  } else {
+    p->crossB_tab = 1;
+    tabB->resize(LA);
+    for (int la = 0; la < LA; ++la) {
+      int64_t r = la, off = 0;
+      for (int m : k.ga) {
+        off += (r % ext[m]) * c.sb[m];
+        r /= ext[m];
+      }
+      (*tabB)[la] = int32_t(off);
+    }
+  }
+  // grid
+  uint64_t ntiles = 1;
+  p->ngrid = 0;
+  const int cutA = k.ga.empty() ? -1 : k.ga.back();
+  const int cutB = k.gb.empty() ? -1 : k.gb.back();
+  for (int gk : k.order) {
+    GridDim& g = p->g[p->ngrid++];
+    const int64_t nb = (c.s[gk] + ext[gk] - 1) / ext[gk];
+    g.div = make_fastdiv(uint32_t(nb));
+    g.stepA = ext[gk] * c.sa[gk];
+    g.stepB = ext[gk] * c.sb[gk];
+    g.kind = 0;
+    g.t = int(ext[gk]);
+    g.s = int(std::min<int64_t>(c.s[gk], INT32_MAX));
+    if (gk == cutA && ext[gk] < c.s[gk]) g.kind = 1;
+    if (gk == cutB && ext[gk] < c.s[gk]) g.kind = 2;
+    ntiles *= uint64_t(nb);
+  }
+  p->ntiles = uint32_t(ntiles);
+  const int smem_cap = 160 * 1024;
+  p->P = pick_pitch(p->U, LC, LB, din, smem_cap);
+  // thread steps
+  p->rd_du = kThreads % p->U;
+  p->rd_dlb = kThreads / p->U;
+  p->wr_dlc = kThreads % LC;
+  p->wr_dlb = (kThreads / LC) % LB;
+  p->wr_dla = kThreads / (LC * LB);
+  *smem_bytes = int(((tabA->size() + tabB->size()) * sizeof(int32_t) + 15) & ~size_t(15)) +
+                p->P * LB * stage_bytes(din);
+}
+
+void build_row_params(const Canon& c, int64_t chunk, RowParams* p) {
+  *p = RowParams();
+  p->len = c.s[0];
+  p->sa0 = c.sa[0];
+  p->sb0 = c.sb[0];
+  p->chunk = chunk > 0 ? chunk : c.s[0];
+  const int64_t nch = (p->len + p->chunk - 1) / p->chunk;
+  p->chunks = make_fastdiv(uint32_t(nch));
+  uint64_t rows = 1;
+  p->nrd = 0;
+  for (int k = 1; k < c.N; ++k) {
+    p->div[p->nrd] = make_fastdiv(uint32_t(c.s[k]));
+    p->stA[p->nrd] = c.sa[k];
+    p->stB[p->nrd] = c.sb[k];
+    ++p->nrd;
+    rows *= uint64_t(c.s[k]);
+  }
+  p->nitems = uint32_t(rows * uint64_t(nch));
+}
+
+}  // namespace ttc

@@ -1,0 +1,181 @@
+// simulate.cu -- host-side schedule checker (include/ttc_debug.h).
+//
+// Runs the kernels' own index walks (kernels.cuh, compiled for the host) for
+// every tile / row chunk and every thread, and checks bounds, coverage and
+// the element mapping of Eq. 1 against the problem as given to ttc_plan.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ttc.h"
+#include "../../include/ttc_debug.h"
+#include "kernels.cuh"
+#include "plan_impl.h"
+#include "planner.h"
+
+using namespace ttc;
+
+namespace {
+
+struct Checker {
+  const ttc_plan_s* p;
+  int64_t stA[kMaxDim], stB[kMaxDim];
+  int64_t spanA, spanB;
+  std::vector<uint8_t> wrote;   // per B element of the span
+  int64_t writes = 0;
+  std::string err;
+
+  explicit Checker(const ttc_plan_s* plan) : p(plan) {
+    int64_t a = 1, b = 1;
+    for (int k = 0; k < p->ndim; ++k) {
+      stA[k] = a;
+      a *= p->outerA0[k];
+    }
+    for (int d = 0; d < p->ndim; ++d) {
+      stB[d] = b;
+      b *= p->outerB0[d];
+    }
+    spanA = p->canon.spanA;
+    spanB = p->canon.spanB;
+    wrote.assign(size_t(spanB), 0);
+  }
+
+  bool fail(const char* what, int64_t x, int64_t y) {
+    if (err.empty()) {
+      char buf[256];
+      std::snprintf(buf, sizeof(buf), "%s (%lld, %lld)", what, (long long)x, (long long)y);
+      err = buf;
+    }
+    return false;
+  }
+
+  // Eq. 1: the B offset of the A element at offset offA (outer sizes as given)
+  bool expected_b(int64_t offA, int64_t* offB) {
+    int64_t idx[kMaxDim];
+    int64_t r = offA;
+    for (int k = p->ndim - 1; k >= 0; --k) {
+      idx[k] = r / stA[k];
+      r -= idx[k] * stA[k];
+    }
+    for (int k = 0; k < p->ndim; ++k)
+      if (idx[k] < 0 || idx[k] >= p->sizes0[k]) return fail("A offset outside the sub-tensor", offA, k);
+    int64_t b = 0;
+    for (int d = 0; d < p->ndim; ++d) b += idx[p->perm0[d]] * stB[d];
+    *offB = b;
+    return true;
+  }
+
+  bool pair(int64_t offA, int64_t offB) {
+    if (offA < 0 || offA >= spanA) return fail("A access out of range", offA, spanA);
+    if (offB < 0 || offB >= spanB) return fail("B access out of range", offB, spanB);
+    int64_t want = 0;
+    if (!expected_b(offA, &want)) return false;
+    if (want != offB) return fail("element lands at the wrong B offset", offB, want);
+    if (wrote[size_t(offB)]) return fail("B element written twice", offB, offA);
+    wrote[size_t(offB)] = 1;
+    ++writes;
+    return true;
+  }
+
+  bool tile(const Candidate& k) {
+    TileParams tp;
+    std::vector<int32_t> ta, tb;
+    int smem = 0;
+    build_tile_params(p->canon, k, p->din, &tp, &ta, &tb, &smem);
+    if (smem > 200 * 1024) return fail("shared memory over budget", smem, 0);
+    if (tp.V > kTileVmax) return fail("tile larger than the threads cover", tp.V, kTileVmax);
+    const int ncap = tp.P * tp.LB;
+    std::vector<int64_t> posA(static_cast<size_t>(ncap));
+    std::vector<uint8_t> used(static_cast<size_t>(ncap));
+    for (uint32_t tid = 0; tid < tp.ntiles; ++tid) {
+      const TileCoord c = tile_coord(tid, tp);
+      std::fill(posA.begin(), posA.end(), -1);
+      std::fill(used.begin(), used.end(), 0);
+      bool ok = true;
+      for (int t = 0; t < kThreads && ok; ++t) {
+        walk_read(c, tp, ta.data(), t % tp.U, t / tp.U, [&](int, int32_t off, int pos) {
+          if (!ok) return;
+          if (pos < 0 || pos >= ncap) { ok = fail("shared-memory position out of range (read)", pos, ncap); return; }
+          if (posA[size_t(pos)] != -1) { ok = fail("shared-memory position written twice", pos, tid); return; }
+          posA[size_t(pos)] = c.baseA + off;
+        });
+      }
+      for (int t = 0; t < kThreads && ok; ++t) {
+        walk_write(c, tp, tb.data(), t % tp.LC, (t / tp.LC) % tp.LB, t / tp.W, [&](int, int32_t off, int pos) {
+          if (!ok) return;
+          if (pos < 0 || pos >= ncap) { ok = fail("shared-memory position out of range (write)", pos, ncap); return; }
+          if (posA[size_t(pos)] < 0) { ok = fail("shared-memory position read but never written", pos, tid); return; }
+          if (used[size_t(pos)]) { ok = fail("shared-memory position read twice", pos, tid); return; }
+          used[size_t(pos)] = 1;
+          ok = pair(posA[size_t(pos)], c.baseB + off);
+        });
+      }
+      for (int q = 0; q < ncap && ok; ++q)
+        if (posA[size_t(q)] >= 0 && !used[size_t(q)]) ok = fail("staged element never written out", q, tid);
+      if (!ok) return false;
+    }
+    return true;
+  }
+
+  bool copy(const Candidate& k) {
+    RowParams rp;
+    build_row_params(p->canon, k.chunk, &rp);
+    for (uint32_t item = 0; item < rp.nitems; ++item) {
+      const RowCoord rc = row_coord(item, rp);
+      if (k.vec > 1 && (rc.offA % k.vec || rc.offB % k.vec || rc.start % k.vec || rc.end % k.vec))
+        return fail("vector access not aligned", item, k.vec);
+      for (int64_t x = rc.start; x < rc.end; ++x)
+        if (!pair(rc.offA + x * rp.sa0, rc.offB + x * rp.sb0)) return false;
+    }
+    return true;
+  }
+
+  bool amax() {
+    const RowParams& rp = p->amax_rows;
+    std::vector<uint8_t> seen(size_t(spanA), 0);
+    int64_t visits = 0;
+    for (uint32_t item = 0; item < rp.nitems; ++item) {
+      const RowCoord rc = row_coord(item, rp);
+      for (int64_t x = rc.start; x < rc.end; ++x) {
+        const int64_t a = rc.offA + x * rp.sa0;
+        if (a < 0 || a >= spanA) return fail("amax: A access out of range", a, spanA);
+        if (seen[size_t(a)]) return fail("amax: element visited twice", a, item);
+        seen[size_t(a)] = 1;
+        int64_t b = 0;
+        if (!expected_b(a, &b)) return false;
+        ++visits;
+      }
+    }
+    if (visits != p->canon.n) return fail("amax: wrong number of elements", visits, p->canon.n);
+    return true;
+  }
+};
+
+}  // namespace
+
+extern "C" ttc_status ttc_debug_verify_schedule(ttc_plan_t plan, int candidate, char* msg, int msglen) {
+  auto say = [&](const std::string& s) {
+    if (msg && msglen > 0) {
+      std::snprintf(msg, size_t(msglen), "%s", s.c_str());
+    }
+  };
+  if (!plan || candidate < 0 || candidate >= int(plan->cands.size())) {
+    say("bad plan or candidate");
+    return TTC_ERR_INVALID_ARG;
+  }
+  say("");
+  if (plan->canon.n == 0) return TTC_OK;
+  Checker ck(plan);
+  const Candidate& k = plan->cands[candidate];
+  bool ok = true;
+  if (k.variant == VAR_TILE) ok = ck.tile(k);
+  else if (k.variant == VAR_COPY) ok = ck.copy(k);
+  if (ok && ck.writes != plan->canon.n) ok = ck.fail("wrong number of B elements written", ck.writes, plan->canon.n);
+  if (ok && plan->dout == DT_E4M3) ok = ck.amax();
+  if (!ok) {
+    say(k.describe() + ": " + ck.err);
+    return TTC_ERR_INVALID_ARG;
+  }
+  return TTC_OK;
+}

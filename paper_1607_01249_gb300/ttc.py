@@ -1,0 +1,210 @@
+"""Thin ctypes binding of libttc (include/ttc.h).
+
+Argument marshalling only: every step of the permute-scale-add runs in the
+library's CUDA kernels.  Tensors may be passed as torch tensors (their
+``data_ptr()`` is used) or as raw integer device pointers; streams as
+``torch.cuda.Stream`` objects, raw ``cudaStream_t`` integers, or None (the
+current torch stream when torch is loaded, else the legacy default stream).
+
+There is no fallback: if ``libttc.so`` is missing or fails to load, ``lib()``
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libttc.so")
+
+DTYPES = {"f32": 0, "f64": 1, "bf16": 2, "e4m3": 3}
+DTYPE_BYTES = {"f32": 4, "f64": 8, "bf16": 2, "e4m3": 1}
+MAX_DIM = 16
+STATUS = {0: "TTC_OK", 1: "TTC_ERR_INVALID_PERM", 2: "TTC_ERR_INVALID_SIZE", 3: "TTC_ERR_INVALID_OUTER",
+          4: "TTC_ERR_UNSUPPORTED_DTYPE", 5: "TTC_ERR_ALIAS", 6: "TTC_ERR_ALIGN", 7: "TTC_ERR_OOM",
+          8: "TTC_ERR_CUDA", 9: "TTC_ERR_TIMEOUT", 10: "TTC_ERR_BUDGET", 11: "TTC_ERR_INVALID_ARG",
+          12: "TTC_ERR_NOT_READY"}
+STATUS_CODE = {v: k for k, v in STATUS.items()}
+
+
+class TTCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("perm", ctypes.c_int * MAX_DIM),
+                ("sizes", ctypes.c_int64 * MAX_DIM), ("stride_A", ctypes.c_int64 * MAX_DIM),
+                ("stride_B", ctypes.c_int64 * MAX_DIM), ("n", ctypes.c_int64),
+                ("algorithmic_bytes", ctypes.c_int64), ("variant", ctypes.c_int),
+                ("tile_c", ctypes.c_int), ("tile_a", ctypes.c_int), ("tile_b", ctypes.c_int),
+                ("ntiles", ctypes.c_int64), ("vec_in", ctypes.c_int), ("vec_out", ctypes.c_int),
+                ("candidate", ctypes.c_int), ("ncandidates", ctypes.c_int)]
+
+
+# Every symbol include/ttc.h declares, with (restype, argtypes).
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = {
+    "ttc_plan": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i64p,
+                                _i64p, _i64p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+    "ttc_execute": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "ttc_plan_destroy": (ctypes.c_int, [_vp]),
+    "ttc_plan_set_fp8_scale": (ctypes.c_int, [_vp, _vp]),
+    "ttc_plan_get_fp8_scale": (ctypes.c_int, [_vp, _vp, _vp]),
+    "ttc_plan_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(PlanInfo)]),
+    "ttc_plan_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_float)]),
+    "ttc_plan_select_candidate": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "ttc_tune_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "ttc_tune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "ttc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ttc_last_error": (ctypes.c_char_p, []),
+    "ttc_launch_count": (ctypes.c_int64, []),
+    # include/ttc_debug.h
+    "ttc_debug_verify_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libttc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_1607_01249_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise TTCError(status, lib().ttc_last_error().decode(errors="replace"))
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s) -> int:
+    if s is None:
+        try:
+            import sys
+            if "torch" in sys.modules:
+                import torch
+                if torch.cuda.is_available() and torch.cuda.is_initialized():
+                    return int(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return 0
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _i64arr(vals):
+    if vals is None:
+        return None
+    return (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+
+
+class Plan:
+    """A planned permute-scale-add B <- alpha*A + beta*B under `perm` (Eq. 1)."""
+
+    def __init__(self, perm, sizes, dtype_in="f32", dtype_out=None, alpha=1.0, beta=0.0,
+                 outer_a=None, outer_b=None):
+        dtype_out = dtype_out or dtype_in
+        self.perm = tuple(int(p) for p in perm)
+        self.sizes = tuple(int(s) for s in sizes)
+        self.dtype_in, self.dtype_out = dtype_in, dtype_out
+        self.alpha, self.beta = float(alpha), float(beta)
+        self.outer_a = tuple(outer_a) if outer_a is not None else None
+        self.outer_b = tuple(outer_b) if outer_b is not None else None
+        h = ctypes.c_void_p()
+        n = len(self.perm)
+        if len(self.sizes) != n:
+            raise ValueError("perm and sizes differ in length")
+        _check(lib().ttc_plan(ctypes.byref(h), n, (ctypes.c_int * n)(*self.perm), _i64arr(self.sizes),
+                              _i64arr(self.outer_a), _i64arr(self.outer_b), DTYPES[dtype_in],
+                              DTYPES[dtype_out], self.alpha, self.beta))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def execute(self, A, B, stream=None):
+        _check(lib().ttc_execute(self._h, _ptr(A), _ptr(B), _stream(stream)))
+        return B
+
+    __call__ = execute
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(lib().ttc_plan_get_info(self._h, ctypes.byref(inf)))
+        N = inf.ndim
+        return {"ndim": N, "perm": list(inf.perm[:N]), "sizes": list(inf.sizes[:N]),
+                "stride_A": list(inf.stride_A[:N]), "stride_B": list(inf.stride_B[:N]), "n": inf.n,
+                "algorithmic_bytes": inf.algorithmic_bytes,
+                "variant": {0: "empty", 1: "copy", 2: "tile"}[inf.variant],
+                "tile": (inf.tile_c, inf.tile_a, inf.tile_b), "ntiles": inf.ntiles,
+                "vec": (inf.vec_in, inf.vec_out), "candidate": inf.candidate,
+                "ncandidates": inf.ncandidates}
+
+    def autotune(self, max_candidates=8, stream=None) -> float:
+        ms = ctypes.c_float(0)
+        _check(lib().ttc_plan_autotune(self._h, int(max_candidates), _stream(stream), ctypes.byref(ms)))
+        return float(ms.value)
+
+    def verify_schedule(self, candidate=None) -> str:
+        """Host-side check of a schedule's index arithmetic (no GPU); returns
+        "" when it is sound, else a description of the first violation."""
+        if candidate is None:
+            candidate = self.info()["candidate"]
+        buf = ctypes.create_string_buffer(512)
+        st = lib().ttc_debug_verify_schedule(self._h, int(candidate), buf, 512)
+        return "" if st == 0 else buf.value.decode(errors="replace") or "failed"
+
+    def select(self, index: int):
+        _check(lib().ttc_plan_select_candidate(self._h, int(index)))
+
+    def set_fp8_scale(self, d_scale=None):
+        _check(lib().ttc_plan_set_fp8_scale(self._h, _ptr(d_scale)))
+
+    def get_fp8_scale(self, d_out, stream=None):
+        _check(lib().ttc_plan_get_fp8_scale(self._h, _ptr(d_out), _stream(stream)))
+        return d_out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ttc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def launch_count() -> int:
+    return int(lib().ttc_launch_count())
+
+
+def tune_cache_save(path: str):
+    _check(lib().ttc_tune_cache_save(path.encode()))
+
+
+def tune_cache_load(path: str):
+    _check(lib().ttc_tune_cache_load(path.encode()))

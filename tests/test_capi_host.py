@@ -1,0 +1,231 @@
+"""Host-side tests of libttc (no GPU): exports, validation, canonicalisation,
+schedule choice, and the checks ttc_execute makes before touching the device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1607_01249_gb300 import build as ttc_build
+from paper_1607_01249_gb300 import inputs
+from paper_1607_01249_gb300 import ttc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    ttc_build.build()
+    ttc.lib()
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "ttc.h")).read() + open(os.path.join(ROOT, "include", "ttc_debug.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ttc_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol():
+    names = declared_functions()
+    assert "ttc_plan" in names and "ttc_execute" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", ttc.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(l.split()[-1] for l in out.splitlines() if l.strip())
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert n in ttc.SIGNATURES, f"binding lacks {n}"
+
+
+def test_status_strings():
+    L = ttc.lib()
+    for code, name in ttc.STATUS.items():
+        assert L.ttc_status_string(code).decode() == name
+
+
+@pytest.mark.parametrize("perm,sizes,outer_a,outer_b,status", [
+    ((0, 0), (2, 3), None, None, "TTC_ERR_INVALID_PERM"),
+    ((0, 2), (2, 3), None, None, "TTC_ERR_INVALID_PERM"),
+    ((1, 0), (2, -3), None, None, "TTC_ERR_INVALID_SIZE"),
+    ((1, 0), (4, 3), (3, 3), None, "TTC_ERR_INVALID_OUTER"),
+    ((1, 0), (4, 3), None, (2, 4), "TTC_ERR_INVALID_OUTER"),
+    ((1, 0), (1 << 40, 1 << 40), None, None, "TTC_ERR_INVALID_SIZE"),
+])
+def test_plan_validation(perm, sizes, outer_a, outer_b, status):
+    with pytest.raises(ttc.TTCError) as ei:
+        ttc.Plan(perm, sizes, outer_a=outer_a, outer_b=outer_b)
+    assert ei.value.name == status
+
+
+def test_plan_validation_ndim_and_dtypes():
+    with pytest.raises(ttc.TTCError) as ei:
+        ttc.Plan(tuple(range(17)), (1,) * 17)
+    assert ei.value.name == "TTC_ERR_INVALID_PERM"
+    for din, dout in [("f64", "bf16"), ("f64", "e4m3"), ("e4m3", "f32"), ("bf16", "f64")]:
+        with pytest.raises(ttc.TTCError) as ei:
+            ttc.Plan((1, 0), (4, 4), din, dout)
+        assert ei.value.name == "TTC_ERR_UNSUPPORTED_DTYPE"
+    with pytest.raises(ttc.TTCError) as ei:
+        ttc.Plan((1, 0), (4, 4), "f32", "e4m3", beta=0.5)
+    assert ei.value.name == "TTC_ERR_UNSUPPORTED_DTYPE"
+    for din, dout in [("f32", "f32"), ("f32", "f64"), ("f32", "bf16"), ("f32", "e4m3"), ("f64", "f64"),
+                      ("f64", "f32"), ("bf16", "bf16"), ("bf16", "f32"), ("bf16", "e4m3")]:
+        ttc.Plan((1, 0), (4, 4), din, dout)
+
+
+def test_merge_examples_from_the_paper():
+    rows = [l for l in open(os.path.join(GOLDEN, "merge_examples.txt")).read().splitlines()
+            if l.strip() and not l.startswith("#")]
+    assert rows
+    for row in rows:
+        name, perm, sizes, oa, cperm, csizes, cite = [x.strip() for x in row.split("|")]
+        p = ttc.Plan([int(x) for x in perm.split(",")], [int(x) for x in sizes.split(",")],
+                     outer_a=None if oa == "-" else [int(x) for x in oa.split(",")])
+        inf = p.info()
+        assert inf["perm"] == [int(x) for x in cperm.split(",")], name
+        assert inf["sizes"] == [int(x) for x in csizes.split(",")], name
+
+
+def test_canonical_form_properties():
+    g = inputs.rng(21)
+    for _ in range(300):
+        N = int(g.integers(1, 7))
+        sizes = tuple(int(x) for x in g.integers(1, 5, size=N))
+        perm = tuple(int(x) for x in g.permutation(N))
+        oa = tuple(s + int(g.integers(0, 2)) for s in sizes) if g.random() < 0.3 else None
+        p = ttc.Plan(perm, sizes, outer_a=oa)
+        inf = p.info()
+        n = 1
+        for s in sizes:
+            n *= s
+        assert inf["n"] == n
+        prod = 1
+        for s in inf["sizes"]:
+            prod *= s
+        assert prod == n
+        assert sorted(inf["perm"]) == list(range(inf["ndim"]))
+        assert all(s > 1 for s in inf["sizes"]) or inf["ndim"] == 1
+        # no two neighbours that could still merge
+        for k in range(inf["ndim"] - 1):
+            posb = inf["perm"].index(k)
+            adjacent = posb + 1 < inf["ndim"] and inf["perm"][posb + 1] == k + 1
+            dense = (inf["stride_A"][k + 1] == inf["stride_A"][k] * inf["sizes"][k] and
+                     inf["stride_B"][k + 1] == inf["stride_B"][k] * inf["sizes"][k])
+            assert not (adjacent and dense)
+        if inf["perm"][0] == 0:
+            assert inf["variant"] in ("copy", "tile")
+        else:
+            assert inf["variant"] == "tile"
+
+
+def test_schedule_of_the_workloads():
+    p0 = inputs.single_4d()
+    inf = ttc.Plan(p0.perm, p0.sizes).info()
+    assert inf["variant"] == "tile" and inf["ndim"] == 4
+    assert inf["algorithmic_bytes"] == p0.n * 8
+    for case in inputs.sweep_cases(perms_per_n=8, dtypes=("f32",), betas=(0.0,)):
+        inf = ttc.Plan(case.perm, case.sizes, alpha=case.alpha).info()
+        c, a, b = inf["tile"]
+        if inf["variant"] == "tile":
+            assert c * a * b <= 4096
+        assert inf["ncandidates"] >= 1
+    for case in inputs.packing_cases():
+        inf = ttc.Plan(case.perm, case.sizes, case.dtype_in, case.dtype_out, outer_a=case.outer_a).info()
+        assert inf["n"] == case.n
+
+
+def test_empty_problem_is_a_noop():
+    p = ttc.Plan((1, 0), (0, 5))
+    assert p.info()["variant"] == "empty"
+    p.execute(0, 0)          # no pointers needed, no device touched
+
+
+def test_execute_host_checks_before_any_device_work():
+    p = ttc.Plan((1, 0), (64, 32))
+    with pytest.raises(ttc.TTCError) as ei:
+        p.execute(0, 0x10000)
+    assert ei.value.name == "TTC_ERR_INVALID_ARG"
+    with pytest.raises(ttc.TTCError) as ei:
+        p.execute(0x10002, 0x100000)
+    assert ei.value.name == "TTC_ERR_ALIGN"
+    # overlapping byte ranges (A spans 8 KiB)
+    with pytest.raises(ttc.TTCError) as ei:
+        p.execute(0x100000, 0x100000 + 4096)
+    assert ei.value.name == "TTC_ERR_ALIAS"
+    with pytest.raises(ttc.TTCError) as ei:
+        p.execute(0x100000 + 4096, 0x100000)
+    assert ei.value.name == "TTC_ERR_ALIAS"
+
+
+def test_fastdiv_matches_integer_division(tmp_path):
+    src = tmp_path / "fd.cpp"
+    src.write_text(r'''
+#include "ttc_internal.h"
+#include <cstdio>
+#include <cstdlib>
+int main() {
+  unsigned long long bad = 0, n_checked = 0;
+  unsigned ds[] = {1,2,3,5,7,10,20,36,90,406,641,1000,4095,4096,4097,65535,65536,65537,
+                   1000003,16777213,16777216,2147483647u};
+  unsigned long long x = 88172645463325252ull;
+  for (unsigned d : ds) {
+    ttc::FastDiv f = ttc::make_fastdiv(d);
+    for (int i = 0; i < 200000; ++i) {
+      x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+      unsigned n = (unsigned)(x & 0x7fffffffu);
+      if (i < 1000) n = i;
+      if (i >= 1000 && i < 2000) n = 0x7fffffffu - (i - 1000);
+      if (ttc::fast_div(n, f) != n / d) ++bad;
+      ++n_checked;
+    }
+  }
+  for (unsigned d = 1; d < 5000; ++d) {
+    ttc::FastDiv f = ttc::make_fastdiv(d);
+    for (unsigned n = 0; n < 20000; n += 7) { if (ttc::fast_div(n, f) != n / d) ++bad; ++n_checked; }
+    for (unsigned n = 0x7fffffffu - 20000; n < 0x7fffffffu; n += 13) { if (ttc::fast_div(n, f) != n / d) ++bad; ++n_checked; }
+  }
+  printf("%llu %llu\n", bad, n_checked);
+  return bad != 0;
+}
+''')
+    exe = tmp_path / "fd"
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-I", os.path.join(ROOT, "paper_1607_01249_gb300", "csrc"),
+                           str(src), "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout
+
+
+def _verify_all(plan, label):
+    for i in range(plan.info()["ncandidates"]):
+        msg = plan.verify_schedule(i)
+        assert msg == "", f"{label} candidate {i}: {msg}"
+
+
+def test_schedules_are_sound_on_random_problems():
+    """Every candidate schedule of many random problems: the kernels' own index
+    walks stay in bounds and put every A element at its Eq. 1 position in B."""
+    g = inputs.rng(31)
+    for trial in range(150):
+        N = int(g.integers(1, 7))
+        sizes = tuple(int(x) for x in g.integers(1, 12 if N > 3 else 90, size=N))
+        perm = tuple(int(x) for x in g.permutation(N))
+        oa = tuple(s + int(g.integers(0, 3)) for s in sizes) if g.random() < 0.4 else None
+        sb = tuple(sizes[q] for q in perm)
+        ob = tuple(s + int(g.integers(0, 3)) for s in sb) if g.random() < 0.3 else None
+        din, dout = [("f32", "f32"), ("f64", "f64"), ("bf16", "bf16"), ("f32", "e4m3"), ("f32", "bf16")][trial % 5]
+        plan = ttc.Plan(perm, sizes, din, dout, outer_a=oa, outer_b=ob)
+        _verify_all(plan, (perm, sizes, oa, ob, din, dout))
+
+
+def test_schedules_are_sound_on_the_workloads():
+    p = inputs.single_4d()
+    _verify_all(ttc.Plan(p.perm, p.sizes), "single4d")
+    for c in inputs.packing_cases():
+        _verify_all(ttc.Plan(c.perm, c.sizes, c.dtype_in, c.dtype_out, outer_a=c.outer_a), c.tag)
+    # the 2D..6D sweep shapes at a reduced size (same index structure)
+    g = inputs.rng(5)
+    for N in (2, 3, 4, 5, 6):
+        for perm in inputs.sweep_perms(N, g, 8):
+            sizes = inputs.near_equal_sizes(N, 1 << 17, g, tol=0.05)
+            _verify_all(ttc.Plan(perm, sizes, "f32", "f32", 1.7, 0.4), (perm, sizes))

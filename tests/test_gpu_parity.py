@@ -1,0 +1,221 @@
+"""GPU parity: libttc (sm_103a kernels, through the C ABI) against the CPU
+oracle, element by element, on seeded inputs.
+
+Bar: bit-exact against the oracle's rounding sequence for every dtype (NaN
+payloads only for pure bit copies), and within the stated tolerance of the
+exact value (2 FP32 ulps for FP32 data, 1e-15 relative for FP64 data, 1 BF16
+ulp for BF16 output, all at the scale max(|alpha a|, |beta b|, |r|)).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1607_01249_gb300 import build as ttc_build
+from paper_1607_01249_gb300 import inputs
+from paper_1607_01249_gb300 import ttc
+from tests import gpu_helpers as H
+from paper_1607_01249_gb300.inputs import Problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    ttc_build.build()
+    ttc.lib()
+
+
+def small_sweep(Ns=(2, 3, 4, 5, 6), target=1 << 15, perms=4, seed=11):
+    g = inputs.rng(seed)
+    out = []
+    for N in Ns:
+        for perm in inputs.sweep_perms(N, g, perms):
+            out.append((perm, inputs.near_equal_sizes(N, target, g, tol=0.05)))
+    return out
+
+
+SMALL = small_sweep()
+
+
+def test_single_4d_workload():
+    p = inputs.single_4d()
+    H.full_check(p, seed=0)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("beta", [0.0, 0.4])
+@pytest.mark.parametrize("case", range(len(SMALL)))
+def test_small_sweep(case, dt, beta):
+    perm, sizes = SMALL[case]
+    p = Problem(perm=perm, sizes=sizes, dtype_in=dt, dtype_out=dt, alpha=1.7, beta=beta)
+    H.full_check(p, seed=case)
+
+
+PAIRS = [("f32", "f32"), ("f32", "f64"), ("f32", "bf16"), ("f32", "e4m3"), ("f64", "f64"), ("f64", "f32"),
+         ("bf16", "bf16"), ("bf16", "f32"), ("bf16", "e4m3")]
+
+
+@pytest.mark.parametrize("din,dout", PAIRS)
+@pytest.mark.parametrize("ab", [(1.0, 0.0), (1.7, 0.0), (-0.75, 0.4)])
+@pytest.mark.parametrize("shape", [((2, 0, 3, 1), (33, 17, 20, 9)), ((0, 2, 1), (300, 21, 13)),
+                                   ((0, 2, 1), (7, 61, 40)), ((1, 0), (1000, 3))])
+def test_dtype_pairs(din, dout, ab, shape):
+    alpha, beta = ab
+    if dout == "e4m3" and beta != 0.0:
+        pytest.skip("FP8 output is beta == 0 only")
+    perm, sizes = shape
+    p = Problem(perm=perm, sizes=sizes, dtype_in=din, dtype_out=dout, alpha=alpha, beta=beta)
+    H.full_check(p, seed=3, dist="normal")
+
+
+@pytest.mark.parametrize("trial", range(12))
+def test_outer_sizes_and_canaries(trial):
+    g = inputs.rng(200 + trial)
+    N = int(g.integers(2, 6))
+    perm = inputs.random_perm(N, g)
+    sizes = tuple(int(x) for x in g.integers(2, 40 if N < 4 else 14, size=N))
+    oa = tuple(s + int(g.integers(0, 5)) for s in sizes)
+    sb = tuple(sizes[q] for q in perm)
+    ob = tuple(s + int(g.integers(0, 5)) for s in sb) if trial % 2 else None
+    dt = ["f32", "f64", "bf16"][trial % 3]
+    beta = 0.0 if trial % 4 < 2 else 0.5
+    p = Problem(perm=perm, sizes=sizes, dtype_in=dt, dtype_out=dt, alpha=1.25, beta=beta, outer_a=oa,
+                outer_b=ob)
+    H.full_check(p, seed=trial)   # whole B buffer compared: elements outside the sub-tensor unchanged
+
+
+@pytest.mark.parametrize("case", inputs.packing_cases(), ids=lambda c: f"{c.tag}-{c.dtype_out}")
+def test_packing_workloads(case):
+    if case.tag.startswith("panel"):
+        M, K = case.extra["matrix"]
+        m0, k0 = case.extra["offset"]
+        full = inputs.tensor_for("f32", M * K, 5, "normal")
+        A = full[m0 + k0 * M:]              # A points at the sub-block's first element
+        B0 = np.zeros(case.vol_b, inputs.STORAGE[case.dtype_out])
+        got, scale = H.run_gpu(case, A, B0)
+        want, oscale = H.oracle_mirror(case, A, B0)
+    else:
+        A, B0 = H.make_inputs(case, 6, "normal")
+        got, scale = H.run_gpu(case, A, B0)
+        want, oscale = H.oracle_mirror(case, A, B0)
+    if case.dtype_out == "e4m3":
+        assert scale == oscale
+        rep = H.fp8_error_report(case, A, got, scale)
+        assert rep["bound_ok"], rep
+    ok, msg = H.compare_bits(got, want, case.dtype_out, nan_as_nan=True)
+    assert ok, msg
+    ok, msg = H.tolerance_check(case, A, B0, got)
+    assert ok, msg
+
+
+def test_fp8_caller_scale_and_degenerate_amax():
+    p = Problem(perm=(1, 0), sizes=(96, 70), dtype_in="f32", dtype_out="e4m3")
+    A, B0 = H.make_inputs(p, 7, "normal")
+    s = torch.tensor([0.01], dtype=torch.float32, device="cuda")
+    got, scale = H.run_gpu(p, A, B0, scale_dev=s)
+    assert scale == np.float32(0.01)
+    want, _ = H.oracle_mirror(p, A, B0, scale=float(np.float32(0.01)))
+    assert np.array_equal(got, want)
+    Z = Problem(perm=(1, 0), sizes=(96, 70), dtype_in="f32", dtype_out="e4m3")
+    A0 = np.zeros(Z.vol_a, np.float32)
+    got, scale = H.run_gpu(Z, A0, np.zeros(Z.vol_b, np.uint8))
+    assert scale == 1.0 and not got.any()
+
+
+def test_beta_zero_never_reads_B():
+    for dt in ("f32", "f64", "bf16"):
+        for perm, sizes in [((2, 0, 1), (40, 30, 20)), ((0, 2, 1), (200, 10, 30))]:
+            p = Problem(perm=perm, sizes=sizes, dtype_in=dt, dtype_out=dt, alpha=1.7, beta=0.0)
+            fill = {"f32": np.float32(np.nan), "f64": np.nan, "bf16": np.uint16(0x7FC1)}[dt]
+            A, B0, got, _ = H.full_check(p, seed=9, b_fill=fill)
+            assert not np.isnan(H.as_float(got, dt)).any()
+
+
+def test_bitcopy_special_patterns():
+    pats32 = np.array([0x80000000, 0x00000001, 0x807FFFFF, 0x7FC00123, 0xFFA00001, 0x7F800000, 0xFF800000,
+                       0x00800000, 0x7F7FFFFF, 0x3F800000], np.uint32)
+    for perm, sizes in [((1, 0), (50, 37)), ((0, 2, 1), (64, 5, 7)), ((2, 1, 0), (9, 10, 11))]:
+        n = int(np.prod(sizes))
+        A = np.resize(pats32, n).view(np.float32)
+        p = Problem(perm=perm, sizes=sizes)
+        got, _ = H.run_gpu(p, A, np.zeros(n, np.float32))
+        want, _ = H.oracle_mirror(p, A, np.zeros(n, np.float32))
+        assert got.tobytes() == want.tobytes()
+        A64 = np.resize(np.array([0x8000000000000000, 1, 0x7FF8000000000123, 0xFFF0000000000001], np.uint64),
+                        n).view(np.float64)
+        p64 = Problem(perm=perm, sizes=sizes, dtype_in="f64", dtype_out="f64")
+        got, _ = H.run_gpu(p64, A64, np.zeros(n, np.float64))
+        want, _ = H.oracle_mirror(p64, A64, np.zeros(n, np.float64))
+        assert got.tobytes() == want.tobytes()
+        A16 = np.resize(np.array([0x8000, 0x0001, 0x7FC3, 0xFF81, 0x7F80], np.uint16), n)
+        p16 = Problem(perm=perm, sizes=sizes, dtype_in="bf16", dtype_out="bf16")
+        got, _ = H.run_gpu(p16, A16, np.zeros(n, np.uint16))
+        want, _ = H.oracle_mirror(p16, A16, np.zeros(n, np.uint16))
+        assert got.tobytes() == want.tobytes()
+
+
+@pytest.mark.parametrize("perm,sizes", [((0,), (1,)), ((0,), (1000003,)), ((1, 0), (1, 1)),
+                                        ((2, 1, 0), (1, 1, 7)), ((1, 0, 2), (1, 5, 1)),
+                                        (tuple(range(15, -1, -1)), (2,) * 16),
+                                        ((3, 1, 0, 2), (2, 3, 1, 4)), ((1, 0), (3, 100003))])
+def test_edge_shapes(perm, sizes):
+    for dt, beta in (("f32", 0.0), ("f64", 0.5)):
+        p = Problem(perm=perm, sizes=sizes, dtype_in=dt, dtype_out=dt, alpha=1.7, beta=beta)
+        H.full_check(p, seed=4)
+
+
+def test_empty_problem_launches_nothing():
+    p = ttc.Plan((1, 0), (0, 7))
+    before = ttc.launch_count()
+    p.execute(torch.empty(0, device="cuda"), torch.empty(0, device="cuda"))
+    assert ttc.launch_count() == before
+
+
+def test_every_candidate_schedule_agrees():
+    for perm, sizes in [SMALL[3], SMALL[9], SMALL[15], ((2, 0, 3, 1), (32, 40, 24, 36))]:
+        p = Problem(perm=perm, sizes=sizes, alpha=1.7, beta=0.4)
+        plan = ttc.Plan(p.perm, p.sizes, alpha=p.alpha, beta=p.beta)
+        A, B0 = H.make_inputs(p, 1)
+        want, _ = H.oracle_mirror(p, A, B0)
+        for i in range(plan.info()["ncandidates"]):
+            plan.select(i)
+            got, _ = H.run_gpu(p, A, B0, plan=plan)
+            ok, msg = H.compare_bits(got, want, "f32", nan_as_nan=True)
+            assert ok, (i, msg)
+
+
+def test_autotune_keeps_results_and_uses_no_user_memory():
+    p = Problem(perm=(2, 0, 3, 1), sizes=(32, 40, 24, 36), alpha=1.7, beta=0.4)
+    plan = ttc.Plan(p.perm, p.sizes, alpha=p.alpha, beta=p.beta)
+    ms = plan.autotune(max_candidates=6)
+    assert ms > 0
+    H.full_check(p, seed=2, plan=plan)
+
+
+def test_non_default_stream():
+    p = Problem(perm=(1, 2, 0), sizes=(70, 80, 90), alpha=1.7, beta=0.4)
+    A, B0 = H.make_inputs(p, 8)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        got, _ = H.run_gpu(p, A, B0, stream=s)
+    want, _ = H.oracle_mirror(p, A, B0)
+    ok, msg = H.compare_bits(got, want, "f32", True)
+    assert ok, msg
+
+
+# ---- full-size cases of the 2D..6D sweep (2^26 elements), whole output compared
+
+FULL = [c for c in inputs.sweep_cases() if c.beta == 0.4 and
+        ((c.dtype_in == "f32" and c.tag.endswith("p1")) or (c.dtype_in == "f64" and c.tag in ("N4p0", "N6p1")))]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("case", FULL, ids=lambda c: f"{c.tag}-{c.dtype_in}")
+def test_full_size_sweep_case(case):
+    H.full_check(case, seed=1)
