@@ -129,9 +129,13 @@ def sweep_problems():
     return inputs.sweep_cases()
 
 
-def workload_problems(name: str):
+def workload_problems(name: str, target: int = 1 << 26, only: str = ""):
     if name == "sweep":
-        return sweep_problems()
+        probs = inputs.sweep_cases(target=target)
+        if only:
+            keep = set(only.split(","))
+            probs = [p for p in probs if p.tag in keep or f"{p.tag}/{p.dtype_in}/b{p.beta}" in keep]
+        return probs
     if name == "single4d":
         return [inputs.single_4d()]
     if name == "packing":
@@ -191,7 +195,7 @@ def run_ours(args, rank, world):
     ttc.lib()
     dev = rank % max(torch.cuda.device_count(), 1)
     torch.cuda.set_device(dev)
-    probs = workload_problems(args.workload)
+    probs = workload_problems(args.workload, args.target, args.only)
     plans = [ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta, p.outer_a, p.outer_b)
              for p in probs]
     if args.autotune:
@@ -288,7 +292,9 @@ def run_ours(args, rank, world):
         "cases": {"min_GBs": round(min(case_gbs), 1), "median_GBs": round(float(np.median(case_gbs)), 1),
                   "max_GBs": round(max(case_gbs), 1),
                   "frac_ge_256MiB_at_80pct_of_8TBs": (round(sum(g >= 6400 for g in big) / len(big), 3)
-                                                      if big else None)},
+                                                      if big else None),
+                  "frac_ge_256MiB_at_80pct_of_measured": (round(sum(g >= 0.8 * peak for g in big) / len(big), 3)
+                                                          if big else None)},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,
@@ -390,14 +396,15 @@ def oracle_slabs(p, A, B, threads):
         list(ex.map(work, chunks))
 
 
-def cpu_baseline(budget_s: float, probs, threads: int, max_cases: int = 3):
+def cpu_baseline(budget_s: float, probs, threads: int, max_cases: int = 10):
     """Time the oracle as it stands on a bounded sample: the first few cases of
     the workload, full size, until budget_s is spent."""
     import oracle
     oracle.build()
     done_bytes, t_total, names = 0, 0.0, []
     t_start = time.perf_counter()
-    for p in probs[:max_cases]:
+    step = max(1, len(probs) // max_cases)
+    for p in probs[::step][:max_cases]:
         A = inputs.tensor_for(p.dtype_in, p.vol_a, 1)
         B = inputs.tensor_for(p.dtype_out, p.vol_b, 2)
         t0 = time.perf_counter()
@@ -414,7 +421,7 @@ def cpu_baseline(budget_s: float, probs, threads: int, max_cases: int = 3):
 
 
 def run_reference(args, rank, world):
-    probs = workload_problems(args.workload)
+    probs = workload_problems(args.workload, args.target, args.only)
     threads = os.cpu_count() or 1
     import oracle
     oracle.build()
@@ -454,6 +461,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--target", type=int, default=1 << 26, help="elements per tensor of the sweep")
+    ap.add_argument("--only", default="", help="comma-separated case tags of the sweep (e.g. N5p3)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -472,7 +481,8 @@ def main():
     out = run_ours(args, rank, world)
     if rank == 0:
         if not args.no_cpu and world == 1:
-            out["cpu_baseline"] = cpu_baseline(args.cpu_budget, workload_problems(args.workload),
+            out["cpu_baseline"] = cpu_baseline(args.cpu_budget,
+                                               workload_problems(args.workload, args.target, args.only),
                                                os.cpu_count() or 1)
         print(json.dumps(out), flush=True)
     if world > 1:
