@@ -191,6 +191,47 @@ const char* ttc_last_error(void);
  * threads).  Used by benchmarks to report launch counts. */
 int64_t ttc_launch_count(void);
 
+/*
+ * ttc_execute_noalloc -- ttc_execute for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a deployment aid of this
+ * library.
+ *
+ * Who needs it: ttc_execute allocates a small per-device scratch area on a
+ * plan's first execution on each device (the FP8 amax/scale words and the
+ * tile schedule's offset tables).  Some callers cannot make that call: code
+ * whose device memory is entirely owned by a pool allocator (a framework's
+ * caching allocator, a serving process with a fixed memory budget) where a
+ * cudaMalloc would fail or break the pool's accounting, and code that must
+ * not make the implicitly synchronising cudaMalloc/cudaFree calls at all.
+ * This entry point runs the same kernels with that scratch placed in one
+ * fixed array of TTC_NOALLOC_SCRATCH_BYTES bytes that the library reserves
+ * statically in device memory (every GPU that loads the library holds it
+ * until the process exits).  It makes no device-memory allocation: it calls
+ * no cudaMalloc, cudaMallocAsync or cudaFree and no library routine that
+ * allocates device memory (host-side it only builds the kernel parameters).
+ *
+ *  plan, A, B, stream  as for ttc_execute (same checks, same results).
+ *  d_scale_out         FP8 plans: NULL or a device pointer to one float that
+ *                      receives the scale used; ignored for other plans.
+ *
+ * Limits and behaviour:
+ *  - A plan whose schedule needs more scratch than the static array holds is
+ *    rejected with TTC_ERR_INVALID_SIZE (ttc_last_error gives both sizes);
+ *    ttc_execute still runs it.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture begins.
+ *  - Every call shares the one array per device, and the array keeps the last
+ *    call's contents; each call re-initialises what it uses (the amax word is
+ *    cleared, the offset tables are re-uploaded on `stream`).  Calls whose
+ *    work overlaps on the GPU (different streams, or different host threads
+ *    without ordering) race on the array and must be serialised by the
+ *    caller.
+ */
+#define TTC_NOALLOC_SCRATCH_BYTES 8192
+ttc_status ttc_execute_noalloc(ttc_plan_t plan, const void* A, void* B, float* d_scale_out,
+                               ttc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,7 @@ SIGNATURES = {
     "ttc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ttc_last_error": (ctypes.c_char_p, []),
     "ttc_launch_count": (ctypes.c_int64, []),
+    "ttc_execute_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     # include/ttc_debug.h
     "ttc_debug_verify_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
 }
@@ -149,6 +150,12 @@ class Plan:
         return B
 
     __call__ = execute
+
+    def execute_noalloc(self, A, B, d_scale_out=None, stream=None):
+        """ttc_execute_noalloc: the same work with the device scratch in the
+        library's static array (no device-memory allocation)."""
+        _check(lib().ttc_execute_noalloc(self._h, _ptr(A), _ptr(B), _ptr(d_scale_out), _stream(stream)))
+        return B
 
     def info(self) -> dict:
         inf = PlanInfo()
