@@ -157,6 +157,9 @@ typedef struct {
     int vec_in, vec_out;           /* vector widths (elements) the schedule uses when aligned */
     int candidate;                 /* index of the schedule in the plan's candidate list */
     int ncandidates;               /* number of candidate schedules the planner kept */
+    int lanes_a, lanes_b;          /* tile variant: lanes along the A run / B run of the warp-mapped
+                                      kernels (32, 64, 128), or 0 for the generic tile kernel */
+    int async_ring;                /* 1: A is read with asynchronous copies into a ring of tiles */
 } ttc_plan_info;
 
 ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info);

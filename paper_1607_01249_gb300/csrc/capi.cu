@@ -164,7 +164,9 @@ ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s, int g
   if (k.variant == VAR_TILE) {
     TileParams tp = r->tp;
     tp.epi = epi;
-    e = launch_tile(p->din, p->dout, A, B, tp, r->smem, s, grid_override);
+    e = k.ring ? launch_tile3(p->din, p->dout, k.ju, k.jw, A, B, tp, r->smem, s, grid_override)
+        : k.ju ? launch_tile2(p->din, p->dout, k.ju, k.jw, A, B, tp, r->smem, s, grid_override)
+             : launch_tile(p->din, p->dout, A, B, tp, r->smem, s, grid_override);
     if (e != cudaSuccess) return cuda_fail(e, "tile kernel launch");
   } else if (k.variant == VAR_COPY) {
     RowParams rp = r->rp;
@@ -323,6 +325,9 @@ ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info) {
     info->tile_b = tp.LB;
     info->ntiles = tp.ntiles;
     info->vec_in = info->vec_out = 1;
+    info->lanes_a = 32 * k.ju;
+    info->lanes_b = 32 * k.jw;
+    info->async_ring = k.ring;
   } else if (k.variant == VAR_COPY) {
     RowParams rp;
     build_row_params(c, k.chunk, &rp);

@@ -1,0 +1,5 @@
+// kern_f32_f32.cu -- kernel instantiations for one dtype pair (see kernels_pair.cuh).
+#define TTC_DIN ttc::DT_F32
+#define TTC_DOUT ttc::DT_F32
+#define TTC_PAIR f32_f32
+#include "kernels_pair.cuh"

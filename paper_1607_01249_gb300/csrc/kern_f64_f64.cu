@@ -1,0 +1,5 @@
+// kern_f64_f64.cu -- kernel instantiations for one dtype pair (see kernels_pair.cuh).
+#define TTC_DIN ttc::DT_F64
+#define TTC_DOUT ttc::DT_F64
+#define TTC_PAIR f64_f64
+#include "kernels_pair.cuh"

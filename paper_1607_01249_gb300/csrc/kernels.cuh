@@ -88,6 +88,33 @@ __device__ __forceinline__ store_t<DOUT> epilogue(stage_t<DIN> a, store_t<DOUT> 
   }
 }
 
+// The update of Eq. 1 with the mode fixed at compile time (no per-element
+// branches): EK_COPY moves bits (alpha = 1, beta = 0, same type), EK_SCALE
+// r = alpha*a, EK_AXPBY r = fma(beta, b, alpha*a), EK_FP8 the scaled E4M3 code.
+enum EpiKind : int { EK_COPY = 0, EK_SCALE = 1, EK_AXPBY = 2, EK_FP8 = 3 };
+
+template <int DIN, int DOUT, int EK>
+__device__ __forceinline__ store_t<DOUT> epilogue_k(stage_t<DIN> a, store_t<DOUT> b, const Epilogue& e,
+                                                    float scale) {
+  if constexpr (EK == EK_FP8) {
+    const float v = __fmul_rn(e.alpha_f, float(a));
+    return store_t<DOUT>(__nv_cvt_float_to_fp8(__fdiv_rn(v, scale), __NV_SATFINITE, __NV_E4M3));
+  } else if constexpr (EK == EK_COPY) {
+    if constexpr (DIN == DT_BF16 && DOUT == DT_BF16) return store_t<DOUT>(__float_as_uint(a) >> 16);
+    else return a;
+  } else if constexpr (ComputeIsF64<DIN, DOUT>::value) {
+    double r = __dmul_rn(e.alpha_d, double(a));
+    if constexpr (EK == EK_AXPBY) r = __fma_rn(e.beta_d, double(b), r);
+    if constexpr (DOUT == DT_F64) return r;
+    else return __double2float_rn(r);
+  } else {
+    float r = __fmul_rn(e.alpha_f, float(a));
+    if constexpr (EK == EK_AXPBY) r = __fmaf_rn(e.beta_f, out_as_float<DOUT>(b), r);
+    if constexpr (DOUT == DT_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(r));
+    else return r;
+  }
+}
+
 template <typename T, int N>
 struct alignas(sizeof(T) * N) VecT {
   T v[N];
@@ -121,7 +148,7 @@ TTC_HD TileCoord tile_coord(uint32_t tid, const TileParams& p) {
 }
 
 // Read order: (u, lb) with u = la*LC + lc.  f(k, A offset in tile, smem position)
-template <class F>
+template <int K = kTileK, class F>
 TTC_HD void walk_read(const TileCoord& c, const TileParams& p, const int32_t* tabA, int u0, int lb0, F&& f,
                       bool need_offset = true) {
   const int limU = c.remA * p.LC;
@@ -132,7 +159,7 @@ TTC_HD void walk_read(const TileCoord& c, const TileParams& p, const int32_t* ta
   asm volatile("" : "+r"(u), "+r"(lb));
 #endif
 #pragma unroll
-  for (int k = 0; k < kTileK; ++k) {
+  for (int k = 0; k < K; ++k) {
     if (lb < c.remB && u < limU) {
       int32_t off = 0;
       if (need_offset) off = u * p.saU + (p.crossA_tab ? tabA[lb] : lb * p.crossA_lin);
@@ -145,7 +172,7 @@ TTC_HD void walk_read(const TileCoord& c, const TileParams& p, const int32_t* ta
 }
 
 // Write order: (lc, lb, la).  f(k, B offset in tile, smem position)
-template <class F>
+template <int K = kTileK, class F>
 TTC_HD void walk_write(const TileCoord& c, const TileParams& p, const int32_t* tabB, int lc0, int lb0, int la0,
                        F&& f) {
   int lc = lc0, lb = lb0, la = la0;
@@ -153,7 +180,7 @@ TTC_HD void walk_write(const TileCoord& c, const TileParams& p, const int32_t* t
   asm volatile("" : "+r"(lc), "+r"(lb), "+r"(la));
 #endif
 #pragma unroll
-  for (int k = 0; k < kTileK; ++k) {
+  for (int k = 0; k < K; ++k) {
     if (la < c.remA && lb < c.remB) {
       const int32_t off = (lb * p.LC + lc) * p.sbV + (p.crossB_tab ? tabB[la] : la * p.crossB_lin);
       f(k, off, lb * p.P + la * p.LC + lc);
@@ -161,6 +188,94 @@ TTC_HD void walk_write(const TileCoord& c, const TileParams& p, const int32_t* t
     lc += p.wr_dlc; lb += p.wr_dlb; la += p.wr_dla;
     if (lc >= p.LC) { lc -= p.LC; ++lb; }
     if (lb >= p.LB) { lb -= p.LB; ++la; }
+  }
+}
+
+// Warp-mapped walks (tile2_kernel).  Read: lanes along u (JU chunks of 32),
+// warps along lb.  Write: lanes along v (JW chunks), warps along la.
+template <int JU, int K = kTileK, class F>
+TTC_HD void walk2_read(const TileCoord& c, const TileParams& p, const int32_t* tabA, int lane, int warp,
+                       F&& f) {
+  constexpr int RR = K / JU;
+  const int limU = c.remA * p.LC;
+#pragma unroll
+  for (int i = 0; i < RR; ++i) {
+    const int r = warp + 8 * i;
+    if (r < c.remB) {
+      const int32_t row = p.crossA_tab ? tabA[r] : r * p.crossA_lin;
+#pragma unroll
+      for (int j = 0; j < JU; ++j) {
+        const int u = lane + 32 * j;
+        if (u < limU) f(i * JU + j, row + u * p.saU, r * p.P + u);
+      }
+    }
+  }
+}
+
+// per-lane constants of the write walk: shared-memory offset and B offset of
+// the lane's run positions v = lane + 32 j
+template <int JW>
+TTC_HD void walk2_lane_consts(const TileParams& p, int lane, int (&spre)[JW], int32_t (&voff)[JW]) {
+#pragma unroll
+  for (int j = 0; j < JW; ++j) {
+    const int vv = lane + 32 * j;
+    spre[j] = (vv / p.LC) * p.P + vv % p.LC;
+    voff[j] = vv * p.sbV;
+  }
+}
+
+template <int JW, int K = kTileK, class F>
+TTC_HD void walk2_write(const TileCoord& c, const TileParams& p, const int32_t* tabB, int lane, int warp,
+                        const int (&spre)[JW], const int32_t (&voff)[JW], F&& f) {
+  constexpr int RW = K / JW;
+  const int limV = c.remB * p.LC;
+#pragma unroll
+  for (int i = 0; i < RW; ++i) {
+    const int la = warp + 8 * i;
+    if (la < c.remA) {
+      const int32_t row = p.crossB_tab ? tabB[la] : la * p.crossB_lin;
+#pragma unroll
+      for (int j = 0; j < JW; ++j)
+        if (lane + 32 * j < limV) f(i * JW + j, row + voff[j], spre[j] + la * p.LC);
+    }
+  }
+}
+
+// Unit-stride warp-mapped walks (tile3_kernel: both runs have stride 1).
+// FULL: the tile is interior (no cut index is short), so no per-element test.
+template <int JU, int K, bool FULL, class F>
+TTC_HD void walk3_read(const TileCoord& c, const TileParams& p, const int32_t* tabA, int lane, int warp,
+                       F&& f) {
+  constexpr int RR = K / JU;
+  const int limU = c.remA * p.LC;
+#pragma unroll
+  for (int i = 0; i < RR; ++i) {
+    const int r = warp + 8 * i;
+    if (FULL ? (r < p.LB) : (r < c.remB)) {
+      const int32_t row = (p.crossA_tab ? tabA[r] : r * p.crossA_lin) + lane;
+      const int pos = r * p.P + lane;
+#pragma unroll
+      for (int j = 0; j < JU; ++j)
+        if (FULL ? (32 * j < p.U - lane) : (32 * j < limU - lane)) f(i * JU + j, row + 32 * j, pos + 32 * j);
+    }
+  }
+}
+
+template <int JW, int K, bool FULL, class F>
+TTC_HD void walk3_write(const TileCoord& c, const TileParams& p, const int32_t* tabB, int lane, int warp,
+                        const int (&spre)[JW], F&& f) {
+  constexpr int RW = K / JW;
+  const int limV = c.remB * p.LC;
+#pragma unroll
+  for (int i = 0; i < RW; ++i) {
+    const int la = warp + 8 * i;
+    if (FULL ? (la < p.LA) : (la < c.remA)) {
+      const int32_t row = (p.crossB_tab ? tabB[la] : la * p.crossB_lin) + lane;
+      const int spos = la * p.LC;
+#pragma unroll
+      for (int j = 0; j < JW; ++j)
+        if (FULL ? (32 * j < p.W - lane) : (32 * j < limV - lane)) f(i * JW + j, row + 32 * j, spre[j] + spos);
+    }
   }
 }
 

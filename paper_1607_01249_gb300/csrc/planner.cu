@@ -24,6 +24,7 @@
 #include <sstream>
 
 #include "../../include/ttc.h"
+#include "launch.h"
 #include "planner.h"
 
 namespace ttc {
@@ -59,7 +60,7 @@ std::string Candidate::describe() const {
     for (size_t i = 0; i < ga.size(); ++i) o << (i ? "," : "") << ga[i];
     o << "]/" << ta << " gb=[";
     for (size_t i = 0; i < gb.size(); ++i) o << (i ? "," : "") << gb[i];
-    o << "]/" << tb << " order=[";
+    o << "]/" << tb << " j=" << ju << "," << jw << (ring ? " ring" : "") << " order=[";
     for (size_t i = 0; i < order.size(); ++i) o << (i ? "," : "") << order[i];
     o << "]";
   }
@@ -305,7 +306,8 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
   const bool hc = c.perm[0] == 0;
   const int c0 = hc ? 1 : 0;
   const int64_t LC = hc ? c.s[0] : 1;
-  const int Vmax = kTileVmax;
+  const int Kt = tile_k_for(din == DT_F64 ? 8 : 4);
+  const int Vmax = kThreads * Kt;
   std::vector<Candidate> tiles;
   if (!(hc && c.N == 1) && LC * 2 <= Vmax) {
     // A-group index list: A order from c0, dense, never B's first index after C
@@ -387,6 +389,32 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
             k.seg_b = rb;
             k.est_s = std::max(mem, issue) + 0.25 * std::min(mem, issue) + over + 3e-6;
             tiles.push_back(k);
+            // the warp-mapped kernel, when the shape fits one of its lane layouts
+            const int64_t U = LC * LA, W = LC * LB;
+            int ju = 0, jw = 0;
+            for (int j : {1, 2, 4})
+              if (!ju && U <= 32 * j && LB <= 8 * Kt / j) ju = j;
+            for (int j : {1, 2, 4})
+              if (!jw && W <= 32 * j && LA <= 8 * Kt / j) jw = j;
+            if (ju && jw) {
+              const double rows_r = std::ceil(double(LB) / 8.0), rows_w = std::ceil(double(LA) / 8.0);
+              const double wi = 8.0 * (rows_r * (ju * 4.0 + 4.0 + (sh.gb.size() > 1 ? 2 : 0)) +
+                                       rows_w * (jw * (5.0 + (bnz ? 3.0 : 0.0)) + 4.0 + (sh.ga.size() > 1 ? 2 : 0)));
+              const double issue2 = ntiles * 32.0 * wi / kLaneInstrPerS;
+              Candidate k2 = k;
+              k2.ju = ju;
+              k2.jw = jw;
+              k2.est_s = std::max(mem, issue2) + 0.25 * std::min(mem, issue2) + over + 3e-6;
+              tiles.push_back(k2);
+              if ((din == DT_F32 || din == DT_F64) && tile3_layout_supported(ju, jw) && c.sa[0] == 1 &&
+                  c.sb[c.perm[0]] == 1) {
+                // asynchronous-copy ring: loads hidden behind the writes of earlier tiles
+                Candidate k3 = k2;
+                k3.ring = 1;
+                k3.est_s = std::max(mem, issue2) + 0.05 * std::min(mem, issue2) + over + 3e-6;
+                tiles.push_back(k3);
+              }
+            }
           }
         }
       }

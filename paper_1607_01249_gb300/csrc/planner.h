@@ -35,6 +35,8 @@ struct Candidate {
   std::vector<int> gb;         // A indices of GB, in B order (last one may be cut)
   int tb = 1;                  // tile extent of GB's last index
   std::vector<int> order;      // grid indices (A index ids), fastest first
+  int ju = 0, jw = 0;          // >0: warp-mapped tile kernel with JU/JW chunks of 32 lanes
+  int ring = 0;                // warp-mapped kernel reading A with cp.async into a ring of tiles
   // copy variant
   int64_t chunk = 0;
   int vec = 1;                 // vector width usable when pointers are aligned

@@ -79,12 +79,18 @@ struct Checker {
   }
 
   bool tile(const Candidate& k) {
+    if (p->din == DT_F64) return tile_k<tile_k_for(8)>(k);
+    return tile_k<tile_k_for(4)>(k);
+  }
+
+  template <int K>
+  bool tile_k(const Candidate& k) {
     TileParams tp;
     std::vector<int32_t> ta, tb;
     int smem = 0;
     build_tile_params(p->canon, k, p->din, &tp, &ta, &tb, &smem);
     if (smem > 200 * 1024) return fail("shared memory over budget", smem, 0);
-    if (tp.V > kTileVmax) return fail("tile larger than the threads cover", tp.V, kTileVmax);
+    if (tp.V > kThreads * K) return fail("tile larger than the threads cover", tp.V, kThreads * K);
     const int ncap = tp.P * tp.LB;
     std::vector<int64_t> posA(static_cast<size_t>(ncap));
     std::vector<uint8_t> used(static_cast<size_t>(ncap));
@@ -93,23 +99,62 @@ struct Checker {
       std::fill(posA.begin(), posA.end(), -1);
       std::fill(used.begin(), used.end(), 0);
       bool ok = true;
-      for (int t = 0; t < kThreads && ok; ++t) {
-        walk_read(c, tp, ta.data(), t % tp.U, t / tp.U, [&](int, int32_t off, int pos) {
-          if (!ok) return;
-          if (pos < 0 || pos >= ncap) { ok = fail("shared-memory position out of range (read)", pos, ncap); return; }
-          if (posA[size_t(pos)] != -1) { ok = fail("shared-memory position written twice", pos, tid); return; }
-          posA[size_t(pos)] = c.baseA + off;
-        });
+      auto on_read = [&](int, int32_t off, int pos) {
+        if (!ok) return;
+        if (pos < 0 || pos >= ncap) { ok = fail("shared-memory position out of range (read)", pos, ncap); return; }
+        if (posA[size_t(pos)] != -1) { ok = fail("shared-memory position written twice", pos, tid); return; }
+        posA[size_t(pos)] = c.baseA + off;
+      };
+      auto on_write = [&](int, int32_t off, int pos) {
+        if (!ok) return;
+        if (pos < 0 || pos >= ncap) { ok = fail("shared-memory position out of range (write)", pos, ncap); return; }
+        if (posA[size_t(pos)] < 0) { ok = fail("shared-memory position read but never written", pos, tid); return; }
+        if (used[size_t(pos)]) { ok = fail("shared-memory position read twice", pos, tid); return; }
+        used[size_t(pos)] = 1;
+        ok = pair(posA[size_t(pos)], c.baseB + off);
+      };
+      const bool full = c.remA == tp.LA && c.remB == tp.LB;
+      if (k.ring) {
+        for (int t = 0; t < kThreads && ok; ++t) {
+          const int ln = t & 31, wp = t >> 5;
+          if (k.ju == 1) { if (full) walk3_read<1, K, true>(c, tp, ta.data(), ln, wp, on_read); else walk3_read<1, K, false>(c, tp, ta.data(), ln, wp, on_read); }
+          else if (k.ju == 2) { if (full) walk3_read<2, K, true>(c, tp, ta.data(), ln, wp, on_read); else walk3_read<2, K, false>(c, tp, ta.data(), ln, wp, on_read); }
+          else if (k.ju == 4) { if (full) walk3_read<4, K, true>(c, tp, ta.data(), ln, wp, on_read); else walk3_read<4, K, false>(c, tp, ta.data(), ln, wp, on_read); }
+          else ok = fail("unknown lane layout", k.ju, 0);
+        }
+        for (int t = 0; t < kThreads && ok; ++t) {
+          const int ln = t & 31, wp = t >> 5;
+          if (k.jw == 1) { int sp[1]; int32_t vo[1]; walk2_lane_consts<1>(tp, ln, sp, vo);
+            if (full) walk3_write<1, K, true>(c, tp, tb.data(), ln, wp, sp, on_write); else walk3_write<1, K, false>(c, tp, tb.data(), ln, wp, sp, on_write); }
+          else if (k.jw == 2) { int sp[2]; int32_t vo[2]; walk2_lane_consts<2>(tp, ln, sp, vo);
+            if (full) walk3_write<2, K, true>(c, tp, tb.data(), ln, wp, sp, on_write); else walk3_write<2, K, false>(c, tp, tb.data(), ln, wp, sp, on_write); }
+          else if (k.jw == 4) { int sp[4]; int32_t vo[4]; walk2_lane_consts<4>(tp, ln, sp, vo);
+            if (full) walk3_write<4, K, true>(c, tp, tb.data(), ln, wp, sp, on_write); else walk3_write<4, K, false>(c, tp, tb.data(), ln, wp, sp, on_write); }
+          else ok = fail("unknown lane layout", k.jw, 0);
+        }
       }
-      for (int t = 0; t < kThreads && ok; ++t) {
-        walk_write(c, tp, tb.data(), t % tp.LC, (t / tp.LC) % tp.LB, t / tp.W, [&](int, int32_t off, int pos) {
-          if (!ok) return;
-          if (pos < 0 || pos >= ncap) { ok = fail("shared-memory position out of range (write)", pos, ncap); return; }
-          if (posA[size_t(pos)] < 0) { ok = fail("shared-memory position read but never written", pos, tid); return; }
-          if (used[size_t(pos)]) { ok = fail("shared-memory position read twice", pos, tid); return; }
-          used[size_t(pos)] = 1;
-          ok = pair(posA[size_t(pos)], c.baseB + off);
-        });
+      for (int t = 0; t < kThreads && ok && !k.ring; ++t) {
+        if (k.ju == 0) walk_read<K>(c, tp, ta.data(), t % tp.U, t / tp.U, on_read);
+        else if (k.ju == 1) walk2_read<1, K>(c, tp, ta.data(), t & 31, t >> 5, on_read);
+        else if (k.ju == 2) walk2_read<2, K>(c, tp, ta.data(), t & 31, t >> 5, on_read);
+        else if (k.ju == 4) walk2_read<4, K>(c, tp, ta.data(), t & 31, t >> 5, on_read);
+        else ok = fail("unknown lane layout", k.ju, 0);
+      }
+      for (int t = 0; t < kThreads && ok && !k.ring; ++t) {
+        if (k.jw == 0) {
+          walk_write<K>(c, tp, tb.data(), t % tp.LC, (t / tp.LC) % tp.LB, t / tp.W, on_write);
+        } else if (k.jw == 1) {
+          int sp[1]; int32_t vo[1]; walk2_lane_consts<1>(tp, t & 31, sp, vo);
+          walk2_write<1, K>(c, tp, tb.data(), t & 31, t >> 5, sp, vo, on_write);
+        } else if (k.jw == 2) {
+          int sp[2]; int32_t vo[2]; walk2_lane_consts<2>(tp, t & 31, sp, vo);
+          walk2_write<2, K>(c, tp, tb.data(), t & 31, t >> 5, sp, vo, on_write);
+        } else if (k.jw == 4) {
+          int sp[4]; int32_t vo[4]; walk2_lane_consts<4>(tp, t & 31, sp, vo);
+          walk2_write<4, K>(c, tp, tb.data(), t & 31, t >> 5, sp, vo, on_write);
+        } else {
+          ok = fail("unknown lane layout", k.jw, 0);
+        }
       }
       for (int q = 0; q < ncap && ok; ++q)
         if (posA[size_t(q)] >= 0 && !used[size_t(q)]) ok = fail("staged element never written out", q, tid);

@@ -34,8 +34,11 @@ namespace ttc {
 
 constexpr int kMaxDim = 16;
 constexpr int kThreads = 256;          // threads per CTA of every kernel
-constexpr int kTileK = 16;             // elements per thread per phase (tile kernel)
+constexpr int kTileK = 16;             // elements per thread per phase (tile kernels, 4-byte stage)
 constexpr int kTileVmax = kThreads * kTileK;
+// elements per thread per phase for a stage type of `stage_bytes` bytes:
+// 64 bytes of staged data per thread per phase
+constexpr int tile_k_for(int stage_bytes) { return stage_bytes == 8 ? 8 : 16; }
 
 enum DType : int { DT_F32 = 0, DT_F64 = 1, DT_BF16 = 2, DT_E4M3 = 3 };
 

@@ -219,3 +219,26 @@ FULL = [c for c in inputs.sweep_cases() if c.beta == 0.4 and
 @pytest.mark.parametrize("case", FULL, ids=lambda c: f"{c.tag}-{c.dtype_in}")
 def test_full_size_sweep_case(case):
     H.full_check(case, seed=1)
+
+
+def test_many_schedules_in_one_process():
+    """All candidate schedules of many shapes, back to back in one process (the
+    launcher's per-kernel shared-memory limits must follow every size seen)."""
+    g = inputs.rng(77)
+    for trial in range(24):
+        N = int(g.integers(2, 6))
+        perm = inputs.random_perm(N, g)
+        sizes = inputs.near_equal_sizes(N, int(2 ** g.uniform(12, 16)), g, tol=0.3)
+        dt = ("f32", "f64")[trial % 2]
+        p = Problem(perm=perm, sizes=sizes, dtype_in=dt, dtype_out=dt, alpha=1.5, beta=0.25 * (trial % 3))
+        plan = ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta)
+        A, B0 = H.make_inputs(p, trial)
+        want, _ = H.oracle_mirror(p, A, B0)
+        order = list(range(plan.info()["ncandidates"]))
+        if trial % 2:
+            order.reverse()
+        for i in order:
+            plan.select(i)
+            got, _ = H.run_gpu(p, A, B0, plan=plan)
+            ok, msg = H.compare_bits(got, want, dt, True)
+            assert ok, (perm, sizes, i, msg)
