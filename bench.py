@@ -220,6 +220,9 @@ def run_ours(args, rank, world):
 
     # per-launch durations (CUDA events on the launching stream), one extra pass
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in probs]
+    # keep the device busy while the host enqueues the first launches, so that
+    # no event interval includes host time
+    torch.cuda._sleep(20_000_000)
     step(ev)
     torch.cuda.synchronize()
     per_case_ms = [a.elapsed_time(b) for a, b in ev]
@@ -265,6 +268,13 @@ def run_ours(args, rank, world):
     tr = ncu_traffic(kname, args.workload)
     case_gbs = [p.algorithmic_bytes() / (ms * 1e-3) / 1e9 for p, ms in zip(probs, per_case_ms)]
     big = [g for p, g in zip(probs, case_gbs) if p.n * inputs.DTYPE_BYTES[p.dtype_in] >= (256 << 20)]
+
+    if args.cases_out:
+        with open(args.cases_out, "w") as f:
+            json.dump([{"case": f"{p.tag}/{p.dtype_in}/b{p.beta}", "sizes": p.sizes, "perm": p.perm,
+                        "canon": pl.info()["sizes"], "cperm": pl.info()["perm"], "kernel": pl.info()["kernel"],
+                        "tile": pl.info()["tile"], "GBs": round(g, 1)}
+                       for p, pl, g in zip(probs, plans, case_gbs)], f, indent=0)
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
@@ -463,6 +473,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--target", type=int, default=1 << 26, help="elements per tensor of the sweep")
     ap.add_argument("--only", default="", help="comma-separated case tags of the sweep (e.g. N5p3)")
+    ap.add_argument("--cases-out", default="", help="write per-case timings (JSON) to this file")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

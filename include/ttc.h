@@ -141,7 +141,12 @@ ttc_status ttc_plan_set_fp8_scale(ttc_plan_t plan, const float* d_scale);
 ttc_status ttc_plan_get_fp8_scale(ttc_plan_t plan, float* d_scale_out, ttc_stream_t stream);
 
 /* What the planner made of the problem (for tests and tooling). */
-typedef enum { TTC_VARIANT_EMPTY = 0, TTC_VARIANT_COPY = 1, TTC_VARIANT_TILE = 2 } ttc_variant;
+typedef enum {
+    TTC_VARIANT_EMPTY = 0,    /* nothing to do */
+    TTC_VARIANT_COPY = 1,     /* perm keeps index 0: long runs streamed directly */
+    TTC_VARIANT_TILE = 2,     /* tile staged in shared memory between A's and B's runs */
+    TTC_VARIANT_ROWCOPY = 3   /* perm keeps index 0 with short runs: multi-row blocks, no staging */
+} ttc_variant;
 
 typedef struct {
     int ndim;                      /* canonical number of indices after dropping/merging */
@@ -158,8 +163,7 @@ typedef struct {
     int candidate;                 /* index of the schedule in the plan's candidate list */
     int ncandidates;               /* number of candidate schedules the planner kept */
     int lanes_a, lanes_b;          /* tile variant: lanes along the A run / B run of the warp-mapped
-                                      kernels (32, 64, 128), or 0 for the generic tile kernel */
-    int async_ring;                /* 1: A is read with asynchronous copies into a ring of tiles */
+                                      kernel (32, 64, 128), or 0 for the generic tile kernel */
 } ttc_plan_info;
 
 ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info);

@@ -145,7 +145,7 @@ Epilogue make_epilogue(const ttc_plan_s* p, const DevRes* r) {
 }
 
 // Launch the selected candidate (and the FP8 amax pre-pass when needed).
-ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s, int grid_override) {
+ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s) {
   if (p->canon.n == 0) return TTC_OK;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -164,9 +164,9 @@ ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s, int g
   if (k.variant == VAR_TILE) {
     TileParams tp = r->tp;
     tp.epi = epi;
-    e = k.ring ? launch_tile3(p->din, p->dout, k.ju, k.jw, A, B, tp, r->smem, s, grid_override)
-        : k.ju ? launch_tile2(p->din, p->dout, k.ju, k.jw, A, B, tp, r->smem, s, grid_override)
-             : launch_tile(p->din, p->dout, A, B, tp, r->smem, s, grid_override);
+    e = k.rows ? launch_rowcopy(p->din, p->dout, A, B, tp, s)
+        : k.ju ? launch_tile2(p->din, p->dout, k.ju, k.jw, A, B, tp, r->smem, s)
+             : launch_tile(p->din, p->dout, A, B, tp, r->smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "tile kernel launch");
   } else if (k.variant == VAR_COPY) {
     RowParams rp = r->rp;
@@ -273,7 +273,7 @@ ttc_status ttc_execute(ttc_plan_t plan, const void* A, void* B, ttc_stream_t str
   const uintptr_t ea = a + uintptr_t(plan->canon.spanA) * dtype_size(plan->din);
   const uintptr_t eb = b + uintptr_t(plan->canon.spanB) * dtype_size(plan->dout);
   if (a < eb && b < ea) return fail(TTC_ERR_ALIAS, "the byte ranges of A and B overlap");
-  return run_plan(plan, A, B, reinterpret_cast<cudaStream_t>(stream), 0);
+  return run_plan(plan, A, B, reinterpret_cast<cudaStream_t>(stream));
 }
 
 ttc_status ttc_plan_set_fp8_scale(ttc_plan_t plan, const float* d_scale) {
@@ -312,7 +312,7 @@ ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info) {
   const int sa = dtype_size(plan->din), sb = dtype_size(plan->dout);
   info->algorithmic_bytes = c.n * (sa + (plan->beta != 0.0 ? 2 * sb : sb));
   const Candidate& k = plan->cands[plan->sel];
-  info->variant = k.variant;
+  info->variant = k.rows ? TTC_VARIANT_ROWCOPY : k.variant;
   info->candidate = plan->sel;
   info->ncandidates = int(plan->cands.size());
   if (k.variant == VAR_TILE) {
@@ -327,7 +327,6 @@ ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info) {
     info->vec_in = info->vec_out = 1;
     info->lanes_a = 32 * k.ju;
     info->lanes_b = 32 * k.jw;
-    info->async_ring = k.ring;
   } else if (k.variant == VAR_COPY) {
     RowParams rp;
     build_row_params(c, k.chunk, &rp);
@@ -380,10 +379,10 @@ ttc_status ttc_plan_autotune(ttc_plan_t plan, int max_candidates, ttc_stream_t s
   const int reps = int(std::min(50.0, std::max(3.0, 2e-3 * 5e12 / std::max(bytes, 1.0))));
   for (int i = 0; i < nc && st == TTC_OK; ++i) {
     plan->sel = i;
-    st = run_plan(plan, dA, dB, s, 0);   // warm-up (uploads tables)
+    st = run_plan(plan, dA, dB, s);   // warm-up (uploads tables)
     if (st != TTC_OK) break;
     cudaEventRecord(e0, s);
-    for (int r = 0; r < reps && st == TTC_OK; ++r) st = run_plan(plan, dA, dB, s, 0);
+    for (int r = 0; r < reps && st == TTC_OK; ++r) st = run_plan(plan, dA, dB, s);
     cudaEventRecord(e1, s);
     e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) {

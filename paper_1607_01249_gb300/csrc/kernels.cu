@@ -69,47 +69,42 @@ cudaError_t grid_for(const void* fn, int smem, int64_t work, int* grid) {
 }
 
 
-cudaError_t launch_tile_f32_f32(const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile2_f32_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile3_f32_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
+cudaError_t launch_tile_f32_f32(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile2_f32_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_f32_f32(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_tile_f32_f64(const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile2_f32_f64(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile3_f32_f64(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
+cudaError_t launch_rowcopy_f32_f32(const void*, void*, const TileParams&, cudaStream_t);
+cudaError_t launch_tile_f32_f64(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile2_f32_f64(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_f32_f64(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_tile_f32_bf16(const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile2_f32_bf16(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile3_f32_bf16(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
+cudaError_t launch_rowcopy_f32_f64(const void*, void*, const TileParams&, cudaStream_t);
+cudaError_t launch_tile_f32_bf16(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile2_f32_bf16(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_f32_bf16(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_tile_f32_e4m3(const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile2_f32_e4m3(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile3_f32_e4m3(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
+cudaError_t launch_rowcopy_f32_bf16(const void*, void*, const TileParams&, cudaStream_t);
+cudaError_t launch_tile_f32_e4m3(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile2_f32_e4m3(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_f32_e4m3(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_tile_f64_f64(const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile2_f64_f64(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile3_f64_f64(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
+cudaError_t launch_rowcopy_f32_e4m3(const void*, void*, const TileParams&, cudaStream_t);
+cudaError_t launch_tile_f64_f64(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile2_f64_f64(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_f64_f64(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_tile_f64_f32(const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile2_f64_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile3_f64_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
+cudaError_t launch_rowcopy_f64_f64(const void*, void*, const TileParams&, cudaStream_t);
+cudaError_t launch_tile_f64_f32(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile2_f64_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_f64_f32(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_tile_bf16_bf16(const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile2_bf16_bf16(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile3_bf16_bf16(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
+cudaError_t launch_rowcopy_f64_f32(const void*, void*, const TileParams&, cudaStream_t);
+cudaError_t launch_tile_bf16_bf16(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile2_bf16_bf16(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_bf16_bf16(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_tile_bf16_f32(const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile2_bf16_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile3_bf16_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
+cudaError_t launch_rowcopy_bf16_bf16(const void*, void*, const TileParams&, cudaStream_t);
+cudaError_t launch_tile_bf16_f32(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile2_bf16_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_bf16_f32(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_tile_bf16_e4m3(const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile2_bf16_e4m3(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
-cudaError_t launch_tile3_bf16_e4m3(int, int, const void*, void*, const TileParams&, int, cudaStream_t, int);
+cudaError_t launch_rowcopy_bf16_f32(const void*, void*, const TileParams&, cudaStream_t);
+cudaError_t launch_tile_bf16_e4m3(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile2_bf16_e4m3(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_bf16_e4m3(int, const void*, void*, const RowParams&, cudaStream_t);
-
-// lane layouts the asynchronous-copy kernel is built for
-bool tile3_layout_supported(int ju, int jw) {
-  return (ju == 1 && (jw == 2 || jw == 4)) || (ju == 2 && (jw == 1 || jw == 2)) || (ju == 4 && (jw == 1 || jw == 2));
-}
+cudaError_t launch_rowcopy_bf16_e4m3(const void*, void*, const TileParams&, cudaStream_t);
 
 bool pair_supported(int din, int dout) {
   if (din == DT_F32 && dout == DT_F32) return true;
@@ -132,44 +127,30 @@ int copy_vec_width(int din, int dout) {
 }
 
 cudaError_t launch_tile(int din, int dout, const void* A, void* B, const TileParams& p, int smem,
-                        cudaStream_t s, int grid_override) {
-  if (din == DT_F32 && dout == DT_F32) return launch_tile_f32_f32(A, B, p, smem, s, grid_override);
-  if (din == DT_F32 && dout == DT_F64) return launch_tile_f32_f64(A, B, p, smem, s, grid_override);
-  if (din == DT_F32 && dout == DT_BF16) return launch_tile_f32_bf16(A, B, p, smem, s, grid_override);
-  if (din == DT_F32 && dout == DT_E4M3) return launch_tile_f32_e4m3(A, B, p, smem, s, grid_override);
-  if (din == DT_F64 && dout == DT_F64) return launch_tile_f64_f64(A, B, p, smem, s, grid_override);
-  if (din == DT_F64 && dout == DT_F32) return launch_tile_f64_f32(A, B, p, smem, s, grid_override);
-  if (din == DT_BF16 && dout == DT_BF16) return launch_tile_bf16_bf16(A, B, p, smem, s, grid_override);
-  if (din == DT_BF16 && dout == DT_F32) return launch_tile_bf16_f32(A, B, p, smem, s, grid_override);
-  if (din == DT_BF16 && dout == DT_E4M3) return launch_tile_bf16_e4m3(A, B, p, smem, s, grid_override);
+                        cudaStream_t s) {
+  if (din == DT_F32 && dout == DT_F32) return launch_tile_f32_f32(A, B, p, smem, s);
+  if (din == DT_F32 && dout == DT_F64) return launch_tile_f32_f64(A, B, p, smem, s);
+  if (din == DT_F32 && dout == DT_BF16) return launch_tile_f32_bf16(A, B, p, smem, s);
+  if (din == DT_F32 && dout == DT_E4M3) return launch_tile_f32_e4m3(A, B, p, smem, s);
+  if (din == DT_F64 && dout == DT_F64) return launch_tile_f64_f64(A, B, p, smem, s);
+  if (din == DT_F64 && dout == DT_F32) return launch_tile_f64_f32(A, B, p, smem, s);
+  if (din == DT_BF16 && dout == DT_BF16) return launch_tile_bf16_bf16(A, B, p, smem, s);
+  if (din == DT_BF16 && dout == DT_F32) return launch_tile_bf16_f32(A, B, p, smem, s);
+  if (din == DT_BF16 && dout == DT_E4M3) return launch_tile_bf16_e4m3(A, B, p, smem, s);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tile2(int din, int dout, int ju, int jw, const void* A, void* B, const TileParams& p,
-                         int smem, cudaStream_t s, int grid_override) {
-  if (din == DT_F32 && dout == DT_F32) return launch_tile2_f32_f32(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_F32 && dout == DT_F64) return launch_tile2_f32_f64(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_F32 && dout == DT_BF16) return launch_tile2_f32_bf16(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_F32 && dout == DT_E4M3) return launch_tile2_f32_e4m3(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_F64 && dout == DT_F64) return launch_tile2_f64_f64(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_F64 && dout == DT_F32) return launch_tile2_f64_f32(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_BF16 && dout == DT_BF16) return launch_tile2_bf16_bf16(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_BF16 && dout == DT_F32) return launch_tile2_bf16_f32(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_BF16 && dout == DT_E4M3) return launch_tile2_bf16_e4m3(ju, jw, A, B, p, smem, s, grid_override);
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_tile3(int din, int dout, int ju, int jw, const void* A, void* B, const TileParams& p,
-                         int smem, cudaStream_t s, int grid_override) {
-  if (din == DT_F32 && dout == DT_F32) return launch_tile3_f32_f32(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_F32 && dout == DT_F64) return launch_tile3_f32_f64(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_F32 && dout == DT_BF16) return launch_tile3_f32_bf16(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_F32 && dout == DT_E4M3) return launch_tile3_f32_e4m3(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_F64 && dout == DT_F64) return launch_tile3_f64_f64(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_F64 && dout == DT_F32) return launch_tile3_f64_f32(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_BF16 && dout == DT_BF16) return launch_tile3_bf16_bf16(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_BF16 && dout == DT_F32) return launch_tile3_bf16_f32(ju, jw, A, B, p, smem, s, grid_override);
-  if (din == DT_BF16 && dout == DT_E4M3) return launch_tile3_bf16_e4m3(ju, jw, A, B, p, smem, s, grid_override);
+                         int smem, cudaStream_t s) {
+  if (din == DT_F32 && dout == DT_F32) return launch_tile2_f32_f32(ju, jw, A, B, p, smem, s);
+  if (din == DT_F32 && dout == DT_F64) return launch_tile2_f32_f64(ju, jw, A, B, p, smem, s);
+  if (din == DT_F32 && dout == DT_BF16) return launch_tile2_f32_bf16(ju, jw, A, B, p, smem, s);
+  if (din == DT_F32 && dout == DT_E4M3) return launch_tile2_f32_e4m3(ju, jw, A, B, p, smem, s);
+  if (din == DT_F64 && dout == DT_F64) return launch_tile2_f64_f64(ju, jw, A, B, p, smem, s);
+  if (din == DT_F64 && dout == DT_F32) return launch_tile2_f64_f32(ju, jw, A, B, p, smem, s);
+  if (din == DT_BF16 && dout == DT_BF16) return launch_tile2_bf16_bf16(ju, jw, A, B, p, smem, s);
+  if (din == DT_BF16 && dout == DT_F32) return launch_tile2_bf16_f32(ju, jw, A, B, p, smem, s);
+  if (din == DT_BF16 && dout == DT_E4M3) return launch_tile2_bf16_e4m3(ju, jw, A, B, p, smem, s);
   return cudaErrorInvalidValue;
 }
 
@@ -184,6 +165,19 @@ cudaError_t launch_copy(int din, int dout, int vec, const void* A, void* B, cons
   if (din == DT_BF16 && dout == DT_BF16) return launch_copy_bf16_bf16(vec, A, B, p, s);
   if (din == DT_BF16 && dout == DT_F32) return launch_copy_bf16_f32(vec, A, B, p, s);
   if (din == DT_BF16 && dout == DT_E4M3) return launch_copy_bf16_e4m3(vec, A, B, p, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rowcopy(int din, int dout, const void* A, void* B, const TileParams& p, cudaStream_t s) {
+  if (din == DT_F32 && dout == DT_F32) return launch_rowcopy_f32_f32(A, B, p, s);
+  if (din == DT_F32 && dout == DT_F64) return launch_rowcopy_f32_f64(A, B, p, s);
+  if (din == DT_F32 && dout == DT_BF16) return launch_rowcopy_f32_bf16(A, B, p, s);
+  if (din == DT_F32 && dout == DT_E4M3) return launch_rowcopy_f32_e4m3(A, B, p, s);
+  if (din == DT_F64 && dout == DT_F64) return launch_rowcopy_f64_f64(A, B, p, s);
+  if (din == DT_F64 && dout == DT_F32) return launch_rowcopy_f64_f32(A, B, p, s);
+  if (din == DT_BF16 && dout == DT_BF16) return launch_rowcopy_bf16_bf16(A, B, p, s);
+  if (din == DT_BF16 && dout == DT_F32) return launch_rowcopy_bf16_f32(A, B, p, s);
+  if (din == DT_BF16 && dout == DT_E4M3) return launch_rowcopy_bf16_e4m3(A, B, p, s);
   return cudaErrorInvalidValue;
 }
 

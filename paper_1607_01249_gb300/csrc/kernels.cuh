@@ -147,66 +147,89 @@ TTC_HD TileCoord tile_coord(uint32_t tid, const TileParams& p) {
   return c;
 }
 
-// Read order: (u, lb) with u = la*LC + lc.  f(k, A offset in tile, smem position)
-template <int K = kTileK, class F>
-TTC_HD void walk_read(const TileCoord& c, const TileParams& p, const int32_t* tabA, int u0, int lb0, F&& f,
-                      bool need_offset = true) {
+// The flat walks' first positions for thread t: read order (u, lb) and write
+// order (lc, lb, la), by multiply-high divisions.
+TTC_HD void flat_starts(const TileParams& p, int t, int& u0, int& lb0, int& lc0, int& lbw0, int& la0) {
+  const uint32_t qu = fast_div(uint32_t(t), p.divU);
+  u0 = t - int(qu) * p.U;
+  lb0 = int(qu);
+  const uint32_t qc = fast_div(uint32_t(t), p.divLC);
+  lc0 = t - int(qc) * p.LC;
+  const uint32_t qb = fast_div(qc, p.divLB);
+  lbw0 = int(qc - qb * uint32_t(p.LB));
+  la0 = int(qb);
+}
+
+// Flat walks (tile_kernel).  Thread t handles tile elements t + k*kThreads,
+// k < K.  f(k, ok, offset in tile, smem position) is called for every k; ok
+// tells whether the element exists (a short last block leaves holes), and the
+// offset is 0 when it does not, so a caller may load unconditionally.  The
+// bodies are branch-free (selects instead of ifs): measured ~2x fewer issued
+// instructions than the branchy form.  TAB: the cross offsets come from a
+// table instead of one multiply.
+//
+// Read order: (u, lb) with u = la*LC + lc; offset in A.
+template <int K, bool TAB, class F>
+TTC_HD void walk_read(const TileCoord& c, const TileParams& p, const int32_t* tabA, int u0, int lb0, F&& f) {
   const int limU = c.remA * p.LC;
   int u = u0, lb = lb0;
-#if defined(__CUDA_ARCH__)
-  // opaque: keeps the compiler from precomputing all kTileK index pairs once
-  // per thread and holding them in registers across tiles
-  asm volatile("" : "+r"(u), "+r"(lb));
-#endif
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    if (lb < c.remB && u < limU) {
-      int32_t off = 0;
-      if (need_offset) off = u * p.saU + (p.crossA_tab ? tabA[lb] : lb * p.crossA_lin);
-      f(k, off, lb * p.P + u);
-    }
+    const bool ok = (lb < c.remB) & (u < limU);
+    const int32_t cross = TAB ? (ok ? tabA[lb] : 0) : lb * p.crossA_lin;
+    f(k, ok, ok ? u * p.saU + cross : 0, lb * p.P + u);
     u += p.rd_du;
     lb += p.rd_dlb;
-    if (u >= p.U) { u -= p.U; ++lb; }
+    const bool w = u >= p.U;
+    u -= w ? p.U : 0;
+    lb += w;
   }
 }
 
-// Write order: (lc, lb, la).  f(k, B offset in tile, smem position)
-template <int K = kTileK, class F>
+// Write order: (lc, lb, la); offset in B.
+template <int K, bool TAB, class F>
 TTC_HD void walk_write(const TileCoord& c, const TileParams& p, const int32_t* tabB, int lc0, int lb0, int la0,
                        F&& f) {
   int lc = lc0, lb = lb0, la = la0;
-#if defined(__CUDA_ARCH__)
-  asm volatile("" : "+r"(lc), "+r"(lb), "+r"(la));
-#endif
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    if (la < c.remA && lb < c.remB) {
-      const int32_t off = (lb * p.LC + lc) * p.sbV + (p.crossB_tab ? tabB[la] : la * p.crossB_lin);
-      f(k, off, lb * p.P + la * p.LC + lc);
-    }
-    lc += p.wr_dlc; lb += p.wr_dlb; la += p.wr_dla;
-    if (lc >= p.LC) { lc -= p.LC; ++lb; }
-    if (lb >= p.LB) { lb -= p.LB; ++la; }
+    const bool ok = (la < c.remA) & (lb < c.remB);
+    const int32_t cross = TAB ? (ok ? tabB[la] : 0) : la * p.crossB_lin;
+    f(k, ok, ok ? (lb * p.LC + lc) * p.sbV + cross : 0, lb * p.P + la * p.LC + lc);
+    lc += p.wr_dlc;
+    lb += p.wr_dlb;
+    la += p.wr_dla;
+    const bool w1 = lc >= p.LC;
+    lc -= w1 ? p.LC : 0;
+    lb += w1;
+    const bool w2 = lb >= p.LB;
+    lb -= w2 ? p.LB : 0;
+    la += w2;
   }
 }
 
 // Warp-mapped walks (tile2_kernel).  Read: lanes along u (JU chunks of 32),
 // warps along lb.  Write: lanes along v (JW chunks), warps along la.
-template <int JU, int K = kTileK, class F>
+// FULL: an interior tile (no cut index is short).  f(k, ok, offset, smem
+// position) as for the flat walks; rows past the tile's end are skipped
+// (warp-uniform), lanes past a run's end get ok == false.
+template <int JU, int K, bool FULL, bool TAB, class F>
 TTC_HD void walk2_read(const TileCoord& c, const TileParams& p, const int32_t* tabA, int lane, int warp,
                        F&& f) {
   constexpr int RR = K / JU;
-  const int limU = c.remA * p.LC;
+  const int limU = FULL ? p.U : c.remA * p.LC;
+  const int remB = FULL ? p.LB : c.remB;
 #pragma unroll
   for (int i = 0; i < RR; ++i) {
     const int r = warp + 8 * i;
-    if (r < c.remB) {
-      const int32_t row = p.crossA_tab ? tabA[r] : r * p.crossA_lin;
+    if (r < remB) {
+      const int32_t row = TAB ? tabA[r] : r * p.crossA_lin;
+      const int pos = r * p.P;
 #pragma unroll
       for (int j = 0; j < JU; ++j) {
         const int u = lane + 32 * j;
-        if (u < limU) f(i * JU + j, row + u * p.saU, r * p.P + u);
+        const bool ok = u < limU;
+        f(i * JU + j, ok, ok ? row + u * p.saU : 0, pos + u);
       }
     }
   }
@@ -219,63 +242,52 @@ TTC_HD void walk2_lane_consts(const TileParams& p, int lane, int (&spre)[JW], in
 #pragma unroll
   for (int j = 0; j < JW; ++j) {
     const int vv = lane + 32 * j;
-    spre[j] = (vv / p.LC) * p.P + vv % p.LC;
+    const int q = int(fast_div(uint32_t(vv), p.divLC));
+    spre[j] = q * p.P + (vv - q * p.LC);
     voff[j] = vv * p.sbV;
   }
 }
 
-template <int JW, int K = kTileK, class F>
+template <int JW, int K, bool FULL, bool TAB, class F>
 TTC_HD void walk2_write(const TileCoord& c, const TileParams& p, const int32_t* tabB, int lane, int warp,
                         const int (&spre)[JW], const int32_t (&voff)[JW], F&& f) {
   constexpr int RW = K / JW;
-  const int limV = c.remB * p.LC;
+  const int limV = FULL ? p.W : c.remB * p.LC;
+  const int remA = FULL ? p.LA : c.remA;
 #pragma unroll
   for (int i = 0; i < RW; ++i) {
     const int la = warp + 8 * i;
-    if (la < c.remA) {
-      const int32_t row = p.crossB_tab ? tabB[la] : la * p.crossB_lin;
-#pragma unroll
-      for (int j = 0; j < JW; ++j)
-        if (lane + 32 * j < limV) f(i * JW + j, row + voff[j], spre[j] + la * p.LC);
-    }
-  }
-}
-
-// Unit-stride warp-mapped walks (tile3_kernel: both runs have stride 1).
-// FULL: the tile is interior (no cut index is short), so no per-element test.
-template <int JU, int K, bool FULL, class F>
-TTC_HD void walk3_read(const TileCoord& c, const TileParams& p, const int32_t* tabA, int lane, int warp,
-                       F&& f) {
-  constexpr int RR = K / JU;
-  const int limU = c.remA * p.LC;
-#pragma unroll
-  for (int i = 0; i < RR; ++i) {
-    const int r = warp + 8 * i;
-    if (FULL ? (r < p.LB) : (r < c.remB)) {
-      const int32_t row = (p.crossA_tab ? tabA[r] : r * p.crossA_lin) + lane;
-      const int pos = r * p.P + lane;
-#pragma unroll
-      for (int j = 0; j < JU; ++j)
-        if (FULL ? (32 * j < p.U - lane) : (32 * j < limU - lane)) f(i * JU + j, row + 32 * j, pos + 32 * j);
-    }
-  }
-}
-
-template <int JW, int K, bool FULL, class F>
-TTC_HD void walk3_write(const TileCoord& c, const TileParams& p, const int32_t* tabB, int lane, int warp,
-                        const int (&spre)[JW], F&& f) {
-  constexpr int RW = K / JW;
-  const int limV = c.remB * p.LC;
-#pragma unroll
-  for (int i = 0; i < RW; ++i) {
-    const int la = warp + 8 * i;
-    if (FULL ? (la < p.LA) : (la < c.remA)) {
-      const int32_t row = (p.crossB_tab ? tabB[la] : la * p.crossB_lin) + lane;
+    if (la < remA) {
+      const int32_t row = TAB ? tabB[la] : la * p.crossB_lin;
       const int spos = la * p.LC;
 #pragma unroll
-      for (int j = 0; j < JW; ++j)
-        if (FULL ? (32 * j < p.W - lane) : (32 * j < limV - lane)) f(i * JW + j, row + 32 * j, spre[j] + spos);
+      for (int j = 0; j < JW; ++j) {
+        const bool ok = lane + 32 * j < limV;
+        f(i * JW + j, ok, ok ? row + voff[j] : 0, spre[j] + spos);
+      }
     }
+  }
+}
+
+// Multi-row copy (perm keeps index 0, short runs): a tile is LC x LA elements,
+// LC = the shared stride-1 index, LA consecutive indices of the next A index,
+// contiguous in A; thread t takes the flat positions u = t + kThreads*k.
+// f(k, A offset in tile, B offset in tile).
+template <int K, class F>
+TTC_HD void walk_rows(const TileCoord& c, const TileParams& p, int t, F&& f) {
+  const int limU = c.remA * p.LC;
+  const int q = int(fast_div(uint32_t(t), p.divLC));
+  int u = t, la = q, lc = t - q * p.LC;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const bool ok = u < limU;
+    f(k, ok, ok ? u : 0, ok ? lc + la * p.crossB_lin : 0);
+    u += kThreads;
+    lc += p.wr_dlc;
+    la += p.wr_dla;
+    const bool w = lc >= p.LC;
+    lc -= w ? p.LC : 0;
+    la += w;
   }
 }
 

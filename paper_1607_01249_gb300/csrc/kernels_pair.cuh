@@ -8,25 +8,24 @@
 
 namespace ttc {
 
-cudaError_t TTC_CAT(launch_tile_, TTC_PAIR)(const void* A, void* B, const TileParams& p, int smem, cudaStream_t s,
-                                            int grid_override) {
-  return launch_tile_t<TTC_DIN, TTC_DOUT>(A, B, p, smem, s, grid_override);
+cudaError_t TTC_CAT(launch_tile_, TTC_PAIR)(const void* A, void* B, const TileParams& p, int smem, cudaStream_t s) {
+  return with_ek<TTC_DIN, TTC_DOUT, TileL<TTC_DIN, TTC_DOUT>::template L>(p.epi.mode, p.epi.beta_nz, A, B, p, smem, s);
 }
 
 cudaError_t TTC_CAT(launch_tile2_, TTC_PAIR)(int ju, int jw, const void* A, void* B, const TileParams& p, int smem,
-                                             cudaStream_t s, int grid_override) {
-  return launch_tile2_pair<TTC_DIN, TTC_DOUT>(ju, jw, A, B, p, smem, s, grid_override);
+                                             cudaStream_t s) {
+  return launch_tile2_pair<TTC_DIN, TTC_DOUT>(ju, jw, A, B, p, smem, s);
 }
 
-cudaError_t TTC_CAT(launch_tile3_, TTC_PAIR)(int ju, int jw, const void* A, void* B, const TileParams& p, int smem,
-                                             cudaStream_t s, int grid_override) {
-  return launch_tile3_pair<TTC_DIN, TTC_DOUT>(ju, jw, p.epi.mode, p.epi.beta_nz, A, B, p, smem, s, grid_override);
+cudaError_t TTC_CAT(launch_rowcopy_, TTC_PAIR)(const void* A, void* B, const TileParams& p, cudaStream_t s) {
+  return with_ek<TTC_DIN, TTC_DOUT, RowcopyL<TTC_DIN, TTC_DOUT>::template L>(p.epi.mode, p.epi.beta_nz, A, B, p, s);
 }
 
 cudaError_t TTC_CAT(launch_copy_, TTC_PAIR)(int vec, const void* A, void* B, const RowParams& p, cudaStream_t s) {
   constexpr int W = (dtype_size(TTC_DIN) > dtype_size(TTC_DOUT) ? 16 / dtype_size(TTC_DIN) : 16 / dtype_size(TTC_DOUT));
-  if (vec == W) return launch_copy_t<TTC_DIN, TTC_DOUT, W>(A, B, p, s);
-  return launch_copy_t<TTC_DIN, TTC_DOUT, 1>(A, B, p, s);
+  if (vec == W)
+    return with_ek<TTC_DIN, TTC_DOUT, CopyL<TTC_DIN, TTC_DOUT, W>::template L>(p.epi.mode, p.epi.beta_nz, A, B, p, s);
+  return with_ek<TTC_DIN, TTC_DOUT, CopyL<TTC_DIN, TTC_DOUT, 1>::template L>(p.epi.mode, p.epi.beta_nz, A, B, p, s);
 }
 
 }  // namespace ttc

@@ -10,12 +10,10 @@ namespace ttc {
 bool pair_supported(int din, int dout);
 int copy_vec_width(int din, int dout);
 cudaError_t launch_tile(int din, int dout, const void* A, void* B, const TileParams& p, int smem,
-                        cudaStream_t s, int grid_override);
+                        cudaStream_t s);
 cudaError_t launch_tile2(int din, int dout, int ju, int jw, const void* A, void* B, const TileParams& p,
-                         int smem, cudaStream_t s, int grid_override);
-bool tile3_layout_supported(int ju, int jw);
-cudaError_t launch_tile3(int din, int dout, int ju, int jw, const void* A, void* B, const TileParams& p,
-                         int smem, cudaStream_t s, int grid_override);
+                         int smem, cudaStream_t s);
+cudaError_t launch_rowcopy(int din, int dout, const void* A, void* B, const TileParams& p, cudaStream_t s);
 cudaError_t launch_copy(int din, int dout, int vec, const void* A, void* B, const RowParams& p,
                         cudaStream_t s);
 cudaError_t launch_amax(int din, const void* A, const RowParams& p, float alpha_f, uint32_t* amax_bits,

@@ -108,9 +108,9 @@ extern "C" ttc_status ttc_execute_noalloc(ttc_plan_t plan, const void* A, void* 
     tp.tabA = tables;
     tp.tabB = tables + ta.size();
     tp.epi = epi;
-    e = k.ring ? launch_tile3(plan->din, plan->dout, k.ju, k.jw, A, B, tp, smem, s, 0)
-        : k.ju ? launch_tile2(plan->din, plan->dout, k.ju, k.jw, A, B, tp, smem, s, 0)
-             : launch_tile(plan->din, plan->dout, A, B, tp, smem, s, 0);
+    e = k.rows ? launch_rowcopy(plan->din, plan->dout, A, B, tp, s)
+        : k.ju ? launch_tile2(plan->din, plan->dout, k.ju, k.jw, A, B, tp, smem, s)
+             : launch_tile(plan->din, plan->dout, A, B, tp, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "tile kernel launch");
   } else if (k.variant == VAR_COPY) {
     rp.epi = epi;

@@ -50,7 +50,7 @@ struct ttc_plan_s {
 namespace ttc {
 ttc_status fail(ttc_status s, const std::string& msg);
 ttc_status cuda_fail(cudaError_t e, const char* where);
-ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s, int grid_override);
+ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s);
 ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out);
 Epilogue make_epilogue(const ttc_plan_s* p, const DevRes* r);
 std::string plan_key(const ttc_plan_s* p, int dev);

@@ -42,12 +42,13 @@ constexpr double kLaneInstrPerS = 152.0 * 4 * 32 * 1.9e9;
 
 }  // namespace
 
-double sector_efficiency(double bytes, int elem) {
+double run_efficiency(double bytes, bool write) {
+  // Measured on GB300 (2D transposes of misaligned sizes): a run costs as if
+  // it were `bytes + c` long, with c ~ 16 bytes for reads and ~64 bytes for
+  // writes -- the partial 32-byte sectors at both ends of a write run are
+  // expensive, so B's runs must be long while A's may be short.
   if (bytes <= 0) return 1.0;
-  // a run of `bytes` starting at a random multiple of `elem` inside a sector
-  // touches on average (bytes + 32 - elem) / 32 sectors
-  const double sectors = std::max(1.0, (bytes + 32.0 - elem) / 32.0);
-  return std::min(1.0, bytes / (32.0 * sectors));
+  return bytes / (bytes + (write ? 64.0 : 16.0));
 }
 
 std::string Candidate::describe() const {
@@ -60,7 +61,7 @@ std::string Candidate::describe() const {
     for (size_t i = 0; i < ga.size(); ++i) o << (i ? "," : "") << ga[i];
     o << "]/" << ta << " gb=[";
     for (size_t i = 0; i < gb.size(); ++i) o << (i ? "," : "") << gb[i];
-    o << "]/" << tb << " j=" << ju << "," << jw << (ring ? " ring" : "") << " order=[";
+    o << "]/" << tb << " j=" << ju << "," << jw << (rows ? " rows" : "") << " order=[";
     for (size_t i = 0; i < order.size(); ++i) o << (i ? "," : "") << order[i];
     o << "]";
   }
@@ -293,13 +294,49 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
     const double ra = c.sa[0] == 1 ? double(len) : 1.0, rb = c.sb[0] == 1 ? double(len) : 1.0;
     k.seg_a = ra;
     k.seg_b = rb;
-    const double mem = (n * esA / sector_efficiency(ra * esA, esA) +
-                        n * esB * (bnz ? 2 : 1) / sector_efficiency(rb * esB, esB)) / kHbmBytesPerS;
+    const double mem = (n * esA / run_efficiency(ra * esA, false) +
+                        n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true)) / kHbmBytesPerS;
     const double rows = n / double(len);
     const double lanes_per_row = std::ceil(double(len) / (32.0 * k.vec)) * 32.0;
     const double issue = (rows * lanes_per_row * 10.0 + rows * 32.0 * (8.0 * c.N)) / kLaneInstrPerS;
-    k.est_s = std::max(mem, issue) + 0.2 * std::min(mem, issue) + 2e-6;
+    // one warp per row chunk: short rows leave few loads in flight per warp
+    const double mlp = std::min(1.0, double(len) / (32.0 * 4 * k.vec));
+    k.est_s = std::max(mem / std::max(mlp, 0.1), issue) + 0.2 * std::min(mem, issue) + 2e-6;
     if (k.variant == VAR_COPY) out.push_back(k);
+  }
+
+  // ---- multi-row copy: perm keeps index 0 with short runs; G consecutive
+  // indices of A's next index make one contiguous block of A per tile
+  if (c.perm[0] == 0 && c.N >= 2 && c.sa[0] == 1 && c.sb[0] == 1 && c.sa[1] == c.s[0]) {
+    const int Kt = tile_k_for(din == DT_F64 ? 8 : 4);
+    const int64_t cap = int64_t(kThreads) * Kt / c.s[0];
+    if (cap >= 2) {
+      for (int G : cut_options(c.s[1], cap)) {
+        Candidate k;
+        k.variant = VAR_TILE;
+        k.rows = 1;
+        k.has_c = 1;
+        k.ga = {1};
+        k.ta = G;
+        int64_t ext[kMaxDim];
+        TileShape sh{1, k.ga, {}, G, 1};
+        tile_extents(c, sh, ext);
+        double ntiles = 1;
+        for (int q = 0; q < c.N; ++q) ntiles *= std::ceil(double(c.s[q]) / double(ext[q]));
+        if (ntiles >= 2147483647.0) continue;
+        k.order = grid_order(c, ext, 0);
+        const double ra = run_length(c, ext, orderA, c.sa), rb = run_length(c, ext, orderB, c.sb);
+        k.seg_a = ra;
+        k.seg_b = rb;
+        const double mem = (n * esA / run_efficiency(ra * esA, false) +
+                            n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true)) / kHbmBytesPerS;
+        const double issue = ntiles * kThreads * Kt * (10.0 + (bnz ? 3 : 0)) / kLaneInstrPerS;
+        const double over = ntiles * kThreads * (40.0 + 10.0 * c.N) / kLaneInstrPerS;
+        const double fill = double(c.s[0]) * G / double(kThreads * Kt);   // share of the unrolled slots in use
+        k.est_s = std::max(mem, issue / std::max(fill, 0.05)) + 0.1 * std::min(mem, issue) + over + 3e-6;
+        out.push_back(k);
+      }
+    }
   }
 
   // ---- staged tile
@@ -372,8 +409,8 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
                 (!sh.gb.empty() && c.s[sh.gb.back()] >= (int64_t(1) << 30)))
               continue;
             const double ra = run_length(c, ext, orderA, c.sa), rb = run_length(c, ext, orderB, c.sb);
-            const double mem = (n * esA / sector_efficiency(ra * esA, esA) +
-                                n * esB * (bnz ? 2 : 1) / sector_efficiency(rb * esB, esB)) / kHbmBytesPerS;
+            const double mem = (n * esA / run_efficiency(ra * esA, false) +
+                                n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true)) / kHbmBytesPerS;
             const double per_slot = 26.0 + (sh.ga.size() > 1 ? 3 : 0) + (sh.gb.size() > 1 ? 3 : 0) + (bnz ? 6 : 0);
             const double issue = ntiles * kTileK * kThreads * per_slot / kLaneInstrPerS;
             const double over = ntiles * kThreads * (60.0 + 10.0 * c.N) / kLaneInstrPerS;
@@ -406,14 +443,7 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
               k2.jw = jw;
               k2.est_s = std::max(mem, issue2) + 0.25 * std::min(mem, issue2) + over + 3e-6;
               tiles.push_back(k2);
-              if ((din == DT_F32 || din == DT_F64) && tile3_layout_supported(ju, jw) && c.sa[0] == 1 &&
-                  c.sb[c.perm[0]] == 1) {
-                // asynchronous-copy ring: loads hidden behind the writes of earlier tiles
-                Candidate k3 = k2;
-                k3.ring = 1;
-                k3.est_s = std::max(mem, issue2) + 0.05 * std::min(mem, issue2) + over + 3e-6;
-                tiles.push_back(k3);
-              }
+
             }
           }
         }
@@ -535,6 +565,10 @@ void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* 
   p->wr_dlc = kThreads % LC;
   p->wr_dlb = (kThreads / LC) % LB;
   p->wr_dla = kThreads / (LC * LB);
+  p->divU = make_fastdiv(uint32_t(p->U));
+  p->divLC = make_fastdiv(uint32_t(LC));
+  p->divLB = make_fastdiv(uint32_t(LB));
+  p->divW = make_fastdiv(uint32_t(p->W));
   *smem_bytes = int(((tabA->size() + tabB->size()) * sizeof(int32_t) + 15) & ~size_t(15)) +
                 p->P * LB * stage_bytes(din);
 }

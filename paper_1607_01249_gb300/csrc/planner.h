@@ -36,7 +36,7 @@ struct Candidate {
   int tb = 1;                  // tile extent of GB's last index
   std::vector<int> order;      // grid indices (A index ids), fastest first
   int ju = 0, jw = 0;          // >0: warp-mapped tile kernel with JU/JW chunks of 32 lanes
-  int ring = 0;                // warp-mapped kernel reading A with cp.async into a ring of tiles
+  int rows = 0;                // multi-row copy kernel (perm keeps index 0, GB empty, no staging)
   // copy variant
   int64_t chunk = 0;
   int vec = 1;                 // vector width usable when pointers are aligned
@@ -60,8 +60,8 @@ void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* 
                        std::vector<int32_t>* tabA, std::vector<int32_t>* tabB, int* smem_bytes);
 void build_row_params(const Canon& c, int64_t chunk, RowParams* p);
 
-// Estimated memory efficiency of a contiguous segment of `bytes` bytes whose
-// start is a random multiple of `elem` bytes within a 32-byte sector.
-double sector_efficiency(double bytes, int elem);
+// Estimated memory efficiency of reading (write = false) or writing a
+// contiguous run of `bytes` bytes that starts at an arbitrary element offset.
+double run_efficiency(double bytes, bool write);
 
 }  // namespace ttc

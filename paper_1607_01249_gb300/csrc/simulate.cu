@@ -18,6 +18,39 @@ using namespace ttc;
 
 namespace {
 
+template <int JU, int K, bool FULL, class F>
+void read2j(const TileCoord& c, const TileParams& tp, const int32_t* tab, int ln, int wp, F&& f) {
+  if (tp.crossA_tab) walk2_read<JU, K, FULL, true>(c, tp, tab, ln, wp, f);
+  else walk2_read<JU, K, FULL, false>(c, tp, tab, ln, wp, f);
+}
+
+template <int K, bool FULL, class F>
+bool read2(int ju, const TileCoord& c, const TileParams& tp, const int32_t* tab, int ln, int wp, F&& f) {
+  if (ju == 1) read2j<1, K, FULL>(c, tp, tab, ln, wp, f);
+  else if (ju == 2) read2j<2, K, FULL>(c, tp, tab, ln, wp, f);
+  else if (ju == 4) read2j<4, K, FULL>(c, tp, tab, ln, wp, f);
+  else return false;
+  return true;
+}
+
+template <int JW, int K, bool FULL, class F>
+void write2j(const TileCoord& c, const TileParams& tp, const int32_t* tab, int ln, int wp, F&& f) {
+  int sp[JW];
+  int32_t vo[JW];
+  walk2_lane_consts<JW>(tp, ln, sp, vo);
+  if (tp.crossB_tab) walk2_write<JW, K, FULL, true>(c, tp, tab, ln, wp, sp, vo, f);
+  else walk2_write<JW, K, FULL, false>(c, tp, tab, ln, wp, sp, vo, f);
+}
+
+template <int K, bool FULL, class F>
+bool write2(int jw, const TileCoord& c, const TileParams& tp, const int32_t* tab, int ln, int wp, F&& f) {
+  if (jw == 1) write2j<1, K, FULL>(c, tp, tab, ln, wp, f);
+  else if (jw == 2) write2j<2, K, FULL>(c, tp, tab, ln, wp, f);
+  else if (jw == 4) write2j<4, K, FULL>(c, tp, tab, ln, wp, f);
+  else return false;
+  return true;
+}
+
 struct Checker {
   const ttc_plan_s* p;
   int64_t stA[kMaxDim], stB[kMaxDim];
@@ -99,14 +132,14 @@ struct Checker {
       std::fill(posA.begin(), posA.end(), -1);
       std::fill(used.begin(), used.end(), 0);
       bool ok = true;
-      auto on_read = [&](int, int32_t off, int pos) {
-        if (!ok) return;
+      auto on_read = [&](int, bool valid, int32_t off, int pos) {
+        if (!ok || !valid) return;
         if (pos < 0 || pos >= ncap) { ok = fail("shared-memory position out of range (read)", pos, ncap); return; }
         if (posA[size_t(pos)] != -1) { ok = fail("shared-memory position written twice", pos, tid); return; }
         posA[size_t(pos)] = c.baseA + off;
       };
-      auto on_write = [&](int, int32_t off, int pos) {
-        if (!ok) return;
+      auto on_write = [&](int, bool valid, int32_t off, int pos) {
+        if (!ok || !valid) return;
         if (pos < 0 || pos >= ncap) { ok = fail("shared-memory position out of range (write)", pos, ncap); return; }
         if (posA[size_t(pos)] < 0) { ok = fail("shared-memory position read but never written", pos, tid); return; }
         if (used[size_t(pos)]) { ok = fail("shared-memory position read twice", pos, tid); return; }
@@ -114,46 +147,41 @@ struct Checker {
         ok = pair(posA[size_t(pos)], c.baseB + off);
       };
       const bool full = c.remA == tp.LA && c.remB == tp.LB;
-      if (k.ring) {
+      if (k.rows) {
+        // no staging: each element goes straight from A to B
+        for (int t = 0; t < kThreads && ok; ++t)
+          walk_rows<K>(c, tp, t, [&](int, bool valid, int32_t offA, int32_t offB) {
+            if (ok && valid) ok = pair(c.baseA + offA, c.baseB + offB);
+          });
+        if (!ok) return false;
+        continue;
+      }
+      if (k.ju == 0) {
+        for (int t = 0; t < kThreads && ok; ++t) {
+          int u0, lb0, lc0, lbw0, la0;
+          flat_starts(tp, t, u0, lb0, lc0, lbw0, la0);
+          if (tp.crossA_tab) walk_read<K, true>(c, tp, ta.data(), u0, lb0, on_read);
+          else walk_read<K, false>(c, tp, ta.data(), u0, lb0, on_read);
+        }
+        for (int t = 0; t < kThreads && ok; ++t) {
+          int u0, lb0, lc0, lbw0, la0;
+          flat_starts(tp, t, u0, lb0, lc0, lbw0, la0);
+          if (tp.crossB_tab) walk_write<K, true>(c, tp, tb.data(), lc0, lbw0, la0, on_write);
+          else walk_write<K, false>(c, tp, tb.data(), lc0, lbw0, la0, on_write);
+        }
+      } else {
+        bool known = true;
         for (int t = 0; t < kThreads && ok; ++t) {
           const int ln = t & 31, wp = t >> 5;
-          if (k.ju == 1) { if (full) walk3_read<1, K, true>(c, tp, ta.data(), ln, wp, on_read); else walk3_read<1, K, false>(c, tp, ta.data(), ln, wp, on_read); }
-          else if (k.ju == 2) { if (full) walk3_read<2, K, true>(c, tp, ta.data(), ln, wp, on_read); else walk3_read<2, K, false>(c, tp, ta.data(), ln, wp, on_read); }
-          else if (k.ju == 4) { if (full) walk3_read<4, K, true>(c, tp, ta.data(), ln, wp, on_read); else walk3_read<4, K, false>(c, tp, ta.data(), ln, wp, on_read); }
-          else ok = fail("unknown lane layout", k.ju, 0);
+          if (full) known = read2<K, true>(k.ju, c, tp, ta.data(), ln, wp, on_read);
+          else known = read2<K, false>(k.ju, c, tp, ta.data(), ln, wp, on_read);
+          if (!known) ok = fail("unknown lane layout", k.ju, 0);
         }
         for (int t = 0; t < kThreads && ok; ++t) {
           const int ln = t & 31, wp = t >> 5;
-          if (k.jw == 1) { int sp[1]; int32_t vo[1]; walk2_lane_consts<1>(tp, ln, sp, vo);
-            if (full) walk3_write<1, K, true>(c, tp, tb.data(), ln, wp, sp, on_write); else walk3_write<1, K, false>(c, tp, tb.data(), ln, wp, sp, on_write); }
-          else if (k.jw == 2) { int sp[2]; int32_t vo[2]; walk2_lane_consts<2>(tp, ln, sp, vo);
-            if (full) walk3_write<2, K, true>(c, tp, tb.data(), ln, wp, sp, on_write); else walk3_write<2, K, false>(c, tp, tb.data(), ln, wp, sp, on_write); }
-          else if (k.jw == 4) { int sp[4]; int32_t vo[4]; walk2_lane_consts<4>(tp, ln, sp, vo);
-            if (full) walk3_write<4, K, true>(c, tp, tb.data(), ln, wp, sp, on_write); else walk3_write<4, K, false>(c, tp, tb.data(), ln, wp, sp, on_write); }
-          else ok = fail("unknown lane layout", k.jw, 0);
-        }
-      }
-      for (int t = 0; t < kThreads && ok && !k.ring; ++t) {
-        if (k.ju == 0) walk_read<K>(c, tp, ta.data(), t % tp.U, t / tp.U, on_read);
-        else if (k.ju == 1) walk2_read<1, K>(c, tp, ta.data(), t & 31, t >> 5, on_read);
-        else if (k.ju == 2) walk2_read<2, K>(c, tp, ta.data(), t & 31, t >> 5, on_read);
-        else if (k.ju == 4) walk2_read<4, K>(c, tp, ta.data(), t & 31, t >> 5, on_read);
-        else ok = fail("unknown lane layout", k.ju, 0);
-      }
-      for (int t = 0; t < kThreads && ok && !k.ring; ++t) {
-        if (k.jw == 0) {
-          walk_write<K>(c, tp, tb.data(), t % tp.LC, (t / tp.LC) % tp.LB, t / tp.W, on_write);
-        } else if (k.jw == 1) {
-          int sp[1]; int32_t vo[1]; walk2_lane_consts<1>(tp, t & 31, sp, vo);
-          walk2_write<1, K>(c, tp, tb.data(), t & 31, t >> 5, sp, vo, on_write);
-        } else if (k.jw == 2) {
-          int sp[2]; int32_t vo[2]; walk2_lane_consts<2>(tp, t & 31, sp, vo);
-          walk2_write<2, K>(c, tp, tb.data(), t & 31, t >> 5, sp, vo, on_write);
-        } else if (k.jw == 4) {
-          int sp[4]; int32_t vo[4]; walk2_lane_consts<4>(tp, t & 31, sp, vo);
-          walk2_write<4, K>(c, tp, tb.data(), t & 31, t >> 5, sp, vo, on_write);
-        } else {
-          ok = fail("unknown lane layout", k.jw, 0);
+          if (full) known = write2<K, true>(k.jw, c, tp, tb.data(), ln, wp, on_write);
+          else known = write2<K, false>(k.jw, c, tp, tb.data(), ln, wp, on_write);
+          if (!known) ok = fail("unknown lane layout", k.jw, 0);
         }
       }
       for (int q = 0; q < ncap && ok; ++q)

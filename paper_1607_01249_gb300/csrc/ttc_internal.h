@@ -124,6 +124,8 @@ struct TileParams {
   // per-thread step of kThreads in the read order (u, lb) and write order (lc, lb, la)
   int rd_du, rd_dlb;
   int wr_dlc, wr_dlb, wr_dla;
+  // invariant divisors of the lane/thread decompositions
+  FastDiv divU, divLC, divLB, divW;
   Epilogue epi;
 };
 

@@ -42,7 +42,7 @@ class PlanInfo(ctypes.Structure):
                 ("tile_c", ctypes.c_int), ("tile_a", ctypes.c_int), ("tile_b", ctypes.c_int),
                 ("ntiles", ctypes.c_int64), ("vec_in", ctypes.c_int), ("vec_out", ctypes.c_int),
                 ("candidate", ctypes.c_int), ("ncandidates", ctypes.c_int),
-                ("lanes_a", ctypes.c_int), ("lanes_b", ctypes.c_int), ("async_ring", ctypes.c_int)]
+                ("lanes_a", ctypes.c_int), ("lanes_b", ctypes.c_int)]
 
 
 # Every symbol include/ttc.h declares, with (restype, argtypes).
@@ -165,13 +165,12 @@ class Plan:
         return {"ndim": N, "perm": list(inf.perm[:N]), "sizes": list(inf.sizes[:N]),
                 "stride_A": list(inf.stride_A[:N]), "stride_B": list(inf.stride_B[:N]), "n": inf.n,
                 "algorithmic_bytes": inf.algorithmic_bytes,
-                "variant": {0: "empty", 1: "copy", 2: "tile"}[inf.variant],
+                "variant": {0: "empty", 1: "copy", 2: "tile", 3: "rowcopy"}[inf.variant],
                 "tile": (inf.tile_c, inf.tile_a, inf.tile_b), "ntiles": inf.ntiles,
                 "vec": (inf.vec_in, inf.vec_out), "candidate": inf.candidate,
                 "ncandidates": inf.ncandidates, "lanes": (inf.lanes_a, inf.lanes_b),
-                "kernel": ({0: "empty", 1: "copy_kernel"}.get(inf.variant) or
-                           ("tile3_kernel" if inf.async_ring else
-                            "tile2_kernel" if inf.lanes_a else "tile_kernel"))}
+                "kernel": ({0: "empty", 1: "copy_kernel", 3: "rowcopy_kernel"}.get(inf.variant) or
+                           ("tile2_kernel" if inf.lanes_a else "tile_kernel"))}
 
     def autotune(self, max_candidates=8, stream=None) -> float:
         ms = ctypes.c_float(0)

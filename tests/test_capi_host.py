@@ -114,7 +114,7 @@ def test_canonical_form_properties():
                      inf["stride_B"][k + 1] == inf["stride_B"][k] * inf["sizes"][k])
             assert not (adjacent and dense)
         if inf["perm"][0] == 0:
-            assert inf["variant"] in ("copy", "tile")
+            assert inf["variant"] in ("copy", "tile", "rowcopy")
         else:
             assert inf["variant"] == "tile"
 
