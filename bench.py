@@ -323,6 +323,101 @@ def workload_desc(name, probs):
     return name
 
 
+def pack_buffers(probs, seed=0):
+    """One device arena for all A's and one for all B's (256-byte aligned
+    slices), filled with seeded uniform data."""
+    import torch
+    offs_a, offs_b, ta, tb = [], [], 0, 0
+    for p in probs:
+        offs_a.append(ta)
+        offs_b.append(tb)
+        ta += (p.vol_a * inputs.DTYPE_BYTES[p.dtype_in] + 255) // 256 * 256
+        tb += (p.vol_b * inputs.DTYPE_BYTES[p.dtype_out] + 255) // 256 * 256
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    A = torch.empty(ta // 4, dtype=torch.float32, device="cuda").uniform_(-1, 1, generator=g)
+    B = torch.empty(tb // 4, dtype=torch.float32, device="cuda").uniform_(-1, 1, generator=g)
+    pa = [A.data_ptr() + o for o in offs_a]
+    pb = [B.data_ptr() + o for o in offs_b]
+    return A, B, pa, pb
+
+
+def run_batch(args, rank, world):
+    """Thousands of uneven transposes: one graph-launched persistent batch vs
+    one ttc_execute call per transpose on the same stream."""
+    import torch
+    from paper_1607_01249_gb300 import build as ttc_build
+    from paper_1607_01249_gb300 import ttc
+
+    ttc_build.build()
+    ttc.lib()
+    torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
+    probs = inputs.batch_problems(args.batch_count)
+    plans = [ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta) for p in probs]
+    A, B, pa, pb = pack_buffers(probs)
+    batch = ttc.Batch()
+    for pl, a, b in zip(plans, pa, pb):
+        batch.add(pl, a, b)
+    stream = torch.cuda.current_stream()
+    bytes_step = sum(p.algorithmic_bytes() for p in probs)
+
+    def timed(fn, steps):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ttc.launch_count()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            import torch.distributed as tdist
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, (ttc.launch_count() - l0) // steps
+
+    def per_call():
+        for pl, a, b in zip(plans, pa, pb):
+            pl.execute(a, b, stream)
+
+    clk = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clk:
+        clk.start()
+    ms_b, launches_b = timed(lambda: batch.graph_launch(stream), args.steps)
+    clocks = clk.stop() if clk else None
+    ms_c, launches_c = timed(per_call, max(1, args.steps // 2))
+    info = batch.info()
+    value = world * bytes_step / (ms_b * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    return {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_b, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic (seeded sizes/perms; uniform data)",
+        "config": {"workload": f"batch of {len(probs)} transposes, N 2..5, 2^10..2^22 elements log-uniform, "
+                               "f32/bf16 50/50, alpha=1, beta in {0,0.5}; one CUDA-graph launch per step",
+                   "tiles": info["tiles"], "algorithmic_bytes_per_step": bytes_step,
+                   "parallelism": f"replicas x{world}"},
+        "batch": {"transposes_per_s": round(world * len(probs) / (ms_b * 1e-3), 1), "ms": round(ms_b, 4),
+                  "kernel_launches_per_step": launches_b},
+        "per_call": {"transposes_per_s": round(world * len(probs) / (ms_c * 1e-3), 1), "ms": round(ms_c, 4),
+                     "GB/s": round(world * bytes_step / (ms_c * 1e-3) / 1e9, 2),
+                     "kernel_launches_per_step": launches_c},
+        "speedup_vs_per_call": round(ms_c / ms_b, 3),
+        "roofline": {"bound": "hbm", "achieved": round(bytes_step / (ms_b * 1e-3) / 1e9, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(bytes_step / (ms_b * 1e-3) / 1e9 / peak, 4),
+                     "kernel": "batch_kernel", "traffic": None},
+        "gpu_launches": launches_b * args.steps,
+        "clocks": clocks,
+    }
+
+
 def run_e2e(args, probs, plans, bufs, stream, world):
     """Same metric with host (pinned) inputs: every step copies A (and B when
     beta != 0) host->device, runs the plan, and copies B back."""
@@ -466,7 +561,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "single4d", "packing"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "single4d", "packing", "batch"])
+    ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--autotune", type=int, default=0, help="time up to this many candidates per plan first")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -489,9 +585,9 @@ def main():
         import torch.distributed as tdist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
         tdist.init_process_group("nccl")
-    out = run_ours(args, rank, world)
+    out = run_batch(args, rank, world) if args.workload == "batch" else run_ours(args, rank, world)
     if rank == 0:
-        if not args.no_cpu and world == 1:
+        if not args.no_cpu and world == 1 and args.workload != "batch":
             out["cpu_baseline"] = cpu_baseline(args.cpu_budget,
                                                workload_problems(args.workload, args.target, args.only),
                                                os.cpu_count() or 1)

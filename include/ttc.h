@@ -199,6 +199,42 @@ const char* ttc_last_error(void);
 int64_t ttc_launch_count(void);
 
 /*
+ * Batches: many independent permute-scale-adds (Eq. 1) -- different
+ * permutations, sizes, dtypes, alpha/beta -- in ONE persistent kernel launch.
+ * Every problem is cut into tiles (the paper's macro-tiles, section 2.2);
+ * resident CTAs claim tiles through an atomic counter, so uneven problems
+ * balance across the GPU, and each tile is processed with its own problem's
+ * parameters.  This is the analogue of scheduling the macro-tiles of section
+ * 2.2 across threadblocks, extended across problems.
+ *
+ *  ttc_batch_create   new empty batch (host only).
+ *  ttc_batch_add      append (plan, A, B): the plan must stay alive and
+ *                     unchanged while the batch is used; A and B are device
+ *                     pointers as for ttc_execute (checked the same way).
+ *                     FP8 plans are rejected (TTC_ERR_UNSUPPORTED_DTYPE): their
+ *                     scale needs a pre-pass of its own.
+ *  ttc_batch_execute  enqueue the batch on `stream`: one counter reset and one
+ *                     kernel launch.  The first execution after an add builds
+ *                     and uploads the descriptors (synchronous, allocates
+ *                     device memory owned by the batch).
+ *  ttc_batch_graph_launch  the same work as a CUDA graph: captured on the
+ *                     first call (after the descriptors are uploaded), then
+ *                     replayed with one cudaGraphLaunch per call.
+ *  ttc_batch_destroy  release the batch (not the plans); no work using it may
+ *                     be queued.
+ *  ttc_batch_info     number of problems and of tiles of the batch.
+ * Problems of one batch must not write overlapping bytes of B, and no B may
+ * overlap any A of the batch (they run concurrently).
+ */
+typedef struct ttc_batch_s* ttc_batch_t;
+ttc_status ttc_batch_create(ttc_batch_t* out);
+ttc_status ttc_batch_add(ttc_batch_t batch, ttc_plan_t plan, const void* A, void* B);
+ttc_status ttc_batch_execute(ttc_batch_t batch, ttc_stream_t stream);
+ttc_status ttc_batch_graph_launch(ttc_batch_t batch, ttc_stream_t stream);
+ttc_status ttc_batch_destroy(ttc_batch_t batch);
+ttc_status ttc_batch_info(ttc_batch_t batch, int64_t* problems, int64_t* tiles);
+
+/*
  * ttc_execute_noalloc -- ttc_execute for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a deployment aid of this
  * library.

@@ -1,0 +1,499 @@
+// batch.cu -- many permute-scale-adds in one persistent kernel launch
+// (include/ttc.h, ttc_batch_*).
+//
+// Every problem of a batch is cut into tiles by its own plan.  A tile is
+// processed by one CTA with one of three bodies:
+//   BP_TILE -- the generic staged tile (flat walks, offset tables for both
+//              cross offsets), for problems whose perm moves index 0;
+//   BP_ROWS -- the multi-row copy (perm keeps index 0, short runs);
+//   BP_COPY -- one chunk of one long run (perm keeps index 0, long runs).
+// Resident CTAs claim tiles from one atomic counter (uneven problems balance
+// themselves); a per-tile map names the problem, whose descriptor (pointers,
+// tile parameters, epilogue) sits in one device arena owned by the batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ttc.h"
+#include "kernels.cuh"
+#include "launch.h"
+#include "plan_impl.h"
+#include "planner.h"
+
+namespace ttc {
+
+extern std::atomic<int64_t> g_launches;
+cudaError_t grid_for(const void* fn, int smem, int64_t work, int* grid);
+
+enum BatchPath : int { BP_TILE = 0, BP_ROWS = 1, BP_COPY = 2 };
+
+struct alignas(16) BatchDesc {
+  const void* A;
+  void* B;
+  int din, dout, path, pad;
+  uint32_t tile0;    // first global tile of this problem
+  uint32_t ntiles;
+  TileParams tp;     // BP_TILE, BP_ROWS
+  RowParams rp;      // BP_COPY
+};
+
+constexpr int kBatchCopyChunk = 2048;   // elements of a run per BP_COPY tile
+
+// elements per thread per phase in the batch body: half of the single-plan
+// kernels' (tiles of at most 2048 four-byte or 1024 eight-byte elements), so
+// that the descriptor fields fit in registers next to the staged data
+constexpr int batch_k_for(int stage_bytes) { return tile_k_for(stage_bytes) / 2; }
+
+// Where one tile of the batch lies, precomputed on the host so that a CTA
+// needs one load to start on a claimed tile.  For BP_COPY: baseA/baseB are
+// the run's offsets, remA the first element of the chunk, remB its length.
+struct TileRec {
+  uint32_t prob;
+  int32_t remA, remB, pad;
+  int64_t baseA, baseB;
+};
+
+// --------------------------------------------------------------- device --
+
+template <int DIN, int DOUT, bool BNZ>
+__device__ __forceinline__ void batch_tile(const BatchDesc& d, const TileCoord& c, unsigned char* smem) {
+  using S = stage_t<DIN>;
+  using TO = store_t<DOUT>;
+  constexpr int K = batch_k_for(sizeof(S));
+  const WalkP p = walk_params(d.tp);      // registers, not shared-memory loads per element
+  const int t = threadIdx.x;
+  const store_t<DIN>* Ab = static_cast<const store_t<DIN>*>(d.A) + c.baseA;
+  TO* Bb = static_cast<TO*>(d.B) + c.baseB;
+  S v[K];
+  TO bo[K];
+  if (d.path == BP_ROWS) {
+    walk_rows<K>(c, p, t, [&](int k, bool, int32_t offA, int32_t offB) {
+      v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + offA));
+      if constexpr (BNZ) bo[k] = Bb[offB];
+    });
+    walk_rows<K>(c, p, t, [&](int k, bool ok, int32_t, int32_t offB) {
+      if (ok) Bb[offB] = epilogue<DIN, DOUT>(v[k], bo[k], p.epi, 1.f);
+    });
+    return;
+  }
+  S* tile = reinterpret_cast<S*>(smem);
+  int u0, lb0, lc0, lbw0, la0;
+  flat_starts(p, t, u0, lb0, lc0, lbw0, la0);
+  walk_read<K, true>(c, p, p.tabA, u0, lb0,
+                     [&](int k, bool, int32_t off, int) { v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + off)); });
+  walk_read<K, true>(c, p, p.tabA, u0, lb0, [&](int k, bool ok, int32_t, int pos) {
+    if (ok) tile[pos] = v[k];
+  });
+  __syncthreads();
+  if constexpr (BNZ)
+    walk_write<K, true>(c, p, p.tabB, lc0, lbw0, la0, [&](int k, bool, int32_t off, int) { bo[k] = Bb[off]; });
+  walk_write<K, true>(c, p, p.tabB, lc0, lbw0, la0, [&](int k, bool ok, int32_t off, int pos) {
+    if (ok) Bb[off] = epilogue<DIN, DOUT>(tile[pos], bo[k], p.epi, 1.f);
+  });
+}
+
+template <int DIN, int DOUT, bool BNZ>
+__device__ __forceinline__ void batch_copy(const BatchDesc& d, const RowCoord& rc) {
+  using S = stage_t<DIN>;
+  using TO = store_t<DOUT>;
+  constexpr int K = kBatchCopyChunk / kThreads / (sizeof(S) == 8 ? 2 : 1);
+  const int64_t sa0 = d.rp.sa0, sb0 = d.rp.sb0;
+  const Epilogue epi = d.rp.epi;
+  const int t = threadIdx.x;
+  const store_t<DIN>* Ar = static_cast<const store_t<DIN>*>(d.A) + rc.offA;
+  TO* Br = static_cast<TO*>(d.B) + rc.offB;
+  S v[K];
+  TO bo[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int64_t x = rc.start + t + int64_t(k) * kThreads;
+    const int64_t xs = x < rc.end ? x : rc.start;
+    v[k] = to_stage<DIN>(ldg_elem<DIN>(Ar + xs * sa0));
+    if constexpr (BNZ) bo[k] = Br[xs * sb0];
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int64_t x = rc.start + t + int64_t(k) * kThreads;
+    if (x < rc.end) Br[x * sb0] = epilogue<DIN, DOUT>(v[k], bo[k], epi, 1.f);
+  }
+}
+
+// one claimed tile of one problem
+template <int DIN, int DOUT>
+__device__ __noinline__ void batch_unit(const BatchDesc& d, const TileRec& r, unsigned char* smem) {
+  if (d.path == BP_COPY) {
+    const RowCoord rc{r.baseA, r.baseB, int64_t(r.remA), int64_t(r.remA) + r.remB};
+    if (d.rp.epi.beta_nz) batch_copy<DIN, DOUT, true>(d, rc);
+    else batch_copy<DIN, DOUT, false>(d, rc);
+  } else {
+    const TileCoord c{r.baseA, r.baseB, r.remA, r.remB};
+    if (d.tp.epi.beta_nz) batch_tile<DIN, DOUT, true>(d, c, smem);
+    else batch_tile<DIN, DOUT, false>(d, c, smem);
+  }
+}
+
+__device__ __forceinline__ void batch_dispatch(const BatchDesc& d, const TileRec& r, unsigned char* smem) {
+  switch (d.din * 4 + d.dout) {
+    case DT_F32 * 4 + DT_F32: batch_unit<DT_F32, DT_F32>(d, r, smem); break;
+    case DT_F32 * 4 + DT_F64: batch_unit<DT_F32, DT_F64>(d, r, smem); break;
+    case DT_F32 * 4 + DT_BF16: batch_unit<DT_F32, DT_BF16>(d, r, smem); break;
+    case DT_F64 * 4 + DT_F64: batch_unit<DT_F64, DT_F64>(d, r, smem); break;
+    case DT_F64 * 4 + DT_F32: batch_unit<DT_F64, DT_F32>(d, r, smem); break;
+    case DT_BF16 * 4 + DT_BF16: batch_unit<DT_BF16, DT_BF16>(d, r, smem); break;
+    case DT_BF16 * 4 + DT_F32: batch_unit<DT_BF16, DT_F32>(d, r, smem); break;
+    default: break;
+  }
+}
+
+// Persistent: resident CTAs claim tiles from one counter (uneven problems
+// balance themselves).  The claim of the next tile is issued while the
+// current one is processed, so only its record load is exposed; the current
+// problem's descriptor is kept in shared memory and reloaded only when the
+// problem changes.
+__global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc* __restrict__ descs,
+                                                            const TileRec* __restrict__ recs,
+                                                            uint32_t total, uint32_t* counter) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t s_g;
+  __shared__ TileRec s_rec;
+  __shared__ __align__(16) BatchDesc s_desc;
+  constexpr int kWords = int(sizeof(BatchDesc) / sizeof(int4));
+  static_assert(sizeof(BatchDesc) % sizeof(int4) == 0, "descriptor copied as 16-byte words");
+  const int t = threadIdx.x;
+  uint32_t have = 0xffffffffu;
+  if (t == 0) {
+    s_g = atomicAdd(counter, 1u);
+    if (s_g < total) s_rec = recs[s_g];
+  }
+  __syncthreads();
+  for (;;) {
+    const uint32_t g = s_g;
+    if (g >= total) break;
+    const TileRec r = s_rec;
+    uint32_t gn = 0;
+    if (t == 0) gn = atomicAdd(counter, 1u);
+    if (r.prob != have) {
+      const int4* src = reinterpret_cast<const int4*>(descs + r.prob);
+      int4* dst = reinterpret_cast<int4*>(&s_desc);
+      for (int i = t; i < kWords; i += kThreads) dst[i] = src[i];
+      have = r.prob;
+      __syncthreads();
+    }
+    batch_dispatch(s_desc, r, smem);
+    __syncthreads();   // the tile buffer and s_rec are reused
+    if (t == 0) {
+      s_g = gn;
+      if (gn < total) s_rec = recs[gn];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace ttc
+
+// ------------------------------------------------------------------ host --
+
+using namespace ttc;
+
+struct ttc_batch_s {
+  struct Item {
+    ttc_plan_t plan;
+    const void* A;
+    void* B;
+  };
+  std::mutex mu;
+  std::vector<Item> items;
+  bool dirty = true;
+  int dev = -1;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  BatchDesc* d_descs = nullptr;
+  TileRec* d_recs = nullptr;
+  uint32_t* d_counter = nullptr;
+  uint32_t total = 0;
+  int smem = 0;
+  int grid = 0;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  ~ttc_batch_s() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (arena) cudaFree(arena);
+  }
+};
+
+namespace {
+
+bool batch_pair_supported(int din, int dout) { return pair_supported(din, dout) && dout != DT_E4M3; }
+
+// Build the descriptors of every problem and upload them (synchronous).
+ttc_status batch_build(ttc_batch_s* b) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::vector<BatchDesc> descs;
+  std::vector<std::vector<int32_t>> tabs;   // per problem: tabA then tabB
+  std::vector<size_t> tab_sizeA;
+  descs.reserve(b->items.size());
+  uint64_t total = 0;
+  int smem = 0;
+  for (auto& it : b->items) {
+    ttc_plan_s* p = it.plan;
+    if (p->canon.n == 0) continue;
+    BatchDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.A = it.A;
+    d.B = it.B;
+    d.din = p->din;
+    d.dout = p->dout;
+    // tiles for the batch body: the best schedule with at most the batch's
+    // tile volume
+    const std::vector<Candidate> bc =
+        make_candidates(p->canon, p->din, p->dout, p->beta, 4, kThreads * batch_k_for(p->din == DT_F64 ? 8 : 4));
+    const Candidate& k = bc.front();
+    std::vector<int32_t> ta, tb;
+    if (k.variant == VAR_TILE) {
+      int sm = 0;
+      build_tile_params(p->canon, k, p->din, &d.tp, &ta, &tb, &sm);
+      d.path = k.rows ? BP_ROWS : BP_TILE;
+      if (d.path == BP_TILE) {
+        // the batch body always reads both cross offsets from tables
+        if (!d.tp.crossA_tab) {
+          ta.resize(d.tp.LB);
+          for (int i = 0; i < d.tp.LB; ++i) ta[i] = i * d.tp.crossA_lin;
+          d.tp.crossA_tab = 1;
+        }
+        if (!d.tp.crossB_tab) {
+          tb.resize(d.tp.LA);
+          for (int i = 0; i < d.tp.LA; ++i) tb[i] = i * d.tp.crossB_lin;
+          d.tp.crossB_tab = 1;
+        }
+        smem = std::max(smem, d.tp.P * d.tp.LB * (p->din == DT_F64 ? 8 : 4));
+      }
+      d.ntiles = d.tp.ntiles;
+      d.tp.epi = make_epilogue(p, nullptr);
+    } else {
+      build_row_params(p->canon, kBatchCopyChunk / (p->din == DT_F64 ? 2 : 1), &d.rp);
+      d.path = BP_COPY;
+      d.ntiles = d.rp.nitems;
+      d.rp.epi = make_epilogue(p, nullptr);
+    }
+    d.tile0 = uint32_t(total);
+    total += d.ntiles;
+    if (total >= 0x7fffffffull) return fail(TTC_ERR_INVALID_SIZE, "batch has too many tiles");
+    tab_sizeA.push_back(ta.size());
+    ta.insert(ta.end(), tb.begin(), tb.end());
+    tabs.push_back(std::move(ta));
+    descs.push_back(d);
+  }
+  // arena: descriptors | tables | tile records | counter
+  size_t ntab = 0;
+  for (auto& t : tabs) ntab += t.size();
+  const size_t off_tab = (descs.size() * sizeof(BatchDesc) + 255) & ~size_t(255);
+  const size_t off_map = (off_tab + ntab * 4 + 255) & ~size_t(255);
+  const size_t off_cnt = (off_map + total * sizeof(TileRec) + 255) & ~size_t(255);
+  const size_t bytes = off_cnt + 256;
+  if (b->arena) {
+    cudaFree(b->arena);
+    b->arena = nullptr;
+  }
+  e = cudaMalloc(&b->arena, bytes);
+  if (e != cudaSuccess) {
+    b->arena = nullptr;
+    return fail(TTC_ERR_OOM, "batch arena allocation failed");
+  }
+  char* base = static_cast<char*>(b->arena);
+  int32_t* d_tab = reinterpret_cast<int32_t*>(base + off_tab);
+  // fix the table pointers, build the tile map
+  std::vector<int32_t> alltab;
+  alltab.reserve(ntab);
+  std::vector<TileRec> map(total);
+  for (size_t i = 0; i < descs.size(); ++i) {
+    BatchDesc& d = descs[i];
+    if (d.path == BP_TILE) {
+      d.tp.tabA = d_tab + alltab.size();
+      d.tp.tabB = d_tab + alltab.size() + tab_sizeA[i];
+    }
+    alltab.insert(alltab.end(), tabs[i].begin(), tabs[i].end());
+    for (uint32_t q = 0; q < d.ntiles; ++q) {
+      TileRec& r = map[d.tile0 + q];
+      r.prob = uint32_t(i);
+      r.pad = 0;
+      if (d.path == BP_COPY) {
+        const RowCoord rc = row_coord(q, d.rp);
+        r.baseA = rc.offA;
+        r.baseB = rc.offB;
+        r.remA = int32_t(rc.start);
+        r.remB = int32_t(rc.end - rc.start);
+      } else {
+        const TileCoord c = tile_coord(q, d.tp);
+        r.baseA = c.baseA;
+        r.baseB = c.baseB;
+        r.remA = c.remA;
+        r.remB = c.remB;
+      }
+    }
+  }
+  e = cudaMemcpy(base, descs.data(), descs.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !alltab.empty())
+    e = cudaMemcpy(d_tab, alltab.data(), alltab.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && total)
+    e = cudaMemcpy(base + off_map, map.data(), total * sizeof(TileRec), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "batch upload");
+  b->arena_bytes = bytes;
+  b->d_descs = reinterpret_cast<BatchDesc*>(base);
+  b->d_recs = reinterpret_cast<TileRec*>(base + off_map);
+  b->d_counter = reinterpret_cast<uint32_t*>(base + off_cnt);
+  b->total = uint32_t(total);
+  b->smem = smem;
+  b->dev = dev;
+  const void* fn = reinterpret_cast<const void*>(&batch_kernel);
+  e = grid_for(fn, smem, int64_t(total), &b->grid);
+  if (e != cudaSuccess) return cuda_fail(e, "batch occupancy");
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  if (b->graph) {
+    cudaGraphDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->dirty = false;
+  return TTC_OK;
+}
+
+ttc_status batch_enqueue(ttc_batch_s* b, cudaStream_t s) {
+  if (b->total == 0) return TTC_OK;
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  batch_kernel<<<b->grid, kThreads, b->smem, s>>>(b->d_descs, b->d_recs, b->total, b->d_counter);
+  ++g_launches;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+  return TTC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ttc_status ttc_batch_create(ttc_batch_t* out) {
+  if (!out) return fail(TTC_ERR_INVALID_ARG, "out is NULL");
+  *out = new (std::nothrow) ttc_batch_s();
+  return *out ? TTC_OK : fail(TTC_ERR_OOM, "host allocation failed");
+}
+
+ttc_status ttc_batch_add(ttc_batch_t b, ttc_plan_t plan, const void* A, void* B) {
+  if (!b || !plan) return fail(TTC_ERR_INVALID_ARG, "NULL batch or plan");
+  if (!batch_pair_supported(plan->din, plan->dout))
+    return fail(TTC_ERR_UNSUPPORTED_DTYPE, "FP8 output is not supported in a batch");
+  if (plan->canon.n > 0) {
+    if (!A || !B) return fail(TTC_ERR_INVALID_ARG, "A or B is NULL");
+    const uintptr_t a = reinterpret_cast<uintptr_t>(A), bb = reinterpret_cast<uintptr_t>(B);
+    if (a % dtype_size(plan->din) || bb % dtype_size(plan->dout))
+      return fail(TTC_ERR_ALIGN, "A or B not aligned to its element size");
+    const uintptr_t ea = a + uintptr_t(plan->canon.spanA) * dtype_size(plan->din);
+    const uintptr_t eb = bb + uintptr_t(plan->canon.spanB) * dtype_size(plan->dout);
+    if (a < eb && bb < ea) return fail(TTC_ERR_ALIAS, "the byte ranges of A and B overlap");
+  }
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->items.push_back({plan, A, B});
+  b->dirty = true;
+  return TTC_OK;
+}
+
+ttc_status ttc_batch_execute(ttc_batch_t b, ttc_stream_t stream) {
+  if (!b) return fail(TTC_ERR_INVALID_ARG, "batch is NULL");
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (b->dirty) {
+    ttc_status st = batch_build(b);
+    if (st != TTC_OK) return st;
+  }
+  return batch_enqueue(b, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ttc_status ttc_batch_graph_launch(ttc_batch_t b, ttc_stream_t stream) {
+  if (!b) return fail(TTC_ERR_INVALID_ARG, "batch is NULL");
+  std::lock_guard<std::mutex> lk(b->mu);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (b->dirty) {
+    ttc_status st = batch_build(b);
+    if (st != TTC_OK) return st;
+  }
+  if (!b->gexec) {
+    // capture on a private stream so that the caller's stream may be any stream
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    const int64_t before = g_launches.load();
+    ttc_status st = batch_enqueue(b, cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    g_launches -= g_launches.load() - before;    // captured, not launched
+    if (st != TTC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      b->gexec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    b->graph = g;
+  }
+  cudaError_t e = cudaGraphLaunch(b->gexec, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  if (b->total) ++g_launches;
+  return TTC_OK;
+}
+
+ttc_status ttc_batch_destroy(ttc_batch_t b) {
+  if (!b) return fail(TTC_ERR_INVALID_ARG, "batch is NULL");
+  delete b;
+  return TTC_OK;
+}
+
+ttc_status ttc_batch_info(ttc_batch_t b, int64_t* problems, int64_t* tiles) {
+  if (!b) return fail(TTC_ERR_INVALID_ARG, "batch is NULL");
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (problems) *problems = int64_t(b->items.size());
+  if (tiles) {
+    int64_t t = 0;
+    for (auto& it : b->items) {
+      const ttc_plan_s* p = it.plan;
+      if (p->canon.n == 0) continue;
+      const std::vector<Candidate> bc =
+          make_candidates(p->canon, p->din, p->dout, p->beta, 4, kThreads * batch_k_for(p->din == DT_F64 ? 8 : 4));
+      const Candidate& k = bc.front();
+      if (k.variant == VAR_TILE) {
+        TileParams tp;
+        std::vector<int32_t> ta, tb;
+        int sm = 0;
+        build_tile_params(p->canon, k, p->din, &tp, &ta, &tb, &sm);
+        t += tp.ntiles;
+      } else {
+        RowParams rp;
+        build_row_params(p->canon, kBatchCopyChunk / (p->din == DT_F64 ? 2 : 1), &rp);
+        t += rp.nitems;
+      }
+    }
+    *tiles = t;
+  }
+  return TTC_OK;
+}
+
+}  // extern "C"

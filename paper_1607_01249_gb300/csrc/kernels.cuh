@@ -147,9 +147,34 @@ TTC_HD TileCoord tile_coord(uint32_t tid, const TileParams& p) {
   return c;
 }
 
+// The subset of a tile's parameters the walks and the epilogue read, for
+// kernels whose parameters are not kernel arguments (the batch): copied into
+// registers once per tile instead of being reloaded inside the element loops.
+struct WalkP {
+  int LC, LA, LB, U, W, P;
+  int32_t saU, sbV, crossA_lin, crossB_lin;
+  int rd_du, rd_dlb, wr_dlc, wr_dlb, wr_dla;
+  FastDiv divU, divLC, divLB;
+  const int32_t* tabA;
+  const int32_t* tabB;
+  Epilogue epi;
+};
+
+TTC_HD WalkP walk_params(const TileParams& t) {
+  WalkP w;
+  w.LC = t.LC; w.LA = t.LA; w.LB = t.LB; w.U = t.U; w.W = t.W; w.P = t.P;
+  w.saU = t.saU; w.sbV = t.sbV; w.crossA_lin = t.crossA_lin; w.crossB_lin = t.crossB_lin;
+  w.rd_du = t.rd_du; w.rd_dlb = t.rd_dlb; w.wr_dlc = t.wr_dlc; w.wr_dlb = t.wr_dlb; w.wr_dla = t.wr_dla;
+  w.divU = t.divU; w.divLC = t.divLC; w.divLB = t.divLB;
+  w.tabA = t.tabA; w.tabB = t.tabB;
+  w.epi = t.epi;
+  return w;
+}
+
 // The flat walks' first positions for thread t: read order (u, lb) and write
 // order (lc, lb, la), by multiply-high divisions.
-TTC_HD void flat_starts(const TileParams& p, int t, int& u0, int& lb0, int& lc0, int& lbw0, int& la0) {
+template <class PT>
+TTC_HD void flat_starts(const PT& p, int t, int& u0, int& lb0, int& lc0, int& lbw0, int& la0) {
   const uint32_t qu = fast_div(uint32_t(t), p.divU);
   u0 = t - int(qu) * p.U;
   lb0 = int(qu);
@@ -169,8 +194,8 @@ TTC_HD void flat_starts(const TileParams& p, int t, int& u0, int& lb0, int& lc0,
 // table instead of one multiply.
 //
 // Read order: (u, lb) with u = la*LC + lc; offset in A.
-template <int K, bool TAB, class F>
-TTC_HD void walk_read(const TileCoord& c, const TileParams& p, const int32_t* tabA, int u0, int lb0, F&& f) {
+template <int K, bool TAB, class PT, class F>
+TTC_HD void walk_read(const TileCoord& c, const PT& p, const int32_t* tabA, int u0, int lb0, F&& f) {
   const int limU = c.remA * p.LC;
   int u = u0, lb = lb0;
 #pragma unroll
@@ -187,8 +212,8 @@ TTC_HD void walk_read(const TileCoord& c, const TileParams& p, const int32_t* ta
 }
 
 // Write order: (lc, lb, la); offset in B.
-template <int K, bool TAB, class F>
-TTC_HD void walk_write(const TileCoord& c, const TileParams& p, const int32_t* tabB, int lc0, int lb0, int la0,
+template <int K, bool TAB, class PT, class F>
+TTC_HD void walk_write(const TileCoord& c, const PT& p, const int32_t* tabB, int lc0, int lb0, int la0,
                        F&& f) {
   int lc = lc0, lb = lb0, la = la0;
 #pragma unroll
@@ -213,8 +238,8 @@ TTC_HD void walk_write(const TileCoord& c, const TileParams& p, const int32_t* t
 // FULL: an interior tile (no cut index is short).  f(k, ok, offset, smem
 // position) as for the flat walks; rows past the tile's end are skipped
 // (warp-uniform), lanes past a run's end get ok == false.
-template <int JU, int K, bool FULL, bool TAB, class F>
-TTC_HD void walk2_read(const TileCoord& c, const TileParams& p, const int32_t* tabA, int lane, int warp,
+template <int JU, int K, bool FULL, bool TAB, class PT, class F>
+TTC_HD void walk2_read(const TileCoord& c, const PT& p, const int32_t* tabA, int lane, int warp,
                        F&& f) {
   constexpr int RR = K / JU;
   const int limU = FULL ? p.U : c.remA * p.LC;
@@ -237,8 +262,8 @@ TTC_HD void walk2_read(const TileCoord& c, const TileParams& p, const int32_t* t
 
 // per-lane constants of the write walk: shared-memory offset and B offset of
 // the lane's run positions v = lane + 32 j
-template <int JW>
-TTC_HD void walk2_lane_consts(const TileParams& p, int lane, int (&spre)[JW], int32_t (&voff)[JW]) {
+template <int JW, class PT>
+TTC_HD void walk2_lane_consts(const PT& p, int lane, int (&spre)[JW], int32_t (&voff)[JW]) {
 #pragma unroll
   for (int j = 0; j < JW; ++j) {
     const int vv = lane + 32 * j;
@@ -248,8 +273,8 @@ TTC_HD void walk2_lane_consts(const TileParams& p, int lane, int (&spre)[JW], in
   }
 }
 
-template <int JW, int K, bool FULL, bool TAB, class F>
-TTC_HD void walk2_write(const TileCoord& c, const TileParams& p, const int32_t* tabB, int lane, int warp,
+template <int JW, int K, bool FULL, bool TAB, class PT, class F>
+TTC_HD void walk2_write(const TileCoord& c, const PT& p, const int32_t* tabB, int lane, int warp,
                         const int (&spre)[JW], const int32_t (&voff)[JW], F&& f) {
   constexpr int RW = K / JW;
   const int limV = FULL ? p.W : c.remB * p.LC;
@@ -273,8 +298,8 @@ TTC_HD void walk2_write(const TileCoord& c, const TileParams& p, const int32_t* 
 // LC = the shared stride-1 index, LA consecutive indices of the next A index,
 // contiguous in A; thread t takes the flat positions u = t + kThreads*k.
 // f(k, A offset in tile, B offset in tile).
-template <int K, class F>
-TTC_HD void walk_rows(const TileCoord& c, const TileParams& p, int t, F&& f) {
+template <int K, class PT, class F>
+TTC_HD void walk_rows(const TileCoord& c, const PT& p, int t, F&& f) {
   const int limU = c.remA * p.LC;
   const int q = int(fast_div(uint32_t(t), p.divLC));
   int u = t, la = q, lc = t - q * p.LC;

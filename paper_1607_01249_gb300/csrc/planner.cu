@@ -264,7 +264,7 @@ std::vector<int> grid_order(const Canon& c, const int64_t* ext, int mode) {
 
 }  // namespace
 
-std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double beta, int max_keep) {
+std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double beta, int max_keep, int vmax) {
   std::vector<Candidate> out;
   if (c.N == 0) {
     out.push_back(Candidate());
@@ -299,9 +299,12 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
     const double rows = n / double(len);
     const double lanes_per_row = std::ceil(double(len) / (32.0 * k.vec)) * 32.0;
     const double issue = (rows * lanes_per_row * 10.0 + rows * 32.0 * (8.0 * c.N)) / kLaneInstrPerS;
-    // one warp per row chunk: short rows leave few loads in flight per warp
-    const double mlp = std::min(1.0, double(len) / (32.0 * 4 * k.vec));
-    k.est_s = std::max(mem / std::max(mlp, 0.1), issue) + 0.2 * std::min(mem, issue) + 2e-6;
+    // one warp per row chunk: short rows leave few loads in flight per warp,
+    // and scalar rows sustain less than the tile kernels (measured ~0.6x of
+    // the multi-row copy for runs of a few hundred elements)
+    const double mlp = std::min(1.0, double(len) / (32.0 * 8 * k.vec));
+    const double scalar_penalty = (k.vec > 1 || len > 4096) ? 1.0 : 1.6;
+    k.est_s = std::max(mem / std::max(mlp, 0.1), issue) * scalar_penalty + 0.2 * std::min(mem, issue) + 2e-6;
     if (k.variant == VAR_COPY) out.push_back(k);
   }
 
@@ -309,7 +312,8 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
   // indices of A's next index make one contiguous block of A per tile
   if (c.perm[0] == 0 && c.N >= 2 && c.sa[0] == 1 && c.sb[0] == 1 && c.sa[1] == c.s[0]) {
     const int Kt = tile_k_for(din == DT_F64 ? 8 : 4);
-    const int64_t cap = int64_t(kThreads) * Kt / c.s[0];
+    const int64_t vcap = vmax > 0 ? std::min<int64_t>(vmax, int64_t(kThreads) * Kt) : int64_t(kThreads) * Kt;
+    const int64_t cap = vcap / c.s[0];
     if (cap >= 2) {
       for (int G : cut_options(c.s[1], cap)) {
         Candidate k;
@@ -332,7 +336,7 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
                             n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true)) / kHbmBytesPerS;
         const double issue = ntiles * kThreads * Kt * (10.0 + (bnz ? 3 : 0)) / kLaneInstrPerS;
         const double over = ntiles * kThreads * (40.0 + 10.0 * c.N) / kLaneInstrPerS;
-        const double fill = double(c.s[0]) * G / double(kThreads * Kt);   // share of the unrolled slots in use
+        const double fill = double(c.s[0]) * G / double(vcap);   // share of the unrolled slots in use
         k.est_s = std::max(mem, issue / std::max(fill, 0.05)) + 0.1 * std::min(mem, issue) + over + 3e-6;
         out.push_back(k);
       }
@@ -344,7 +348,7 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
   const int c0 = hc ? 1 : 0;
   const int64_t LC = hc ? c.s[0] : 1;
   const int Kt = tile_k_for(din == DT_F64 ? 8 : 4);
-  const int Vmax = kThreads * Kt;
+  const int Vmax = vmax > 0 ? std::min(vmax, kThreads * Kt) : kThreads * Kt;
   std::vector<Candidate> tiles;
   if (!(hc && c.N == 1) && LC * 2 <= Vmax) {
     // A-group index list: A order from c0, dense, never B's first index after C

@@ -52,7 +52,8 @@ int canonicalize(int ndim, const int* perm, const int64_t* sizes, const int64_t*
                  const int64_t* outerB, Canon* c, std::string* err);
 
 // Candidate schedules, best estimate first (at most max_keep).
-std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double beta, int max_keep);
+// vmax > 0 caps the tile volume (elements) below the single-plan kernels' cap.
+std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double beta, int max_keep, int vmax = 0);
 
 // Kernel parameters of a candidate.  Host tables (crossA, crossB) are
 // returned in tabA/tabB; the device pointers are filled in by the caller.

@@ -64,6 +64,12 @@ SIGNATURES = {
     "ttc_last_error": (ctypes.c_char_p, []),
     "ttc_launch_count": (ctypes.c_int64, []),
     "ttc_execute_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ttc_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp)]),
+    "ttc_batch_add": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "ttc_batch_execute": (ctypes.c_int, [_vp, _vp]),
+    "ttc_batch_graph_launch": (ctypes.c_int, [_vp, _vp]),
+    "ttc_batch_destroy": (ctypes.c_int, [_vp]),
+    "ttc_batch_info": (ctypes.c_int, [_vp, _i64p, _i64p]),
     # include/ttc_debug.h
     "ttc_debug_verify_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
 }
@@ -200,6 +206,45 @@ class Plan:
         if getattr(self, "_h", None):
             lib().ttc_plan_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many permute-scale-adds in one persistent kernel launch (ttc_batch_*).
+    The batch keeps references to its plans so that they outlive it."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(lib().ttc_batch_create(ctypes.byref(h)))
+        self._h = h
+        self._keep = []
+
+    def add(self, plan: Plan, A, B):
+        _check(lib().ttc_batch_add(self._h, plan.handle, _ptr(A), _ptr(B)))
+        self._keep.append((plan, A, B))
+        return self
+
+    def execute(self, stream=None):
+        _check(lib().ttc_batch_execute(self._h, _stream(stream)))
+
+    def graph_launch(self, stream=None):
+        _check(lib().ttc_batch_graph_launch(self._h, _stream(stream)))
+
+    def info(self):
+        p, t = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().ttc_batch_info(self._h, ctypes.byref(p), ctypes.byref(t)))
+        return {"problems": p.value, "tiles": t.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ttc_batch_destroy(self._h)
+            self._h = None
+        self._keep = []
 
     def __del__(self):
         try:
