@@ -418,6 +418,147 @@ def run_batch(args, rank, world):
     }
 
 
+def serve_trace(srv, ttc, trace, plans, pa, pb, paced: bool):
+    """Submit the trace's requests at their arrival times (paced) or all at
+    once, wait for every one, and return per-request latency from arrival
+    (microseconds), the served wall time and the largest submission lag."""
+    t0 = time.perf_counter() + 2e-3
+    tickets, lag, sub_perf = [], 0.0, []
+    for (ta, _), pl, a, b in zip(trace, plans, pa, pb):
+        if paced:
+            target = t0 + ta
+            while time.perf_counter() < target:
+                pass
+        else:
+            target = t0
+        now = time.perf_counter()
+        tickets.append(srv.submit(pl, a, b))
+        sub_perf.append(now)
+        lag = max(lag, now - target)
+    srv.drain(600_000_000)
+    lat, first, last, detail = [], None, None, []
+    for (ta, _), t, sp in zip(trace, tickets, sub_perf):
+        s_sub, s_launch, s_done = srv.times(t)
+        arrival = (t0 + ta) if paced else t0
+        lat.append(((s_done - s_sub) + (sp - arrival)) * 1e6)
+        detail.append(((s_launch - s_sub) * 1e6, (s_done - s_launch) * 1e6))
+        first = s_sub if first is None else min(first, s_sub)
+        last = s_done if last is None else max(last, s_done)
+    serve_trace.detail = detail
+    return np.array(lat), last - first, lag
+
+
+def run_serving(args, rank, world):
+    """Requests arriving over time (Poisson), served by the continuous-batching
+    server (ttc_server_*) and, for comparison, one launch per request in
+    arrival order on one stream.  Plans and buffers stay on the device."""
+    import torch
+    from paper_1607_01249_gb300 import build as ttc_build
+    from paper_1607_01249_gb300 import ttc
+
+    ttc_build.build()
+    ttc.lib()
+    dev = rank % max(torch.cuda.device_count(), 1)
+    torch.cuda.set_device(dev)
+    trace = inputs.serving_requests(args.serve_count, seed=4, rate_per_s=args.serve_rate)
+    probs = [p for _, p in trace]
+    plans = [ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta, p.outer_a, p.outer_b)
+             for p in probs]
+    # A: one shared read-only region, each request reading a slice of it;
+    # B: a buffer of its own per request (the results of concurrent requests
+    # never share bytes)
+    span_a = [p.vol_a * inputs.DTYPE_BYTES[p.dtype_in] for p in probs]
+    span_b = [(p.vol_b * inputs.DTYPE_BYTES[p.dtype_out] + 255) // 256 * 256 for p in probs]
+    region_a = max(max(span_a) + (64 << 20), 1 << 30)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    A = torch.empty(region_a // 4, dtype=torch.float32, device="cuda").uniform_(-1, 1, generator=g)
+    B = torch.zeros(sum(span_b) // 4, dtype=torch.float32, device="cuda")
+    h = inputs.rng(12)
+    pa = [A.data_ptr() + int(h.integers(0, (region_a - sa) // 256 + 1)) * 256 for sa in span_a]
+    offs = np.concatenate([[0], np.cumsum(span_b)[:-1]]).astype(np.int64)
+    pb = [B.data_ptr() + int(o) for o in offs]
+    torch.cuda.synchronize()
+    bytes_trace = sum(p.algorithmic_bytes() for p in probs)
+    budget = int(args.serve_budget_gb * 1e9)
+    arms = {"continuous": (args.serve_streams, args.serve_small_tiles), "per_call": (1, 0)}
+    res = {}
+    clk = ClockSampler(dev) if rank == 0 else None
+    for name, (ns, small) in arms.items():
+        warm = ttc.Server(budget, ns, small)         # plans' device resources, batch descriptions
+        serve_trace(warm, ttc, trace, plans, pa, pb, paced=False)
+        warm.close()
+        srv = ttc.Server(budget, ns, small)
+        l0 = ttc.launch_count()
+        if clk and name == "continuous":
+            clk.start()
+        lat_all, lags, walls = [], [], []
+        for _ in range(args.steps):
+            lat, wall, lag = serve_trace(srv, ttc, trace, plans, pa, pb, paced=True)
+            if args.serve_dump:
+                with open(f"{args.serve_dump}.{name}.json", "w") as f:
+                    json.dump([{"perm": p.perm, "sizes": p.sizes, "din": p.dtype_in, "dout": p.dtype_out,
+                                "outer": p.outer_a is not None, "bytes": p.algorithmic_bytes(),
+                                "kernel": pl.info()["kernel"], "lat_us": round(float(l), 1),
+                                "queue_us": round(d[0], 1), "run_us": round(d[1], 1)}
+                               for p, pl, l, d in zip(probs, plans, lat, serve_trace.detail)], f)
+            lat_all.append(lat)
+            lags.append(lag)
+            walls.append(wall)
+        clocks = clk.stop() if (clk and name == "continuous") else None
+        st = srv.stats()
+        launches = ttc.launch_count() - l0
+        srv.close()
+        sat = ttc.Server(budget, ns, small)
+        _, sat_wall, _ = serve_trace(sat, ttc, trace, plans, pa, pb, paced=False)
+        sat.close()
+        lat = np.concatenate(lat_all)
+        res[name] = {
+            "offered_req_per_s": args.serve_rate,
+            "served_transposes_per_s": round(len(probs) / float(np.mean(walls)), 1),
+            "served_GB/s": round(bytes_trace / float(np.mean(walls)) / 1e9, 1),
+            "p50_us": round(float(np.percentile(lat, 50)), 1), "p90_us": round(float(np.percentile(lat, 90)), 1),
+            "p99_us": round(float(np.percentile(lat, 99)), 1), "max_us": round(float(lat.max()), 1),
+            "max_submit_lag_us": round(max(lags) * 1e6, 1),
+            "saturated_transposes_per_s": round(len(probs) / sat_wall, 1),
+            "saturated_GB/s": round(bytes_trace / sat_wall / 1e9, 1),
+            "epochs": st["epochs"], "kernel_launches": launches, "peak_inflight_GB": round(st["peak_inflight_bytes"] / 1e9, 2),
+            "streams": ns, "small_tiles": small, "clocks": clocks,
+        }
+        log(name, json.dumps(res[name]))
+    c, q = res["continuous"], res["per_call"]
+    return {
+        "workload": (f"serving: {len(probs)} requests, Poisson {args.serve_rate:g} req/s, A 4 KiB..512 MiB "
+                     "log-uniform, N 2..6, f32/f64/bf16 50/20/30, 10% packing f32->bf16 with outer sizes, "
+                     f"admission budget {args.serve_budget_gb:g} GB; {args.steps} paced passes of the trace "
+                     "per arm, host steady clock from arrival to detected completion"),
+        "algorithmic_bytes_per_trace": bytes_trace,
+        "continuous": c, "per_call": q,
+        "p99_ratio_per_call_over_continuous": round(q["p99_us"] / c["p99_us"], 3),
+        "saturated_speedup_vs_per_call": round(c["saturated_transposes_per_s"] / q["saturated_transposes_per_s"], 3),
+    }
+
+
+def run_serving_line(args, rank, world):
+    s = run_serving(args, rank, world)
+    c = s["continuous"]
+    peak, _ = measured_peaks()
+    return {
+        "metric": METRIC, "value": c["saturated_GB/s"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": 1, "ms_per_step": round(1e3 * args.serve_count / c["served_transposes_per_s"], 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64+bf16",
+        "data": "synthetic (seeded trace; uniform data)",
+        "config": {"workload": s["workload"], "parallelism": f"replicas x{world}",
+                   "timing": "host steady clock (served throughput and latency are host-observed)"},
+        "serving": s,
+        "roofline": {"bound": "hbm", "achieved": c["saturated_GB/s"], "peak": peak, "unit": "GB/s",
+                     "frac": round(c["saturated_GB/s"] / peak, 4), "kernel": "whole served trace",
+                     "traffic": None},
+        "gpu_launches": c["kernel_launches"],
+        "clocks": c["clocks"],
+    }
+
+
 def run_e2e(args, probs, plans, bufs, stream, world):
     """Same metric with host (pinned) inputs: every step copies A (and B when
     beta != 0) host->device, runs the plan, and copies B back."""
@@ -561,7 +702,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "single4d", "packing", "batch"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "single4d", "packing", "batch", "serving"])
+    ap.add_argument("--serve-count", type=int, default=1500)
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-small-tiles", type=int, default=1024)
+    ap.add_argument("--serve-dump", default="", help="write per-request latencies (JSON) to <path>.<arm>.json")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--autotune", type=int, default=0, help="time up to this many candidates per plan first")
     ap.add_argument("--no-e2e", action="store_true")
@@ -585,9 +732,14 @@ def main():
         import torch.distributed as tdist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
         tdist.init_process_group("nccl")
-    out = run_batch(args, rank, world) if args.workload == "batch" else run_ours(args, rank, world)
+    if args.workload == "batch":
+        out = run_batch(args, rank, world)
+    elif args.workload == "serving":
+        out = run_serving_line(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
     if rank == 0:
-        if not args.no_cpu and world == 1 and args.workload != "batch":
+        if not args.no_cpu and world == 1 and args.workload not in ("batch", "serving"):
             out["cpu_baseline"] = cpu_baseline(args.cpu_budget,
                                                workload_problems(args.workload, args.target, args.only),
                                                os.cpu_count() or 1)

@@ -235,6 +235,67 @@ ttc_status ttc_batch_destroy(ttc_batch_t batch);
 ttc_status ttc_batch_info(ttc_batch_t batch, int64_t* problems, int64_t* tiles);
 
 /*
+ * Server: continuous batching of permute-scale-add requests (Eq. 1) that
+ * arrive over time.  A scheduler thread admits pending requests in arrival
+ * order while the bytes of admitted, unfinished requests (A's and B's
+ * sub-tensor spans) stay within `budget_bytes`, groups what it admitted into
+ * an epoch and launches it on a stream: consecutive requests of at most
+ * `small_tiles` tiles go together into one batched persistent launch (see
+ * ttc_batch_*), other requests get their own launch.  Epochs on different
+ * streams run concurrently, so requests that arrive while others are on the
+ * GPU start as soon as budget and a stream allow.  Requests fall into three
+ * size classes (batchable; up to 64 MB of algorithmic bytes; larger), each
+ * with `nstreams` streams of its own, the smaller classes at higher stream
+ * priority, so that small requests are not held behind the thread blocks of
+ * large ones.  A completion thread detects finished epochs (event queries),
+ * releases their budget and stamps each request's latency (submission to
+ * detected completion).
+ *
+ *  ttc_server_create   budget_bytes > 0; nstreams 1..16; small_tiles >= 0.
+ *                      small_tiles = 0 turns batching and size classes off:
+ *                      every request gets its own launch, in arrival order
+ *                      over `nstreams` streams of default priority.  Uses the
+ *                      current device.  Allocates its own streams, events,
+ *                      pinned staging and device descriptor slots.
+ *  ttc_server_submit   enqueue (plan, A, B); returns a ticket.  A and B are
+ *                      device pointers owned by the caller and must stay
+ *                      valid until the request completes; the plan must
+ *                      outlive the request.  TTC_ERR_BUDGET if the request
+ *                      alone exceeds the budget.  FP8 plans run one at a
+ *                      time per plan (their amax scratch belongs to the plan).
+ *  ttc_server_poll     wait up to timeout_us microseconds (0: do not wait)
+ *                      for the ticket: TTC_OK when it completed,
+ *                      TTC_ERR_NOT_READY if it has not, TTC_ERR_TIMEOUT if the
+ *                      watchdog gave it up, another status if it failed.
+ *  ttc_server_drain    wait until every submitted request has completed
+ *                      (bounded by timeout_us; TTC_ERR_TIMEOUT otherwise).
+ *  ttc_server_stats    counters and latency percentiles of completed requests.
+ *  ttc_server_times    submission time, launch time (when its kernel was
+ *                      enqueued) and detected-completion time of one request
+ *                      (host steady clock, seconds); TTC_ERR_NOT_READY until
+ *                      it has completed.
+ *  ttc_server_destroy  drain, stop the threads, free everything.
+ */
+typedef struct ttc_server_s* ttc_server_t;
+
+typedef struct {
+    int64_t submitted, completed, failed, epochs, launches;
+    int64_t bytes;                 /* algorithmic bytes of the completed requests */
+    double p50_us, p90_us, p99_us, max_us, mean_us;   /* latency of completed requests */
+    double first_submit_s, last_complete_s;           /* host clock, seconds */
+    int64_t peak_inflight_bytes;   /* largest admitted-and-unfinished byte count seen */
+} ttc_server_stats_t;
+
+ttc_status ttc_server_create(ttc_server_t* out, int64_t budget_bytes, int nstreams, int64_t small_tiles);
+ttc_status ttc_server_submit(ttc_server_t server, ttc_plan_t plan, const void* A, void* B, int64_t* ticket);
+ttc_status ttc_server_poll(ttc_server_t server, int64_t ticket, int64_t timeout_us);
+ttc_status ttc_server_drain(ttc_server_t server, int64_t timeout_us);
+ttc_status ttc_server_stats(ttc_server_t server, ttc_server_stats_t* stats);
+ttc_status ttc_server_times(ttc_server_t server, int64_t ticket, double* submit_s, double* launch_s,
+                            double* complete_s);
+ttc_status ttc_server_destroy(ttc_server_t server);
+
+/*
  * ttc_execute_noalloc -- ttc_execute for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a deployment aid of this
  * library.

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/ttc.h"
+#include "batch_impl.h"
 #include "kernels.cuh"
 #include "launch.h"
 #include "plan_impl.h"
@@ -30,34 +31,6 @@ namespace ttc {
 
 extern std::atomic<int64_t> g_launches;
 cudaError_t grid_for(const void* fn, int smem, int64_t work, int* grid);
-
-enum BatchPath : int { BP_TILE = 0, BP_ROWS = 1, BP_COPY = 2 };
-
-struct alignas(16) BatchDesc {
-  const void* A;
-  void* B;
-  int din, dout, path, pad;
-  uint32_t tile0;    // first global tile of this problem
-  uint32_t ntiles;
-  TileParams tp;     // BP_TILE, BP_ROWS
-  RowParams rp;      // BP_COPY
-};
-
-constexpr int kBatchCopyChunk = 2048;   // elements of a run per BP_COPY tile
-
-// elements per thread per phase in the batch body: half of the single-plan
-// kernels' (tiles of at most 2048 four-byte or 1024 eight-byte elements), so
-// that the descriptor fields fit in registers next to the staged data
-constexpr int batch_k_for(int stage_bytes) { return tile_k_for(stage_bytes) / 2; }
-
-// Where one tile of the batch lies, precomputed on the host so that a CTA
-// needs one load to start on a claimed tile.  For BP_COPY: baseA/baseB are
-// the run's offsets, remA the first element of the chunk, remB its length.
-struct TileRec {
-  uint32_t prob;
-  int32_t remA, remB, pad;
-  int64_t baseA, baseB;
-};
 
 // --------------------------------------------------------------- device --
 
@@ -71,7 +44,7 @@ __device__ __forceinline__ void batch_tile(const BatchDesc& d, const TileCoord& 
   const store_t<DIN>* Ab = static_cast<const store_t<DIN>*>(d.A) + c.baseA;
   TO* Bb = static_cast<TO*>(d.B) + c.baseB;
   S v[K];
-  TO bo[K];
+  TO bo[K] = {};
   if (d.path == BP_ROWS) {
     walk_rows<K>(c, p, t, [&](int k, bool, int32_t offA, int32_t offB) {
       v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + offA));
@@ -109,7 +82,7 @@ __device__ __forceinline__ void batch_copy(const BatchDesc& d, const RowCoord& r
   const store_t<DIN>* Ar = static_cast<const store_t<DIN>*>(d.A) + rc.offA;
   TO* Br = static_cast<TO*>(d.B) + rc.offB;
   S v[K];
-  TO bo[K];
+  TO bo[K] = {};
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int64_t x = rc.start + t + int64_t(k) * kThreads;
@@ -199,6 +172,122 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc* __r
 
 // ------------------------------------------------------------------ host --
 
+namespace ttc {
+
+namespace {
+
+std::shared_ptr<const BatchTemplate> make_template(const ttc_plan_s* p) {
+  auto t = std::make_shared<BatchTemplate>();
+  if (p->canon.n == 0 || p->dout == DT_E4M3) return t;
+  BatchDesc* d = &t->d;
+  std::memset(d, 0, sizeof(*d));
+  d->din = p->din;
+  d->dout = p->dout;
+  // tiles for the batch body: the best schedule with at most its tile volume
+  const std::vector<Candidate> bc =
+      make_candidates(p->canon, p->din, p->dout, p->beta, 4, kThreads * batch_k_for(p->din == DT_F64 ? 8 : 4));
+  const Candidate& k = bc.front();
+  if (k.variant == VAR_TILE) {
+    std::vector<int32_t> ta, tb;
+    int sm = 0;
+    build_tile_params(p->canon, k, p->din, &d->tp, &ta, &tb, &sm);
+    d->path = k.rows ? BP_ROWS : BP_TILE;
+    if (d->path == BP_TILE) {
+      // the batch body always reads both cross offsets from tables
+      if (!d->tp.crossA_tab) {
+        ta.resize(d->tp.LB);
+        for (int i = 0; i < d->tp.LB; ++i) ta[i] = i * d->tp.crossA_lin;
+        d->tp.crossA_tab = 1;
+      }
+      if (!d->tp.crossB_tab) {
+        tb.resize(d->tp.LA);
+        for (int i = 0; i < d->tp.LA; ++i) tb[i] = i * d->tp.crossB_lin;
+        d->tp.crossB_tab = 1;
+      }
+      t->smem = d->tp.P * d->tp.LB * (p->din == DT_F64 ? 8 : 4);
+      t->tabA_count = ta.size();
+      t->tabs.insert(t->tabs.end(), ta.begin(), ta.end());
+      t->tabs.insert(t->tabs.end(), tb.begin(), tb.end());
+    }
+    d->ntiles = d->tp.ntiles;
+    d->tp.epi = make_epilogue(p, nullptr);
+  } else {
+    build_row_params(p->canon, kBatchCopyChunk / (p->din == DT_F64 ? 2 : 1), &d->rp);
+    d->path = BP_COPY;
+    d->ntiles = d->rp.nitems;
+    d->rp.epi = make_epilogue(p, nullptr);
+  }
+  t->ok = true;
+  return t;
+}
+
+}  // namespace
+
+namespace {
+
+std::shared_ptr<const BatchTemplate> plan_template(ttc_plan_s* p) {
+  std::lock_guard<std::mutex> lk(p->batch_mu);
+  if (!p->batch_tmpl) p->batch_tmpl = make_template(p);
+  return p->batch_tmpl;
+}
+
+}  // namespace
+
+int64_t batch_tiles(ttc_plan_s* p) {
+  const std::shared_ptr<const BatchTemplate> t = plan_template(p);
+  return t->ok ? int64_t(t->d.ntiles) : -1;
+}
+
+bool batch_describe(ttc_plan_s* p, const void* A, void* B, BatchDesc* d, std::vector<int32_t>* tabs,
+                    size_t* tabA_count, int* smem) {
+  const std::shared_ptr<const BatchTemplate> t = plan_template(p);
+  if (!t->ok) return false;
+  *d = t->d;
+  d->A = A;
+  d->B = B;
+  *tabA_count = t->tabA_count;
+  tabs->insert(tabs->end(), t->tabs.begin(), t->tabs.end());
+  *smem = std::max(*smem, t->smem);
+  return true;
+}
+
+void batch_records(const BatchDesc& d, uint32_t prob, std::vector<TileRec>* recs) {
+  for (uint32_t q = 0; q < d.ntiles; ++q) {
+    TileRec r;
+    r.prob = prob;
+    r.pad = 0;
+    if (d.path == BP_COPY) {
+      const RowCoord rc = row_coord(q, d.rp);
+      r.baseA = rc.offA;
+      r.baseB = rc.offB;
+      r.remA = int32_t(rc.start);
+      r.remB = int32_t(rc.end - rc.start);
+    } else {
+      const TileCoord c = tile_coord(q, d.tp);
+      r.baseA = c.baseA;
+      r.baseB = c.baseB;
+      r.remA = c.remA;
+      r.remB = c.remB;
+    }
+    recs->push_back(r);
+  }
+}
+
+cudaError_t batch_launch(const BatchDesc* d_descs, const TileRec* d_recs, uint32_t total, uint32_t* d_counter,
+                         int smem, cudaStream_t s) {
+  if (total == 0) return cudaSuccess;
+  int grid = 0;
+  cudaError_t e = grid_for(reinterpret_cast<const void*>(&batch_kernel), smem, int64_t(total), &grid);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  batch_kernel<<<grid, kThreads, smem, s>>>(d_descs, d_recs, total, d_counter);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace ttc
+
 using namespace ttc;
 
 struct ttc_batch_s {
@@ -218,7 +307,6 @@ struct ttc_batch_s {
   uint32_t* d_counter = nullptr;
   uint32_t total = 0;
   int smem = 0;
-  int grid = 0;
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   ~ttc_batch_s() {
@@ -238,66 +326,27 @@ ttc_status batch_build(ttc_batch_s* b) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   std::vector<BatchDesc> descs;
-  std::vector<std::vector<int32_t>> tabs;   // per problem: tabA then tabB
-  std::vector<size_t> tab_sizeA;
+  std::vector<int32_t> tabs;
+  std::vector<size_t> tab_at, tab_na;
   descs.reserve(b->items.size());
   uint64_t total = 0;
   int smem = 0;
   for (auto& it : b->items) {
-    ttc_plan_s* p = it.plan;
-    if (p->canon.n == 0) continue;
     BatchDesc d;
-    std::memset(&d, 0, sizeof(d));
-    d.A = it.A;
-    d.B = it.B;
-    d.din = p->din;
-    d.dout = p->dout;
-    // tiles for the batch body: the best schedule with at most the batch's
-    // tile volume
-    const std::vector<Candidate> bc =
-        make_candidates(p->canon, p->din, p->dout, p->beta, 4, kThreads * batch_k_for(p->din == DT_F64 ? 8 : 4));
-    const Candidate& k = bc.front();
-    std::vector<int32_t> ta, tb;
-    if (k.variant == VAR_TILE) {
-      int sm = 0;
-      build_tile_params(p->canon, k, p->din, &d.tp, &ta, &tb, &sm);
-      d.path = k.rows ? BP_ROWS : BP_TILE;
-      if (d.path == BP_TILE) {
-        // the batch body always reads both cross offsets from tables
-        if (!d.tp.crossA_tab) {
-          ta.resize(d.tp.LB);
-          for (int i = 0; i < d.tp.LB; ++i) ta[i] = i * d.tp.crossA_lin;
-          d.tp.crossA_tab = 1;
-        }
-        if (!d.tp.crossB_tab) {
-          tb.resize(d.tp.LA);
-          for (int i = 0; i < d.tp.LA; ++i) tb[i] = i * d.tp.crossB_lin;
-          d.tp.crossB_tab = 1;
-        }
-        smem = std::max(smem, d.tp.P * d.tp.LB * (p->din == DT_F64 ? 8 : 4));
-      }
-      d.ntiles = d.tp.ntiles;
-      d.tp.epi = make_epilogue(p, nullptr);
-    } else {
-      build_row_params(p->canon, kBatchCopyChunk / (p->din == DT_F64 ? 2 : 1), &d.rp);
-      d.path = BP_COPY;
-      d.ntiles = d.rp.nitems;
-      d.rp.epi = make_epilogue(p, nullptr);
-    }
+    size_t na = 0;
+    const size_t at = tabs.size();
+    if (!batch_describe(it.plan, it.A, it.B, &d, &tabs, &na, &smem)) continue;
     d.tile0 = uint32_t(total);
     total += d.ntiles;
     if (total >= 0x7fffffffull) return fail(TTC_ERR_INVALID_SIZE, "batch has too many tiles");
-    tab_sizeA.push_back(ta.size());
-    ta.insert(ta.end(), tb.begin(), tb.end());
-    tabs.push_back(std::move(ta));
     descs.push_back(d);
+    tab_at.push_back(at);
+    tab_na.push_back(na);
   }
   // arena: descriptors | tables | tile records | counter
-  size_t ntab = 0;
-  for (auto& t : tabs) ntab += t.size();
   const size_t off_tab = (descs.size() * sizeof(BatchDesc) + 255) & ~size_t(255);
-  const size_t off_map = (off_tab + ntab * 4 + 255) & ~size_t(255);
-  const size_t off_cnt = (off_map + total * sizeof(TileRec) + 255) & ~size_t(255);
+  const size_t off_rec = (off_tab + tabs.size() * 4 + 255) & ~size_t(255);
+  const size_t off_cnt = (off_rec + total * sizeof(TileRec) + 255) & ~size_t(255);
   const size_t bytes = off_cnt + 256;
   if (b->arena) {
     cudaFree(b->arena);
@@ -310,52 +359,28 @@ ttc_status batch_build(ttc_batch_s* b) {
   }
   char* base = static_cast<char*>(b->arena);
   int32_t* d_tab = reinterpret_cast<int32_t*>(base + off_tab);
-  // fix the table pointers, build the tile map
-  std::vector<int32_t> alltab;
-  alltab.reserve(ntab);
-  std::vector<TileRec> map(total);
+  std::vector<TileRec> recs;
+  recs.reserve(total);
   for (size_t i = 0; i < descs.size(); ++i) {
     BatchDesc& d = descs[i];
     if (d.path == BP_TILE) {
-      d.tp.tabA = d_tab + alltab.size();
-      d.tp.tabB = d_tab + alltab.size() + tab_sizeA[i];
+      d.tp.tabA = d_tab + tab_at[i];
+      d.tp.tabB = d_tab + tab_at[i] + tab_na[i];
     }
-    alltab.insert(alltab.end(), tabs[i].begin(), tabs[i].end());
-    for (uint32_t q = 0; q < d.ntiles; ++q) {
-      TileRec& r = map[d.tile0 + q];
-      r.prob = uint32_t(i);
-      r.pad = 0;
-      if (d.path == BP_COPY) {
-        const RowCoord rc = row_coord(q, d.rp);
-        r.baseA = rc.offA;
-        r.baseB = rc.offB;
-        r.remA = int32_t(rc.start);
-        r.remB = int32_t(rc.end - rc.start);
-      } else {
-        const TileCoord c = tile_coord(q, d.tp);
-        r.baseA = c.baseA;
-        r.baseB = c.baseB;
-        r.remA = c.remA;
-        r.remB = c.remB;
-      }
-    }
+    batch_records(d, uint32_t(i), &recs);
   }
   e = cudaMemcpy(base, descs.data(), descs.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !alltab.empty())
-    e = cudaMemcpy(d_tab, alltab.data(), alltab.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !tabs.empty()) e = cudaMemcpy(d_tab, tabs.data(), tabs.size() * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && total)
-    e = cudaMemcpy(base + off_map, map.data(), total * sizeof(TileRec), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(base + off_rec, recs.data(), total * sizeof(TileRec), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "batch upload");
   b->arena_bytes = bytes;
   b->d_descs = reinterpret_cast<BatchDesc*>(base);
-  b->d_recs = reinterpret_cast<TileRec*>(base + off_map);
+  b->d_recs = reinterpret_cast<TileRec*>(base + off_rec);
   b->d_counter = reinterpret_cast<uint32_t*>(base + off_cnt);
   b->total = uint32_t(total);
   b->smem = smem;
   b->dev = dev;
-  const void* fn = reinterpret_cast<const void*>(&batch_kernel);
-  e = grid_for(fn, smem, int64_t(total), &b->grid);
-  if (e != cudaSuccess) return cuda_fail(e, "batch occupancy");
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
@@ -370,11 +395,7 @@ ttc_status batch_build(ttc_batch_s* b) {
 
 ttc_status batch_enqueue(ttc_batch_s* b, cudaStream_t s) {
   if (b->total == 0) return TTC_OK;
-  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), s);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-  batch_kernel<<<b->grid, kThreads, b->smem, s>>>(b->d_descs, b->d_recs, b->total, b->d_counter);
-  ++g_launches;
-  e = cudaGetLastError();
+  cudaError_t e = batch_launch(b->d_descs, b->d_recs, b->total, b->d_counter, b->smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
   return TTC_OK;
 }
@@ -474,22 +495,11 @@ ttc_status ttc_batch_info(ttc_batch_t b, int64_t* problems, int64_t* tiles) {
   if (tiles) {
     int64_t t = 0;
     for (auto& it : b->items) {
-      const ttc_plan_s* p = it.plan;
-      if (p->canon.n == 0) continue;
-      const std::vector<Candidate> bc =
-          make_candidates(p->canon, p->din, p->dout, p->beta, 4, kThreads * batch_k_for(p->din == DT_F64 ? 8 : 4));
-      const Candidate& k = bc.front();
-      if (k.variant == VAR_TILE) {
-        TileParams tp;
-        std::vector<int32_t> ta, tb;
-        int sm = 0;
-        build_tile_params(p->canon, k, p->din, &tp, &ta, &tb, &sm);
-        t += tp.ntiles;
-      } else {
-        RowParams rp;
-        build_row_params(p->canon, kBatchCopyChunk / (p->din == DT_F64 ? 2 : 1), &rp);
-        t += rp.nitems;
-      }
+      BatchDesc d;
+      std::vector<int32_t> tabs;
+      size_t na = 0;
+      int sm = 0;
+      if (batch_describe(it.plan, it.A, it.B, &d, &tabs, &na, &sm)) t += d.ntiles;
     }
     *tiles = t;
   }

@@ -70,7 +70,7 @@ __device__ __forceinline__ void tile_body(const store_t<DIN>* __restrict__ Ab, s
     if (ok) tile[pos] = v[k];
   });
   __syncthreads();
-  TO bo[K];
+  TO bo[K] = {};
   if constexpr (EK == EK_AXPBY)
     walk_write<K, TB>(c, p, p.tabB, lc0, lbw0, la0, [&](int k, bool, int32_t off, int) { bo[k] = Bb[off]; });
   walk_write<K, TB>(c, p, p.tabB, lc0, lbw0, la0, [&](int k, bool ok, int32_t off, int pos) {
@@ -121,7 +121,7 @@ __device__ __forceinline__ void tile2_body(const store_t<DIN>* __restrict__ Ab, 
   int spre[JW];
   int32_t voff[JW];
   walk2_lane_consts<JW>(p, lane, spre, voff);
-  TO bo[K];
+  TO bo[K] = {};
   if constexpr (EK == EK_AXPBY)
     walk2_write<JW, K, FULL, TB>(c, p, p.tabB, lane, warp, spre, voff,
                                  [&](int k, bool, int32_t off, int) { bo[k] = Bb[off]; });
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) rowcopy_kernel(const store_t<DIN>* _
   const store_t<DIN>* Ab = A + c.baseA;
   TO* Bb = B + c.baseB;
   S v[K];
-  TO bo[K];
+  TO bo[K] = {};
   walk_rows<K>(c, p, t, [&](int k, bool, int32_t offA, int32_t offB) {
     v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + offA));
     if constexpr (EK == EK_AXPBY) bo[k] = Bb[offB];

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -28,6 +29,8 @@ struct DevRes {
   int smem = 0;
 };
 
+struct BatchTemplate;   // the plan's description for the batch body (batch_impl.h)
+
 }  // namespace ttc
 
 struct ttc_plan_s {
@@ -45,6 +48,10 @@ struct ttc_plan_s {
   const float* user_scale = nullptr;
   ttc::RowParams amax_rows;
   std::map<int, ttc::DevRes> dev;
+  // computed on first use by batch_describe, then shared by every batch and
+  // server request of this plan
+  std::mutex batch_mu;
+  std::shared_ptr<const ttc::BatchTemplate> batch_tmpl;
 };
 
 namespace ttc {

@@ -45,6 +45,15 @@ class PlanInfo(ctypes.Structure):
                 ("lanes_a", ctypes.c_int), ("lanes_b", ctypes.c_int)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("epochs", ctypes.c_int64), ("launches", ctypes.c_int64), ("bytes", ctypes.c_int64),
+                ("p50_us", ctypes.c_double), ("p90_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("first_submit_s", ctypes.c_double), ("last_complete_s", ctypes.c_double),
+                ("peak_inflight_bytes", ctypes.c_int64)]
+
+
 # Every symbol include/ttc.h declares, with (restype, argtypes).
 _vp = ctypes.c_void_p
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -70,6 +79,14 @@ SIGNATURES = {
     "ttc_batch_graph_launch": (ctypes.c_int, [_vp, _vp]),
     "ttc_batch_destroy": (ctypes.c_int, [_vp]),
     "ttc_batch_info": (ctypes.c_int, [_vp, _i64p, _i64p]),
+    "ttc_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_int, ctypes.c_int64]),
+    "ttc_server_submit": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64p]),
+    "ttc_server_poll": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64]),
+    "ttc_server_drain": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "ttc_server_stats": (ctypes.c_int, [_vp, _vp]),
+    "ttc_server_destroy": (ctypes.c_int, [_vp]),
+    "ttc_server_times": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     # include/ttc_debug.h
     "ttc_debug_verify_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
 }
@@ -245,6 +262,62 @@ class Batch:
             lib().ttc_batch_destroy(self._h)
             self._h = None
         self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous batching of requests (ttc_server_*).  The binding keeps a
+    reference to each request's plan and tensors until the request is seen
+    complete (poll or drain), so that they outlive it."""
+
+    def __init__(self, budget_bytes: int, nstreams: int = 4, small_tiles: int = 4096):
+        h = ctypes.c_void_p()
+        _check(lib().ttc_server_create(ctypes.byref(h), int(budget_bytes), int(nstreams), int(small_tiles)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, plan: Plan, A, B) -> int:
+        t = ctypes.c_int64(-1)
+        _check(lib().ttc_server_submit(self._h, plan.handle, _ptr(A), _ptr(B), ctypes.byref(t)))
+        self._keep[t.value] = (plan, A, B)
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = 0) -> bool:
+        """True once the request completed, False while it has not; raises
+        if it failed."""
+        st = lib().ttc_server_poll(self._h, int(ticket), int(timeout_us))
+        if st == STATUS_CODE["TTC_ERR_NOT_READY"]:
+            return False
+        self._keep.pop(int(ticket), None)
+        _check(st)
+        return True
+
+    def drain(self, timeout_us: int = 60_000_000):
+        _check(lib().ttc_server_drain(self._h, int(timeout_us)))
+        self._keep.clear()
+
+    def times(self, ticket: int):
+        """(submit_s, launch_s, complete_s) of a completed request, host
+        steady clock."""
+        a, b, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        _check(lib().ttc_server_times(self._h, int(ticket), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().ttc_server_stats(self._h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ttc_server_destroy(self._h)
+            self._h = None
+        self._keep = {}
 
     def __del__(self):
         try:
