@@ -198,9 +198,6 @@ def run_ours(args, rank, world):
     probs = workload_problems(args.workload, args.target, args.only)
     plans = [ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta, p.outer_a, p.outer_b)
              for p in probs]
-    if args.autotune:
-        for pl in plans:
-            pl.autotune(max_candidates=args.autotune)
     bufs = DeviceSet(probs)
     stream = torch.cuda.current_stream()
     bytes_step = sum(p.algorithmic_bytes() for p in probs)
@@ -214,18 +211,32 @@ def run_ours(args, rank, world):
             if events is not None:
                 events[i][1].record(stream)
 
+    def event_pass():
+        # per-launch durations (CUDA events on the launching stream); the
+        # device is kept busy while the host enqueues the first launches, so
+        # that no event interval includes host time
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in probs]
+        torch.cuda._sleep(20_000_000)
+        step(ev)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
     for _ in range(max(args.warmup, 3) if args.warmup >= 0 else 3):
         step()
     torch.cuda.synchronize()
-
-    # per-launch durations (CUDA events on the launching stream), one extra pass
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in probs]
-    # keep the device busy while the host enqueues the first launches, so that
-    # no event interval includes host time
-    torch.cuda._sleep(20_000_000)
-    step(ev)
-    torch.cuda.synchronize()
-    per_case_ms = [a.elapsed_time(b) for a, b in ev]
+    cost_model_ms = None
+    if args.autotune:
+        # the cost model's schedules, then the autotuner's (timed per plan on
+        # scratch buffers of the same size)
+        cost_model_ms = event_pass()
+        t_tune = time.perf_counter()
+        for pl in plans:
+            pl.autotune(max_candidates=args.autotune)
+        t_tune = time.perf_counter() - t_tune
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+    per_case_ms = event_pass()
 
     dist = world > 1
     if dist:
@@ -291,6 +302,10 @@ def run_ours(args, rank, world):
                    "algorithmic_bytes_per_step": bytes_step, "l2": "inputs > L2 (256-512 MiB per tensor), "
                    "two alternating buffer sets" if args.workload == "sweep" else "see workload",
                    "parallelism": f"replicas x{world}", "autotune": bool(args.autotune)},
+        "schedule": ({"autotuned_case_sum_GB/s": round(bytes_step / (sum(per_case_ms) * 1e-3) / 1e9, 1),
+                      "cost_model_case_sum_GB/s": round(bytes_step / (sum(cost_model_ms) * 1e-3) / 1e9, 1),
+                      "candidates_timed_per_plan": args.autotune, "tuning_wall_s": round(t_tune, 1)}
+                     if cost_model_ms else None),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
@@ -642,27 +657,34 @@ def oracle_slabs(p, A, B, threads):
         list(ex.map(work, chunks))
 
 
-def cpu_baseline(budget_s: float, probs, threads: int, max_cases: int = 10):
-    """Time the oracle as it stands on a bounded sample: the first few cases of
-    the workload, full size, until budget_s is spent."""
+def cpu_baseline(budget_s: float, probs, threads: int):
+    """Time the oracle as it stands on a bounded sample of the workload: its
+    cases at full size, taken in an order that spreads over N, perm and dtype,
+    until budget_s seconds of oracle time are spent (the input buffers are
+    generated once per dtype and sliced per case)."""
     import oracle
     oracle.build()
+    pool = {}
+    for p in probs:
+        for dt, v in ((p.dtype_in, p.vol_a), (p.dtype_out, p.vol_b)):
+            pool[dt] = max(pool.get(dt, 0), v)
+    bufs = {dt: inputs.tensor_for(dt, v, 1) for dt, v in pool.items()}
     done_bytes, t_total, names = 0, 0.0, []
-    t_start = time.perf_counter()
-    step = max(1, len(probs) // max_cases)
-    for p in probs[::step][:max_cases]:
-        A = inputs.tensor_for(p.dtype_in, p.vol_a, 1)
-        B = inputs.tensor_for(p.dtype_out, p.vol_b, 2)
+    stride = 7 if len(probs) % 7 else 11
+    for i in range(4 * len(probs)):
+        p = probs[(i * stride) % len(probs)]
+        A = bufs[p.dtype_in][:p.vol_a]
+        B = bufs[p.dtype_out][:p.vol_b].copy()
         t0 = time.perf_counter()
         oracle_slabs(p, A, B, threads)
-        dt = time.perf_counter() - t0
-        t_total += dt
+        t_total += time.perf_counter() - t0
         done_bytes += p.algorithmic_bytes()
         names.append(f"{p.tag}/{p.dtype_in}/b{p.beta}")
-        if time.perf_counter() - t_start > budget_s:
+        if t_total > budget_s:
             break
+    shown = ", ".join(names[:6]) + (", ..." if len(names) > 6 else "")
     return {"value": round(done_bytes / t_total / 1e9, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
-            "sample": f"{len(names)} full-size cases of the workload ({', '.join(names)}), "
+            "sample": f"{len(names)} runs over the workload's {len(probs)} cases at full size ({shown}), "
                       f"{t_total:.1f} s of oracle time on {threads} threads (slabs along the last index)"}
 
 
@@ -710,7 +732,8 @@ def main():
     ap.add_argument("--serve-small-tiles", type=int, default=1024)
     ap.add_argument("--serve-dump", default="", help="write per-request latencies (JSON) to <path>.<arm>.json")
     ap.add_argument("--batch-count", type=int, default=4096)
-    ap.add_argument("--autotune", type=int, default=0, help="time up to this many candidates per plan first")
+    ap.add_argument("--autotune", type=int, default=12,
+                    help="time up to this many candidates per plan before the timed steps (0: cost model only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
