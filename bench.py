@@ -248,11 +248,15 @@ def run_ours(args, rank, world):
         clk.start()
     l0 = ttc.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.profile_timed:
+        torch.cuda.cudart().cudaProfilerStart()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    if args.profile_timed:
+        torch.cuda.cudart().cudaProfilerStop()
     launches = ttc.launch_count() - l0
     clocks = clk.stop() if clk else None
     ms_total = e0.elapsed_time(e1)
@@ -740,6 +744,8 @@ def main():
     ap.add_argument("--target", type=int, default=1 << 26, help="elements per tensor of the sweep")
     ap.add_argument("--only", default="", help="comma-separated case tags of the sweep (e.g. N5p3)")
     ap.add_argument("--cases-out", default="", help="write per-case timings (JSON) to this file")
+    ap.add_argument("--profile-timed", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
