@@ -164,6 +164,9 @@ typedef struct {
     int ncandidates;               /* number of candidate schedules the planner kept */
     int lanes_a, lanes_b;          /* tile variant: lanes along the A run / B run of the warp-mapped
                                       kernel (32, 64, 128), or 0 for the generic tile kernel */
+    int slot_tables;               /* generic tile kernel: whole tiles read their per-thread
+                                      offsets from precomputed slot tables (1) or walk the
+                                      indices (0) */
 } ttc_plan_info;
 
 ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info);

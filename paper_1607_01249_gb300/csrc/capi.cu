@@ -75,8 +75,10 @@ ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out) {
   std::lock_guard<std::mutex> lk(p->mu);
   DevRes& r = p->dev[dev];
   if (r.base == nullptr) {
-    // scratch: amax word + scale, then room for the largest cross tables
+    // scratch: amax word + scale, room for the largest cross tables, then
+    // (16-byte aligned) the slot tables if a candidate uses them
     size_t tab = 0;
+    bool slots = false;
     for (auto& c : p->cands) {
       if (c.variant != VAR_TILE) continue;
       TileParams tp;
@@ -84,8 +86,10 @@ ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out) {
       int sm = 0;
       build_tile_params(p->canon, c, p->din, &tp, &ta, &tb, &sm);
       tab = std::max(tab, (ta.size() + tb.size()) * sizeof(int32_t));
+      slots = slots || c.slots;
     }
-    r.bytes = 256 + tab;
+    tab = (tab + 255) & ~size_t(255);
+    r.bytes = 256 + tab + (slots ? slot_table_ints(p->din) * sizeof(int32_t) : 0);
     cudaError_t e = cudaMalloc(&r.base, r.bytes);
     if (e != cudaSuccess) {
       r.base = nullptr;
@@ -95,6 +99,7 @@ ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out) {
     r.amax = reinterpret_cast<uint32_t*>(r.base);
     r.scale = reinterpret_cast<float*>(static_cast<char*>(r.base) + 16);
     r.tables = reinterpret_cast<int32_t*>(static_cast<char*>(r.base) + 256);
+    r.slots = slots ? reinterpret_cast<int4*>(static_cast<char*>(r.base) + 256 + tab) : nullptr;
     r.sel = -1;
     // a remembered autotune result for this canonical problem on this device
     if (!p->user_selected) {
@@ -119,6 +124,14 @@ ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out) {
       }
       r.tp.tabA = r.tables;
       r.tp.tabB = r.tables + ta.size();
+      r.tp.slots = nullptr;
+      if (k.slots && r.slots) {
+        std::vector<int32_t> st;
+        build_slot_tables(r.tp, p->din, ta, tb, &st);
+        cudaError_t e = cudaMemcpy(r.slots, st.data(), st.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "slot table upload");
+        r.tp.slots = r.slots;
+      }
     } else if (k.variant == VAR_COPY) {
       build_row_params(p->canon, k.chunk, &r.rp);
     }
@@ -327,6 +340,7 @@ ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info) {
     info->vec_in = info->vec_out = 1;
     info->lanes_a = 32 * k.ju;
     info->lanes_b = 32 * k.jw;
+    info->slot_tables = k.slots;
   } else if (k.variant == VAR_COPY) {
     RowParams rp;
     build_row_params(c, k.chunk, &rp);

@@ -78,6 +78,52 @@ __device__ __forceinline__ void tile_body(const store_t<DIN>* __restrict__ Ab, s
   });
 }
 
+// A whole tile from the plan's slot tables (TileParams::slots): the table
+// gives each (k, thread) slot its offset in the tile and shared-memory
+// position, so the loops carry no index arithmetic at all.  Table reads are
+// 16-byte loads of two slots, coalesced across the warp and shared by every
+// CTA on the SM through L1.
+template <int DIN, int DOUT, int EK>
+__device__ __forceinline__ void tile_slots(const store_t<DIN>* __restrict__ Ab, store_t<DOUT>* __restrict__ Bb,
+                                           const TileParams& p, stage_t<DIN>* tile, float scale) {
+  using S = stage_t<DIN>;
+  using TO = store_t<DOUT>;
+  constexpr int K = tile_k_for(sizeof(S));
+  const int4* __restrict__ rs = p.slots + threadIdx.x;
+  const int4* __restrict__ ws = p.slots + (K / 2) * kThreads + threadIdx.x;
+  S v[K];
+  int pos[K];
+#pragma unroll
+  for (int k = 0; k < K / 2; ++k) {
+    const int4 e = __ldg(rs + k * kThreads);
+    pos[2 * k] = e.y;
+    pos[2 * k + 1] = e.w;
+    v[2 * k] = to_stage<DIN>(ldg_elem<DIN>(Ab + e.x));
+    v[2 * k + 1] = to_stage<DIN>(ldg_elem<DIN>(Ab + e.z));
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (pos[k] >= 0) tile[pos[k]] = v[k];
+  __syncthreads();
+  int32_t off[K];
+#pragma unroll
+  for (int k = 0; k < K / 2; ++k) {
+    const int4 e = __ldg(ws + k * kThreads);
+    off[2 * k] = e.x;
+    pos[2 * k] = e.y;
+    off[2 * k + 1] = e.z;
+    pos[2 * k + 1] = e.w;
+  }
+  TO bo[K] = {};
+  if constexpr (EK == EK_AXPBY) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) bo[k] = Bb[off[k]];
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (pos[k] >= 0) Bb[off[k]] = epilogue_k<DIN, DOUT, EK>(tile[pos[k]], bo[k], p.epi, scale);
+}
+
 template <int DIN, int DOUT, int EK>
 __global__ void __launch_bounds__(kThreads, 4) tile_kernel(const store_t<DIN>* __restrict__ A,
                                                            store_t<DOUT>* __restrict__ B,
@@ -89,6 +135,10 @@ __global__ void __launch_bounds__(kThreads, 4) tile_kernel(const store_t<DIN>* _
   const TileCoord c = cta_tile_coord(p);
   const store_t<DIN>* Ab = A + c.baseA;
   store_t<DOUT>* Bb = B + c.baseB;
+  if (p.slots != nullptr && c.remA == p.LA && c.remB == p.LB) {
+    tile_slots<DIN, DOUT, EK>(Ab, Bb, p, tile, scale);
+    return;
+  }
   if (p.crossA_tab) {
     if (p.crossB_tab) tile_body<DIN, DOUT, EK, true, true>(Ab, Bb, p, c, tile, scale);
     else tile_body<DIN, DOUT, EK, true, false>(Ab, Bb, p, c, tile, scale);

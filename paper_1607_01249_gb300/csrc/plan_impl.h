@@ -23,6 +23,7 @@ struct DevRes {
   uint32_t* amax = nullptr;
   float* scale = nullptr;
   int32_t* tables = nullptr;
+  int4* slots = nullptr;     // slot tables of tile_kernel (when a candidate uses them)
   int sel = -1;          // candidate the parameters below were built for
   TileParams tp;
   RowParams rp;

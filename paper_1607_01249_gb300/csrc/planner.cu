@@ -24,6 +24,7 @@
 #include <sstream>
 
 #include "../../include/ttc.h"
+#include "kernels.cuh"
 #include "launch.h"
 #include "planner.h"
 
@@ -61,7 +62,7 @@ std::string Candidate::describe() const {
     for (size_t i = 0; i < ga.size(); ++i) o << (i ? "," : "") << ga[i];
     o << "]/" << ta << " gb=[";
     for (size_t i = 0; i < gb.size(); ++i) o << (i ? "," : "") << gb[i];
-    o << "]/" << tb << " j=" << ju << "," << jw << (rows ? " rows" : "") << " order=[";
+    o << "]/" << tb << " j=" << ju << "," << jw << (rows ? " rows" : "") << (slots ? " slots" : "") << " order=[";
     for (size_t i = 0; i < order.size(); ++i) o << (i ? "," : "") << order[i];
     o << "]";
   }
@@ -412,7 +413,14 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
             if ((!sh.ga.empty() && c.s[sh.ga.back()] >= (int64_t(1) << 30)) ||
                 (!sh.gb.empty() && c.s[sh.gb.back()] >= (int64_t(1) << 30)))
               continue;
-            const double ra = run_length(c, ext, orderA, c.sa), rb = run_length(c, ext, orderB, c.sb);
+            // A tile without a C or GA index (U = 1) is loaded in GB's order,
+            // which steps through A by large strides: a warp's loads do not
+            // coalesce.  When the whole tile is one contiguous block of A, L1
+            // still catches most of the reuse (measured as if the runs were
+            // 8 elements long); otherwise nothing does.  Likewise for W = 1.
+            double ra = run_length(c, ext, orderA, c.sa), rb = run_length(c, ext, orderB, c.sb);
+            if (LC * LA == 1) ra = ra >= double(V) ? 8.0 : 1.0;
+            if (LC * LB == 1) rb = rb >= double(V) ? 8.0 : 1.0;
             const double mem = (n * esA / run_efficiency(ra * esA, false) +
                                 n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true)) / kHbmBytesPerS;
             const double per_slot = 26.0 + (sh.ga.size() > 1 ? 3 : 0) + (sh.gb.size() > 1 ? 3 : 0) + (bnz ? 6 : 0);
@@ -429,6 +437,17 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
             k.seg_a = ra;
             k.seg_b = rb;
             k.est_s = std::max(mem, issue) + 0.25 * std::min(mem, issue) + over + 3e-6;
+            if (vmax == 0) {
+              // single-plan tiles read their whole tiles from slot tables: two
+              // slots per 16-byte table read and no index arithmetic.  The
+              // table reads cost L1 bandwidth and one more dependent load per
+              // phase: measured ~9 % below the warp-mapped kernel on shapes
+              // both fit, 30-40 % above the index walk on every shape tried.
+              const double per_slot3 = 14.0 + (bnz ? 4 : 0);
+              const double issue3 = ntiles * kTileK * kThreads * per_slot3 / kLaneInstrPerS;
+              k.slots = 1;
+              k.est_s = std::max(1.08 * mem, issue3) + 0.25 * std::min(mem, issue3) + over + 3e-6;
+            }
             tiles.push_back(k);
             // the warp-mapped kernel, when the shape fits one of its lane layouts
             const int64_t U = LC * LA, W = LC * LB;
@@ -443,6 +462,7 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
                                        rows_w * (jw * (5.0 + (bnz ? 3.0 : 0.0)) + 4.0 + (sh.ga.size() > 1 ? 2 : 0)));
               const double issue2 = ntiles * 32.0 * wi / kLaneInstrPerS;
               Candidate k2 = k;
+              k2.slots = 0;
               k2.ju = ju;
               k2.jw = jw;
               k2.est_s = std::max(mem, issue2) + 0.25 * std::min(mem, issue2) + over + 3e-6;
@@ -595,6 +615,43 @@ void build_row_params(const Canon& c, int64_t chunk, RowParams* p) {
     rows *= uint64_t(c.s[k]);
   }
   p->nitems = uint32_t(rows * uint64_t(nch));
+}
+
+namespace {
+
+// One whole tile (no cut index short) run through the kernel's own index
+// walks on the host; every slot records what the walk gives it.
+template <int K>
+void slot_tables_k(const TileParams& p, const std::vector<int32_t>& tabA, const std::vector<int32_t>& tabB,
+                   std::vector<int32_t>* out) {
+  const TileCoord c{0, 0, p.LA, p.LB};
+  int32_t* q = out->data();
+  auto put = [&](int phase, int t, int k, bool ok, int32_t off, int pos) {
+    int32_t* e = q + ((size_t(phase) * (K / 2) + size_t(k / 2)) * kThreads + size_t(t)) * 4 + (k & 1) * 2;
+    e[0] = ok ? off : 0;
+    e[1] = ok ? pos : -1;
+  };
+  for (int t = 0; t < kThreads; ++t) {
+    int u0, lb0, lc0, lbw0, la0;
+    flat_starts(p, t, u0, lb0, lc0, lbw0, la0);
+    auto rd = [&](int k, bool ok, int32_t off, int pos) { put(0, t, k, ok, off, pos); };
+    auto wr = [&](int k, bool ok, int32_t off, int pos) { put(1, t, k, ok, off, pos); };
+    if (p.crossA_tab) walk_read<K, true>(c, p, tabA.data(), u0, lb0, rd);
+    else walk_read<K, false>(c, p, tabA.data(), u0, lb0, rd);
+    if (p.crossB_tab) walk_write<K, true>(c, p, tabB.data(), lc0, lbw0, la0, wr);
+    else walk_write<K, false>(c, p, tabB.data(), lc0, lbw0, la0, wr);
+  }
+}
+
+}  // namespace
+
+size_t slot_table_ints(int din) { return size_t(tile_k_for(stage_bytes(din))) * kThreads * 4; }
+
+void build_slot_tables(const TileParams& p, int din, const std::vector<int32_t>& tabA,
+                       const std::vector<int32_t>& tabB, std::vector<int32_t>* out) {
+  out->assign(slot_table_ints(din), 0);
+  if (tile_k_for(stage_bytes(din)) == 16) slot_tables_k<16>(p, tabA, tabB, out);
+  else slot_tables_k<8>(p, tabA, tabB, out);
 }
 
 }  // namespace ttc

@@ -37,6 +37,7 @@ struct Candidate {
   std::vector<int> order;      // grid indices (A index ids), fastest first
   int ju = 0, jw = 0;          // >0: warp-mapped tile kernel with JU/JW chunks of 32 lanes
   int rows = 0;                // multi-row copy kernel (perm keeps index 0, GB empty, no staging)
+  int slots = 0;               // tile_kernel from precomputed slot tables (whole tiles)
   // copy variant
   int64_t chunk = 0;
   int vec = 1;                 // vector width usable when pointers are aligned
@@ -60,6 +61,13 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
 void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* p,
                        std::vector<int32_t>* tabA, std::vector<int32_t>* tabB, int* smem_bytes);
 void build_row_params(const Canon& c, int64_t chunk, RowParams* p);
+
+// Slot tables of a whole tile for tile_kernel (layout: TileParams::slots),
+// as int32 quadruples; `tabA`/`tabB` are the host cross tables of the same
+// parameters.  Returns the number of int32 values written (4 per two slots).
+void build_slot_tables(const TileParams& p, int din, const std::vector<int32_t>& tabA,
+                       const std::vector<int32_t>& tabB, std::vector<int32_t>* out);
+size_t slot_table_ints(int din);
 
 // Estimated memory efficiency of reading (write = false) or writing a
 // contiguous run of `bytes` bytes that starts at an arbitrary element offset.

@@ -125,6 +125,8 @@ struct Checker {
     if (smem > 200 * 1024) return fail("shared memory over budget", smem, 0);
     if (tp.V > kThreads * K) return fail("tile larger than the threads cover", tp.V, kThreads * K);
     const int ncap = tp.P * tp.LB;
+    std::vector<int32_t> slots;
+    if (k.slots) build_slot_tables(tp, p->din, ta, tb, &slots);
     std::vector<int64_t> posA(static_cast<size_t>(ncap));
     std::vector<uint8_t> used(static_cast<size_t>(ncap));
     for (uint32_t tid = 0; tid < tp.ntiles; ++tid) {
@@ -156,7 +158,23 @@ struct Checker {
         if (!ok) return false;
         continue;
       }
-      if (k.ju == 0) {
+      if (k.slots && full) {
+        // the kernel's slot-table path: slot (k, t) of phase f sits in int4
+        // (f*K/2 + k/2)*kThreads + t, half k&1; pos < 0 marks an empty slot
+        for (int f = 0; f < 2 && ok; ++f)
+          for (int t = 0; t < kThreads && ok; ++t)
+            for (int kk = 0; kk < K && ok; ++kk) {
+              const int32_t* e =
+                  slots.data() + ((size_t(f) * (K / 2) + size_t(kk / 2)) * kThreads + size_t(t)) * 4 + (kk & 1) * 2;
+              if (f == 0) {
+                if (e[0] < 0 || (e[1] < 0 && e[0] != 0)) ok = fail("slot table: bad empty read slot", e[0], e[1]);
+                else on_read(kk, e[1] >= 0, e[0], e[1]);
+              } else {
+                if (e[0] < 0) ok = fail("slot table: negative write offset", e[0], e[1]);
+                else on_write(kk, e[1] >= 0, e[0], e[1]);
+              }
+            }
+      } else if (k.ju == 0) {
         for (int t = 0; t < kThreads && ok; ++t) {
           int u0, lb0, lc0, lbw0, la0;
           flat_starts(tp, t, u0, lb0, lc0, lbw0, la0);

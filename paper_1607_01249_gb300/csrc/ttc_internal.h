@@ -24,6 +24,8 @@
 
 #include <cstdint>
 
+struct int4;   // CUDA vector type (vector_types.h); only pointers to it appear here
+
 #if defined(__CUDACC__)
 #define TTC_HD __host__ __device__ __forceinline__
 #else
@@ -121,6 +123,12 @@ struct TileParams {
   int crossB_tab;      // nonzero: crossB comes from a table of LA entries
   const int32_t* tabA; // device table crossA[LB]
   const int32_t* tabB; // device table crossB[LA]
+  // Optional slot tables of a whole tile (tile_kernel): for every (k, thread)
+  // slot of the read and of the write order, the element's offset in the tile
+  // and its shared-memory position (-1: no element), two slots per int4:
+  // read slots [K/2][kThreads], then write slots [K/2][kThreads].  Null: the
+  // kernel walks the indices instead.
+  const int4* slots;
   // per-thread step of kThreads in the read order (u, lb) and write order (lc, lb, la)
   int rd_du, rd_dlb;
   int wr_dlc, wr_dlb, wr_dla;

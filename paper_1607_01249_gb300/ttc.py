@@ -42,7 +42,7 @@ class PlanInfo(ctypes.Structure):
                 ("tile_c", ctypes.c_int), ("tile_a", ctypes.c_int), ("tile_b", ctypes.c_int),
                 ("ntiles", ctypes.c_int64), ("vec_in", ctypes.c_int), ("vec_out", ctypes.c_int),
                 ("candidate", ctypes.c_int), ("ncandidates", ctypes.c_int),
-                ("lanes_a", ctypes.c_int), ("lanes_b", ctypes.c_int)]
+                ("lanes_a", ctypes.c_int), ("lanes_b", ctypes.c_int), ("slot_tables", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -192,6 +192,7 @@ class Plan:
                 "tile": (inf.tile_c, inf.tile_a, inf.tile_b), "ntiles": inf.ntiles,
                 "vec": (inf.vec_in, inf.vec_out), "candidate": inf.candidate,
                 "ncandidates": inf.ncandidates, "lanes": (inf.lanes_a, inf.lanes_b),
+                "slot_tables": bool(inf.slot_tables),
                 "kernel": ({0: "empty", 1: "copy_kernel", 3: "rowcopy_kernel"}.get(inf.variant) or
                            ("tile2_kernel" if inf.lanes_a else "tile_kernel"))}
 

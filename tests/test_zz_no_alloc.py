@@ -118,7 +118,9 @@ def test_noalloc_interleaved_plans_share_the_array():
 
 
 def test_noalloc_refuses_schedules_beyond_the_static_scratch():
-    p = Problem(perm=(2, 0, 3, 1), sizes=(17, 15, 15, 17))
+    # a shape whose candidate list holds tiles with multi-index groups on both
+    # sides, i.e. cross-offset tables of several thousand entries
+    p = Problem(perm=(1, 0, 3, 2), sizes=(70, 3, 70, 3))
     plan = ttc.Plan(p.perm, p.sizes)
     dA = torch.zeros(p.vol_a, dtype=torch.float32, device="cuda")
     dB = torch.zeros(p.vol_b, dtype=torch.float32, device="cuda")
