@@ -25,6 +25,14 @@ extern "C" {
  */
 ttc_status ttc_debug_verify_schedule(ttc_plan_t plan, int candidate, char* msg, int msglen);
 
+/*
+ * Text description of candidate `candidate` of `plan`: its kernel, tile
+ * groups and extents, lane layout, grid order (fastest first) and the cost
+ * model's estimate, written NUL-terminated into buf (buflen bytes).
+ * TTC_ERR_INVALID_ARG for a bad plan, candidate or buffer.
+ */
+ttc_status ttc_debug_describe_candidate(ttc_plan_t plan, int candidate, char* buf, int buflen);
+
 #ifdef __cplusplus
 }
 #endif

@@ -179,7 +179,8 @@ ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s) {
     tp.epi = epi;
     e = k.rows ? launch_rowcopy(p->din, p->dout, A, B, tp, s)
         : k.ju ? launch_tile2(p->din, p->dout, k.ju, k.jw, A, B, tp, r->smem, s)
-             : launch_tile(p->din, p->dout, A, B, tp, r->smem, s);
+        : tp.slots ? launch_tile_slots(p->din, p->dout, A, B, tp, r->smem, s)
+                   : launch_tile(p->din, p->dout, A, B, tp, r->smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "tile kernel launch");
   } else if (k.variant == VAR_COPY) {
     RowParams rp = r->rp;

@@ -70,38 +70,47 @@ cudaError_t grid_for(const void* fn, int smem, int64_t work, int* grid) {
 
 
 cudaError_t launch_tile_f32_f32(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile_slots_f32_f32(const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_tile2_f32_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_f32_f32(int, const void*, void*, const RowParams&, cudaStream_t);
 cudaError_t launch_rowcopy_f32_f32(const void*, void*, const TileParams&, cudaStream_t);
 cudaError_t launch_tile_f32_f64(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile_slots_f32_f64(const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_tile2_f32_f64(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_f32_f64(int, const void*, void*, const RowParams&, cudaStream_t);
 cudaError_t launch_rowcopy_f32_f64(const void*, void*, const TileParams&, cudaStream_t);
 cudaError_t launch_tile_f32_bf16(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile_slots_f32_bf16(const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_tile2_f32_bf16(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_f32_bf16(int, const void*, void*, const RowParams&, cudaStream_t);
 cudaError_t launch_rowcopy_f32_bf16(const void*, void*, const TileParams&, cudaStream_t);
 cudaError_t launch_tile_f32_e4m3(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile_slots_f32_e4m3(const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_tile2_f32_e4m3(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_f32_e4m3(int, const void*, void*, const RowParams&, cudaStream_t);
 cudaError_t launch_rowcopy_f32_e4m3(const void*, void*, const TileParams&, cudaStream_t);
 cudaError_t launch_tile_f64_f64(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile_slots_f64_f64(const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_tile2_f64_f64(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_f64_f64(int, const void*, void*, const RowParams&, cudaStream_t);
 cudaError_t launch_rowcopy_f64_f64(const void*, void*, const TileParams&, cudaStream_t);
 cudaError_t launch_tile_f64_f32(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile_slots_f64_f32(const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_tile2_f64_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_f64_f32(int, const void*, void*, const RowParams&, cudaStream_t);
 cudaError_t launch_rowcopy_f64_f32(const void*, void*, const TileParams&, cudaStream_t);
 cudaError_t launch_tile_bf16_bf16(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile_slots_bf16_bf16(const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_tile2_bf16_bf16(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_bf16_bf16(int, const void*, void*, const RowParams&, cudaStream_t);
 cudaError_t launch_rowcopy_bf16_bf16(const void*, void*, const TileParams&, cudaStream_t);
 cudaError_t launch_tile_bf16_f32(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile_slots_bf16_f32(const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_tile2_bf16_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_bf16_f32(int, const void*, void*, const RowParams&, cudaStream_t);
 cudaError_t launch_rowcopy_bf16_f32(const void*, void*, const TileParams&, cudaStream_t);
 cudaError_t launch_tile_bf16_e4m3(const void*, void*, const TileParams&, int, cudaStream_t);
+cudaError_t launch_tile_slots_bf16_e4m3(const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_tile2_bf16_e4m3(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
 cudaError_t launch_copy_bf16_e4m3(int, const void*, void*, const RowParams&, cudaStream_t);
 cudaError_t launch_rowcopy_bf16_e4m3(const void*, void*, const TileParams&, cudaStream_t);
@@ -124,6 +133,20 @@ bool pair_supported(int din, int dout) {
 int copy_vec_width(int din, int dout) {
   int w = dtype_size(din) > dtype_size(dout) ? dtype_size(din) : dtype_size(dout);
   return 16 / w;
+}
+
+cudaError_t launch_tile_slots(int din, int dout, const void* A, void* B, const TileParams& p, int smem,
+                              cudaStream_t s) {
+  if (din == DT_F32 && dout == DT_F32) return launch_tile_slots_f32_f32(A, B, p, smem, s);
+  if (din == DT_F32 && dout == DT_F64) return launch_tile_slots_f32_f64(A, B, p, smem, s);
+  if (din == DT_F32 && dout == DT_BF16) return launch_tile_slots_f32_bf16(A, B, p, smem, s);
+  if (din == DT_F32 && dout == DT_E4M3) return launch_tile_slots_f32_e4m3(A, B, p, smem, s);
+  if (din == DT_F64 && dout == DT_F64) return launch_tile_slots_f64_f64(A, B, p, smem, s);
+  if (din == DT_F64 && dout == DT_F32) return launch_tile_slots_f64_f32(A, B, p, smem, s);
+  if (din == DT_BF16 && dout == DT_BF16) return launch_tile_slots_bf16_bf16(A, B, p, smem, s);
+  if (din == DT_BF16 && dout == DT_F32) return launch_tile_slots_bf16_f32(A, B, p, smem, s);
+  if (din == DT_BF16 && dout == DT_E4M3) return launch_tile_slots_bf16_e4m3(A, B, p, smem, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tile(int din, int dout, const void* A, void* B, const TileParams& p, int smem,

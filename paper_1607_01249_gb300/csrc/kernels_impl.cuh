@@ -78,41 +78,97 @@ __device__ __forceinline__ void tile_body(const store_t<DIN>* __restrict__ Ab, s
   });
 }
 
-// A whole tile from the plan's slot tables (TileParams::slots): the table
-// gives each (k, thread) slot its offset in the tile and shared-memory
-// position, so the loops carry no index arithmetic at all.  Table reads are
-// 16-byte loads of two slots, coalesced across the warp and shared by every
-// CTA on the SM through L1.
 template <int DIN, int DOUT, int EK>
-__device__ __forceinline__ void tile_slots(const store_t<DIN>* __restrict__ Ab, store_t<DOUT>* __restrict__ Bb,
-                                           const TileParams& p, stage_t<DIN>* tile, float scale) {
+__global__ void __launch_bounds__(kThreads, 4) tile_kernel(const store_t<DIN>* __restrict__ A,
+                                                           store_t<DOUT>* __restrict__ B,
+                                                           const __grid_constant__ TileParams p) {
+  using S = stage_t<DIN>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  S* tile = reinterpret_cast<S*>(smem);
+  const float scale = cta_fp8_scale<EK>(p.epi);
+  const TileCoord c = cta_tile_coord(p);
+  const store_t<DIN>* Ab = A + c.baseA;
+  store_t<DOUT>* Bb = B + c.baseB;
+  if (p.crossA_tab) {
+    if (p.crossB_tab) tile_body<DIN, DOUT, EK, true, true>(Ab, Bb, p, c, tile, scale);
+    else tile_body<DIN, DOUT, EK, true, false>(Ab, Bb, p, c, tile, scale);
+  } else {
+    if (p.crossB_tab) tile_body<DIN, DOUT, EK, false, true>(Ab, Bb, p, c, tile, scale);
+    else tile_body<DIN, DOUT, EK, false, false>(Ab, Bb, p, c, tile, scale);
+  }
+}
+
+// ------------------------------------------------------ slot-table tile --
+//
+// The same tiles as tile_kernel, driven by the plan's slot tables
+// (TileParams::slots): for every (k, thread) slot of the load order and of
+// the store order, the element's offset in the tile and its shared-memory
+// position, two slots per 16-byte table read; the slots visit the tile's
+// elements in increasing A offset (loads) and increasing B offset (stores),
+// so both sides coalesce whatever the tile's index structure.  A tile cut
+// short by the tensor's edge reads each slot's (la, lb) coordinate from a
+// second table and masks the slots outside the tile.  The loops carry no
+// index arithmetic; the tables are shared by every CTA through L1.
+
+template <int DIN, int DOUT, int EK, bool FULL>
+__device__ __forceinline__ void slots_body(const store_t<DIN>* __restrict__ Ab, store_t<DOUT>* __restrict__ Bb,
+                                           const TileParams& p, const TileCoord& c, stage_t<DIN>* tile,
+                                           float scale) {
   using S = stage_t<DIN>;
   using TO = store_t<DOUT>;
   constexpr int K = tile_k_for(sizeof(S));
-  const int4* __restrict__ rs = p.slots + threadIdx.x;
-  const int4* __restrict__ ws = p.slots + (K / 2) * kThreads + threadIdx.x;
+  const int t = threadIdx.x;
+  const int4* __restrict__ rs = p.slots + t;
+  const int4* __restrict__ ws = p.slots + (K / 2) * kThreads + t;
+  // slot k of this thread holds an element of this tile iff bit k is set
+  auto inside = [&](int phase) -> uint32_t {
+    if constexpr (FULL) {
+      return 0xffffffffu;
+    } else {
+      const uint4* __restrict__ tab = reinterpret_cast<const uint4*>(p.slots + K * kThreads) + t +
+                                      phase * (K / 4) * kThreads;
+      uint32_t m = 0;
+#pragma unroll
+      for (int q = 0; q < K / 4; ++q) {
+        const uint4 e = __ldg(tab + q * kThreads);
+        m |= uint32_t((int(e.x >> 16) < c.remA) & (int(e.x & 0xffffu) < c.remB)) << (4 * q);
+        m |= uint32_t((int(e.y >> 16) < c.remA) & (int(e.y & 0xffffu) < c.remB)) << (4 * q + 1);
+        m |= uint32_t((int(e.z >> 16) < c.remA) & (int(e.z & 0xffffu) < c.remB)) << (4 * q + 2);
+        m |= uint32_t((int(e.w >> 16) < c.remA) & (int(e.w & 0xffffu) < c.remB)) << (4 * q + 3);
+      }
+      return m;
+    }
+  };
   S v[K];
   int pos[K];
+  {
+    const uint32_t m = inside(0);
 #pragma unroll
-  for (int k = 0; k < K / 2; ++k) {
-    const int4 e = __ldg(rs + k * kThreads);
-    pos[2 * k] = e.y;
-    pos[2 * k + 1] = e.w;
-    v[2 * k] = to_stage<DIN>(ldg_elem<DIN>(Ab + e.x));
-    v[2 * k + 1] = to_stage<DIN>(ldg_elem<DIN>(Ab + e.z));
+    for (int k = 0; k < K / 2; ++k) {
+      const int4 e = __ldg(rs + k * kThreads);
+      const bool i0 = FULL || ((m >> (2 * k)) & 1u), i1 = FULL || ((m >> (2 * k + 1)) & 1u);
+      pos[2 * k] = i0 ? e.y : -1;
+      pos[2 * k + 1] = i1 ? e.w : -1;
+      v[2 * k] = to_stage<DIN>(ldg_elem<DIN>(Ab + (i0 ? e.x : 0)));
+      v[2 * k + 1] = to_stage<DIN>(ldg_elem<DIN>(Ab + (i1 ? e.z : 0)));
+    }
   }
 #pragma unroll
   for (int k = 0; k < K; ++k)
     if (pos[k] >= 0) tile[pos[k]] = v[k];
   __syncthreads();
   int32_t off[K];
+  {
+    const uint32_t m = inside(1);
 #pragma unroll
-  for (int k = 0; k < K / 2; ++k) {
-    const int4 e = __ldg(ws + k * kThreads);
-    off[2 * k] = e.x;
-    pos[2 * k] = e.y;
-    off[2 * k + 1] = e.z;
-    pos[2 * k + 1] = e.w;
+    for (int k = 0; k < K / 2; ++k) {
+      const int4 e = __ldg(ws + k * kThreads);
+      const bool i0 = FULL || ((m >> (2 * k)) & 1u), i1 = FULL || ((m >> (2 * k + 1)) & 1u);
+      off[2 * k] = i0 ? e.x : 0;
+      pos[2 * k] = i0 ? e.y : -1;
+      off[2 * k + 1] = i1 ? e.z : 0;
+      pos[2 * k + 1] = i1 ? e.w : -1;
+    }
   }
   TO bo[K] = {};
   if constexpr (EK == EK_AXPBY) {
@@ -125,9 +181,9 @@ __device__ __forceinline__ void tile_slots(const store_t<DIN>* __restrict__ Ab, 
 }
 
 template <int DIN, int DOUT, int EK>
-__global__ void __launch_bounds__(kThreads, 4) tile_kernel(const store_t<DIN>* __restrict__ A,
-                                                           store_t<DOUT>* __restrict__ B,
-                                                           const __grid_constant__ TileParams p) {
+__global__ void __launch_bounds__(kThreads, 4) tile_slots_kernel(const store_t<DIN>* __restrict__ A,
+                                                                 store_t<DOUT>* __restrict__ B,
+                                                                 const __grid_constant__ TileParams p) {
   using S = stage_t<DIN>;
   extern __shared__ __align__(16) unsigned char smem[];
   S* tile = reinterpret_cast<S*>(smem);
@@ -135,17 +191,8 @@ __global__ void __launch_bounds__(kThreads, 4) tile_kernel(const store_t<DIN>* _
   const TileCoord c = cta_tile_coord(p);
   const store_t<DIN>* Ab = A + c.baseA;
   store_t<DOUT>* Bb = B + c.baseB;
-  if (p.slots != nullptr && c.remA == p.LA && c.remB == p.LB) {
-    tile_slots<DIN, DOUT, EK>(Ab, Bb, p, tile, scale);
-    return;
-  }
-  if (p.crossA_tab) {
-    if (p.crossB_tab) tile_body<DIN, DOUT, EK, true, true>(Ab, Bb, p, c, tile, scale);
-    else tile_body<DIN, DOUT, EK, true, false>(Ab, Bb, p, c, tile, scale);
-  } else {
-    if (p.crossB_tab) tile_body<DIN, DOUT, EK, false, true>(Ab, Bb, p, c, tile, scale);
-    else tile_body<DIN, DOUT, EK, false, false>(Ab, Bb, p, c, tile, scale);
-  }
+  if (c.remA == p.LA && c.remB == p.LB) slots_body<DIN, DOUT, EK, true>(Ab, Bb, p, c, tile, scale);
+  else slots_body<DIN, DOUT, EK, false>(Ab, Bb, p, c, tile, scale);
 }
 
 // --------------------------------------------------------- warp-mapped tile --
@@ -363,6 +410,24 @@ struct TileL {
       }
       tile_kernel<DIN, DOUT, EK><<<p.ntiles, kThreads, smem, s>>>(static_cast<const store_t<DIN>*>(A),
                                                                   static_cast<store_t<DOUT>*>(B), p);
+      ++g_launches;
+      return cudaGetLastError();
+    }
+  };
+};
+
+template <int DIN, int DOUT>
+struct TileSlotsL {
+  template <int EK>
+  struct L {
+    static cudaError_t run(const void* A, void* B, const TileParams& p, int smem, cudaStream_t s) {
+      if (smem > 48 * 1024) {
+        int g = 0;
+        cudaError_t err = grid_for(reinterpret_cast<const void*>(&tile_slots_kernel<DIN, DOUT, EK>), smem, 1, &g);
+        if (err != cudaSuccess) return err;
+      }
+      tile_slots_kernel<DIN, DOUT, EK><<<p.ntiles, kThreads, smem, s>>>(static_cast<const store_t<DIN>*>(A),
+                                                                        static_cast<store_t<DOUT>*>(B), p);
       ++g_launches;
       return cudaGetLastError();
     }

@@ -12,6 +12,12 @@ cudaError_t TTC_CAT(launch_tile_, TTC_PAIR)(const void* A, void* B, const TilePa
   return with_ek<TTC_DIN, TTC_DOUT, TileL<TTC_DIN, TTC_DOUT>::template L>(p.epi.mode, p.epi.beta_nz, A, B, p, smem, s);
 }
 
+cudaError_t TTC_CAT(launch_tile_slots_, TTC_PAIR)(const void* A, void* B, const TileParams& p, int smem,
+                                                  cudaStream_t s) {
+  return with_ek<TTC_DIN, TTC_DOUT, TileSlotsL<TTC_DIN, TTC_DOUT>::template L>(p.epi.mode, p.epi.beta_nz, A, B, p, smem,
+                                                                              s);
+}
+
 cudaError_t TTC_CAT(launch_tile2_, TTC_PAIR)(int ju, int jw, const void* A, void* B, const TileParams& p, int smem,
                                              cudaStream_t s) {
   return launch_tile2_pair<TTC_DIN, TTC_DOUT>(ju, jw, A, B, p, smem, s);

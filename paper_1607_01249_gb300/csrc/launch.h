@@ -11,6 +11,8 @@ bool pair_supported(int din, int dout);
 int copy_vec_width(int din, int dout);
 cudaError_t launch_tile(int din, int dout, const void* A, void* B, const TileParams& p, int smem,
                         cudaStream_t s);
+cudaError_t launch_tile_slots(int din, int dout, const void* A, void* B, const TileParams& p, int smem,
+                              cudaStream_t s);
 cudaError_t launch_tile2(int din, int dout, int ju, int jw, const void* A, void* B, const TileParams& p,
                          int smem, cudaStream_t s);
 cudaError_t launch_rowcopy(int din, int dout, const void* A, void* B, const TileParams& p, cudaStream_t s);

@@ -44,12 +44,14 @@ constexpr double kLaneInstrPerS = 152.0 * 4 * 32 * 1.9e9;
 }  // namespace
 
 double run_efficiency(double bytes, bool write) {
-  // Measured on GB300 (2D transposes of misaligned sizes): a run costs as if
-  // it were `bytes + c` long, with c ~ 16 bytes for reads and ~64 bytes for
-  // writes -- the partial 32-byte sectors at both ends of a write run are
-  // expensive, so B's runs must be long while A's may be short.
+  // Measured on GB300 with the current kernels (2D and 3D transposes of
+  // aligned and misaligned sizes): a run costs as if it were `bytes + c`
+  // long, with c ~ 48 bytes for reads and ~16 bytes for writes.  Loads are
+  // what the kernels wait on, so long A runs pay off; partial sectors at the
+  // ends of B runs are mostly completed in L2 by the neighbouring tile before
+  // they are written back.
   if (bytes <= 0) return 1.0;
-  return bytes / (bytes + (write ? 64.0 : 16.0));
+  return bytes / (bytes + (write ? 16.0 : 48.0));
 }
 
 std::string Candidate::describe() const {
@@ -413,16 +415,22 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
             if ((!sh.ga.empty() && c.s[sh.ga.back()] >= (int64_t(1) << 30)) ||
                 (!sh.gb.empty() && c.s[sh.gb.back()] >= (int64_t(1) << 30)))
               continue;
-            // A tile without a C or GA index (U = 1) is loaded in GB's order,
-            // which steps through A by large strides: a warp's loads do not
-            // coalesce.  When the whole tile is one contiguous block of A, L1
-            // still catches most of the reuse (measured as if the runs were
-            // 8 elements long); otherwise nothing does.  Likewise for W = 1.
-            double ra = run_length(c, ext, orderA, c.sa), rb = run_length(c, ext, orderB, c.sb);
+            // Slot tables visit a tile's elements in address order on each
+            // side, so their runs are the tile footprint's contiguous runs.
+            // The index walks (tile2, the batch) load a tile without a C or GA
+            // index (U = 1) in GB's order, which steps through A by large
+            // strides: a warp's loads do not coalesce.  When the whole tile is
+            // one contiguous block of A, L1 still catches most of the reuse
+            // (measured as if the runs were 8 elements long); otherwise
+            // nothing does.  Likewise for W = 1.
+            const double ra_s = run_length(c, ext, orderA, c.sa), rb_s = run_length(c, ext, orderB, c.sb);
+            double ra = ra_s, rb = rb_s;
             if (LC * LA == 1) ra = ra >= double(V) ? 8.0 : 1.0;
             if (LC * LB == 1) rb = rb >= double(V) ? 8.0 : 1.0;
             const double mem = (n * esA / run_efficiency(ra * esA, false) +
                                 n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true)) / kHbmBytesPerS;
+            const double mem_s = (n * esA / run_efficiency(ra_s * esA, false) +
+                                  n * esB * (bnz ? 2 : 1) / run_efficiency(rb_s * esB, true)) / kHbmBytesPerS;
             const double per_slot = 26.0 + (sh.ga.size() > 1 ? 3 : 0) + (sh.gb.size() > 1 ? 3 : 0) + (bnz ? 6 : 0);
             const double issue = ntiles * kTileK * kThreads * per_slot / kLaneInstrPerS;
             const double over = ntiles * kThreads * (60.0 + 10.0 * c.N) / kLaneInstrPerS;
@@ -446,7 +454,7 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
               const double per_slot3 = 14.0 + (bnz ? 4 : 0);
               const double issue3 = ntiles * kTileK * kThreads * per_slot3 / kLaneInstrPerS;
               k.slots = 1;
-              k.est_s = std::max(1.08 * mem, issue3) + 0.25 * std::min(mem, issue3) + over + 3e-6;
+              k.est_s = std::max(1.08 * mem_s, issue3) + 0.25 * std::min(mem_s, issue3) + over + 3e-6;
             }
             tiles.push_back(k);
             // the warp-mapped kernel, when the shape fits one of its lane layouts
@@ -620,32 +628,68 @@ void build_row_params(const Canon& c, int64_t chunk, RowParams* p) {
 namespace {
 
 // One whole tile (no cut index short) run through the kernel's own index
-// walks on the host; every slot records what the walk gives it.
+// walks on the host collects every element's A offset, B offset and
+// shared-memory position.  The slots then take the elements in increasing A
+// offset (loads) and increasing B offset (stores): consecutive threads touch
+// consecutive addresses on both sides whatever the tile's index structure, so
+// a tile whose footprint is contiguous in A and in B (e.g. two small indices
+// swapped) is read and written as two dense blocks.
+struct SlotElem {
+  int32_t off;
+  int32_t pos;
+};
+
 template <int K>
 void slot_tables_k(const TileParams& p, const std::vector<int32_t>& tabA, const std::vector<int32_t>& tabB,
                    std::vector<int32_t>* out) {
   const TileCoord c{0, 0, p.LA, p.LB};
-  int32_t* q = out->data();
-  auto put = [&](int phase, int t, int k, bool ok, int32_t off, int pos) {
-    int32_t* e = q + ((size_t(phase) * (K / 2) + size_t(k / 2)) * kThreads + size_t(t)) * 4 + (k & 1) * 2;
-    e[0] = ok ? off : 0;
-    e[1] = ok ? pos : -1;
-  };
+  std::vector<SlotElem> rd, wr;
+  rd.reserve(size_t(p.V));
+  wr.reserve(size_t(p.V));
   for (int t = 0; t < kThreads; ++t) {
     int u0, lb0, lc0, lbw0, la0;
     flat_starts(p, t, u0, lb0, lc0, lbw0, la0);
-    auto rd = [&](int k, bool ok, int32_t off, int pos) { put(0, t, k, ok, off, pos); };
-    auto wr = [&](int k, bool ok, int32_t off, int pos) { put(1, t, k, ok, off, pos); };
-    if (p.crossA_tab) walk_read<K, true>(c, p, tabA.data(), u0, lb0, rd);
-    else walk_read<K, false>(c, p, tabA.data(), u0, lb0, rd);
-    if (p.crossB_tab) walk_write<K, true>(c, p, tabB.data(), lc0, lbw0, la0, wr);
-    else walk_write<K, false>(c, p, tabB.data(), lc0, lbw0, la0, wr);
+    auto on_rd = [&](int, bool ok, int32_t off, int pos) {
+      if (ok) rd.push_back({off, pos});
+    };
+    auto on_wr = [&](int, bool ok, int32_t off, int pos) {
+      if (ok) wr.push_back({off, pos});
+    };
+    if (p.crossA_tab) walk_read<K, true>(c, p, tabA.data(), u0, lb0, on_rd);
+    else walk_read<K, false>(c, p, tabA.data(), u0, lb0, on_rd);
+    if (p.crossB_tab) walk_write<K, true>(c, p, tabB.data(), lc0, lbw0, la0, on_wr);
+    else walk_write<K, false>(c, p, tabB.data(), lc0, lbw0, la0, on_wr);
+  }
+  auto by_off = [](const SlotElem& a, const SlotElem& b) { return a.off < b.off || (a.off == b.off && a.pos < b.pos); };
+  std::sort(rd.begin(), rd.end(), by_off);
+  std::sort(wr.begin(), wr.end(), by_off);
+  // layout (int32 units): read pairs, write pairs (K*kThreads*2 each), then
+  // read and write tile coordinates (K*kThreads each)
+  int32_t* q = out->data();
+  const size_t pairs = size_t(K) * kThreads * 2, coords = size_t(K) * kThreads;
+  auto put = [&](int phase, size_t f, const SlotElem* e) {
+    const size_t k = f / kThreads, t = f % kThreads;
+    int32_t* d = q + size_t(phase) * pairs + ((k / 2) * kThreads + t) * 4 + (k & 1) * 2;
+    d[0] = e ? e->off : 0;
+    d[1] = e ? e->pos : -1;
+    // the element's (la, lb) in the tile, from its shared-memory position
+    // (lb * P + la * LC + lc); 0xffffffff marks an empty slot
+    uint32_t lalb = 0xffffffffu;
+    if (e) {
+      const int lb = e->pos / p.P, la = (e->pos - lb * p.P) / p.LC;
+      lalb = (uint32_t(la) << 16) | uint32_t(lb);
+    }
+    q[2 * pairs + size_t(phase) * coords + ((k / 4) * kThreads + t) * 4 + (k & 3)] = int32_t(lalb);
+  };
+  for (size_t f = 0; f < size_t(K) * kThreads; ++f) {
+    put(0, f, f < rd.size() ? &rd[f] : nullptr);
+    put(1, f, f < wr.size() ? &wr[f] : nullptr);
   }
 }
 
 }  // namespace
 
-size_t slot_table_ints(int din) { return size_t(tile_k_for(stage_bytes(din))) * kThreads * 4; }
+size_t slot_table_ints(int din) { return size_t(tile_k_for(stage_bytes(din))) * kThreads * 6; }
 
 void build_slot_tables(const TileParams& p, int din, const std::vector<int32_t>& tabA,
                        const std::vector<int32_t>& tabB, std::vector<int32_t>* out) {

@@ -158,21 +158,23 @@ struct Checker {
         if (!ok) return false;
         continue;
       }
-      if (k.slots && full) {
-        // the kernel's slot-table path: slot (k, t) of phase f sits in int4
-        // (f*K/2 + k/2)*kThreads + t, half k&1; pos < 0 marks an empty slot
+      if (k.slots) {
+        // tile_slots_kernel: slot (k, t) of phase f sits in int4
+        // (f*K/2 + k/2)*kThreads + t, half k&1 (pos < 0: empty); a tile cut
+        // short keeps the slots whose coordinate (la << 16 | lb) lies inside
+        const size_t pairs = size_t(K) * kThreads * 2, coords = size_t(K) * kThreads;
         for (int f = 0; f < 2 && ok; ++f)
           for (int t = 0; t < kThreads && ok; ++t)
             for (int kk = 0; kk < K && ok; ++kk) {
               const int32_t* e =
-                  slots.data() + ((size_t(f) * (K / 2) + size_t(kk / 2)) * kThreads + size_t(t)) * 4 + (kk & 1) * 2;
-              if (f == 0) {
-                if (e[0] < 0 || (e[1] < 0 && e[0] != 0)) ok = fail("slot table: bad empty read slot", e[0], e[1]);
-                else on_read(kk, e[1] >= 0, e[0], e[1]);
-              } else {
-                if (e[0] < 0) ok = fail("slot table: negative write offset", e[0], e[1]);
-                else on_write(kk, e[1] >= 0, e[0], e[1]);
-              }
+                  slots.data() + size_t(f) * pairs + ((size_t(kk / 2)) * kThreads + size_t(t)) * 4 + (kk & 1) * 2;
+              const uint32_t lalb = uint32_t(
+                  slots[2 * pairs + size_t(f) * coords + (size_t(kk / 4) * kThreads + size_t(t)) * 4 + (kk & 3)]);
+              const bool in = full || (int(lalb >> 16) < c.remA && int(lalb & 0xffffu) < c.remB);
+              const bool valid = in && e[1] >= 0;
+              if (e[0] < 0) ok = fail("slot table: negative offset", e[0], e[1]);
+              else if (f == 0) on_read(kk, valid, e[0], e[1]);
+              else on_write(kk, valid, e[0], e[1]);
             }
       } else if (k.ju == 0) {
         for (int t = 0; t < kThreads && ok; ++t) {
@@ -268,5 +270,12 @@ extern "C" ttc_status ttc_debug_verify_schedule(ttc_plan_t plan, int candidate, 
     say(k.describe() + ": " + ck.err);
     return TTC_ERR_INVALID_ARG;
   }
+  return TTC_OK;
+}
+
+extern "C" ttc_status ttc_debug_describe_candidate(ttc_plan_t plan, int candidate, char* buf, int buflen) {
+  if (!plan || !buf || buflen <= 0 || candidate < 0 || candidate >= int(plan->cands.size()))
+    return TTC_ERR_INVALID_ARG;
+  std::snprintf(buf, size_t(buflen), "%s", plan->cands[size_t(candidate)].describe().c_str());
   return TTC_OK;
 }

@@ -123,11 +123,12 @@ struct TileParams {
   int crossB_tab;      // nonzero: crossB comes from a table of LA entries
   const int32_t* tabA; // device table crossA[LB]
   const int32_t* tabB; // device table crossB[LA]
-  // Optional slot tables of a whole tile (tile_kernel): for every (k, thread)
-  // slot of the read and of the write order, the element's offset in the tile
-  // and its shared-memory position (-1: no element), two slots per int4:
-  // read slots [K/2][kThreads], then write slots [K/2][kThreads].  Null: the
-  // kernel walks the indices instead.
+  // Slot tables of tile_slots_kernel: for every (k, thread) slot of the load
+  // and of the store order, the element's offset in the tile and its
+  // shared-memory position (-1: no element), two slots per int4 -- load slots
+  // [K/2][kThreads], then store slots [K/2][kThreads] -- followed by each
+  // slot's tile coordinate (la << 16 | lb, 0xffffffff: no element), four per
+  // int4: load [K/4][kThreads], then store [K/4][kThreads].
   const int4* slots;
   // per-thread step of kThreads in the read order (u, lb) and write order (lc, lb, la)
   int rd_du, rd_dlb;

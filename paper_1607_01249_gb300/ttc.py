@@ -89,6 +89,7 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     # include/ttc_debug.h
     "ttc_debug_verify_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
+    "ttc_debug_describe_candidate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
 }
 
 _lib = None
@@ -194,7 +195,8 @@ class Plan:
                 "ncandidates": inf.ncandidates, "lanes": (inf.lanes_a, inf.lanes_b),
                 "slot_tables": bool(inf.slot_tables),
                 "kernel": ({0: "empty", 1: "copy_kernel", 3: "rowcopy_kernel"}.get(inf.variant) or
-                           ("tile2_kernel" if inf.lanes_a else "tile_kernel"))}
+                           ("tile2_kernel" if inf.lanes_a else
+                            "tile_slots_kernel" if inf.slot_tables else "tile_kernel"))}
 
     def autotune(self, max_candidates=8, stream=None) -> float:
         ms = ctypes.c_float(0)
@@ -209,6 +211,15 @@ class Plan:
         buf = ctypes.create_string_buffer(512)
         st = lib().ttc_debug_verify_schedule(self._h, int(candidate), buf, 512)
         return "" if st == 0 else buf.value.decode(errors="replace") or "failed"
+
+    def describe(self, candidate=None) -> str:
+        """The planner's description of a candidate schedule (kernel, tile
+        groups, lanes, grid order, estimate)."""
+        if candidate is None:
+            candidate = self.info()["candidate"]
+        buf = ctypes.create_string_buffer(1024)
+        _check(lib().ttc_debug_describe_candidate(self._h, int(candidate), buf, 1024))
+        return buf.value.decode(errors="replace")
 
     def select(self, index: int):
         _check(lib().ttc_plan_select_candidate(self._h, int(index)))
