@@ -457,10 +457,10 @@ def serve_trace(srv, ttc, trace, plans, pa, pb, paced: bool):
     srv.drain(600_000_000)
     lat, first, last, detail = [], None, None, []
     for (ta, _), t, sp in zip(trace, tickets, sub_perf):
-        s_sub, s_launch, s_done = srv.times(t)
+        s_sub, s_admit, s_launch, s_done = srv.times(t)
         arrival = (t0 + ta) if paced else t0
         lat.append(((s_done - s_sub) + (sp - arrival)) * 1e6)
-        detail.append(((s_launch - s_sub) * 1e6, (s_done - s_launch) * 1e6))
+        detail.append(((s_admit - s_sub) * 1e6, (s_launch - s_admit) * 1e6, (s_done - s_launch) * 1e6))
         first = s_sub if first is None else min(first, s_sub)
         last = s_done if last is None else max(last, s_done)
     serve_trace.detail = detail
@@ -519,7 +519,7 @@ def run_serving(args, rank, world):
                     json.dump([{"perm": p.perm, "sizes": p.sizes, "din": p.dtype_in, "dout": p.dtype_out,
                                 "outer": p.outer_a is not None, "bytes": p.algorithmic_bytes(),
                                 "kernel": pl.info()["kernel"], "lat_us": round(float(l), 1),
-                                "queue_us": round(d[0], 1), "run_us": round(d[1], 1)}
+                                "queue_us": round(d[0], 1), "launch_us": round(d[1], 1), "run_us": round(d[2], 1)}
                                for p, pl, l, d in zip(probs, plans, lat, serve_trace.detail)], f)
             lat_all.append(lat)
             lags.append(lag)

@@ -273,7 +273,8 @@ ttc_status ttc_batch_info(ttc_batch_t batch, int64_t* problems, int64_t* tiles);
  *  ttc_server_drain    wait until every submitted request has completed
  *                      (bounded by timeout_us; TTC_ERR_TIMEOUT otherwise).
  *  ttc_server_stats    counters and latency percentiles of completed requests.
- *  ttc_server_times    submission time, launch time (when its kernel was
+ *  ttc_server_times    submission time, admission time (taken from the
+ *                      queue by the scheduler), launch time (its kernel
  *                      enqueued) and detected-completion time of one request
  *                      (host steady clock, seconds); TTC_ERR_NOT_READY until
  *                      it has completed.
@@ -294,8 +295,8 @@ ttc_status ttc_server_submit(ttc_server_t server, ttc_plan_t plan, const void* A
 ttc_status ttc_server_poll(ttc_server_t server, int64_t ticket, int64_t timeout_us);
 ttc_status ttc_server_drain(ttc_server_t server, int64_t timeout_us);
 ttc_status ttc_server_stats(ttc_server_t server, ttc_server_stats_t* stats);
-ttc_status ttc_server_times(ttc_server_t server, int64_t ticket, double* submit_s, double* launch_s,
-                            double* complete_s);
+ttc_status ttc_server_times(ttc_server_t server, int64_t ticket, double* submit_s, double* admit_s,
+                            double* launch_s, double* complete_s);
 ttc_status ttc_server_destroy(ttc_server_t server);
 
 /*

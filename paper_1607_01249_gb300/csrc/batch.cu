@@ -4,7 +4,9 @@
 // Every problem of a batch is cut into tiles by its own plan.  A tile is
 // processed by one CTA with one of three bodies:
 //   BP_TILE -- the generic staged tile (flat walks, offset tables for both
-//              cross offsets), for problems whose perm moves index 0;
+//              cross offsets), for problems whose perm moves index 0 (the
+//              warp-mapped walks of tile2_kernel measured slower here: the
+//              batch's small problems leave most of their lanes idle);
 //   BP_ROWS -- the multi-row copy (perm keeps index 0, short runs);
 //   BP_COPY -- one chunk of one long run (perm keeps index 0, long runs).
 // Resident CTAs claim tiles from one atomic counter (uneven problems balance
@@ -124,46 +126,97 @@ __device__ __forceinline__ void batch_dispatch(const BatchDesc& d, const TileRec
   }
 }
 
+// The record of tile q of a problem, computed on the device (thread 0) when
+// the launch has no precomputed records.
+__device__ __forceinline__ TileRec device_rec(const BatchDesc& d, uint32_t prob, uint32_t q) {
+  TileRec r;
+  r.prob = prob;
+  r.pad = 0;
+  if (d.path == BP_COPY) {
+    const RowCoord rc = row_coord(q, d.rp);
+    r.baseA = rc.offA;
+    r.baseB = rc.offB;
+    r.remA = int32_t(rc.start);
+    r.remB = int32_t(rc.end - rc.start);
+  } else {
+    const TileCoord c = tile_coord(q, d.tp);
+    r.baseA = c.baseA;
+    r.baseB = c.baseB;
+    r.remA = c.remA;
+    r.remB = c.remB;
+  }
+  return r;
+}
+
+// problem of global tile g: the last p with tile0[p] <= g (tile0 ascending,
+// tile0[0] = 0, nprob entries)
+__device__ __forceinline__ uint32_t find_problem(const uint32_t* __restrict__ tile0, uint32_t nprob, uint32_t g) {
+  uint32_t lo = 0, hi = nprob;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(tile0 + mid) <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // Persistent: resident CTAs claim tiles from one counter (uneven problems
 // balance themselves).  The claim of the next tile is issued while the
-// current one is processed, so only its record load is exposed; the current
-// problem's descriptor is kept in shared memory and reloaded only when the
-// problem changes.
+// current one is processed; the current problem's descriptor is kept in
+// shared memory and reloaded only when the problem changes.  A tile's record
+// comes either from the precomputed array `recs` (ttc_batch_*, built once and
+// replayed) or, when recs is null, from the problem's tile prefix `tile0`
+// and its tile parameters on the device (the server, whose epochs are built
+// per launch and should cost the host nothing per tile).
 __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc* __restrict__ descs,
                                                             const TileRec* __restrict__ recs,
+                                                            const uint32_t* __restrict__ tile0, uint32_t nprob,
                                                             uint32_t total, uint32_t* counter) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ uint32_t s_g;
+  __shared__ uint32_t s_g, s_p;
   __shared__ TileRec s_rec;
-  __shared__ __align__(16) BatchDesc s_desc;
+  // raw storage: BatchDesc has member initializers, which a __shared__
+  // variable cannot run
+  __shared__ __align__(16) unsigned char s_desc_raw[sizeof(BatchDesc)];
+  BatchDesc& s_desc = *reinterpret_cast<BatchDesc*>(s_desc_raw);
   constexpr int kWords = int(sizeof(BatchDesc) / sizeof(int4));
   static_assert(sizeof(BatchDesc) % sizeof(int4) == 0, "descriptor copied as 16-byte words");
   const int t = threadIdx.x;
   uint32_t have = 0xffffffffu;
-  if (t == 0) {
-    s_g = atomicAdd(counter, 1u);
-    if (s_g < total) s_rec = recs[s_g];
-  }
+  auto claim = [&](uint32_t g) {   // thread 0: remember tile g and its problem
+    s_g = g;
+    if (g < total) {
+      if (recs) {
+        s_rec = recs[g];
+        s_p = s_rec.prob;
+      } else {
+        s_p = find_problem(tile0, nprob, g);
+      }
+    }
+  };
+  if (t == 0) claim(atomicAdd(counter, 1u));
   __syncthreads();
   for (;;) {
     const uint32_t g = s_g;
     if (g >= total) break;
-    const TileRec r = s_rec;
+    const uint32_t prob = s_p;
     uint32_t gn = 0;
     if (t == 0) gn = atomicAdd(counter, 1u);
-    if (r.prob != have) {
-      const int4* src = reinterpret_cast<const int4*>(descs + r.prob);
+    if (prob != have) {
+      const int4* src = reinterpret_cast<const int4*>(descs + prob);
       int4* dst = reinterpret_cast<int4*>(&s_desc);
       for (int i = t; i < kWords; i += kThreads) dst[i] = src[i];
-      have = r.prob;
+      have = prob;
       __syncthreads();
     }
+    if (!recs) {
+      if (t == 0) s_rec = device_rec(s_desc, prob, g - __ldg(tile0 + prob));
+      __syncthreads();
+    }
+    const TileRec r = s_rec;
     batch_dispatch(s_desc, r, smem);
     __syncthreads();   // the tile buffer and s_rec are reused
-    if (t == 0) {
-      s_g = gn;
-      if (gn < total) s_rec = recs[gn];
-    }
+    if (t == 0) claim(gn);
     __syncthreads();
   }
 }
@@ -273,15 +326,15 @@ void batch_records(const BatchDesc& d, uint32_t prob, std::vector<TileRec>* recs
   }
 }
 
-cudaError_t batch_launch(const BatchDesc* d_descs, const TileRec* d_recs, uint32_t total, uint32_t* d_counter,
-                         int smem, cudaStream_t s) {
+cudaError_t batch_launch(const BatchDesc* d_descs, const TileRec* d_recs, const uint32_t* d_tile0, uint32_t nprob,
+                         uint32_t total, uint32_t* d_counter, int smem, cudaStream_t s) {
   if (total == 0) return cudaSuccess;
   int grid = 0;
   cudaError_t e = grid_for(reinterpret_cast<const void*>(&batch_kernel), smem, int64_t(total), &grid);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  batch_kernel<<<grid, kThreads, smem, s>>>(d_descs, d_recs, total, d_counter);
+  batch_kernel<<<grid, kThreads, smem, s>>>(d_descs, d_recs, d_tile0, nprob, total, d_counter);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -395,7 +448,7 @@ ttc_status batch_build(ttc_batch_s* b) {
 
 ttc_status batch_enqueue(ttc_batch_s* b, cudaStream_t s) {
   if (b->total == 0) return TTC_OK;
-  cudaError_t e = batch_launch(b->d_descs, b->d_recs, b->total, b->d_counter, b->smem, s);
+  cudaError_t e = batch_launch(b->d_descs, b->d_recs, nullptr, 0, b->total, b->d_counter, b->smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
   return TTC_OK;
 }

@@ -63,7 +63,9 @@ int64_t batch_tiles(ttc_plan_s* p);
 void batch_records(const BatchDesc& d, uint32_t prob, std::vector<TileRec>* recs);
 
 // Enqueue the counter reset and the persistent kernel (grid from occupancy).
-cudaError_t batch_launch(const BatchDesc* d_descs, const TileRec* d_recs, uint32_t total, uint32_t* d_counter,
-                         int smem, cudaStream_t s);
+// With d_recs null the kernel derives each tile's record on the device from
+// d_tile0 (the first global tile of each of the nprob problems, ascending).
+cudaError_t batch_launch(const BatchDesc* d_descs, const TileRec* d_recs, const uint32_t* d_tile0, uint32_t nprob,
+                         uint32_t total, uint32_t* d_counter, int smem, cudaStream_t s);
 
 }  // namespace ttc

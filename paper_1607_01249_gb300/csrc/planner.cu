@@ -43,14 +43,16 @@ constexpr double kLaneInstrPerS = 152.0 * 4 * 32 * 1.9e9;
 
 }  // namespace
 
-double run_efficiency(double bytes, bool write) {
-  // Measured on GB300 with the current kernels (2D and 3D transposes of
-  // aligned and misaligned sizes): a run costs as if it were `bytes + c`
-  // long, with c ~ 48 bytes for reads and ~16 bytes for writes.  Loads are
-  // what the kernels wait on, so long A runs pay off; partial sectors at the
-  // ends of B runs are mostly completed in L2 by the neighbouring tile before
-  // they are written back.
+double run_efficiency(double bytes, bool write, bool flat) {
+  // Measured on GB300 (2D and 3D transposes of aligned and misaligned
+  // sizes): a run costs as if it were `bytes + c` long.  For the single-plan
+  // kernels c ~ 48 bytes for reads and ~16 bytes for writes: loads are what
+  // they wait on, so long A runs pay off, while partial sectors at the ends of
+  // B runs are mostly completed in L2 by the neighbouring tile before they are
+  // written back.  The batch body's flat walks (half-size tiles, every CTA on
+  // a different problem) fit c ~ 16 for reads and ~64 for writes instead.
   if (bytes <= 0) return 1.0;
+  if (flat) return bytes / (bytes + (write ? 64.0 : 16.0));
   return bytes / (bytes + (write ? 16.0 : 48.0));
 }
 
@@ -269,6 +271,7 @@ std::vector<int> grid_order(const Canon& c, const int64_t* ext, int mode) {
 
 std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double beta, int max_keep, int vmax) {
   std::vector<Candidate> out;
+  const bool flat = vmax > 0;   // the batch body
   if (c.N == 0) {
     out.push_back(Candidate());
     return out;
@@ -297,8 +300,8 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
     const double ra = c.sa[0] == 1 ? double(len) : 1.0, rb = c.sb[0] == 1 ? double(len) : 1.0;
     k.seg_a = ra;
     k.seg_b = rb;
-    const double mem = (n * esA / run_efficiency(ra * esA, false) +
-                        n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true)) / kHbmBytesPerS;
+    const double mem = (n * esA / run_efficiency(ra * esA, false, flat) +
+                        n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true, flat)) / kHbmBytesPerS;
     const double rows = n / double(len);
     const double lanes_per_row = std::ceil(double(len) / (32.0 * k.vec)) * 32.0;
     const double issue = (rows * lanes_per_row * 10.0 + rows * 32.0 * (8.0 * c.N)) / kLaneInstrPerS;
@@ -335,8 +338,8 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
         const double ra = run_length(c, ext, orderA, c.sa), rb = run_length(c, ext, orderB, c.sb);
         k.seg_a = ra;
         k.seg_b = rb;
-        const double mem = (n * esA / run_efficiency(ra * esA, false) +
-                            n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true)) / kHbmBytesPerS;
+        const double mem = (n * esA / run_efficiency(ra * esA, false, flat) +
+                            n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true, flat)) / kHbmBytesPerS;
         const double issue = ntiles * kThreads * Kt * (10.0 + (bnz ? 3 : 0)) / kLaneInstrPerS;
         const double over = ntiles * kThreads * (40.0 + 10.0 * c.N) / kLaneInstrPerS;
         const double fill = double(c.s[0]) * G / double(vcap);   // share of the unrolled slots in use
@@ -427,10 +430,10 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
             double ra = ra_s, rb = rb_s;
             if (LC * LA == 1) ra = ra >= double(V) ? 8.0 : 1.0;
             if (LC * LB == 1) rb = rb >= double(V) ? 8.0 : 1.0;
-            const double mem = (n * esA / run_efficiency(ra * esA, false) +
-                                n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true)) / kHbmBytesPerS;
-            const double mem_s = (n * esA / run_efficiency(ra_s * esA, false) +
-                                  n * esB * (bnz ? 2 : 1) / run_efficiency(rb_s * esB, true)) / kHbmBytesPerS;
+            const double mem = (n * esA / run_efficiency(ra * esA, false, flat) +
+                                n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true, flat)) / kHbmBytesPerS;
+            const double mem_s = (n * esA / run_efficiency(ra_s * esA, false, flat) +
+                                  n * esB * (bnz ? 2 : 1) / run_efficiency(rb_s * esB, true, flat)) / kHbmBytesPerS;
             const double per_slot = 26.0 + (sh.ga.size() > 1 ? 3 : 0) + (sh.gb.size() > 1 ? 3 : 0) + (bnz ? 6 : 0);
             const double issue = ntiles * kTileK * kThreads * per_slot / kLaneInstrPerS;
             const double over = ntiles * kThreads * (60.0 + 10.0 * c.N) / kLaneInstrPerS;
@@ -457,13 +460,18 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
               k.est_s = std::max(1.08 * mem_s, issue3) + 0.25 * std::min(mem_s, issue3) + over + 3e-6;
             }
             tiles.push_back(k);
-            // the warp-mapped kernel, when the shape fits one of its lane layouts
+            // the warp-mapped kernel (single-plan only), when the shape fits
+            // one of its lane layouts
             const int64_t U = LC * LA, W = LC * LB;
             int ju = 0, jw = 0;
             for (int j : {1, 2, 4})
-              if (!ju && U <= 32 * j && LB <= 8 * Kt / j) ju = j;
+              if (!ju && vmax == 0 && U <= 32 * j && LB <= 8 * Kt / j) ju = j;
             for (int j : {1, 2, 4})
-              if (!jw && W <= 32 * j && LA <= 8 * Kt / j) jw = j;
+              if (!jw && vmax == 0 && W <= 32 * j && LA <= 8 * Kt / j) jw = j;
+            // a run shorter than half a warp leaves most lanes idle: every
+            // warp access then carries a few elements only (measured slower
+            // than the flat walk in the batch body)
+            if (U < 16 || W < 16) ju = jw = 0;
             if (ju && jw) {
               const double rows_r = std::ceil(double(LB) / 8.0), rows_w = std::ceil(double(LA) / 8.0);
               const double wi = 8.0 * (rows_r * (ju * 4.0 + 4.0 + (sh.gb.size() > 1 ? 2 : 0)) +

@@ -70,7 +70,8 @@ void build_slot_tables(const TileParams& p, int din, const std::vector<int32_t>&
 size_t slot_table_ints(int din);
 
 // Estimated memory efficiency of reading (write = false) or writing a
-// contiguous run of `bytes` bytes that starts at an arbitrary element offset.
-double run_efficiency(double bytes, bool write);
+// contiguous run of `bytes` bytes that starts at an arbitrary element offset,
+// for the single-plan kernels or (flat = true) the batch body.
+double run_efficiency(double bytes, bool write, bool flat = false);
 
 }  // namespace ttc

@@ -59,7 +59,7 @@ struct Req {
   int64_t alg_bytes;   // algorithmic bytes
   int64_t tiles;       // tiles in the batch body, or -1 if it cannot take the request
   int cls;             // size class: 0 batchable, 1 medium, 2 large
-  double t_submit = 0, t_launch = 0, t_done = 0;
+  double t_submit = 0, t_admit = 0, t_launch = 0, t_done = 0;
   int state = RQ_PENDING;
   ttc_status status = TTC_OK;
 };
@@ -113,11 +113,13 @@ bool is_small(const ttc_server_s* S, const Req& r) { return r.tiles >= 0 && r.ti
 
 // Lay out the batched launch of `small` in descriptor slot `slot` of lane L
 // (pinned staging, then one copy to the device slot on the lane's stream)
-// and launch it.
+// and launch it.  Per problem the host writes its descriptor, its offset
+// tables and its first global tile; the kernel derives the tiles' records.
 ttc_status launch_batched(Lane& L, int slot, const std::vector<Req*>& small, int* launches) {
   std::vector<BatchDesc> descs;
   std::vector<int32_t> tabs;
   std::vector<size_t> tab_at, tab_na;
+  std::vector<uint32_t> tile0;
   int smem = 0;
   uint64_t total = 0;
   for (Req* r : small) {
@@ -126,6 +128,7 @@ ttc_status launch_batched(Lane& L, int slot, const std::vector<Req*>& small, int
     const size_t at = tabs.size();
     if (!batch_describe(r->plan, r->A, r->B, &d, &tabs, &na, &smem)) continue;
     d.tile0 = uint32_t(total);
+    tile0.push_back(uint32_t(total));
     total += d.ntiles;
     descs.push_back(d);
     tab_at.push_back(at);
@@ -133,28 +136,25 @@ ttc_status launch_batched(Lane& L, int slot, const std::vector<Req*>& small, int
   }
   if (descs.empty()) return TTC_OK;
   const size_t off_tab = (descs.size() * sizeof(BatchDesc) + 255) & ~size_t(255);
-  const size_t off_rec = (off_tab + tabs.size() * 4 + 255) & ~size_t(255);
-  const size_t off_cnt = (off_rec + total * sizeof(TileRec) + 255) & ~size_t(255);
+  const size_t off_t0 = (off_tab + tabs.size() * 4 + 255) & ~size_t(255);
+  const size_t off_cnt = (off_t0 + tile0.size() * 4 + 255) & ~size_t(255);
   if (off_cnt + 256 > kSlotBytes) return fail(TTC_ERR_INVALID_SIZE, "epoch exceeds the descriptor slot");
   char* hb = L.h_slots + size_t(slot) * kSlotBytes;
   char* db = L.d_slots + size_t(slot) * kSlotBytes;
   int32_t* d_tab = reinterpret_cast<int32_t*>(db + off_tab);
-  std::vector<TileRec> recs;
-  recs.reserve(total);
   for (size_t i = 0; i < descs.size(); ++i) {
     if (descs[i].path == BP_TILE) {
       descs[i].tp.tabA = d_tab + tab_at[i];
       descs[i].tp.tabB = d_tab + tab_at[i] + tab_na[i];
     }
-    batch_records(descs[i], uint32_t(i), &recs);
   }
   std::memcpy(hb, descs.data(), descs.size() * sizeof(BatchDesc));
   if (!tabs.empty()) std::memcpy(hb + off_tab, tabs.data(), tabs.size() * 4);
-  std::memcpy(hb + off_rec, recs.data(), recs.size() * sizeof(TileRec));
+  std::memcpy(hb + off_t0, tile0.data(), tile0.size() * 4);
   cudaError_t e = cudaMemcpyAsync(db, hb, off_cnt, cudaMemcpyHostToDevice, L.s);
   if (e != cudaSuccess) return cuda_fail(e, "server descriptor upload");
-  e = batch_launch(reinterpret_cast<BatchDesc*>(db), reinterpret_cast<TileRec*>(db + off_rec), uint32_t(total),
-                   reinterpret_cast<uint32_t*>(db + off_cnt), smem, L.s);
+  e = batch_launch(reinterpret_cast<BatchDesc*>(db), nullptr, reinterpret_cast<uint32_t*>(db + off_t0),
+                   uint32_t(descs.size()), uint32_t(total), reinterpret_cast<uint32_t*>(db + off_cnt), smem, L.s);
   if (e != cudaSuccess) return cuda_fail(e, "server batch launch");
   ++*launches;
   return TTC_OK;
@@ -214,7 +214,7 @@ void scheduler(ttc_server_s* S) {
       const bool small = is_small(S, r);
       if (small != f_small || r.cls != f_cls) break;
       if (small) {
-        const size_t need = sizeof(BatchDesc) + 16384 + size_t(r.tiles) * sizeof(TileRec);
+        const size_t need = sizeof(BatchDesc) + 16384 + 4;
         if (slot_need + need > kSlotBytes) break;
         slot_need += need;
       }
@@ -250,9 +250,11 @@ void scheduler(ttc_server_s* S) {
     }
     std::vector<Req*> rs;
     std::vector<ttc_plan_t> fp8s;
+    const double ta = now_s();
     for (int64_t t : take) {
       Req& r = S->reqs[size_t(t)];
       r.state = RQ_RUNNING;
+      r.t_admit = ta;
       if (r.plan->dout == DT_E4M3) fp8s.push_back(r.plan);
       rs.push_back(&r);
     }
@@ -462,6 +464,19 @@ ttc_status ttc_server_submit(ttc_server_t S, ttc_plan_t plan, const void* A, voi
   }
   r.tiles = -1;
   if (S->small_tiles > 0 && plan->dout != DT_E4M3 && plan->canon.n > 0) r.tiles = batch_tiles(plan);
+  if (plan->canon.n > 0) {
+    // the plan's device scratch and tables are set up here, on the caller's
+    // thread, the first time the plan meets this device: done by the
+    // scheduler it would stall every request queued behind this one
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e == cudaSuccess && cur != S->dev) e = cudaSetDevice(S->dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    DevRes* res = nullptr;
+    const ttc_status st = ensure_device(plan, S->dev, &res);
+    if (cur != S->dev) cudaSetDevice(cur);
+    if (st != TTC_OK) return st;
+  }
   r.cls = S->small_tiles == 0 ? 0 : is_small(S, r) ? 0 : r.alg_bytes <= kMediumBytes ? 1 : 2;
   r.t_submit = now_s();
   std::lock_guard<std::mutex> lk(S->mu);
@@ -537,12 +552,14 @@ ttc_status ttc_server_stats(ttc_server_t S, ttc_server_stats_t* st) {
   return TTC_OK;
 }
 
-ttc_status ttc_server_times(ttc_server_t S, int64_t ticket, double* submit_s, double* launch_s, double* complete_s) {
-  if (!S || !submit_s || !launch_s || !complete_s) return fail(TTC_ERR_INVALID_ARG, "NULL argument");
+ttc_status ttc_server_times(ttc_server_t S, int64_t ticket, double* submit_s, double* admit_s, double* launch_s,
+                            double* complete_s) {
+  if (!S || !submit_s || !admit_s || !launch_s || !complete_s) return fail(TTC_ERR_INVALID_ARG, "NULL argument");
   std::lock_guard<std::mutex> lk(S->mu);
   if (ticket < 0 || ticket >= int64_t(S->reqs.size())) return fail(TTC_ERR_INVALID_ARG, "no such ticket");
   const Req& r = S->reqs[size_t(ticket)];
   *submit_s = r.t_submit;
+  *admit_s = r.t_admit;
   *launch_s = r.t_launch;
   *complete_s = r.t_done;
   return r.state == RQ_DONE ? TTC_OK : fail(TTC_ERR_NOT_READY, "request not finished");

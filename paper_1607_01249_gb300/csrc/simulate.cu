@@ -12,6 +12,7 @@
 #include "../../include/ttc_debug.h"
 #include "kernels.cuh"
 #include "plan_impl.h"
+#include "batch_impl.h"
 #include "planner.h"
 
 using namespace ttc;
@@ -114,6 +115,12 @@ struct Checker {
   bool tile(const Candidate& k) {
     if (p->din == DT_F64) return tile_k<tile_k_for(8)>(k);
     return tile_k<tile_k_for(4)>(k);
+  }
+
+  // the batch body's tiles (half the slots per thread)
+  bool tile_batch(const Candidate& k) {
+    if (p->din == DT_F64) return tile_k<batch_k_for(8)>(k);
+    return tile_k<batch_k_for(4)>(k);
   }
 
   template <int K>
@@ -253,19 +260,29 @@ extern "C" ttc_status ttc_debug_verify_schedule(ttc_plan_t plan, int candidate, 
       std::snprintf(msg, size_t(msglen), "%s", s.c_str());
     }
   };
-  if (!plan || candidate < 0 || candidate >= int(plan->cands.size())) {
+  if (!plan || candidate < -1 || candidate >= int(plan->cands.size())) {
     say("bad plan or candidate");
     return TTC_ERR_INVALID_ARG;
   }
   say("");
   if (plan->canon.n == 0) return TTC_OK;
   Checker ck(plan);
-  const Candidate& k = plan->cands[candidate];
+  Candidate k;
+  bool batch = candidate == -1;
+  if (batch) {
+    // the schedule the batch body (ttc_batch_*, the server) runs for this plan
+    if (plan->dout == DT_E4M3) return TTC_OK;
+    k = make_candidates(plan->canon, plan->din, plan->dout, plan->beta, 4,
+                        kThreads * batch_k_for(plan->din == DT_F64 ? 8 : 4)).front();
+    if (k.variant == VAR_COPY) k.chunk = kBatchCopyChunk / (plan->din == DT_F64 ? 2 : 1);
+  } else {
+    k = plan->cands[candidate];
+  }
   bool ok = true;
-  if (k.variant == VAR_TILE) ok = ck.tile(k);
+  if (k.variant == VAR_TILE) ok = batch ? ck.tile_batch(k) : ck.tile(k);
   else if (k.variant == VAR_COPY) ok = ck.copy(k);
   if (ok && ck.writes != plan->canon.n) ok = ck.fail("wrong number of B elements written", ck.writes, plan->canon.n);
-  if (ok && plan->dout == DT_E4M3) ok = ck.amax();
+  if (ok && plan->dout == DT_E4M3 && !batch) ok = ck.amax();
   if (!ok) {
     say(k.describe() + ": " + ck.err);
     return TTC_ERR_INVALID_ARG;

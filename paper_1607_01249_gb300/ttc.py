@@ -85,8 +85,7 @@ SIGNATURES = {
     "ttc_server_drain": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "ttc_server_stats": (ctypes.c_int, [_vp, _vp]),
     "ttc_server_destroy": (ctypes.c_int, [_vp]),
-    "ttc_server_times": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
-                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "ttc_server_times": (ctypes.c_int, [_vp, ctypes.c_int64] + [ctypes.POINTER(ctypes.c_double)] * 4),
     # include/ttc_debug.h
     "ttc_debug_verify_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
     "ttc_debug_describe_candidate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
@@ -205,7 +204,8 @@ class Plan:
 
     def verify_schedule(self, candidate=None) -> str:
         """Host-side check of a schedule's index arithmetic (no GPU); returns
-        "" when it is sound, else a description of the first violation."""
+        "" when it is sound, else a description of the first violation.
+        candidate=-1 checks the batched body's schedule for this plan."""
         if candidate is None:
             candidate = self.info()["candidate"]
         buf = ctypes.create_string_buffer(512)
@@ -314,11 +314,11 @@ class Server:
         self._keep.clear()
 
     def times(self, ticket: int):
-        """(submit_s, launch_s, complete_s) of a completed request, host
-        steady clock."""
-        a, b, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
-        _check(lib().ttc_server_times(self._h, int(ticket), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-        return a.value, b.value, c.value
+        """(submit_s, admit_s, launch_s, complete_s) of a completed request,
+        host steady clock."""
+        v = [ctypes.c_double(0) for _ in range(4)]
+        _check(lib().ttc_server_times(self._h, int(ticket), *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def stats(self) -> dict:
         st = ServerStats()
