@@ -6,6 +6,12 @@ N, FP32 and FP64, alpha = 1.7, beta in {0, 0.4}) = 160 transposes through the
 C ABI, inputs resident in HBM.  Metric: effective HBM bandwidth (decimal GB/s)
 counting n*(s_A + s_B) bytes for beta = 0 and n*(s_A + 2 s_B) otherwise.
 
+With the default workload on one GPU the line also carries `batch` (4096
+uneven transposes in one graph-launched persistent kernel against one launch
+per transpose) and `serving` (a Poisson request trace through the
+continuous-batching server against one launch per request, in arrival order,
+on one stream) summaries; --no-batch / --no-serving skip them.
+
 Other workloads (`--workload`): single4d, packing, batch, serving.
 
 --impl reference times the CPU oracle (plain C, FP64 arithmetic) on the host
@@ -740,6 +746,8 @@ def main():
                     help="time up to this many candidates per plan before the timed steps (0: cost model only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="default workload: skip the batched-launch summary")
+    ap.add_argument("--no-serving", action="store_true", help="default workload: skip the serving summary")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--target", type=int, default=1 << 26, help="elements per tensor of the sweep")
     ap.add_argument("--only", default="", help="comma-separated case tags of the sweep (e.g. N5p3)")
@@ -767,6 +775,31 @@ def main():
         out = run_serving_line(args, rank, world)
     else:
         out = run_ours(args, rank, world)
+        if args.workload == "sweep" and world == 1:
+            # the other two headline patterns, summarised in the same line:
+            # the batched launch and the server, each against one launch per
+            # transpose on the same GPU
+            import copy
+            sub = copy.copy(args)
+            sub.steps, sub.warmup = min(args.steps, 5), max(args.warmup, 3)
+            if not args.no_batch:
+                b = run_batch(sub, rank, world)
+                out["batch"] = {"workload": b["config"]["workload"], "GB/s": b["value"],
+                                "transposes_per_s": b["batch"]["transposes_per_s"],
+                                "per_call_transposes_per_s": b["per_call"]["transposes_per_s"],
+                                "speedup_vs_per_call": b["speedup_vs_per_call"], "ms_per_step": b["ms_per_step"],
+                                "roofline_frac": b["roofline"]["frac"], "timing": "CUDA events"}
+            if not args.no_serving:
+                sub.steps = min(args.steps, 3)
+                sv = run_serving(sub, rank, world)
+                c, q = sv["continuous"], sv["per_call"]
+                keys = ("served_transposes_per_s", "p50_us", "p90_us", "p99_us", "saturated_transposes_per_s",
+                        "saturated_GB/s")
+                out["serving"] = {"workload": sv["workload"], "continuous": {k: c[k] for k in keys},
+                                  "per_call": {k: q[k] for k in keys},
+                                  "p99_ratio_per_call_over_continuous": sv["p99_ratio_per_call_over_continuous"],
+                                  "saturated_speedup_vs_per_call": sv["saturated_speedup_vs_per_call"],
+                                  "timing": "host steady clock, arrival to detected completion"}
     if rank == 0:
         if not args.no_cpu and world == 1 and args.workload not in ("batch", "serving"):
             out["cpu_baseline"] = cpu_baseline(args.cpu_budget,
