@@ -131,6 +131,7 @@ ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out) {
         cudaError_t e = cudaMemcpy(r.slots, st.data(), st.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "slot table upload");
         r.tp.slots = r.slots;
+        r.smem = slot_smem_bytes(r.tp, p->din);
       }
     } else if (k.variant == VAR_COPY) {
       build_row_params(p->canon, k.chunk, &r.rp);

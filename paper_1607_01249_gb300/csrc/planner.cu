@@ -671,6 +671,13 @@ void slot_tables_k(const TileParams& p, const std::vector<int32_t>& tabA, const 
   auto by_off = [](const SlotElem& a, const SlotElem& b) { return a.off < b.off || (a.off == b.off && a.pos < b.pos); };
   std::sort(rd.begin(), rd.end(), by_off);
   std::sort(wr.begin(), wr.end(), by_off);
+  // Shared-memory layout of the slot kernel: the element of load rank f sits
+  // at f + f/32 (one pad word per 32), so the loads' stores are consecutive
+  // and the stores' loads, which step through the load ranks by a regular
+  // stride, spread over the banks whatever that stride is.  The walk's own
+  // position (lb*P + la*LC + lc) still gives the tile coordinate.
+  std::vector<int32_t> remap(size_t(p.P) * size_t(p.LB), -1);
+  for (size_t f = 0; f < rd.size(); ++f) remap[size_t(rd[f].pos)] = int32_t(f + f / 32);
   // layout (int32 units): read pairs, write pairs (K*kThreads*2 each), then
   // read and write tile coordinates (K*kThreads each)
   int32_t* q = out->data();
@@ -679,7 +686,7 @@ void slot_tables_k(const TileParams& p, const std::vector<int32_t>& tabA, const 
     const size_t k = f / kThreads, t = f % kThreads;
     int32_t* d = q + size_t(phase) * pairs + ((k / 2) * kThreads + t) * 4 + (k & 1) * 2;
     d[0] = e ? e->off : 0;
-    d[1] = e ? e->pos : -1;
+    d[1] = e ? remap[size_t(e->pos)] : -1;
     // the element's (la, lb) in the tile, from its shared-memory position
     // (lb * P + la * LC + lc); 0xffffffff marks an empty slot
     uint32_t lalb = 0xffffffffu;
@@ -698,6 +705,8 @@ void slot_tables_k(const TileParams& p, const std::vector<int32_t>& tabA, const 
 }  // namespace
 
 size_t slot_table_ints(int din) { return size_t(tile_k_for(stage_bytes(din))) * kThreads * 6; }
+
+int slot_smem_bytes(const TileParams& p, int din) { return (p.V + (p.V + 31) / 32) * stage_bytes(din); }
 
 void build_slot_tables(const TileParams& p, int din, const std::vector<int32_t>& tabA,
                        const std::vector<int32_t>& tabB, std::vector<int32_t>* out) {

@@ -68,6 +68,8 @@ void build_row_params(const Canon& c, int64_t chunk, RowParams* p);
 void build_slot_tables(const TileParams& p, int din, const std::vector<int32_t>& tabA,
                        const std::vector<int32_t>& tabB, std::vector<int32_t>* out);
 size_t slot_table_ints(int din);
+// shared memory of tile_slots_kernel for a tile (its own layout, see above)
+int slot_smem_bytes(const TileParams& p, int din);
 
 // Estimated memory efficiency of reading (write = false) or writing a
 // contiguous run of `bytes` bytes that starts at an arbitrary element offset,

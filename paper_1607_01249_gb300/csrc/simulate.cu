@@ -131,9 +131,10 @@ struct Checker {
     build_tile_params(p->canon, k, p->din, &tp, &ta, &tb, &smem);
     if (smem > 200 * 1024) return fail("shared memory over budget", smem, 0);
     if (tp.V > kThreads * K) return fail("tile larger than the threads cover", tp.V, kThreads * K);
-    const int ncap = tp.P * tp.LB;
     std::vector<int32_t> slots;
     if (k.slots) build_slot_tables(tp, p->din, ta, tb, &slots);
+    const int ncap = k.slots ? slot_smem_bytes(tp, p->din) / (p->din == DT_F64 ? 8 : 4) : tp.P * tp.LB;
+    if (k.slots && slot_smem_bytes(tp, p->din) > 200 * 1024) return fail("shared memory over budget", 0, 0);
     std::vector<int64_t> posA(static_cast<size_t>(ncap));
     std::vector<uint8_t> used(static_cast<size_t>(ncap));
     for (uint32_t tid = 0; tid < tp.ntiles; ++tid) {
