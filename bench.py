@@ -437,7 +437,9 @@ def run_batch(args, rank, world):
         "speedup_vs_per_call": round(ms_c / ms_b, 3),
         "roofline": {"bound": "hbm", "achieved": round(bytes_step / (ms_b * 1e-3) / 1e9, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(bytes_step / (ms_b * 1e-3) / 1e9 / peak, 4),
-                     "kernel": "batch_kernel", "traffic": None},
+                     "kernel": "batch_kernel",
+                     "traffic": (ncu_traffic("batch_kernel", "batch") or {}).get("bytes_per_launch")
+                     if args.batch_count == 4096 else None},
         "gpu_launches": launches_b * args.steps,
         "clocks": clocks,
     }
