@@ -98,6 +98,9 @@ ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out) {
     }
     r.amax = reinterpret_cast<uint32_t*>(r.base);
     r.scale = reinterpret_cast<float*>(static_cast<char*>(r.base) + 16);
+    r.amax_phase = 0;
+    e = cudaMemset(r.base, 0, 256);     // both amax words start at 0
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
     r.tables = reinterpret_cast<int32_t*>(static_cast<char*>(r.base) + 256);
     r.slots = slots ? reinterpret_cast<int4*>(static_cast<char*>(r.base) + 256 + tab) : nullptr;
     r.sel = -1;
@@ -127,11 +130,11 @@ ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out) {
       r.tp.slots = nullptr;
       if (k.slots && r.slots) {
         std::vector<int32_t> st;
-        build_slot_tables(r.tp, p->din, ta, tb, &st);
+        const int sbytes = build_slot_tables(r.tp, p->din, ta, tb, &st);
         cudaError_t e = cudaMemcpy(r.slots, st.data(), st.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "slot table upload");
         r.tp.slots = r.slots;
-        r.smem = slot_smem_bytes(r.tp, p->din);
+        r.smem = sbytes;
       }
     } else if (k.variant == VAR_COPY) {
       build_row_params(p->canon, k.chunk, &r.rp);
@@ -170,10 +173,17 @@ ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s) {
   const Candidate& k = p->cands[r->sel];
   Epilogue epi = make_epilogue(p, r);
   if (p->dout == DT_E4M3 && !p->user_scale) {
-    e = cudaMemsetAsync(r->amax, 0, sizeof(uint32_t), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    e = launch_amax(p->din, A, p->amax_rows, float(p->alpha), r->amax, s);
-    if (e != cudaSuccess) return cuda_fail(e, "amax kernel launch");
+    // this execution accumulates into one amax word and clears the other for
+    // the next execution (in stream order, after this one's kernels)
+    uint32_t* cur = r->amax + r->amax_phase;
+    uint32_t* next = r->amax + (1 - r->amax_phase);
+    r->amax_phase ^= 1;
+    epi.amax_bits = cur;
+    e = launch_amax(p->din, A, p->amax_rows, float(p->alpha), cur, next, s);
+    if (e != cudaSuccess) {
+      r->amax_phase ^= 1;      // `next` was not cleared: this word is still the one to use
+      return cuda_fail(e, "amax kernel launch");
+    }
   }
   if (k.variant == VAR_TILE) {
     TileParams tp = r->tp;

@@ -205,9 +205,9 @@ cudaError_t launch_rowcopy(int din, int dout, const void* A, void* B, const Tile
 }
 
 cudaError_t launch_amax(int din, const void* A, const RowParams& p, float alpha_f, uint32_t* amax_bits,
-                        cudaStream_t s) {
-  if (din == DT_F32) return launch_amax_t<DT_F32>(A, p, alpha_f, amax_bits, s);
-  if (din == DT_BF16) return launch_amax_t<DT_BF16>(A, p, alpha_f, amax_bits, s);
+                        uint32_t* clear_bits, cudaStream_t s) {
+  if (din == DT_F32) return launch_amax_t<DT_F32>(A, p, alpha_f, amax_bits, clear_bits, s);
+  if (din == DT_BF16) return launch_amax_t<DT_BF16>(A, p, alpha_f, amax_bits, clear_bits, s);
   return cudaErrorInvalidValue;
 }
 

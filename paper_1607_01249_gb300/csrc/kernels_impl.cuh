@@ -356,27 +356,55 @@ __global__ void __launch_bounds__(kThreads) copy_kernel(const store_t<DIN>* __re
 
 // ---------------------------------------------------------------- amax ----
 
+// A warp takes kAmaxItems consecutive row chunks of A's sub-tensor at a time
+// (their coordinates decomposed once per chunk, not per element) and keeps
+// kAmaxItems x kAmaxUnroll loads per lane in flight, so that short rows (a
+// packing panel's 48- or 256-element columns) still stream.  One CTA also
+// clears `clear_bits`, the word the next execution of the plan accumulates
+// into, so no separate reset is launched (two words alternate per plan).
+constexpr int kAmaxItems = 4;
+constexpr int kAmaxUnroll = 2;
+
 template <int DIN>
 __global__ void __launch_bounds__(kThreads) amax_kernel(const store_t<DIN>* __restrict__ A,
-                                                        const __grid_constant__ RowParams p,
-                                                        float alpha_f, uint32_t* amax_bits) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t warp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+                                                        const __grid_constant__ RowParams p, float alpha_f,
+                                                        uint32_t* amax_bits, uint32_t* clear_bits) {
+  const int t = threadIdx.x, lane = t & 31;
+  if (blockIdx.x == 0 && t == 0 && clear_bits) *clear_bits = 0u;
+  const uint32_t warp = (blockIdx.x * kThreads + t) >> 5;
   const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
   float m = 0.f;
-  for (uint32_t item = warp; item < p.nitems; item += nwarps) {
-    const RowCoord rc = row_coord(item, p);
-    const store_t<DIN>* Ar = A + rc.offA;
-    for (int64_t x = rc.start + lane; x < rc.end; x += 32) {
-      const float v = fabsf(__fmul_rn(alpha_f, float(to_stage<DIN>(ldg_elem<DIN>(Ar + x * p.sa0)))));
-      if (v > m) m = v;     // NaN compares false: ignored
+  for (uint64_t i0 = uint64_t(warp) * kAmaxItems; i0 < p.nitems; i0 += uint64_t(nwarps) * kAmaxItems) {
+    RowCoord rc[kAmaxItems];
+#pragma unroll
+    for (int j = 0; j < kAmaxItems; ++j) {
+      rc[j] = row_coord(uint32_t(i0 + j < p.nitems ? i0 + j : i0), p);
+      if (i0 + j >= p.nitems) rc[j].end = rc[j].start;     // no such chunk
+    }
+    for (int64_t x0 = lane; x0 < p.chunk; x0 += 32 * kAmaxUnroll) {
+      float v[kAmaxItems][kAmaxUnroll];
+      bool ok[kAmaxItems][kAmaxUnroll];
+#pragma unroll
+      for (int j = 0; j < kAmaxItems; ++j)
+#pragma unroll
+        for (int u = 0; u < kAmaxUnroll; ++u) {
+          const int64_t x = rc[j].start + x0 + 32 * u;
+          ok[j][u] = x < rc[j].end;
+          v[j][u] = fabsf(__fmul_rn(alpha_f, float(to_stage<DIN>(ldg_elem<DIN>(A + (ok[j][u] ? rc[j].offA + x * p.sa0
+                                                                                                 : int64_t(0)))))));
+        }
+#pragma unroll
+      for (int j = 0; j < kAmaxItems; ++j)
+#pragma unroll
+        for (int u = 0; u < kAmaxUnroll; ++u)
+          if (ok[j][u] && v[j][u] > m) m = v[j][u];     // NaN compares false: ignored
     }
   }
   for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   __shared__ float red[kThreads / 32];
-  if (lane == 0) red[threadIdx.x >> 5] = m;
+  if (lane == 0) red[t >> 5] = m;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (t == 0) {
     float b = 0.f;
     for (int i = 0; i < kThreads / 32; ++i) b = fmaxf(b, red[i]);
     if (b > 0.f) atomicMax(amax_bits, __float_as_uint(b));
@@ -492,12 +520,14 @@ cudaError_t launch_tile2_pair(int ju, int jw, const void* A, void* B, const Tile
 
 template <int DIN>
 cudaError_t launch_amax_t(const void* A, const RowParams& p, float alpha_f, uint32_t* amax_bits,
-                          cudaStream_t s) {
+                          uint32_t* clear_bits, cudaStream_t s) {
   const void* fn = reinterpret_cast<const void*>(&amax_kernel<DIN>);
   int grid = 0;
-  cudaError_t err = grid_for(fn, 0, (int64_t(p.nitems) + 7) / 8, &grid);
+  const int64_t groups = (int64_t(p.nitems) + kAmaxItems - 1) / kAmaxItems;
+  cudaError_t err = grid_for(fn, 0, (groups + kThreads / 32 - 1) / (kThreads / 32), &grid);
   if (err != cudaSuccess) return err;
-  amax_kernel<DIN><<<grid, kThreads, 0, s>>>(static_cast<const store_t<DIN>*>(A), p, alpha_f, amax_bits);
+  amax_kernel<DIN><<<grid, kThreads, 0, s>>>(static_cast<const store_t<DIN>*>(A), p, alpha_f, amax_bits,
+                                             clear_bits);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -18,8 +18,10 @@ cudaError_t launch_tile2(int din, int dout, int ju, int jw, const void* A, void*
 cudaError_t launch_rowcopy(int din, int dout, const void* A, void* B, const TileParams& p, cudaStream_t s);
 cudaError_t launch_copy(int din, int dout, int vec, const void* A, void* B, const RowParams& p,
                         cudaStream_t s);
+// FP8 pre-pass: max |alpha a| over A's sub-tensor into *amax_bits (which
+// must start at 0); clear_bits (may be null) is set to 0 on the way.
 cudaError_t launch_amax(int din, const void* A, const RowParams& p, float alpha_f, uint32_t* amax_bits,
-                        cudaStream_t s);
+                        uint32_t* clear_bits, cudaStream_t s);
 int64_t launch_count();
 
 }  // namespace ttc

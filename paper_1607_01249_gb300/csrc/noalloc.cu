@@ -92,7 +92,7 @@ extern "C" ttc_status ttc_execute_noalloc(ttc_plan_t plan, const void* A, void* 
   if (plan->dout == DT_E4M3 && !plan->user_scale) {
     e = cudaMemsetAsync(amax, 0, sizeof(uint32_t), s);    // the array keeps the last call's amax
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    e = launch_amax(plan->din, A, plan->amax_rows, float(plan->alpha), amax, s);
+    e = launch_amax(plan->din, A, plan->amax_rows, float(plan->alpha), amax, nullptr, s);
     if (e != cudaSuccess) return cuda_fail(e, "amax kernel launch");
   }
   if (k.variant == VAR_TILE) {

@@ -20,7 +20,8 @@ namespace ttc {
 struct DevRes {
   void* base = nullptr;
   size_t bytes = 0;
-  uint32_t* amax = nullptr;
+  uint32_t* amax = nullptr;   // two words: executions alternate between them
+  int amax_phase = 0;         // the word the next execution accumulates into
   float* scale = nullptr;
   int32_t* tables = nullptr;
   int4* slots = nullptr;     // slot tables of tile_kernel (when a candidate uses them)

@@ -648,8 +648,8 @@ struct SlotElem {
 };
 
 template <int K>
-void slot_tables_k(const TileParams& p, const std::vector<int32_t>& tabA, const std::vector<int32_t>& tabB,
-                   std::vector<int32_t>* out) {
+void slot_tables_k(const TileParams& p, int stage_words, const std::vector<int32_t>& tabA,
+                   const std::vector<int32_t>& tabB, std::vector<int32_t>* out, int* smem_elems) {
   const TileCoord c{0, 0, p.LA, p.LB};
   std::vector<SlotElem> rd, wr;
   rd.reserve(size_t(p.V));
@@ -672,12 +672,63 @@ void slot_tables_k(const TileParams& p, const std::vector<int32_t>& tabA, const 
   std::sort(rd.begin(), rd.end(), by_off);
   std::sort(wr.begin(), wr.end(), by_off);
   // Shared-memory layout of the slot kernel: the element of load rank f sits
-  // at f + f/32 (one pad word per 32), so the loads' stores are consecutive
-  // and the stores' loads, which step through the load ranks by a regular
-  // stride, spread over the banks whatever that stride is.  The walk's own
-  // position (lb*P + la*LC + lc) still gives the tile coordinate.
-  std::vector<int32_t> remap(size_t(p.P) * size_t(p.LB), -1);
-  for (size_t f = 0; f < rd.size(); ++f) remap[size_t(rd[f].pos)] = int32_t(f + f / 32);
+  // at q = f + (f / g) * s, and then, with x != 0, at q with its low five
+  // bits XORed by x times its 32-element block number (a permutation inside
+  // each block of 32).  The loads' stores then hit 32 distinct banks per
+  // warp (for g >= 32), and the stores' loads, which step through the load
+  // ranks by the tile's strides, are spread over the banks by the padding or
+  // the swizzle.  (g, s, x) is chosen here by counting the shared-memory
+  // wavefronts of both phases, warp by warp, for a few candidates (4-byte
+  // banks; an 8-byte element is two words).  The walk's own position
+  // (lb*P + la*LC + lc) still gives the tile coordinate.
+  std::vector<int32_t> rank(size_t(p.P) * size_t(p.LB), -1);
+  for (size_t f = 0; f < rd.size(); ++f) rank[size_t(rd[f].pos)] = int32_t(f);
+  const int words = stage_words;
+  auto layout = [](int64_t f, int g, int sp, int x) {
+    const int64_t q = g ? f + (f / g) * sp : f;
+    return x ? (q & ~int64_t(31)) | ((q ^ ((q >> 5) * x)) & 31) : q;
+  };
+  auto wavefronts = [&](int g, int sp, int x) {
+    auto lay = [&](int64_t f) { return layout(f, g, sp, x); };
+    int64_t total = 0;
+    int cnt[32];
+    for (int phase = 0; phase < 2; ++phase) {
+      const std::vector<SlotElem>& v = phase ? wr : rd;
+      for (size_t w0 = 0; w0 < v.size(); w0 += 32) {
+        // one warp access: 32 consecutive slots of one k (kThreads % 32 == 0)
+        std::fill(cnt, cnt + 32, 0);
+        int worst = 0;
+        for (size_t j = w0; j < std::min(v.size(), w0 + 32); ++j) {
+          const int64_t f = phase ? rank[size_t(v[j].pos)] : int64_t(j);
+          const int64_t word = lay(f) * words;
+          for (int x = 0; x < words; ++x) worst = std::max(worst, ++cnt[(word + x) & 31]);
+        }
+        total += worst;
+      }
+    }
+    return total;
+  };
+  static const int kLayouts[][3] = {{32, 1, 0}, {0, 0, 0}, {0, 0, 1}, {0, 0, 3}, {0, 0, 5}, {0, 0, 7},
+                                    {64, 1, 0}, {128, 1, 0}, {32, 3, 0}, {32, 5, 0}, {32, 2, 0}, {32, 1, 1}};
+  int bg = 32, bs = 1, bx = 0;
+  int64_t best = -1;
+  for (const auto& l : kLayouts) {
+    const int64_t w = wavefronts(l[0], l[1], l[2]);
+    if (best < 0 || w < best) {
+      best = w;
+      bg = l[0];
+      bs = l[1];
+      bx = l[2];
+    }
+  }
+  std::vector<int32_t> remap(rank.size(), -1);
+  int32_t top = 0;
+  for (size_t f = 0; f < rd.size(); ++f) {
+    const int32_t at = int32_t(layout(int64_t(f), bg, bs, bx));
+    remap[size_t(rd[f].pos)] = at;
+    top = std::max(top, at + 1);
+  }
+  *smem_elems = top;
   // layout (int32 units): read pairs, write pairs (K*kThreads*2 each), then
   // read and write tile coordinates (K*kThreads each)
   int32_t* q = out->data();
@@ -706,13 +757,13 @@ void slot_tables_k(const TileParams& p, const std::vector<int32_t>& tabA, const 
 
 size_t slot_table_ints(int din) { return size_t(tile_k_for(stage_bytes(din))) * kThreads * 6; }
 
-int slot_smem_bytes(const TileParams& p, int din) { return (p.V + (p.V + 31) / 32) * stage_bytes(din); }
-
-void build_slot_tables(const TileParams& p, int din, const std::vector<int32_t>& tabA,
-                       const std::vector<int32_t>& tabB, std::vector<int32_t>* out) {
+int build_slot_tables(const TileParams& p, int din, const std::vector<int32_t>& tabA,
+                      const std::vector<int32_t>& tabB, std::vector<int32_t>* out) {
   out->assign(slot_table_ints(din), 0);
-  if (tile_k_for(stage_bytes(din)) == 16) slot_tables_k<16>(p, tabA, tabB, out);
-  else slot_tables_k<8>(p, tabA, tabB, out);
+  int elems = 0;
+  if (tile_k_for(stage_bytes(din)) == 16) slot_tables_k<16>(p, stage_bytes(din) / 4, tabA, tabB, out, &elems);
+  else slot_tables_k<8>(p, stage_bytes(din) / 4, tabA, tabB, out, &elems);
+  return elems * stage_bytes(din);
 }
 
 }  // namespace ttc

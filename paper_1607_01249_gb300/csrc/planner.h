@@ -62,14 +62,12 @@ void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* 
                        std::vector<int32_t>* tabA, std::vector<int32_t>* tabB, int* smem_bytes);
 void build_row_params(const Canon& c, int64_t chunk, RowParams* p);
 
-// Slot tables of a whole tile for tile_kernel (layout: TileParams::slots),
-// as int32 quadruples; `tabA`/`tabB` are the host cross tables of the same
-// parameters.  Returns the number of int32 values written (4 per two slots).
-void build_slot_tables(const TileParams& p, int din, const std::vector<int32_t>& tabA,
-                       const std::vector<int32_t>& tabB, std::vector<int32_t>* out);
+// Slot tables of a tile for tile_slots_kernel (layout: TileParams::slots);
+// `tabA`/`tabB` are the host cross tables of the same parameters.  Returns
+// the shared-memory bytes of the tile in the kernel's layout.
+int build_slot_tables(const TileParams& p, int din, const std::vector<int32_t>& tabA,
+                      const std::vector<int32_t>& tabB, std::vector<int32_t>* out);
 size_t slot_table_ints(int din);
-// shared memory of tile_slots_kernel for a tile (its own layout, see above)
-int slot_smem_bytes(const TileParams& p, int din);
 
 // Estimated memory efficiency of reading (write = false) or writing a
 // contiguous run of `bytes` bytes that starts at an arbitrary element offset,

@@ -132,9 +132,10 @@ struct Checker {
     if (smem > 200 * 1024) return fail("shared memory over budget", smem, 0);
     if (tp.V > kThreads * K) return fail("tile larger than the threads cover", tp.V, kThreads * K);
     std::vector<int32_t> slots;
-    if (k.slots) build_slot_tables(tp, p->din, ta, tb, &slots);
-    const int ncap = k.slots ? slot_smem_bytes(tp, p->din) / (p->din == DT_F64 ? 8 : 4) : tp.P * tp.LB;
-    if (k.slots && slot_smem_bytes(tp, p->din) > 200 * 1024) return fail("shared memory over budget", 0, 0);
+    int sbytes = 0;
+    if (k.slots) sbytes = build_slot_tables(tp, p->din, ta, tb, &slots);
+    const int ncap = k.slots ? sbytes / (p->din == DT_F64 ? 8 : 4) : tp.P * tp.LB;
+    if (k.slots && sbytes > 200 * 1024) return fail("shared memory over budget", sbytes, 0);
     std::vector<int64_t> posA(static_cast<size_t>(ncap));
     std::vector<uint8_t> used(static_cast<size_t>(ncap));
     for (uint32_t tid = 0; tid < tp.ntiles; ++tid) {
@@ -295,5 +296,21 @@ extern "C" ttc_status ttc_debug_describe_candidate(ttc_plan_t plan, int candidat
   if (!plan || !buf || buflen <= 0 || candidate < 0 || candidate >= int(plan->cands.size()))
     return TTC_ERR_INVALID_ARG;
   std::snprintf(buf, size_t(buflen), "%s", plan->cands[size_t(candidate)].describe().c_str());
+  return TTC_OK;
+}
+
+extern "C" ttc_status ttc_debug_slot_tables(ttc_plan_t plan, int candidate, int32_t* out, int64_t count,
+                                            int64_t* needed) {
+  if (!plan || !needed || candidate < 0 || candidate >= int(plan->cands.size())) return TTC_ERR_INVALID_ARG;
+  const Candidate& k = plan->cands[size_t(candidate)];
+  if (k.variant != VAR_TILE || !k.slots) return TTC_ERR_INVALID_ARG;
+  TileParams tp;
+  std::vector<int32_t> ta, tb, st;
+  int smem = 0;
+  build_tile_params(plan->canon, k, plan->din, &tp, &ta, &tb, &smem);
+  (void)build_slot_tables(tp, plan->din, ta, tb, &st);
+  *needed = int64_t(st.size());
+  if (!out || count < int64_t(st.size())) return TTC_ERR_INVALID_ARG;
+  std::memcpy(out, st.data(), st.size() * sizeof(int32_t));
   return TTC_OK;
 }

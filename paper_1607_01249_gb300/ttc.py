@@ -89,6 +89,8 @@ SIGNATURES = {
     # include/ttc_debug.h
     "ttc_debug_verify_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
     "ttc_debug_describe_candidate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
+    "ttc_debug_slot_tables": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                                             _i64p]),
 }
 
 _lib = None
@@ -220,6 +222,19 @@ class Plan:
         buf = ctypes.create_string_buffer(1024)
         _check(lib().ttc_debug_describe_candidate(self._h, int(candidate), buf, 1024))
         return buf.value.decode(errors="replace")
+
+    def slot_tables(self, candidate=None):
+        """The slot tables of a tile_slots_kernel candidate, as a list of
+        int32 (layout of TileParams::slots)."""
+        if candidate is None:
+            candidate = self.info()["candidate"]
+        need = ctypes.c_int64(0)
+        lib().ttc_debug_slot_tables(self._h, int(candidate), None, 0, ctypes.byref(need))
+        if need.value <= 0:
+            raise TTCError(STATUS_CODE["TTC_ERR_INVALID_ARG"], "candidate has no slot tables")
+        buf = (ctypes.c_int32 * need.value)()
+        _check(lib().ttc_debug_slot_tables(self._h, int(candidate), buf, need.value, ctypes.byref(need)))
+        return list(buf)
 
     def select(self, index: int):
         _check(lib().ttc_plan_select_candidate(self._h, int(index)))
