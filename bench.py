@@ -48,6 +48,24 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest of every rank's x (each rank's step time): the job is as
+    slow as its slowest replica."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (replicas: each rank processes the same units)."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -265,14 +283,11 @@ def run_ours(args, rank, world):
         torch.cuda.cudart().cudaProfilerStop()
     launches = ttc.launch_count() - l0
     clocks = clk.stop() if clk else None
-    ms_total = e0.elapsed_time(e1)
+    ms_total = max_over_ranks(e0.elapsed_time(e1), world)
     if dist:
-        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_total = float(t.item())
         tdist.barrier()
     ms_step = ms_total / args.steps
-    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+    value = job_rate(bytes_step, world, ms_step) / 1e9
 
     # dominant kernel: group launches by variant
     by_var = {}
@@ -401,12 +416,7 @@ def run_batch(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            import torch.distributed as tdist
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, (ttc.launch_count() - l0) // steps
+        return max_over_ranks(ms, world), (ttc.launch_count() - l0) // steps
 
     def per_call():
         for pl, a, b in zip(plans, pa, pb):
@@ -419,7 +429,7 @@ def run_batch(args, rank, world):
     clocks = clk.stop() if clk else None
     ms_c, launches_c = timed(per_call, max(1, args.steps // 2))
     info = batch.info()
-    value = world * bytes_step / (ms_b * 1e-3) / 1e9
+    value = job_rate(bytes_step, world, ms_b) / 1e9
     peak, peak_kind = measured_peaks()
     return {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -429,10 +439,10 @@ def run_batch(args, rank, world):
                                "f32/bf16 50/50, alpha=1, beta in {0,0.5}; one CUDA-graph launch per step",
                    "tiles": info["tiles"], "algorithmic_bytes_per_step": bytes_step,
                    "parallelism": f"replicas x{world}"},
-        "batch": {"transposes_per_s": round(world * len(probs) / (ms_b * 1e-3), 1), "ms": round(ms_b, 4),
+        "batch": {"transposes_per_s": round(job_rate(len(probs), world, ms_b), 1), "ms": round(ms_b, 4),
                   "kernel_launches_per_step": launches_b},
-        "per_call": {"transposes_per_s": round(world * len(probs) / (ms_c * 1e-3), 1), "ms": round(ms_c, 4),
-                     "GB/s": round(world * bytes_step / (ms_c * 1e-3) / 1e9, 2),
+        "per_call": {"transposes_per_s": round(job_rate(len(probs), world, ms_c), 1), "ms": round(ms_c, 4),
+                     "GB/s": round(job_rate(bytes_step, world, ms_c) / 1e9, 2),
                      "kernel_launches_per_step": launches_c},
         "speedup_vs_per_call": round(ms_c / ms_b, 3),
         "roofline": {"bound": "hbm", "achieved": round(bytes_step / (ms_b * 1e-3) / 1e9, 1), "peak": peak,
@@ -651,13 +661,9 @@ def run_e2e(args, probs, plans, bufs, stream, world):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     ms = e0.elapsed_time(e1) / steps
-    if world > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     bytes_step = sum(p.algorithmic_bytes() for p in probs)
-    return {"value": round(world * bytes_step / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+    return {"value": round(job_rate(bytes_step, world, ms) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3),
             "wall_s": round(wall, 3), "steps": steps,
             "copies": "pinned host buffers; H2D, kernel and D2H of consecutive transposes overlap on three streams"}

@@ -242,3 +242,51 @@ def test_many_schedules_in_one_process():
             got, _ = H.run_gpu(p, A, B0, plan=plan)
             ok, msg = H.compare_bits(got, want, dt, True)
             assert ok, (perm, sizes, i, msg)
+
+
+def test_slot_table_tiles_every_pair_with_ragged_edges():
+    """tile_slots_kernel schedules (tables ordered by address, masked edge
+    tiles) for every dtype pair, with outer sizes and tails that leave most
+    tiles at the tensor's edge cut short."""
+    shapes = [((1, 0, 2), (37, 29, 11)), ((2, 0, 3, 1), (9, 23, 7, 13)), ((4, 2, 0, 3, 1), (5, 6, 7, 3, 9)),
+              ((0, 2, 1), (13, 41, 17))]
+    tried = 0
+    for si, (perm, sizes) in enumerate(shapes):
+        for din, dout in PAIRS:
+            beta = 0.0 if dout == "e4m3" else 0.3
+            oa = tuple(s + (si % 3) for s in sizes)
+            p = Problem(perm=perm, sizes=sizes, dtype_in=din, dtype_out=dout, alpha=1.25, beta=beta, outer_a=oa)
+            plan = ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta, p.outer_a, p.outer_b)
+            A, B0 = H.make_inputs(p, 60 + si, "normal")
+            want, wscale = H.oracle_mirror(p, A, B0)
+            for i in range(plan.info()["ncandidates"]):
+                plan.select(i)
+                if not plan.info()["slot_tables"]:
+                    continue
+                got, scale = H.run_gpu(p, A, B0, plan=plan)
+                if dout == "e4m3":
+                    assert scale == wscale, (perm, sizes, din, dout, i)
+                ok, msg = H.compare_bits(got, want, dout, nan_as_nan=True)
+                assert ok, (perm, sizes, din, dout, i, msg)
+                tried += 1
+    assert tried >= 20
+
+
+def test_fp8_plan_executed_repeatedly_tracks_each_inputs_scale():
+    """Executions of one FP8 plan alternate between two amax words (each
+    execution clears the other's): every execution's scale and codes must
+    follow its own input, whatever the previous inputs were."""
+    for din in ("f32", "bf16"):
+        p = Problem(perm=(2, 0, 1), sizes=(67, 45, 33), dtype_in=din, dtype_out="e4m3", alpha=1.3)
+        plan = ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta)
+        for rep, mag in enumerate((1.0, 1e-3, 50.0, 50.0, 2.0, 1e-3)):
+            A, B0 = H.make_inputs(p, 900 + rep, "normal")
+            if din == "f32":
+                A = (A * np.float32(mag)).astype(np.float32)
+            else:
+                A = inputs.bf16_bits_from_f32_trunc(H.as_float(A, "bf16").astype(np.float32) * np.float32(mag))
+            got, scale = H.run_gpu(p, A, B0, plan=plan)
+            want, wscale = H.oracle_mirror(p, A, B0)
+            assert scale == wscale, (din, rep, scale, wscale)
+            ok, msg = H.compare_bits(got, want, "e4m3", nan_as_nan=True)
+            assert ok, (din, rep, msg)
