@@ -117,20 +117,21 @@ __device__ __forceinline__ void slots_body(const store_t<DIN>* __restrict__ Ab, 
   using S = stage_t<DIN>;
   using TO = store_t<DOUT>;
   constexpr int K = tile_k_for(sizeof(S));
+  constexpr int Q = K / 4;                      // groups of four slots per thread
   const int t = threadIdx.x;
-  const int4* __restrict__ rs = p.slots + t;
-  const int4* __restrict__ ws = p.slots + (K / 2) * kThreads + t;
+  // table regions (TileParams::slots): offsets, tile coordinates, positions
+  const int4* __restrict__ offs = p.slots + t;
+  const uint4* __restrict__ crd = reinterpret_cast<const uint4*>(p.slots + 2 * Q * kThreads) + t;
+  const uint2* __restrict__ poss = reinterpret_cast<const uint2*>(p.slots + 4 * Q * kThreads) + t;
   // slot k of this thread holds an element of this tile iff bit k is set
   auto inside = [&](int phase) -> uint32_t {
     if constexpr (FULL) {
       return 0xffffffffu;
     } else {
-      const uint4* __restrict__ tab = reinterpret_cast<const uint4*>(p.slots + K * kThreads) + t +
-                                      phase * (K / 4) * kThreads;
       uint32_t m = 0;
 #pragma unroll
-      for (int q = 0; q < K / 4; ++q) {
-        const uint4 e = __ldg(tab + q * kThreads);
+      for (int q = 0; q < Q; ++q) {
+        const uint4 e = __ldg(crd + (phase * Q + q) * kThreads);
         m |= uint32_t((int(e.x >> 16) < c.remA) & (int(e.x & 0xffffu) < c.remB)) << (4 * q);
         m |= uint32_t((int(e.y >> 16) < c.remA) & (int(e.y & 0xffffu) < c.remB)) << (4 * q + 1);
         m |= uint32_t((int(e.z >> 16) < c.remA) & (int(e.z & 0xffffu) < c.remB)) << (4 * q + 2);
@@ -139,49 +140,84 @@ __device__ __forceinline__ void slots_body(const store_t<DIN>* __restrict__ Ab, 
       return m;
     }
   };
-  S v[K];
-  int pos[K];
+  // position of slot j (0..3) of a packed group; 0xffff marks an empty slot
+  auto slot_pos = [](uint2 pp, int j) -> int {
+    const uint32_t w = j < 2 ? pp.x : pp.y;
+    return int((w >> (16 * (j & 1))) & 0xffffu);
+  };
+  // ---- load A in address order, stage in shared memory
   {
     const uint32_t m = inside(0);
+    S v[K];
+    uint2 pk[Q];
 #pragma unroll
-    for (int k = 0; k < K / 2; ++k) {
-      const int4 e = __ldg(rs + k * kThreads);
-      const bool i0 = FULL || ((m >> (2 * k)) & 1u), i1 = FULL || ((m >> (2 * k + 1)) & 1u);
-      pos[2 * k] = i0 ? e.y : -1;
-      pos[2 * k + 1] = i1 ? e.w : -1;
-      v[2 * k] = to_stage<DIN>(ldg_elem<DIN>(Ab + (i0 ? e.x : 0)));
-      v[2 * k + 1] = to_stage<DIN>(ldg_elem<DIN>(Ab + (i1 ? e.z : 0)));
+    for (int q = 0; q < Q; ++q) {
+      const int4 o = __ldg(offs + q * kThreads);
+      pk[q] = __ldg(poss + q * kThreads);
+      const int32_t oo[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool in = FULL || ((m >> (4 * q + j)) & 1u);
+        v[4 * q + j] = to_stage<DIN>(ldg_elem<DIN>(Ab + (in ? oo[j] : 0)));
+      }
     }
-  }
 #pragma unroll
-  for (int k = 0; k < K; ++k)
-    if (pos[k] >= 0) tile[pos[k]] = v[k];
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int pos = slot_pos(pk[q], j);
+        const bool in = FULL || ((m >> (4 * q + j)) & 1u);
+        if (in && pos != 0xffff) tile[pos] = v[4 * q + j];
+      }
+  }
   __syncthreads();
-  int32_t off[K];
-  {
-    const uint32_t m = inside(1);
+  // ---- store B in address order
+  const uint32_t m = inside(1);
+  if constexpr (EK == EK_AXPBY) {
+    int32_t off[K];
+    uint2 pk[Q];
+    TO bo[K];
 #pragma unroll
-    for (int k = 0; k < K / 2; ++k) {
-      const int4 e = __ldg(ws + k * kThreads);
-      const bool i0 = FULL || ((m >> (2 * k)) & 1u), i1 = FULL || ((m >> (2 * k + 1)) & 1u);
-      off[2 * k] = i0 ? e.x : 0;
-      pos[2 * k] = i0 ? e.y : -1;
-      off[2 * k + 1] = i1 ? e.z : 0;
-      pos[2 * k + 1] = i1 ? e.w : -1;
+    for (int q = 0; q < Q; ++q) {
+      const int4 o = __ldg(offs + (Q + q) * kThreads);
+      pk[q] = __ldg(poss + (Q + q) * kThreads);
+      const int32_t oo[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool in = FULL || ((m >> (4 * q + j)) & 1u);
+        off[4 * q + j] = in ? oo[j] : 0;
+        bo[4 * q + j] = Bb[off[4 * q + j]];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int pos = slot_pos(pk[q], j);
+        const bool in = FULL || ((m >> (4 * q + j)) & 1u);
+        if (in && pos != 0xffff)
+          Bb[off[4 * q + j]] = epilogue_k<DIN, DOUT, EK>(tile[pos], bo[4 * q + j], p.epi, scale);
+      }
+  } else {
+    // no loads of B: each group's stores go out as soon as its table entry
+    // is in, keeping few registers live
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int4 o = __ldg(offs + (Q + q) * kThreads);
+      const uint2 pp = __ldg(poss + (Q + q) * kThreads);
+      const int32_t oo[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int pos = slot_pos(pp, j);
+        const bool in = FULL || ((m >> (4 * q + j)) & 1u);
+        if (in && pos != 0xffff) Bb[oo[j]] = epilogue_k<DIN, DOUT, EK>(tile[pos], TO{}, p.epi, scale);
+      }
     }
   }
-  TO bo[K] = {};
-  if constexpr (EK == EK_AXPBY) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) bo[k] = Bb[off[k]];
-  }
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-    if (pos[k] >= 0) Bb[off[k]] = epilogue_k<DIN, DOUT, EK>(tile[pos[k]], bo[k], p.epi, scale);
 }
 
 template <int DIN, int DOUT, int EK>
-__global__ void __launch_bounds__(kThreads, 4) tile_slots_kernel(const store_t<DIN>* __restrict__ A,
+__global__ void __launch_bounds__(kThreads, EK == EK_AXPBY ? 4 : 5) tile_slots_kernel(const store_t<DIN>* __restrict__ A,
                                                                  store_t<DOUT>* __restrict__ B,
                                                                  const __grid_constant__ TileParams p) {
   using S = stage_t<DIN>;

@@ -731,13 +731,18 @@ void slot_tables_k(const TileParams& p, int stage_words, const std::vector<int32
   *smem_elems = top;
   // layout (int32 units): read pairs, write pairs (K*kThreads*2 each), then
   // read and write tile coordinates (K*kThreads each)
+  // layout (int32 units, R = K * kThreads): offsets [load R | store R],
+  // tile coordinates [load R | store R], then 16-bit shared-memory positions
+  // [load R/2 | store R/2]; slot k of thread t is entry ((k/4)*kThreads + t)*4
+  // + k%4 of its region (16-bit entries for the positions)
   int32_t* q = out->data();
-  const size_t pairs = size_t(K) * kThreads * 2, coords = size_t(K) * kThreads;
+  const size_t R = size_t(K) * kThreads;
+  uint16_t* posq = reinterpret_cast<uint16_t*>(q + 4 * R);
   auto put = [&](int phase, size_t f, const SlotElem* e) {
     const size_t k = f / kThreads, t = f % kThreads;
-    int32_t* d = q + size_t(phase) * pairs + ((k / 2) * kThreads + t) * 4 + (k & 1) * 2;
-    d[0] = e ? e->off : 0;
-    d[1] = e ? remap[size_t(e->pos)] : -1;
+    const size_t at = ((k / 4) * kThreads + t) * 4 + (k & 3);
+    q[size_t(phase) * R + at] = e ? e->off : 0;
+    posq[size_t(phase) * R + at] = uint16_t(e ? remap[size_t(e->pos)] : 0xffff);
     // the element's (la, lb) in the tile, from its shared-memory position
     // (lb * P + la * LC + lc); 0xffffffff marks an empty slot
     uint32_t lalb = 0xffffffffu;
@@ -745,7 +750,7 @@ void slot_tables_k(const TileParams& p, int stage_words, const std::vector<int32
       const int lb = e->pos / p.P, la = (e->pos - lb * p.P) / p.LC;
       lalb = (uint32_t(la) << 16) | uint32_t(lb);
     }
-    q[2 * pairs + size_t(phase) * coords + ((k / 4) * kThreads + t) * 4 + (k & 3)] = int32_t(lalb);
+    q[2 * R + size_t(phase) * R + at] = int32_t(lalb);
   };
   for (size_t f = 0; f < size_t(K) * kThreads; ++f) {
     put(0, f, f < rd.size() ? &rd[f] : nullptr);
@@ -755,7 +760,7 @@ void slot_tables_k(const TileParams& p, int stage_words, const std::vector<int32
 
 }  // namespace
 
-size_t slot_table_ints(int din) { return size_t(tile_k_for(stage_bytes(din))) * kThreads * 6; }
+size_t slot_table_ints(int din) { return size_t(tile_k_for(stage_bytes(din))) * kThreads * 5; }
 
 int build_slot_tables(const TileParams& p, int din, const std::vector<int32_t>& tabA,
                       const std::vector<int32_t>& tabB, std::vector<int32_t>* out) {

@@ -168,22 +168,24 @@ struct Checker {
         continue;
       }
       if (k.slots) {
-        // tile_slots_kernel: slot (k, t) of phase f sits in int4
-        // (f*K/2 + k/2)*kThreads + t, half k&1 (pos < 0: empty); a tile cut
+        // tile_slots_kernel: slot kk of thread t of phase f is entry
+        // ((kk/4)*kThreads + t)*4 + kk%4 of the phase's offset, coordinate
+        // and 16-bit position regions (position 0xffff: empty); a tile cut
         // short keeps the slots whose coordinate (la << 16 | lb) lies inside
-        const size_t pairs = size_t(K) * kThreads * 2, coords = size_t(K) * kThreads;
+        const size_t R = size_t(K) * kThreads;
+        const uint16_t* posq = reinterpret_cast<const uint16_t*>(slots.data() + 4 * R);
         for (int f = 0; f < 2 && ok; ++f)
           for (int t = 0; t < kThreads && ok; ++t)
             for (int kk = 0; kk < K && ok; ++kk) {
-              const int32_t* e =
-                  slots.data() + size_t(f) * pairs + ((size_t(kk / 2)) * kThreads + size_t(t)) * 4 + (kk & 1) * 2;
-              const uint32_t lalb = uint32_t(
-                  slots[2 * pairs + size_t(f) * coords + (size_t(kk / 4) * kThreads + size_t(t)) * 4 + (kk & 3)]);
+              const size_t at = (size_t(kk / 4) * kThreads + size_t(t)) * 4 + (kk & 3);
+              const int32_t off = slots[size_t(f) * R + at];
+              const uint32_t lalb = uint32_t(slots[2 * R + size_t(f) * R + at]);
+              const int pos = posq[size_t(f) * R + at];
               const bool in = full || (int(lalb >> 16) < c.remA && int(lalb & 0xffffu) < c.remB);
-              const bool valid = in && e[1] >= 0;
-              if (e[0] < 0) ok = fail("slot table: negative offset", e[0], e[1]);
-              else if (f == 0) on_read(kk, valid, e[0], e[1]);
-              else on_write(kk, valid, e[0], e[1]);
+              const bool valid = in && pos != 0xffff;
+              if (off < 0) ok = fail("slot table: negative offset", off, pos);
+              else if (f == 0) on_read(kk, valid, off, pos);
+              else on_write(kk, valid, off, pos);
             }
       } else if (k.ju == 0) {
         for (int t = 0; t < kThreads && ok; ++t) {

@@ -124,11 +124,11 @@ struct TileParams {
   const int32_t* tabA; // device table crossA[LB]
   const int32_t* tabB; // device table crossB[LA]
   // Slot tables of tile_slots_kernel: for every (k, thread) slot of the load
-  // and of the store order, the element's offset in the tile and its
-  // shared-memory position (-1: no element), two slots per int4 -- load slots
-  // [K/2][kThreads], then store slots [K/2][kThreads] -- followed by each
-  // slot's tile coordinate (la << 16 | lb, 0xffffffff: no element), four per
-  // int4: load [K/4][kThreads], then store [K/4][kThreads].
+  // and of the store order, four slots per 16-byte group [K/4][kThreads]:
+  // the element's offset in the tile (int32; load region, then store
+  // region), its tile coordinate (la << 16 | lb, 0xffffffff: no element;
+  // load, then store) and its shared-memory position (uint16, 0xffff: no
+  // element, four per 8 bytes; load, then store).
   const int4* slots;
   // per-thread step of kThreads in the read order (u, lb) and write order (lc, lb, la)
   int rd_du, rd_dlb;
