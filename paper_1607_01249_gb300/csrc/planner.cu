@@ -301,7 +301,8 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
     k.seg_a = ra;
     k.seg_b = rb;
     const double mem = (n * esA / run_efficiency(ra * esA, false, flat) +
-                        n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true, flat)) / kHbmBytesPerS;
+                        n * esB / run_efficiency(rb * esB, true, flat) +
+                        (bnz ? n * esB / run_efficiency(rb * esB, false, flat) : 0.0)) / kHbmBytesPerS;
     const double rows = n / double(len);
     const double lanes_per_row = std::ceil(double(len) / (32.0 * k.vec)) * 32.0;
     const double issue = (rows * lanes_per_row * 10.0 + rows * 32.0 * (8.0 * c.N)) / kLaneInstrPerS;
@@ -339,11 +340,17 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
         k.seg_a = ra;
         k.seg_b = rb;
         const double mem = (n * esA / run_efficiency(ra * esA, false, flat) +
-                            n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true, flat)) / kHbmBytesPerS;
+                            n * esB / run_efficiency(rb * esB, true, flat) +
+                        (bnz ? n * esB / run_efficiency(rb * esB, false, flat) : 0.0)) / kHbmBytesPerS;
         const double issue = ntiles * kThreads * Kt * (10.0 + (bnz ? 3 : 0)) / kLaneInstrPerS;
         const double over = ntiles * kThreads * (40.0 + 10.0 * c.N) / kLaneInstrPerS;
         const double fill = double(c.s[0]) * G / double(vcap);   // share of the unrolled slots in use
-        k.est_s = std::max(mem, issue / std::max(fill, 0.05)) + 0.1 * std::min(mem, issue) + over + 3e-6;
+        // with beta != 0 the multi-row copy reads B in as many separate runs
+        // as it writes: measured 1.4-1.7x slower than a staged tile whose B
+        // footprint is fewer, longer runs (3D (370,377,481) perm (0,2,1):
+        // 3369 against 5405 GB/s), which the per-run overhead does not show
+        const double rows_beta = bnz ? 1.5 : 1.0;
+        k.est_s = (std::max(mem, issue / std::max(fill, 0.05)) + 0.1 * std::min(mem, issue)) * rows_beta + over + 3e-6;
         out.push_back(k);
       }
     }
@@ -431,9 +438,11 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
             if (LC * LA == 1) ra = ra >= double(V) ? 8.0 : 1.0;
             if (LC * LB == 1) rb = rb >= double(V) ? 8.0 : 1.0;
             const double mem = (n * esA / run_efficiency(ra * esA, false, flat) +
-                                n * esB * (bnz ? 2 : 1) / run_efficiency(rb * esB, true, flat)) / kHbmBytesPerS;
+                                n * esB / run_efficiency(rb * esB, true, flat) +
+                        (bnz ? n * esB / run_efficiency(rb * esB, false, flat) : 0.0)) / kHbmBytesPerS;
             const double mem_s = (n * esA / run_efficiency(ra_s * esA, false, flat) +
-                                  n * esB * (bnz ? 2 : 1) / run_efficiency(rb_s * esB, true, flat)) / kHbmBytesPerS;
+                                  n * esB / run_efficiency(rb_s * esB, true, flat) +
+                        (bnz ? n * esB / run_efficiency(rb_s * esB, false, flat) : 0.0)) / kHbmBytesPerS;
             const double per_slot = 26.0 + (sh.ga.size() > 1 ? 3 : 0) + (sh.gb.size() > 1 ? 3 : 0) + (bnz ? 6 : 0);
             const double issue = ntiles * kTileK * kThreads * per_slot / kLaneInstrPerS;
             const double over = ntiles * kThreads * (60.0 + 10.0 * c.N) / kLaneInstrPerS;
