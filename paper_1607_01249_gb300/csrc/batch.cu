@@ -36,7 +36,7 @@ cudaError_t grid_for(const void* fn, int smem, int64_t work, int* grid);
 
 // --------------------------------------------------------------- device --
 
-template <int DIN, int DOUT, bool BNZ>
+template <int DIN, int DOUT, bool BNZ, bool TAB>
 __device__ __forceinline__ void batch_tile(const BatchDesc& d, const TileCoord& c, unsigned char* smem) {
   using S = stage_t<DIN>;
   using TO = store_t<DOUT>;
@@ -60,15 +60,15 @@ __device__ __forceinline__ void batch_tile(const BatchDesc& d, const TileCoord& 
   S* tile = reinterpret_cast<S*>(smem);
   int u0, lb0, lc0, lbw0, la0;
   flat_starts(p, t, u0, lb0, lc0, lbw0, la0);
-  walk_read<K, true>(c, p, p.tabA, u0, lb0,
-                     [&](int k, bool, int32_t off, int) { v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + off)); });
-  walk_read<K, true>(c, p, p.tabA, u0, lb0, [&](int k, bool ok, int32_t, int pos) {
+  walk_read<K, TAB>(c, p, p.tabA, u0, lb0,
+                    [&](int k, bool, int32_t off, int) { v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + off)); });
+  walk_read<K, TAB>(c, p, p.tabA, u0, lb0, [&](int k, bool ok, int32_t, int pos) {
     if (ok) tile[pos] = v[k];
   });
   __syncthreads();
   if constexpr (BNZ)
-    walk_write<K, true>(c, p, p.tabB, lc0, lbw0, la0, [&](int k, bool, int32_t off, int) { bo[k] = Bb[off]; });
-  walk_write<K, true>(c, p, p.tabB, lc0, lbw0, la0, [&](int k, bool ok, int32_t off, int pos) {
+    walk_write<K, TAB>(c, p, p.tabB, lc0, lbw0, la0, [&](int k, bool, int32_t off, int) { bo[k] = Bb[off]; });
+  walk_write<K, TAB>(c, p, p.tabB, lc0, lbw0, la0, [&](int k, bool ok, int32_t off, int pos) {
     if (ok) Bb[off] = epilogue<DIN, DOUT>(tile[pos], bo[k], p.epi, 1.f);
   });
 }
@@ -108,8 +108,14 @@ __device__ __noinline__ void batch_unit(const BatchDesc& d, const TileRec& r, un
     else batch_copy<DIN, DOUT, false>(d, rc);
   } else {
     const TileCoord c{r.baseA, r.baseB, r.remA, r.remB};
-    if (d.tp.epi.beta_nz) batch_tile<DIN, DOUT, true>(d, c, smem);
-    else batch_tile<DIN, DOUT, false>(d, c, smem);
+    // both cross offsets linear, or both from tables
+    if (d.tp.crossA_tab) {
+      if (d.tp.epi.beta_nz) batch_tile<DIN, DOUT, true, true>(d, c, smem);
+      else batch_tile<DIN, DOUT, false, true>(d, c, smem);
+    } else {
+      if (d.tp.epi.beta_nz) batch_tile<DIN, DOUT, true, false>(d, c, smem);
+      else batch_tile<DIN, DOUT, false, false>(d, c, smem);
+    }
   }
 }
 
@@ -245,8 +251,9 @@ std::shared_ptr<const BatchTemplate> make_template(const ttc_plan_s* p) {
     int sm = 0;
     build_tile_params(p->canon, k, p->din, &d->tp, &ta, &tb, &sm);
     d->path = k.rows ? BP_ROWS : BP_TILE;
-    if (d->path == BP_TILE) {
-      // the batch body always reads both cross offsets from tables
+    if (d->path == BP_TILE && (d->tp.crossA_tab || d->tp.crossB_tab)) {
+      // the batch body has two walks: both cross offsets linear, or both
+      // from tables (a linear one is then written out as a table)
       if (!d->tp.crossA_tab) {
         ta.resize(d->tp.LB);
         for (int i = 0; i < d->tp.LB; ++i) ta[i] = i * d->tp.crossA_lin;
@@ -257,11 +264,11 @@ std::shared_ptr<const BatchTemplate> make_template(const ttc_plan_s* p) {
         for (int i = 0; i < d->tp.LA; ++i) tb[i] = i * d->tp.crossB_lin;
         d->tp.crossB_tab = 1;
       }
-      t->smem = d->tp.P * d->tp.LB * (p->din == DT_F64 ? 8 : 4);
       t->tabA_count = ta.size();
       t->tabs.insert(t->tabs.end(), ta.begin(), ta.end());
       t->tabs.insert(t->tabs.end(), tb.begin(), tb.end());
     }
+    if (d->path == BP_TILE) t->smem = d->tp.P * d->tp.LB * (p->din == DT_F64 ? 8 : 4);
     d->ntiles = d->tp.ntiles;
     d->tp.epi = make_epilogue(p, nullptr);
   } else {
