@@ -179,8 +179,10 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc* __r
                                                             const uint32_t* __restrict__ tile0, uint32_t nprob,
                                                             uint32_t total, uint32_t* counter) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ uint32_t s_g, s_p;
-  __shared__ TileRec s_rec;
+  // the claimed tile, double-buffered: thread 0 records the next claim in the
+  // other buffer before the end-of-tile barrier, which then also publishes it
+  __shared__ uint32_t s_g[2], s_p[2];
+  __shared__ TileRec s_rec[2];
   // raw storage: BatchDesc has member initializers, which a __shared__
   // variable cannot run
   __shared__ __align__(16) unsigned char s_desc_raw[sizeof(BatchDesc)];
@@ -189,23 +191,23 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc* __r
   static_assert(sizeof(BatchDesc) % sizeof(int4) == 0, "descriptor copied as 16-byte words");
   const int t = threadIdx.x;
   uint32_t have = 0xffffffffu;
-  auto claim = [&](uint32_t g) {   // thread 0: remember tile g and its problem
-    s_g = g;
+  auto claim = [&](int b, uint32_t g) {   // thread 0: remember tile g and its problem in buffer b
+    s_g[b] = g;
     if (g < total) {
       if (recs) {
-        s_rec = recs[g];
-        s_p = s_rec.prob;
+        s_rec[b] = recs[g];
+        s_p[b] = s_rec[b].prob;
       } else {
-        s_p = find_problem(tile0, nprob, g);
+        s_p[b] = find_problem(tile0, nprob, g);
       }
     }
   };
-  if (t == 0) claim(atomicAdd(counter, 1u));
+  if (t == 0) claim(0, atomicAdd(counter, 1u));
   __syncthreads();
-  for (;;) {
-    const uint32_t g = s_g;
+  for (int b = 0;; b ^= 1) {
+    const uint32_t g = s_g[b];
     if (g >= total) break;
-    const uint32_t prob = s_p;
+    const uint32_t prob = s_p[b];
     uint32_t gn = 0;
     if (t == 0) gn = atomicAdd(counter, 1u);
     if (prob != have) {
@@ -216,14 +218,15 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc* __r
       __syncthreads();
     }
     if (!recs) {
-      if (t == 0) s_rec = device_rec(s_desc, prob, g - __ldg(tile0 + prob));
+      if (t == 0) s_rec[b] = device_rec(s_desc, prob, g - __ldg(tile0 + prob));
       __syncthreads();
     }
-    const TileRec r = s_rec;
+    const TileRec r = s_rec[b];
     batch_dispatch(s_desc, r, smem);
-    __syncthreads();   // the tile buffer and s_rec are reused
-    if (t == 0) claim(gn);
-    __syncthreads();
+    // buffer b^1 was last read at the start of the previous tile, before the
+    // previous end-of-tile barrier, so thread 0 may overwrite it now
+    if (t == 0) claim(b ^ 1, gn);
+    __syncthreads();   // the tile buffer, the descriptor and buffer b^1
   }
 }
 
