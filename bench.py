@@ -41,7 +41,12 @@ import numpy as np  # noqa: E402
 from paper_1607_01249_gb300 import inputs  # noqa: E402
 
 METRIC = "effective HBM GB/s (frac of ~8 TB/s); served transposes/s + p99 vs per-call"
-KERNEL_SOURCES = ["paper_1607_01249_gb300/csrc/kernels_impl.cuh", "paper_1607_01249_gb300/csrc/kernels.cuh"]
+# sources of each workload's kernels: a committed traffic figure counts only
+# while their hash is the one it was measured with
+KERNEL_SOURCES = {
+    "batch": ["paper_1607_01249_gb300/csrc/batch.cu", "paper_1607_01249_gb300/csrc/kernels.cuh"],
+    None: ["paper_1607_01249_gb300/csrc/kernels_impl.cuh", "paper_1607_01249_gb300/csrc/kernels.cuh"],
+}
 
 
 def log(*a):
@@ -75,10 +80,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_hash():
+def kernel_hash(workload=None):
     h = hashlib.sha256()
-    for s in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, s), "rb") as f:
+    for src in KERNEL_SOURCES.get(workload, KERNEL_SOURCES[None]):
+        with open(os.path.join(ROOT, src), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -92,7 +97,7 @@ def ncu_traffic(kernel: str, workload: str):
     with open(p) as f:
         d = json.load(f)
     e = d.get(f"{workload}:{kernel}")
-    if not e or e.get("kernel_hash") != kernel_hash():
+    if not e or e.get("kernel_hash") != kernel_hash(workload):
         return None
     return e
 
@@ -164,6 +169,10 @@ def workload_problems(name: str, target: int = 1 << 26, only: str = ""):
         return [inputs.single_4d()]
     if name == "packing":
         return inputs.packing_cases()
+    if name == "batch":
+        return inputs.batch_problems(4096)
+    if name == "serving":
+        return [p for _, p in inputs.serving_requests(1500, seed=4)]
     raise ValueError(name)
 
 
