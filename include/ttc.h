@@ -279,6 +279,9 @@ ttc_status ttc_batch_info(ttc_batch_t batch, int64_t* problems, int64_t* tiles);
  *                      (host steady clock, seconds); TTC_ERR_NOT_READY until
  *                      it has completed.
  *  ttc_server_destroy  drain, stop the threads, free everything.
+ * The server keeps one record per submitted request (about a hundred bytes,
+ * plus its latency sample) until it is destroyed: a long-running caller
+ * recycles servers (their streams and slots are cheap to recreate).
  */
 typedef struct ttc_server_s* ttc_server_t;
 
