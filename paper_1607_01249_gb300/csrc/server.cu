@@ -189,9 +189,20 @@ void scheduler(ttc_server_s* S) {
     // The front request decides the kind of epoch: a large request runs
     // alone (its budget is released as soon as it finishes), small ones are
     // gathered in arrival order into one batched launch.
-    const Req& front = S->reqs[size_t(S->pending.front())];
+    Req& front = S->reqs[size_t(S->pending.front())];
     const bool f_small = is_small(S, front);
     const int f_cls = front.cls;
+    if (std::none_of(S->lanes.begin(), S->lanes.end(),
+                     [&](const Lane& L) { return L.cls == f_cls && !L.dead; })) {
+      // every stream of its size class was given up by the watchdog
+      front.status = TTC_ERR_TIMEOUT;
+      front.state = RQ_DONE;
+      front.t_done = now_s();
+      S->n_failed += 1;
+      S->pending.pop_front();
+      S->cv_poll.notify_all();
+      continue;
+    }
     int lane = -1;
     for (int i = 0; i < int(S->lanes.size()); ++i) {
       const Lane& c = S->lanes[size_t(i)];
@@ -241,13 +252,10 @@ void scheduler(ttc_server_s* S) {
     S->inflight_bytes += ebytes;
     S->peak_inflight = std::max(S->peak_inflight, S->inflight_bytes);
     L.load += ebytes;
-    cudaEvent_t ev;
-    if (!S->free_events.empty()) {
-      ev = S->free_events.back();
-      S->free_events.pop_back();
-    } else {
-      cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    }
+    // events come from the pool made at creation: a lane holds at most
+    // kLaneMaxQueued epochs, so the pool never runs dry
+    cudaEvent_t ev = S->free_events.back();
+    S->free_events.pop_back();
     std::vector<Req*> rs;
     std::vector<ttc_plan_t> fp8s;
     const double ta = now_s();
@@ -391,6 +399,15 @@ void completer(ttc_server_s* S) {
 
 void free_lanes(std::vector<Lane>& lanes) {
   for (auto& L : lanes) {
+    if (L.dead) {
+      // its stream may still run a given-up epoch: waiting for it, or
+      // freeing memory it may use (cudaFree synchronises), could block
+      // forever, so the stream is released without a wait and its slots
+      // are left allocated
+      if (L.s) cudaStreamDestroy(L.s);
+      L = Lane();
+      continue;
+    }
     if (L.s) {
       cudaStreamSynchronize(L.s);
       cudaStreamDestroy(L.s);
@@ -438,6 +455,17 @@ ttc_status ttc_server_create(ttc_server_t* out, int64_t budget_bytes, int nstrea
       return e == cudaErrorMemoryAllocation ? fail(TTC_ERR_OOM, "server allocation failed")
                                             : cuda_fail(e, "server setup");
     }
+  }
+  const size_t nev = S->lanes.size() * size_t(kLaneMaxQueued);
+  for (size_t i = 0; i < nev; ++i) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      for (auto x : S->free_events) cudaEventDestroy(x);
+      free_lanes(S->lanes);
+      return cuda_fail(e, "server event creation");
+    }
+    S->free_events.push_back(ev);
   }
   S->sched = std::thread(scheduler, S.get());
   S->compl_thread = std::thread(completer, S.get());
