@@ -35,6 +35,27 @@ ttc_status ttc_debug_verify_schedule(ttc_plan_t plan, int candidate, char* msg, 
  */
 ttc_status ttc_debug_describe_candidate(ttc_plan_t plan, int candidate, char* buf, int buflen);
 
+/*
+ * The slot tables tile_slots_kernel reads for candidate `candidate` of
+ * `plan` (layout: TileParams::slots in csrc/ttc_internal.h), copied into
+ * out[0..count) as int32 values; *needed receives the table's length.
+ * TTC_ERR_INVALID_ARG if the candidate does not use slot tables or count is
+ * too small.
+ */
+ttc_status ttc_debug_slot_tables(ttc_plan_t plan, int candidate, int32_t* out, int64_t count, int64_t* needed);
+
+/*
+ * Server failure detection without a GPU fault: set the watchdog (seconds;
+ * default 30) after which a server gives up an epoch whose completion it has
+ * not seen, and submit a request that is a single-thread kernel staying busy
+ * for `microseconds` (0..10 s, bounded by the device timer) on a stream of
+ * the large class.  A delay longer than the watchdog makes the request
+ * complete with TTC_ERR_TIMEOUT and retires its stream; the kernel itself
+ * still ends on its own.
+ */
+ttc_status ttc_debug_server_set_watchdog(ttc_server_t server, double seconds);
+ttc_status ttc_debug_server_submit_delay(ttc_server_t server, int64_t microseconds, int64_t* ticket);
+
 #ifdef __cplusplus
 }
 #endif

@@ -213,4 +213,26 @@ cudaError_t launch_amax(int din, const void* A, const RowParams& p, float alpha_
 
 int64_t launch_count() { return g_launches.load(); }
 
+// One thread that stays busy for `ns` nanoseconds of the device's global
+// timer and returns: bounded by the timer and by an iteration cap, whichever
+// ends first.  Used only to make a server epoch outlast its watchdog in tests.
+__global__ void delay_kernel(uint64_t ns) {
+  uint64_t t0 = 0, t = 0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  // every iteration takes well over 10 ns (a timer read and a sleep), so
+  // ns / 10 iterations cover the requested time even if the sleeps are short
+  const uint64_t cap = ns / 10 + 1000;
+  for (uint64_t i = 0; i < cap; ++i) {
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 >= ns) break;
+    __nanosleep(1000);
+  }
+}
+
+cudaError_t launch_delay(uint64_t ns, cudaStream_t s) {
+  delay_kernel<<<1, 1, 0, s>>>(ns);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
 }  // namespace ttc

@@ -23,5 +23,7 @@ cudaError_t launch_copy(int din, int dout, int vec, const void* A, void* B, cons
 cudaError_t launch_amax(int din, const void* A, const RowParams& p, float alpha_f, uint32_t* amax_bits,
                         uint32_t* clear_bits, cudaStream_t s);
 int64_t launch_count();
+// a kernel that stays busy for ns nanoseconds (bounded), for watchdog tests
+cudaError_t launch_delay(uint64_t ns, cudaStream_t s);
 
 }  // namespace ttc

@@ -46,7 +46,7 @@ constexpr size_t kSlotBytes = size_t(4) << 20;   // descriptors + tables + tile 
 constexpr int kSlots = 8;                        // batched epochs in flight per lane
 constexpr int kLaneMaxQueued = 64;               // epochs in flight per lane
 constexpr int kMaxEpoch = 1024;                  // requests per batched epoch
-constexpr double kWatchdogS = 30.0;              // an epoch older than this is given up
+constexpr double kWatchdogS = 30.0;              // default: an epoch older than this is given up
 constexpr int64_t kMediumBytes = int64_t(64) << 20;  // largest algorithmic bytes of size class 1
 
 enum ReqState : int { RQ_PENDING = 0, RQ_RUNNING = 1, RQ_DONE = 2 };
@@ -59,6 +59,7 @@ struct Req {
   int64_t alg_bytes;   // algorithmic bytes
   int64_t tiles;       // tiles in the batch body, or -1 if it cannot take the request
   int cls;             // size class: 0 batchable, 1 medium, 2 large
+  uint64_t delay_ns = 0;  // plan == nullptr: a bounded delay kernel (tests)
   double t_submit = 0, t_admit = 0, t_launch = 0, t_done = 0;
   int state = RQ_PENDING;
   ttc_status status = TTC_OK;
@@ -87,6 +88,7 @@ struct Lane {
 }  // namespace
 
 struct ttc_server_s {
+  double watchdog_s = kWatchdogS;
   int64_t budget = 0;
   int64_t small_tiles = 0;
   int dev = 0;
@@ -220,7 +222,7 @@ void scheduler(ttc_server_s* S) {
     while (!S->pending.empty() && int(take.size()) < kMaxEpoch) {
       Req& r = S->reqs[size_t(S->pending.front())];
       if (S->inflight_bytes + ebytes + r.bytes > S->budget) break;
-      const bool fp8 = r.plan->dout == DT_E4M3;
+      const bool fp8 = r.plan && r.plan->dout == DT_E4M3;
       if (fp8 && S->fp8_busy.count(r.plan)) break;      // that plan's scale scratch is in use
       const bool small = is_small(S, r);
       if (small != f_small || r.cls != f_cls) break;
@@ -263,7 +265,7 @@ void scheduler(ttc_server_s* S) {
       Req& r = S->reqs[size_t(t)];
       r.state = RQ_RUNNING;
       r.t_admit = ta;
-      if (r.plan->dout == DT_E4M3) fp8s.push_back(r.plan);
+      if (r.plan && r.plan->dout == DT_E4M3) fp8s.push_back(r.plan);
       rs.push_back(&r);
     }
     S->launching += 1;
@@ -276,7 +278,12 @@ void scheduler(ttc_server_s* S) {
     } else {
       for (Req* r : rs) {
         if (st != TTC_OK) break;
-        st = run_plan(r->plan, r->A, r->B, L.s);
+        if (r->plan) {
+          st = run_plan(r->plan, r->A, r->B, L.s);
+        } else {
+          const cudaError_t de = launch_delay(r->delay_ns, L.s);
+          st = de == cudaSuccess ? TTC_OK : cuda_fail(de, "delay kernel launch");
+        }
         ++launches;
       }
     }
@@ -363,7 +370,7 @@ void completer(ttc_server_s* S) {
         const cudaError_t q = cudaEventQuery(heads[i].second);
         if (q == cudaSuccess) done[i] = 1;
         else if (q != cudaErrorNotReady) done[i] = 2;           // the epoch failed
-        else if (t0 - t_launch[i] > kWatchdogS) done[i] = 3;    // watchdog
+        else if (t0 - t_launch[i] > S->watchdog_s) done[i] = 3;  // watchdog
       }
       const double t = now_s();
       lk.lock();
@@ -611,3 +618,35 @@ ttc_status ttc_server_destroy(ttc_server_t S) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------- testing hooks
+
+extern "C" ttc_status ttc_debug_server_set_watchdog(ttc_server_t S, double seconds) {
+  if (!S || !(seconds > 0)) return fail(TTC_ERR_INVALID_ARG, "bad server or watchdog");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->watchdog_s = seconds;
+  return TTC_OK;
+}
+
+extern "C" ttc_status ttc_debug_server_submit_delay(ttc_server_t S, int64_t microseconds, int64_t* ticket) {
+  if (!S || !ticket || microseconds < 0 || microseconds > 10000000)
+    return fail(TTC_ERR_INVALID_ARG, "bad server, ticket or delay (0..10 s)");
+  Req r;
+  r.plan = nullptr;
+  r.A = nullptr;
+  r.B = nullptr;
+  r.bytes = 0;
+  r.alg_bytes = 0;
+  r.tiles = -1;
+  r.cls = S->small_tiles == 0 ? 0 : 2;
+  r.delay_ns = uint64_t(microseconds) * 1000u;
+  r.t_submit = now_s();
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->stop) return fail(TTC_ERR_INVALID_ARG, "server is shutting down");
+  if (S->reqs.empty()) S->first_submit = r.t_submit;
+  *ticket = int64_t(S->reqs.size());
+  S->reqs.push_back(r);
+  S->pending.push_back(*ticket);
+  S->cv_sched.notify_one();
+  return TTC_OK;
+}

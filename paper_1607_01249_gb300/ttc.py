@@ -91,6 +91,8 @@ SIGNATURES = {
     "ttc_debug_describe_candidate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
     "ttc_debug_slot_tables": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
                                              _i64p]),
+    "ttc_debug_server_set_watchdog": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "ttc_debug_server_submit_delay": (ctypes.c_int, [_vp, ctypes.c_int64, _i64p]),
 }
 
 _lib = None
@@ -334,6 +336,17 @@ class Server:
         v = [ctypes.c_double(0) for _ in range(4)]
         _check(lib().ttc_server_times(self._h, int(ticket), *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+    def set_watchdog(self, seconds: float):
+        """Testing hook: give up epochs unseen for this long."""
+        _check(lib().ttc_debug_server_set_watchdog(self._h, float(seconds)))
+
+    def submit_delay(self, microseconds: int) -> int:
+        """Testing hook: a request that keeps one thread busy for the given
+        time on a large-class stream (ends on its own)."""
+        t = ctypes.c_int64(-1)
+        _check(lib().ttc_debug_server_submit_delay(self._h, int(microseconds), ctypes.byref(t)))
+        return t.value
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -156,3 +156,37 @@ def test_server_fp8_requests_of_one_plan_run_in_turn():
     data, st = run_server(probs, 1 << 30, 4, 4096, 1700, shared_fp8_plan=True)
     assert st["completed"] == 6
     check_against_oracle(data)
+
+
+@pytest.mark.gpu
+def test_server_watchdog_gives_up_an_epoch_and_keeps_serving():
+    """Failure detection without a GPU fault: a request whose kernel stays
+    busy (bounded, 0.4 s) longer than the watchdog (0.1 s) completes with
+    TTC_ERR_TIMEOUT, its stream is retired, the other streams keep serving,
+    and the server shuts down without waiting for the given-up stream."""
+    import torch
+    from tests import gpu_helpers as H
+    srv = ttc.Server(1 << 30, 2, 4096)
+    srv.set_watchdog(0.1)
+    t_slow = srv.submit_delay(400_000)
+    with pytest.raises(ttc.TTCError) as ei:
+        srv.poll(t_slow, 3_000_000)
+    assert ei.value.name == "TTC_ERR_TIMEOUT"
+    probs = [Problem(perm=(1, 0), sizes=(300, 200)), Problem(perm=(2, 0, 1), sizes=(64, 50, 70), alpha=1.5)]
+    data = []
+    for i, p in enumerate(probs):
+        plan = ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta)
+        A, B0 = H.make_inputs(p, 40 + i)
+        dA, dB = H.to_device(A, p.dtype_in), H.to_device(B0, p.dtype_out)
+        data.append((p, A, B0, dB, srv.submit(plan, dA, dB)))
+    for p, A, B0, dB, t in data:
+        assert srv.poll(t, 5_000_000)
+        torch.cuda.synchronize()
+        want, _ = H.oracle_mirror(p, A, B0)
+        assert H.compare_bits(H.to_host(dB, p.dtype_out), want, p.dtype_out, True)[0]
+    st = srv.stats()
+    assert st["failed"] == 1 and st["completed"] == len(probs)
+    t0 = time.time()
+    srv.close()
+    assert time.time() - t0 < 5.0
+    torch.cuda.synchronize()          # the delay kernel has ended on its own
