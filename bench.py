@@ -169,6 +169,8 @@ def workload_problems(name: str, target: int = 1 << 26, only: str = ""):
         return [inputs.single_4d()]
     if name == "packing":
         return inputs.packing_cases()
+    if name == "pow2":
+        return inputs.pow2_cases()
     if name == "batch":
         return inputs.batch_problems(4096)
     if name == "serving":
@@ -330,6 +332,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
+        "value_GiB_per_s": round(value * 1e9 / 2 ** 30, 2),   # the unit of the paper's Eq. 2
         "dtype": "f32+f64" if args.workload == "sweep" else "+".join(sorted({p.dtype_in for p in probs})),
         "data": "synthetic (seeded uniform[-1,1], torch Philox on the device)",
         "config": {"workload": workload_desc(args.workload, probs), "transposes_per_step": len(probs),
@@ -367,6 +370,9 @@ def workload_desc(name, probs):
                 "alpha=1.7, beta in {0,0.4}")
     if name == "single4d":
         return "4D f32 (32,40,24,36) perm (2,0,3,1) alpha=1 beta=0"
+    if name == "pow2":
+        return ("single transposes, N=2..6, power-of-two sizes, 2^26 elems/tensor, 1-2 seeded perms per N, "
+                "f32+f64, alpha=1.7, beta=0")
     if name == "packing":
         return "GEMM packing 4096x2048 of 8192^2 f32 -> 256x128 panels, and (48,64,40,56) in (64,80,48,64) perm (1,3,0,2); -> bf16 / e4m3+scale"
     return name
@@ -777,7 +783,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "single4d", "packing", "batch", "serving"])
+    ap.add_argument("--workload", default="sweep",
+                    choices=["sweep", "pow2", "single4d", "packing", "batch", "serving"])
     ap.add_argument("--serve-count", type=int, default=1500)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
@@ -790,6 +797,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="default workload: skip the batched-launch summary")
+    ap.add_argument("--no-pow2", action="store_true", help="default workload: skip the power-of-two-sizes row")
     ap.add_argument("--no-serving", action="store_true", help="default workload: skip the serving summary")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--target", type=int, default=1 << 26, help="elements per tensor of the sweep")
@@ -825,6 +833,14 @@ def main():
             import copy
             sub = copy.copy(args)
             sub.steps, sub.warmup = min(args.steps, 5), max(args.warmup, 3)
+            if not args.no_pow2:
+                # the same shapes with power-of-two sizes (a separate row, not
+                # part of the headline value)
+                pw = copy.copy(sub)
+                pw.workload, pw.no_e2e, pw.cases_out, pw.only = "pow2", True, "", ""
+                r = run_ours(pw, rank, world)
+                out["pow2"] = {"workload": r["config"]["workload"], "GB/s": r["value"], "cases": r["cases"],
+                               "per_variant": r["per_variant"], "timing": "CUDA events"}
             if not args.no_batch:
                 b = run_batch(sub, rank, world)
                 out["batch"] = {"workload": b["config"]["workload"], "GB/s": b["value"],

@@ -138,6 +138,24 @@ def sweep_cases(seed: int = 1, target: int = 1 << 26, Ns=(2, 3, 4, 5, 6), perms_
     return cases
 
 
+def pow2_cases(seed: int = 2, log2n: int = 26, Ns=(2, 3, 4, 5, 6), perms_per_n=2, dtypes=("f32", "f64"),
+               alpha=1.7) -> list:
+    """The sweep's shapes with power-of-two sizes: 2^log2n elements, the
+    exponent split as evenly as possible over the N indices (larger ones
+    first); perms_per_n seeded perms per N (one keeping index 0 when N >= 3),
+    beta = 0."""
+    g = rng(seed)
+    cases = []
+    for N in Ns:
+        e = [log2n // N + (1 if k < log2n % N else 0) for k in range(N)]
+        sizes = tuple(1 << x for x in e)
+        for pi, perm in enumerate(dict.fromkeys(sweep_perms(N, g, perms_per_n))):
+            for dt in dtypes:
+                cases.append(Problem(perm=perm, sizes=sizes, dtype_in=dt, dtype_out=dt, alpha=alpha, beta=0.0,
+                                     tag=f"P{N}p{pi}"))
+    return cases
+
+
 def packing_cases(out_dtypes=("bf16", "e4m3")) -> list:
     """GEMM packing (section 2.1, Fig. 3: a matrix reinterpreted as a 3D/4D
     tensor whose permutation lays out contiguous panels; Fig. 2: a sub-tensor
@@ -154,6 +172,11 @@ def packing_cases(out_dtypes=("bf16", "e4m3")) -> list:
                              extra={"matrix": (8192, 8192), "offset": (64, 128)}))
         cases.append(Problem(perm=(1, 3, 0, 2), sizes=(48, 64, 40, 56), dtype_in="f32",
                              dtype_out=dt, outer_a=(64, 80, 48, 64), tag="sub4d"))
+        # the other panel order, B(m1,k1,k2,m2): panels of one row block of
+        # m adjacent (a variant of the Fig. 3 reading)
+        cases.append(Problem(perm=(0, 2, 3, 1), sizes=(256, 16, 128, 16), dtype_in="f32",
+                             dtype_out=dt, outer_a=(256, 32, 128, 64), tag="panel_alt",
+                             extra={"matrix": (8192, 8192), "offset": (0, 0)}))
     return cases
 
 
