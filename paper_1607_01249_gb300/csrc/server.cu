@@ -18,6 +18,7 @@
 #include <sys/prctl.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -48,6 +49,7 @@ constexpr int kLaneMaxQueued = 64;               // epochs in flight per lane
 constexpr int kMaxEpoch = 1024;                  // requests per batched epoch
 constexpr double kWatchdogS = 30.0;              // default: an epoch older than this is given up
 constexpr int64_t kMediumBytes = int64_t(64) << 20;  // largest algorithmic bytes of size class 1
+constexpr double kIdleSpinS = 50e-6;             // the scheduler polls this long before it sleeps
 
 enum ReqState : int { RQ_PENDING = 0, RQ_RUNNING = 1, RQ_DONE = 2 };
 
@@ -96,6 +98,8 @@ struct ttc_server_s {
   std::condition_variable cv_sched, cv_done, cv_poll;
   std::deque<Req> reqs;              // ticket = index (references stay valid)
   std::deque<int64_t> pending;
+  std::atomic<int64_t> npending{0};  // pending.size(), readable without the lock
+  std::atomic<bool> stop_flag{false};
   std::vector<Lane> lanes;
   std::vector<cudaEvent_t> free_events;
   std::set<ttc_plan_t> fp8_busy;
@@ -172,6 +176,7 @@ void fail_pending(ttc_server_s* S) {
     S->n_failed += 1;
   }
   S->pending.clear();
+  S->npending.store(0, std::memory_order_release);
   S->cv_poll.notify_all();
 }
 
@@ -181,7 +186,14 @@ void scheduler(ttc_server_s* S) {
   while (true) {
     if (S->stop && S->pending.empty()) break;
     if (S->pending.empty()) {
-      S->cv_sched.wait(lk);
+      // poll for a short while before sleeping: waking a sleeping thread
+      // costs ~10 us, which every request arriving to an idle queue would wait
+      lk.unlock();
+      const double until = now_s() + kIdleSpinS;
+      while (S->npending.load(std::memory_order_acquire) == 0 && !S->stop_flag.load() && now_s() < until)
+        std::this_thread::yield();
+      lk.lock();
+      if (S->pending.empty() && !S->stop) S->cv_sched.wait(lk);
       continue;
     }
     if (std::all_of(S->lanes.begin(), S->lanes.end(), [](const Lane& L) { return L.dead; })) {
@@ -202,6 +214,7 @@ void scheduler(ttc_server_s* S) {
       front.t_done = now_s();
       S->n_failed += 1;
       S->pending.pop_front();
+      S->npending.store(int64_t(S->pending.size()), std::memory_order_release);
       S->cv_poll.notify_all();
       continue;
     }
@@ -234,6 +247,7 @@ void scheduler(ttc_server_s* S) {
       if (fp8) S->fp8_busy.insert(r.plan);
       take.push_back(S->pending.front());
       S->pending.pop_front();
+      S->npending.store(int64_t(S->pending.size()), std::memory_order_release);
       ebytes += r.bytes;
       if (!small) break;
     }
@@ -528,6 +542,7 @@ ttc_status ttc_server_submit(ttc_server_t S, ttc_plan_t plan, const void* A, voi
   }
   S->reqs.push_back(r);
   S->pending.push_back(*ticket);
+  S->npending.store(int64_t(S->pending.size()), std::memory_order_release);
   S->cv_sched.notify_one();
   return TTC_OK;
 }
@@ -605,6 +620,7 @@ ttc_status ttc_server_destroy(ttc_server_t S) {
   {
     std::lock_guard<std::mutex> lk(S->mu);
     S->stop = true;
+    S->stop_flag.store(true);
   }
   S->cv_sched.notify_all();
   S->cv_done.notify_all();
@@ -647,6 +663,7 @@ extern "C" ttc_status ttc_debug_server_submit_delay(ttc_server_t S, int64_t micr
   *ticket = int64_t(S->reqs.size());
   S->reqs.push_back(r);
   S->pending.push_back(*ticket);
+  S->npending.store(int64_t(S->pending.size()), std::memory_order_release);
   S->cv_sched.notify_one();
   return TTC_OK;
 }
