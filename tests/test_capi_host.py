@@ -231,3 +231,21 @@ def test_schedules_are_sound_on_the_workloads():
         for perm in inputs.sweep_perms(N, g, 8):
             sizes = inputs.near_equal_sizes(N, 1 << 17, g, tol=0.05)
             _verify_all(ttc.Plan(perm, sizes, "f32", "f32", 1.7, 0.4), (perm, sizes))
+
+
+def test_tune_cache_file_round_trip(tmp_path):
+    """The autotune cache is a text file of key<TAB>schedule lines: loading a
+    file and saving the cache keeps every entry."""
+    src = tmp_path / "in.txt"
+    entries = {"GB300-test:0>0:b0:N2:100/1/50/1:50/100/1/0": "tile c=0 ga=[0]/32 gb=[1]/64 j=1,2 order=[1,0]",
+               "GB300-test:1>1:b1:N3:7/1/1/0:5/7/35/2:3/35/5/1": "copy chunk=7 vec=1"}
+    src.write_text("".join(f"{k}\t{v}\n" for k, v in entries.items()) + "malformed line without a tab\n")
+    ttc.tune_cache_load(str(src))
+    out = tmp_path / "out.txt"
+    ttc.tune_cache_save(str(out))
+    got = dict(line.split("\t", 1) for line in out.read_text().splitlines())
+    for k, v in entries.items():
+        assert got[k] == v
+    with pytest.raises(ttc.TTCError) as ei:
+        ttc.tune_cache_load(str(tmp_path / "missing.txt"))
+    assert ei.value.name == "TTC_ERR_INVALID_ARG"

@@ -290,3 +290,19 @@ def test_fp8_plan_executed_repeatedly_tracks_each_inputs_scale():
             assert scale == wscale, (din, rep, scale, wscale)
             ok, msg = H.compare_bits(got, want, "e4m3", nan_as_nan=True)
             assert ok, (din, rep, msg)
+
+
+def test_autotune_choice_is_remembered_for_new_plans(tmp_path):
+    """A later plan of the same problem starts from the autotuner's choice
+    (process-wide cache), and the cache survives a save/load."""
+    p = Problem(perm=(1, 0), sizes=(3000, 2000), alpha=1.3)
+    a = ttc.Plan(p.perm, p.sizes, alpha=p.alpha)
+    a.autotune(max_candidates=8)
+    chosen = a.info()["candidate"]
+    path = str(tmp_path / "tune.txt")
+    ttc.tune_cache_save(path)
+    assert any(line.strip() for line in open(path))
+    ttc.tune_cache_load(path)
+    b = ttc.Plan(p.perm, p.sizes, alpha=p.alpha)
+    H.full_check(p, seed=3, plan=b)              # first execution applies the cache
+    assert a.describe(chosen).split(" est_us")[0] == b.describe().split(" est_us")[0]
