@@ -431,7 +431,8 @@ def run_batch(args, rank, world):
     probs = inputs.batch_problems(args.batch_count)
     plans = [ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta) for p in probs]
     A, B, pa, pb = pack_buffers(probs)
-    batch = ttc.Batch()
+    direct_min = ttc.Batch.DIRECT_MIN_DEFAULT
+    batch = ttc.Batch().set_direct_threshold(direct_min)
     for pl, a, b in zip(plans, pa, pb):
         batch.add(pl, a, b)
     stream = torch.cuda.current_stream()
@@ -473,7 +474,9 @@ def run_batch(args, rank, world):
         "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic (seeded sizes/perms; uniform data)",
         "config": {"workload": f"batch of {len(probs)} transposes, N 2..5, 2^10..2^22 elements log-uniform, "
                                "f32/bf16 50/50, alpha=1, beta in {0,0.5}; one CUDA-graph launch per step",
-                   "tiles": info["tiles"], "algorithmic_bytes_per_step": bytes_step,
+                   "tiles": info["tiles"],
+                   "direct_problems": sum(p.n >= direct_min for p in probs),
+                   "direct_threshold_elements": direct_min, "algorithmic_bytes_per_step": bytes_step,
                    "parallelism": f"replicas x{world}"},
         "batch": {"transposes_per_s": round(job_rate(len(probs), world, ms_b), 1), "ms": round(ms_b, 4),
                   "kernel_launches_per_step": launches_b},

@@ -217,12 +217,20 @@ int64_t ttc_launch_count(void);
  *                     FP8 plans are rejected (TTC_ERR_UNSUPPORTED_DTYPE): their
  *                     scale needs a pre-pass of its own.
  *  ttc_batch_execute  enqueue the batch on `stream`: one counter reset and one
- *                     kernel launch.  The first execution after an add builds
- *                     and uploads the descriptors (synchronous, allocates
- *                     device memory owned by the batch).
+ *                     persistent kernel for the problems below the direct
+ *                     threshold, and beside it, on a stream of the batch
+ *                     forked from and joined back into `stream`, one
+ *                     single-plan launch per problem at or above it.  The
+ *                     first execution after an add builds and uploads the
+ *                     descriptors and sets up the direct problems' plans
+ *                     (synchronous, allocates device memory owned by the batch
+ *                     and by the plans).
  *  ttc_batch_graph_launch  the same work as a CUDA graph: captured on the
  *                     first call (after the descriptors are uploaded), then
  *                     replayed with one cudaGraphLaunch per call.
+ *  ttc_batch_set_direct_threshold  problems of at least min_elements
+ *                     elements run as their own kernels (default 2^21); 0 or
+ *                     less puts every problem in the persistent kernel.
  *  ttc_batch_destroy  release the batch (not the plans); no work using it may
  *                     be queued.
  *  ttc_batch_info     number of problems and of tiles of the batch.
@@ -236,6 +244,7 @@ ttc_status ttc_batch_execute(ttc_batch_t batch, ttc_stream_t stream);
 ttc_status ttc_batch_graph_launch(ttc_batch_t batch, ttc_stream_t stream);
 ttc_status ttc_batch_destroy(ttc_batch_t batch);
 ttc_status ttc_batch_info(ttc_batch_t batch, int64_t* problems, int64_t* tiles);
+ttc_status ttc_batch_set_direct_threshold(ttc_batch_t batch, int64_t min_elements);
 
 /*
  * Server: continuous batching of permute-scale-add requests (Eq. 1) that

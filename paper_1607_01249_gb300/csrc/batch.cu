@@ -372,10 +372,22 @@ struct ttc_batch_s {
   int smem = 0;
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
+  // problems of at least direct_min elements run as their own single-plan
+  // kernels on a side stream, beside the persistent kernel
+  int64_t direct_min = int64_t(1) << 21;
+  std::vector<Item> direct;
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   ~ttc_batch_s() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     if (arena) cudaFree(arena);
+    if (side) {
+      cudaStreamSynchronize(side);
+      cudaStreamDestroy(side);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
   }
 };
 
@@ -394,7 +406,17 @@ ttc_status batch_build(ttc_batch_s* b) {
   descs.reserve(b->items.size());
   uint64_t total = 0;
   int smem = 0;
+  b->direct.clear();
   for (auto& it : b->items) {
+    if (b->direct_min > 0 && it.plan->canon.n >= b->direct_min) {
+      // set the plan's device resources up now: nothing may allocate or copy
+      // synchronously while the launch is captured into a graph
+      DevRes* r = nullptr;
+      const ttc_status st = ensure_device(it.plan, dev, &r);
+      if (st != TTC_OK) return st;
+      b->direct.push_back(it);
+      continue;
+    }
     BatchDesc d;
     size_t na = 0;
     const size_t at = tabs.size();
@@ -444,6 +466,12 @@ ttc_status batch_build(ttc_batch_s* b) {
   b->total = uint32_t(total);
   b->smem = smem;
   b->dev = dev;
+  if (!b->direct.empty() && !b->side) {
+    e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "batch side stream");
+  }
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
@@ -456,11 +484,32 @@ ttc_status batch_build(ttc_batch_s* b) {
   return TTC_OK;
 }
 
+// The persistent kernel on s; the direct problems one after another on the
+// side stream, forked from and joined back into s (so that a capture of s
+// records both branches).
 ttc_status batch_enqueue(ttc_batch_s* b, cudaStream_t s) {
-  if (b->total == 0) return TTC_OK;
-  cudaError_t e = batch_launch(b->d_descs, b->d_recs, nullptr, 0, b->total, b->d_counter, b->smem, s);
-  if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
-  return TTC_OK;
+  cudaError_t e = cudaSuccess;
+  ttc_status st = TTC_OK;
+  if (!b->direct.empty()) {
+    e = cudaEventRecord(b->fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+    for (auto& it : b->direct) {
+      st = run_plan(it.plan, it.A, it.B, b->side);
+      if (st != TTC_OK) break;
+    }
+    e = cudaEventRecord(b->join, b->side);
+    if (e != cudaSuccess && st == TTC_OK) st = cuda_fail(e, "batch join");
+  }
+  if (b->total && st == TTC_OK) {
+    e = batch_launch(b->d_descs, b->d_recs, nullptr, 0, b->total, b->d_counter, b->smem, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "batch kernel launch");
+  }
+  if (!b->direct.empty()) {
+    e = cudaStreamWaitEvent(s, b->join, 0);      // always join, so a capture can end
+    if (e != cudaSuccess && st == TTC_OK) st = cuda_fail(e, "batch join");
+  }
+  return st;
 }
 
 }  // namespace
@@ -541,7 +590,15 @@ ttc_status ttc_batch_graph_launch(ttc_batch_t b, ttc_stream_t stream) {
   }
   cudaError_t e = cudaGraphLaunch(b->gexec, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-  if (b->total) ++g_launches;
+  g_launches += (b->total ? 1 : 0) + int64_t(b->direct.size());
+  return TTC_OK;
+}
+
+ttc_status ttc_batch_set_direct_threshold(ttc_batch_t b, int64_t min_elements) {
+  if (!b) return fail(TTC_ERR_INVALID_ARG, "batch is NULL");
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->direct_min = min_elements;
+  b->dirty = true;
   return TTC_OK;
 }
 

@@ -79,6 +79,7 @@ SIGNATURES = {
     "ttc_batch_graph_launch": (ctypes.c_int, [_vp, _vp]),
     "ttc_batch_destroy": (ctypes.c_int, [_vp]),
     "ttc_batch_info": (ctypes.c_int, [_vp, _i64p, _i64p]),
+    "ttc_batch_set_direct_threshold": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "ttc_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_int, ctypes.c_int64]),
     "ttc_server_submit": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64p]),
     "ttc_server_poll": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64]),
@@ -285,6 +286,14 @@ class Batch:
         p, t = ctypes.c_int64(0), ctypes.c_int64(0)
         _check(lib().ttc_batch_info(self._h, ctypes.byref(p), ctypes.byref(t)))
         return {"problems": p.value, "tiles": t.value}
+
+    DIRECT_MIN_DEFAULT = 1 << 21
+
+    def set_direct_threshold(self, min_elements: int):
+        """Problems of at least this many elements run as their own kernels
+        beside the persistent one (<= 0: none; DIRECT_MIN_DEFAULT unless set)."""
+        _check(lib().ttc_batch_set_direct_threshold(self._h, int(min_elements)))
+        return self
 
     def close(self):
         if getattr(self, "_h", None):

@@ -106,3 +106,40 @@ def test_batch_graph_replay():
             want, _ = H.oracle_mirror(p, A, np.zeros_like(B0))
             ok, msg = H.compare_bits(H.to_host(dB, p.dtype_out), want, p.dtype_out, True)
             assert ok, (rep, p, msg)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("threshold", [1 << 17, 0])
+def test_batch_with_direct_problems_matches_oracle(threshold):
+    """Problems at or above the direct threshold run as their own kernels on
+    the batch's side stream, beside the persistent kernel that takes the rest;
+    both ways, and through a graph, every problem matches the oracle."""
+    torch = pytest.importorskip("torch")
+    from tests import gpu_helpers as H
+    g = inputs.rng(17)
+    probs = []
+    for i in range(14):
+        N = int(g.integers(2, 5))
+        n = int(2 ** (g.uniform(17.2, 18.5) if i % 3 == 0 else g.uniform(8, 14)))
+        sizes = inputs.near_equal_sizes(N, n, g, tol=0.3, min_size=1)
+        perm = inputs.random_perm(N, g)
+        dt = ("f32", "bf16", "f64")[i % 3]
+        probs.append(Problem(perm=perm, sizes=sizes, dtype_in=dt, dtype_out=dt, alpha=1.5, beta=0.0))
+    assert sum(p.n >= (1 << 17) for p in probs) >= 3
+    b = ttc.Batch().set_direct_threshold(threshold)
+    data = []
+    for i, p in enumerate(probs):
+        plan = ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta)
+        A, B0 = H.make_inputs(p, 500 + i, "normal")
+        dA, dB = H.to_device(A, p.dtype_in), H.to_device(B0, p.dtype_out)
+        b.add(plan, dA, dB)
+        data.append((p, A, B0, dB))
+    for launch in (b.execute, b.graph_launch, b.graph_launch):
+        for p, A, B0, dB in data:
+            dB.zero_()
+        launch()
+        torch.cuda.synchronize()
+        for p, A, B0, dB in data:
+            want, _ = H.oracle_mirror(p, A, np.zeros_like(B0))
+            ok, msg = H.compare_bits(H.to_host(dB, p.dtype_out), want, p.dtype_out, True)
+            assert ok, (threshold, p, msg)
