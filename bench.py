@@ -44,7 +44,8 @@ METRIC = "effective HBM GB/s (frac of ~8 TB/s); served transposes/s + p99 vs per
 # sources of each workload's kernels: a committed traffic figure counts only
 # while their hash is the one it was measured with
 KERNEL_SOURCES = {
-    "batch": ["paper_1607_01249_gb300/csrc/batch.cu", "paper_1607_01249_gb300/csrc/kernels.cuh"],
+    "batch": ["paper_1607_01249_gb300/csrc/batch.cu", "paper_1607_01249_gb300/csrc/kernels_impl.cuh",
+              "paper_1607_01249_gb300/csrc/kernels.cuh"],
     None: ["paper_1607_01249_gb300/csrc/kernels_impl.cuh", "paper_1607_01249_gb300/csrc/kernels.cuh"],
 }
 
@@ -438,7 +439,7 @@ def run_batch(args, rank, world):
     stream = torch.cuda.current_stream()
     bytes_step = sum(p.algorithmic_bytes() for p in probs)
 
-    def timed(fn, steps):
+    def timed(fn, steps, profile=False):
         for _ in range(max(args.warmup, 3)):
             fn()
         torch.cuda.synchronize()
@@ -447,11 +448,15 @@ def run_batch(args, rank, world):
             tdist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0 = ttc.launch_count()
+        if profile:
+            torch.cuda.cudart().cudaProfilerStart()
         e0.record(stream)
         for _ in range(steps):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
+        if profile:
+            torch.cuda.cudart().cudaProfilerStop()
         ms = e0.elapsed_time(e1) / steps
         return max_over_ranks(ms, world), (ttc.launch_count() - l0) // steps
 
@@ -462,7 +467,7 @@ def run_batch(args, rank, world):
     clk = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if clk:
         clk.start()
-    ms_b, launches_b = timed(lambda: batch.graph_launch(stream), args.steps)
+    ms_b, launches_b = timed(lambda: batch.graph_launch(stream), args.steps, args.profile_timed)
     clocks = clk.stop() if clk else None
     ms_c, launches_c = timed(per_call, max(1, args.steps // 2))
     info = batch.info()
@@ -486,9 +491,9 @@ def run_batch(args, rank, world):
         "speedup_vs_per_call": round(ms_c / ms_b, 3),
         "roofline": {"bound": "hbm", "achieved": round(bytes_step / (ms_b * 1e-3) / 1e9, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(bytes_step / (ms_b * 1e-3) / 1e9 / peak, 4),
-                     "kernel": "batch_kernel",
-                     "traffic": (ncu_traffic("batch_kernel", "batch") or {}).get("bytes_per_launch")
-                     if args.batch_count == 4096 else None},
+                     "kernel": "one graph launch: batch_kernel + the side stream's single-plan kernels",
+                     "traffic": (ncu_traffic("step", "batch") or {}).get("bytes_per_launch")
+                     if args.batch_count == 4096 and direct_min == ttc.Batch.DIRECT_MIN_DEFAULT else None},
         "gpu_launches": launches_b * args.steps,
         "clocks": clocks,
     }
