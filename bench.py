@@ -172,6 +172,8 @@ def workload_problems(name: str, target: int = 1 << 26, only: str = ""):
         return inputs.packing_cases()
     if name == "pow2":
         return inputs.pow2_cases()
+    if name == "complex":
+        return inputs.complex_cases()
     if name == "batch":
         return inputs.batch_problems(4096)
     if name == "serving":
@@ -181,7 +183,8 @@ def workload_problems(name: str, target: int = 1 << 26, only: str = ""):
 
 def storage_torch(dt):
     import torch
-    return {"f32": torch.float32, "f64": torch.float64, "bf16": torch.int16, "e4m3": torch.uint8}[dt]
+    return {"f32": torch.float32, "f64": torch.float64, "bf16": torch.int16, "e4m3": torch.uint8,
+            "c64": torch.complex64, "c128": torch.complex128}[dt]
 
 
 class DeviceSet:
@@ -213,6 +216,11 @@ class DeviceSet:
             t = torch.empty(n, dtype=storage_torch(dt), device="cuda")
             t.uniform_(-1.0, 1.0, generator=g)
             return t
+        if dt in ("c64", "c128"):
+            # both parts uniform[-1, 1]
+            t = torch.empty(2 * n, dtype=torch.float32 if dt == "c64" else torch.float64, device="cuda")
+            t.uniform_(-1.0, 1.0, generator=g)
+            return t.view(storage_torch(dt))
         x = torch.empty(n, dtype=torch.float32, device="cuda").uniform_(-1.0, 1.0, generator=g)
         if dt == "bf16":
             return (x.view(torch.int32) >> 16).to(torch.int16)
@@ -395,6 +403,9 @@ def workload_desc(name, probs):
     if name == "pow2":
         return ("single transposes, N=2..6, power-of-two sizes, 2^26 elems/tensor, 1-2 seeded perms per N, "
                 "f32+f64, alpha=1.7, beta=0")
+    if name == "complex":
+        return ("complex transposes c, z, cz, zc, N=2..6 x 2 seeded perms, 2^25 elems/tensor (+-1%: 256 MiB "
+                "single-, 512 MiB double-complex), alpha=1.7-0.6i, beta in {0, 0.4+0.25i}")
     if name == "packing":
         return "GEMM packing 4096x2048 of 8192^2 f32 -> 256x128 panels, and (48,64,40,56) in (64,80,48,64) perm (1,3,0,2); -> bf16 / e4m3+scale"
     return name
@@ -728,7 +739,8 @@ def oracle_slabs(p, A, B, threads):
     strideA = int(np.prod(oA[:-1], dtype=np.int64))
     posB = p.perm.index(N - 1)
     strideB = int(np.prod(oB[:posB], dtype=np.int64))
-    ODT = {"f32": oracle.F32, "f64": oracle.F64, "bf16": oracle.BF16, "e4m3": oracle.E4M3}
+    ODT = {"f32": oracle.F32, "f64": oracle.F64, "bf16": oracle.BF16, "e4m3": oracle.E4M3, "c64": oracle.C64,
+           "c128": oracle.C128}
     chunks = np.array_split(np.arange(last), min(threads, last))
 
     def work(ch):
@@ -738,8 +750,12 @@ def oracle_slabs(p, A, B, threads):
         sizes = list(p.sizes[:-1]) + [len(ch)]
         subA = A[s0 * strideA:]
         subB = B[s0 * strideB:]
-        oracle.permute(p.perm, sizes, subA, subB, p.alpha, p.beta, ODT[p.dtype_in], ODT[p.dtype_out],
-                       oA, oB)
+        if p.dtype_in in ("c64", "c128"):
+            oracle.permute_complex(p.perm, sizes, subA, subB, p.alpha, p.beta, ODT[p.dtype_in], ODT[p.dtype_out],
+                                   oA, oB)
+        else:
+            oracle.permute(p.perm, sizes, subA, subB, p.alpha, p.beta, ODT[p.dtype_in], ODT[p.dtype_out],
+                           oA, oB)
 
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
         list(ex.map(work, chunks))
@@ -813,7 +829,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "pow2", "single4d", "packing", "batch", "serving"])
+                    choices=["sweep", "pow2", "complex", "single4d", "packing", "batch", "serving"])
     ap.add_argument("--serve-count", type=int, default=1500)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
@@ -828,6 +844,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="default workload: skip the batched-launch summary")
     ap.add_argument("--no-pow2", action="store_true", help="default workload: skip the power-of-two-sizes row")
     ap.add_argument("--no-serving", action="store_true", help="default workload: skip the serving summary")
+    ap.add_argument("--no-complex", action="store_true", help="default workload: skip the complex-types row")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--target", type=int, default=1 << 26, help="elements per tensor of the sweep")
     ap.add_argument("--only", default="", help="comma-separated case tags of the sweep (e.g. N5p3)")
@@ -870,6 +887,14 @@ def main():
                 r = run_ours(pw, rank, world)
                 out["pow2"] = {"workload": r["config"]["workload"], "GB/s": r["value"], "cases": r["cases"],
                                "per_variant": r["per_variant"], "timing": "CUDA events"}
+            if not args.no_complex:
+                # the paper's complex types (a separate row)
+                cx = copy.copy(sub)
+                cx.workload, cx.no_e2e, cx.cases_out, cx.only = "complex", True, "", ""
+                r = run_ours(cx, rank, world)
+                out["complex"] = {"workload": r["config"]["workload"], "GB/s": r["value"], "cases": r["cases"],
+                                  "per_variant": r["per_variant"], "roofline_frac": r["roofline"]["frac"],
+                                  "timing": "CUDA events"}
             if not args.no_batch:
                 b = run_batch(sub, rank, world)
                 out["batch"] = {"workload": b["config"]["workload"], "GB/s": b["value"],

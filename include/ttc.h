@@ -32,6 +32,20 @@
  *    fl32(amax/448), amax = max |fl32(alpha*a)| over the sub-tensor (NaN
  *    ignored; scale = 1 if amax is 0, infinite, or amax/448 underflows).  Only
  *    beta == 0 is supported with FP8 output.
+ *  - Complex types (section 2.1 --dataType=c,z,cz,zc; reading for the
+ *    arithmetic, which the paper does not spell out): alpha and beta are
+ *    complex (ttc_plan_complex; ttc_plan gives them zero imaginary parts).
+ *    The compute type is double-complex when A or B is double-complex, else
+ *    single-complex; each part of alpha and beta is rounded once to it.  With
+ *    alpha = (ar, ai), beta = (br, bi), a = (x, y), b = (u, v), each element
+ *    evaluates, in this order,
+ *        re = fl(ar*x), im = fl(ar*y);
+ *        if ai != 0: re = fma(-ai, y, re), im = fma(ai, x, im);
+ *        if beta != 0: re = fma(br, u, re), im = fma(br, v, im);
+ *                      if bi != 0: re = fma(-bi, v, re), im = fma(bi, u, im);
+ *    and rounds each part once (round-to-nearest-even) to B's type.  With real
+ *    scalars each part is therefore updated exactly as a real tensor of the
+ *    part's type would be.  alpha = 1, beta = 0 with equal types is a bit copy.
  *
  * Streams: every call that takes a ttc_stream_t enqueues work on that CUDA
  * stream (a cudaStream_t; NULL = the legacy default stream) and returns
@@ -59,7 +73,9 @@ typedef enum {
     TTC_F32 = 0,       /* IEEE binary32 ("s" in the paper's --dataType) */
     TTC_F64 = 1,       /* IEEE binary64 ("d") */
     TTC_BF16 = 2,      /* bfloat16 (output of a fused downcast, or input) */
-    TTC_FP8_E4M3 = 3   /* OCP FP8 E4M3 (output only, with a per-tensor scale) */
+    TTC_FP8_E4M3 = 3,  /* OCP FP8 E4M3 (output only, with a per-tensor scale) */
+    TTC_C64 = 4,       /* single-complex ("c"): (real, imaginary) binary32 pair, 8 bytes */
+    TTC_C128 = 5       /* double-complex ("z"): (real, imaginary) binary64 pair, 16 bytes */
 } ttc_dtype;
 
 typedef enum {
@@ -97,8 +113,10 @@ typedef struct ttc_plan_s* ttc_plan_t;
  *  outer_sizes_A  NULL or ndim outer extents of A (in A's index order).
  *  outer_sizes_B  NULL or ndim outer extents of B (in B's index order).
  *  dtype_in/out   types of A and B.  Supported pairs: f32->{f32,f64,bf16,e4m3},
- *                 f64->{f64,f32}, bf16->{bf16,f32,e4m3}.
- *  alpha, beta    the scalars of Eq. 1 (rounded once to the compute type).
+ *                 f64->{f64,f32}, bf16->{bf16,f32,e4m3}, c64->{c64,c128},
+ *                 c128->{c128,c64}.
+ *  alpha, beta    the scalars of Eq. 1 (rounded once to the compute type;
+ *                 real: for complex types their imaginary parts are 0).
  *
  * Host-only: no CUDA call is made; device resources are created on the first
  * execution on each device.  Thread-safe.
@@ -106,6 +124,18 @@ typedef struct ttc_plan_s* ttc_plan_t;
 ttc_status ttc_plan(ttc_plan_t* out, int ndim, const int* perm, const int64_t* sizes,
                     const int64_t* outer_sizes_A, const int64_t* outer_sizes_B,
                     ttc_dtype dtype_in, ttc_dtype dtype_out, double alpha, double beta);
+
+/*
+ * ttc_plan_complex -- ttc_plan with complex scalars alpha = alpha_re + i
+ * alpha_im and beta = beta_re + i beta_im (evaluated as in the conventions
+ * above).  Nonzero imaginary parts need complex tensors
+ * (TTC_ERR_UNSUPPORTED_DTYPE otherwise); any part not finite gives
+ * TTC_ERR_INVALID_ARG.  beta != 0 means either part is nonzero.
+ */
+ttc_status ttc_plan_complex(ttc_plan_t* out, int ndim, const int* perm, const int64_t* sizes,
+                            const int64_t* outer_sizes_A, const int64_t* outer_sizes_B,
+                            ttc_dtype dtype_in, ttc_dtype dtype_out, double alpha_re, double alpha_im,
+                            double beta_re, double beta_im);
 
 /*
  * ttc_execute -- run the plan: B <- alpha*A + beta*B under the permutation
@@ -215,7 +245,8 @@ int64_t ttc_launch_count(void);
  *                     unchanged while the batch is used; A and B are device
  *                     pointers as for ttc_execute (checked the same way).
  *                     FP8 plans are rejected (TTC_ERR_UNSUPPORTED_DTYPE): their
- *                     scale needs a pre-pass of its own.
+ *                     scale needs a pre-pass of its own; so are complex plans
+ *                     (the persistent kernel's epilogue covers the real pairs).
  *  ttc_batch_execute  enqueue the batch on `stream`: one counter reset and one
  *                     persistent kernel for the problems below the direct
  *                     threshold, and beside it, on a stream of the batch
@@ -253,7 +284,8 @@ ttc_status ttc_batch_set_direct_threshold(ttc_batch_t batch, int64_t min_element
  * sub-tensor spans) stay within `budget_bytes`, groups what it admitted into
  * an epoch and launches it on a stream: consecutive requests of at most
  * `small_tiles` tiles go together into one batched persistent launch (see
- * ttc_batch_*), other requests get their own launch.  Epochs on different
+ * ttc_batch_*), other requests (and every FP8 or complex request) get their
+ * own launch.  Epochs on different
  * streams run concurrently, so requests that arrive while others are on the
  * GPU start as soon as budget and a stream allow.  Requests fall into three
  * size classes (batchable; up to 64 MB of algorithmic bytes; larger), each

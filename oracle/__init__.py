@@ -22,9 +22,10 @@ _SRC = os.path.join(_HERE, "ttc_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 # The oracle's own dtype numbering (independent of the product's enum).
-F32, F64, BF16, E4M3 = 0, 1, 2, 3
-NP_DTYPE = {F32: np.float32, F64: np.float64, BF16: np.uint16, E4M3: np.uint8}
-NAMES = {"f32": F32, "f64": F64, "bf16": BF16, "e4m3": E4M3}
+F32, F64, BF16, E4M3, C64, C128 = 0, 1, 2, 3, 4, 5
+NP_DTYPE = {F32: np.float32, F64: np.float64, BF16: np.uint16, E4M3: np.uint8, C64: np.complex64,
+            C128: np.complex128}
+NAMES = {"f32": F32, "f64": F64, "bf16": BF16, "e4m3": E4M3, "c64": C64, "c128": C128}
 
 
 def build(force: bool = False) -> str:
@@ -59,6 +60,12 @@ def lib():
         L.oracle_fp8_scale.argtypes = [ctypes.c_int, i64p, i64p, ctypes.c_int, ctypes.c_double, vp,
                                        ctypes.POINTER(ctypes.c_float)]
         L.oracle_fp8_scale.restype = ctypes.c_float
+        L.oracle_permute_complex.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64p, i64p, i64p,
+                                             ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [vp, vp]
+        L.oracle_permute_complex.restype = ctypes.c_int
+        L.oracle_permute_complex_exact.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64p, i64p, i64p,
+                                                   ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [vp] * 4
+        L.oracle_permute_complex_exact.restype = ctypes.c_int
         for name in ("oracle_bf16_from_f32_n", "oracle_e4m3_from_f32_n", "oracle_e4m3_to_f32_n"):
             getattr(L, name).argtypes = [vp, vp, ctypes.c_int64]
             getattr(L, name).restype = None
@@ -133,6 +140,39 @@ def permute_exact(perm, sizes, A, B, alpha=1.0, beta=0.0, dtA=F32, dtB=F32, oute
     if rc:
         raise ValueError(f"oracle_permute_exact rejected the problem (code {rc})")
     return R, S
+
+
+def permute_complex(perm, sizes, A, B, alpha=1.0, beta=0.0, dtA=C64, dtB=C64, outerA=None, outerB=None):
+    """Complex B <- alpha*A + beta*B under perm (in place on the numpy buffer
+    B); alpha and beta may be complex."""
+    n, oA, sB, oB = dims(perm, sizes, outerA, outerB)
+    _check_buf(A, dtA, sizes, oA, "A")
+    _check_buf(B, dtB, sB, oB, "B")
+    a, b = complex(alpha), complex(beta)
+    rc = lib().oracle_permute_complex(n, (ctypes.c_int * n)(*perm), _i64(sizes), _i64(outerA), _i64(outerB),
+                                      dtA, dtB, a.real, a.imag, b.real, b.imag, _ptr(A), _ptr(B))
+    if rc:
+        raise ValueError(f"oracle_permute_complex rejected the problem (code {rc})")
+    return B
+
+
+def permute_complex_exact(perm, sizes, A, B, alpha=1.0, beta=0.0, dtA=C64, dtB=C64, outerA=None, outerB=None):
+    """Exact complex value (each part rounded once to double) as a complex128
+    array in B's layout, and the tolerance scale of each part as an (n, 2)
+    float64 array (NaN where B has no element)."""
+    n, oA, sB, oB = dims(perm, sizes, outerA, outerB)
+    _check_buf(A, dtA, sizes, oA, "A")
+    _check_buf(B, dtB, sB, oB, "B")
+    vol = B.size
+    R = np.full(2 * vol, np.nan)
+    S = np.full(2 * vol, np.nan)
+    a, b = complex(alpha), complex(beta)
+    rc = lib().oracle_permute_complex_exact(n, (ctypes.c_int * n)(*perm), _i64(sizes), _i64(outerA),
+                                            _i64(outerB), dtA, dtB, a.real, a.imag, b.real, b.imag, _ptr(A),
+                                            _ptr(B), _ptr(R), _ptr(S))
+    if rc:
+        raise ValueError(f"oracle_permute_complex_exact rejected the problem (code {rc})")
+    return R.view(np.complex128), S.reshape(vol, 2)
 
 
 def fp8_scale(sizes, A, alpha=1.0, dtA=F32, outerA=None):

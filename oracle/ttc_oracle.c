@@ -36,6 +36,18 @@
  *    q = RNE_satfinite(fl32(fl32(alpha*a) / scale)), with scale either given
  *    or scale = fl32(amax / 448), amax = max over non-NaN |fl32(alpha*a)|,
  *    and scale = 1 when amax is 0 or not finite or amax/448 underflows to 0.
+ *  - Complex types (section 2.1: single-complex "c", double-complex "z", and
+ *    the mixed cz / zc): an element is a (real, imaginary) pair; alpha and
+ *    beta are complex.  Compute type: double-complex when A or B is
+ *    double-complex, else single-complex; each part of alpha and beta is
+ *    rounded once to it.  With alpha = (ar, ai), beta = (br, bi), a = (x, y),
+ *    b = (u, v), the parts are evaluated in this order:
+ *        re = fl(ar*x), im = fl(ar*y)
+ *        if ai != 0:   re = fma(-ai, y, re), im = fma(ai, x, im)
+ *        if beta != 0: re = fma(br, u, re),  im = fma(br, v, im)
+ *                      if bi != 0: re = fma(-bi, v, re), im = fma(bi, u, im)
+ *    then each part is rounded once to B's part type.  Real scalars thus
+ *    update each part exactly as a real tensor of that type is updated.
  *
  * Build: plain C99, -O2 -ffp-contract=off (no fused operations other than the
  * explicit fma/fmaf calls), no fast-math.
@@ -45,8 +57,9 @@
 #include <stdlib.h>
 #include <string.h>
 
-/* dtype codes of the oracle (its own numbering) */
-enum { OR_F32 = 0, OR_F64 = 1, OR_BF16 = 2, OR_E4M3 = 3 };
+/* dtype codes of the oracle (its own numbering); C64 / C128 are the
+ * single- and double-complex types, stored as (real, imaginary) pairs */
+enum { OR_F32 = 0, OR_F64 = 1, OR_BF16 = 2, OR_E4M3 = 3, OR_C64 = 4, OR_C128 = 5 };
 
 #define OR_MAXDIM 32
 
@@ -56,6 +69,8 @@ static int elem_size(int dt) {
     case OR_F64: return 8;
     case OR_BF16: return 2;
     case OR_E4M3: return 1;
+    case OR_C64: return 8;
+    case OR_C128: return 16;
     }
     return 0;
 }
@@ -365,6 +380,170 @@ int oracle_permute_exact(int n, const int* perm, const int64_t* sizes, const int
         }
         R[offB] = r;
         S[offB] = s;
+    } while (odometer_next(n, i, sizes));
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Complex types                                                        */
+/* ------------------------------------------------------------------ */
+
+static int is_complex_pair(int dtA, int dtB) {
+    return (dtA == OR_C64 || dtA == OR_C128) && (dtB == OR_C64 || dtB == OR_C128);
+}
+
+/* the two parts of a complex element, widened exactly to double */
+static void load_complex(const void* base, int dt, int64_t off, double* re, double* im) {
+    if (dt == OR_C64) {
+        const float* q = (const float*)base + 2 * off;
+        *re = (double)q[0];
+        *im = (double)q[1];
+    } else {
+        const double* q = (const double*)base + 2 * off;
+        *re = q[0];
+        *im = q[1];
+    }
+}
+
+static void store_complex(void* base, int dt, int64_t off, double re, double im) {
+    if (dt == OR_C64) {
+        float* q = (float*)base + 2 * off;
+        q[0] = (float)re;                 /* one RN rounding per part */
+        q[1] = (float)im;
+    } else {
+        double* q = (double*)base + 2 * off;
+        q[0] = re;
+        q[1] = im;
+    }
+}
+
+/*
+ * oracle_permute_complex: B[Pi(i)] <- alpha*A[i] + beta*B[Pi(i)] for the
+ * complex pairs (c->c, z->z, c->z, z->c), alpha = ar + i ai and
+ * beta = br + i bi, following the rounding sequence of the reading in the
+ * header.  Returns 0, or a positive code for an invalid problem.
+ */
+int oracle_permute_complex(int n, const int* perm, const int64_t* sizes, const int64_t* outerA,
+                           const int64_t* outerB, int dtA, int dtB, double ar, double ai, double br,
+                           double bi, const void* A, void* B) {
+    int64_t oA[OR_MAXDIM], oB[OR_MAXDIM], sB[OR_MAXDIM];
+    int64_t i[OR_MAXDIM], j[OR_MAXDIM];
+    int rc = setup(n, perm, sizes, outerA, outerB, oA, oB, sB);
+    if (rc) return rc;
+    if (!is_complex_pair(dtA, dtB)) return 5;
+    if (volume(n, sizes) == 0) return 0;
+    const int bitcopy = (ar == 1.0 && ai == 0.0 && br == 0.0 && bi == 0.0 && dtA == dtB);
+    const int beta_nz = (br != 0.0 || bi != 0.0);
+    const int wide = (dtA == OR_C128 || dtB == OR_C128);
+    const float arf = (float)ar, aif = (float)ai, brf = (float)br, bif = (float)bi;
+    const int sa = elem_size(dtA);
+
+    memset(i, 0, sizeof(i));
+    do {
+        for (int d = 0; d < n; ++d) j[d] = i[perm[d]];
+        int64_t offA = colmajor_offset(n, i, oA);
+        int64_t offB = colmajor_offset(n, j, oB);
+        if (bitcopy) {
+            memcpy((char*)B + offB * sa, (const char*)A + offA * sa, (size_t)sa);
+            continue;
+        }
+        double x, y, u = 0.0, v = 0.0;
+        load_complex(A, dtA, offA, &x, &y);
+        if (beta_nz) load_complex(B, dtB, offB, &u, &v);
+        if (wide) {
+            double re = ar * x, im = ar * y;
+            if (ai != 0.0) {
+                re = fma(-ai, y, re);
+                im = fma(ai, x, im);
+            }
+            if (beta_nz) {
+                re = fma(br, u, re);
+                im = fma(br, v, im);
+                if (bi != 0.0) {
+                    re = fma(-bi, v, re);
+                    im = fma(bi, u, im);
+                }
+            }
+            store_complex(B, dtB, offB, re, im);
+        } else {
+            /* single-complex data: x, y, u, v hold floats exactly */
+            const float xf = (float)x, yf = (float)y, uf = (float)u, vf = (float)v;
+            float re = arf * xf, im = arf * yf;
+            if (aif != 0.0f) {
+                re = fmaf(-aif, yf, re);
+                im = fmaf(aif, xf, im);
+            }
+            if (beta_nz) {
+                re = fmaf(brf, uf, re);
+                im = fmaf(brf, vf, im);
+                if (bif != 0.0f) {
+                    re = fmaf(-bif, vf, re);
+                    im = fmaf(bif, uf, im);
+                }
+            }
+            store_complex(B, dtB, offB, (double)re, (double)im);
+        }
+    } while (odometer_next(n, i, sizes));
+    return 0;
+}
+
+/* sum of k products x[t]*y[t], evaluated as if in twice double precision
+ * (Ogita, Rump, Oishi 2005, Algorithm Dot2: TwoProduct of every term, the
+ * running sum by TwoSum, the error terms added at the end). */
+static double dot2(int k, const double* x, const double* y) {
+    double p, s, h, r, q;
+    two_prod(x[0], y[0], &p, &s);
+    for (int t = 1; t < k; ++t) {
+        two_prod(x[t], y[t], &h, &r);
+        two_sum(p, h, &p, &q);
+        s += q + r;
+    }
+    return p + s;
+}
+
+/*
+ * oracle_permute_complex_exact: the exact value of alpha_c*a + beta_c*b by
+ * the definition of the complex product, (ar + i ai)(x + i y) =
+ * (ar x - ai y) + i (ar y + ai x), with alpha_c, beta_c the scalars rounded
+ * part by part to the compute type; each part evaluated by Dot2 and rounded
+ * to double.  R receives (re, im) and S the tolerance scale of each part (the
+ * sum of the absolute values of its products), two doubles per element in
+ * B's layout.  B is read only when beta != 0.
+ */
+int oracle_permute_complex_exact(int n, const int* perm, const int64_t* sizes, const int64_t* outerA,
+                                 const int64_t* outerB, int dtA, int dtB, double ar, double ai, double br,
+                                 double bi, const void* A, const void* B, double* R, double* S) {
+    int64_t oA[OR_MAXDIM], oB[OR_MAXDIM], sB[OR_MAXDIM];
+    int64_t i[OR_MAXDIM], j[OR_MAXDIM];
+    int rc = setup(n, perm, sizes, outerA, outerB, oA, oB, sB);
+    if (rc) return rc;
+    if (!is_complex_pair(dtA, dtB)) return 5;
+    if (volume(n, sizes) == 0) return 0;
+    const int wide = (dtA == OR_C128 || dtB == OR_C128);
+    const int beta_nz = (br != 0.0 || bi != 0.0);
+    const double arc = wide ? ar : (double)(float)ar, aic = wide ? ai : (double)(float)ai;
+    const double brc = wide ? br : (double)(float)br, bic = wide ? bi : (double)(float)bi;
+
+    memset(i, 0, sizeof(i));
+    do {
+        for (int d = 0; d < n; ++d) j[d] = i[perm[d]];
+        int64_t offA = colmajor_offset(n, i, oA);
+        int64_t offB = colmajor_offset(n, j, oB);
+        double x, y, u = 0.0, v = 0.0;
+        load_complex(A, dtA, offA, &x, &y);
+        if (beta_nz) load_complex(B, dtB, offB, &u, &v);
+        const int k = beta_nz ? 4 : 2;
+        const double cre[4] = {arc, -aic, brc, -bic}, vre[4] = {x, y, u, v};
+        const double cim[4] = {arc, aic, brc, bic}, vim[4] = {y, x, v, u};
+        double sre = 0.0, sim = 0.0;
+        for (int t = 0; t < k; ++t) {
+            sre += fabs(cre[t] * vre[t]);
+            sim += fabs(cim[t] * vim[t]);
+        }
+        R[2 * offB] = dot2(k, cre, vre);
+        R[2 * offB + 1] = dot2(k, cim, vim);
+        S[2 * offB] = sre;
+        S[2 * offB + 1] = sim;
     } while (odometer_next(n, i, sizes));
     return 0;
 }

@@ -240,7 +240,7 @@ namespace {
 
 std::shared_ptr<const BatchTemplate> make_template(const ttc_plan_s* p) {
   auto t = std::make_shared<BatchTemplate>();
-  if (p->canon.n == 0 || p->dout == DT_E4M3) return t;
+  if (p->canon.n == 0 || p->dout == DT_E4M3 || is_complex(p->din)) return t;
   BatchDesc* d = &t->d;
   std::memset(d, 0, sizeof(*d));
   d->din = p->din;
@@ -393,7 +393,10 @@ struct ttc_batch_s {
 
 namespace {
 
-bool batch_pair_supported(int din, int dout) { return pair_supported(din, dout) && dout != DT_E4M3; }
+// the batch body's runtime epilogue covers the real non-FP8 pairs only
+bool batch_pair_supported(int din, int dout) {
+  return pair_supported(din, dout) && dout != DT_E4M3 && !is_complex(din);
+}
 
 // Build the descriptors of every problem and upload them (synchronous).
 ttc_status batch_build(ttc_batch_s* b) {
@@ -525,7 +528,7 @@ ttc_status ttc_batch_create(ttc_batch_t* out) {
 ttc_status ttc_batch_add(ttc_batch_t b, ttc_plan_t plan, const void* A, void* B) {
   if (!b || !plan) return fail(TTC_ERR_INVALID_ARG, "NULL batch or plan");
   if (!batch_pair_supported(plan->din, plan->dout))
-    return fail(TTC_ERR_UNSUPPORTED_DTYPE, "FP8 output is not supported in a batch");
+    return fail(TTC_ERR_UNSUPPORTED_DTYPE, "FP8 output and complex types are not supported in a batch");
   if (plan->canon.n > 0) {
     if (!A || !B) return fail(TTC_ERR_INVALID_ARG, "A or B is NULL");
     const uintptr_t a = reinterpret_cast<uintptr_t>(A), bb = reinterpret_cast<uintptr_t>(B);

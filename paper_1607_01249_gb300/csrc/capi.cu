@@ -63,7 +63,7 @@ std::string cand_key(const Candidate& c) {
 
 std::string plan_key(const ttc_plan_s* p, int dev) {
   std::ostringstream o;
-  o << device_name(dev) << ":" << p->din << ">" << p->dout << ":b" << (p->beta != 0) << ":N" << p->canon.N;
+  o << device_name(dev) << ":" << p->din << ">" << p->dout << ":b" << p->beta_nonzero() << ":N" << p->canon.N;
   for (int k = 0; k < p->canon.N; ++k)
     o << ":" << p->canon.s[k] << "/" << p->canon.sa[k] << "/" << p->canon.sb[k] << "/" << p->canon.perm[k];
   return o.str();
@@ -147,14 +147,17 @@ ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out) {
 
 Epilogue make_epilogue(const ttc_plan_s* p, const DevRes* r) {
   Epilogue e;
-  e.mode = (p->dout == DT_E4M3) ? MODE_FP8
-           : (p->alpha == 1.0 && p->beta == 0.0 && p->din == p->dout) ? MODE_BITCOPY
-                                                                        : MODE_AXPBY;
-  e.beta_nz = p->beta != 0.0;
+  const bool unit = p->alpha == 1.0 && p->alpha_im == 0.0 && !p->beta_nonzero();
+  e.mode = (p->dout == DT_E4M3) ? MODE_FP8 : (unit && p->din == p->dout) ? MODE_BITCOPY : MODE_AXPBY;
+  e.beta_nz = p->beta_nonzero();
   e.alpha_f = float(p->alpha);
   e.beta_f = float(p->beta);
   e.alpha_d = p->alpha;
   e.beta_d = p->beta;
+  e.alpha_fi = float(p->alpha_im);
+  e.beta_fi = float(p->beta_im);
+  e.alpha_di = p->alpha_im;
+  e.beta_di = p->beta_im;
   e.scale_in = p->user_scale;
   e.amax_bits = r ? r->amax : nullptr;
   e.scale_out = r ? r->scale : nullptr;
@@ -235,17 +238,24 @@ const char* ttc_last_error(void) { return ttc::g_last_error.c_str(); }
 
 int64_t ttc_launch_count(void) { return ttc::launch_count(); }
 
-ttc_status ttc_plan(ttc_plan_t* out, int ndim, const int* perm, const int64_t* sizes,
-                    const int64_t* outer_sizes_A, const int64_t* outer_sizes_B, ttc_dtype dtype_in,
-                    ttc_dtype dtype_out, double alpha, double beta) {
+}  // extern "C"
+
+namespace {
+
+ttc_status plan_create(ttc_plan_t* out, int ndim, const int* perm, const int64_t* sizes,
+                       const int64_t* outer_sizes_A, const int64_t* outer_sizes_B, ttc_dtype dtype_in,
+                       ttc_dtype dtype_out, double alpha, double alpha_im, double beta, double beta_im) {
   if (!out) return fail(TTC_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   const int din = int(dtype_in), dout = int(dtype_out);
-  if (din < 0 || din > 3 || dout < 0 || dout > 3 || !pair_supported(din, dout))
+  if (din < 0 || din >= kNumDTypes || dout < 0 || dout >= kNumDTypes || !pair_supported(din, dout))
     return fail(TTC_ERR_UNSUPPORTED_DTYPE, "unsupported dtype pair");
   if (dout == DT_E4M3 && beta != 0.0)
     return fail(TTC_ERR_UNSUPPORTED_DTYPE, "FP8 output supports beta == 0 only");
-  if (!std::isfinite(alpha) || !std::isfinite(beta)) return fail(TTC_ERR_INVALID_ARG, "alpha/beta not finite");
+  if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(alpha_im) || !std::isfinite(beta_im))
+    return fail(TTC_ERR_INVALID_ARG, "alpha/beta not finite");
+  if (!is_complex(din) && (alpha_im != 0.0 || beta_im != 0.0))
+    return fail(TTC_ERR_UNSUPPORTED_DTYPE, "complex alpha/beta need complex tensors");
   std::unique_ptr<ttc_plan_s> p(new (std::nothrow) ttc_plan_s());
   if (!p) return fail(TTC_ERR_OOM, "host allocation failed");
   std::string err;
@@ -262,7 +272,9 @@ ttc_status ttc_plan(ttc_plan_t* out, int ndim, const int* perm, const int64_t* s
   p->dout = dout;
   p->alpha = alpha;
   p->beta = beta;
-  p->cands = make_candidates(p->canon, din, dout, beta, 12);
+  p->alpha_im = alpha_im;
+  p->beta_im = beta_im;
+  p->cands = make_candidates(p->canon, din, dout, p->beta_nonzero() ? 1.0 : 0.0, 12);
   if (p->cands.empty()) return fail(TTC_ERR_INVALID_SIZE, "no schedule fits this problem");
   if (p->canon.n > 0) {
     build_row_params(p->canon, p->canon.s[0] <= 16384 ? p->canon.s[0] : 8192, &p->amax_rows);
@@ -271,6 +283,25 @@ ttc_status ttc_plan(ttc_plan_t* out, int ndim, const int* perm, const int64_t* s
   }
   *out = p.release();
   return TTC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ttc_status ttc_plan(ttc_plan_t* out, int ndim, const int* perm, const int64_t* sizes,
+                    const int64_t* outer_sizes_A, const int64_t* outer_sizes_B, ttc_dtype dtype_in,
+                    ttc_dtype dtype_out, double alpha, double beta) {
+  return plan_create(out, ndim, perm, sizes, outer_sizes_A, outer_sizes_B, dtype_in, dtype_out, alpha, 0.0, beta,
+                     0.0);
+}
+
+ttc_status ttc_plan_complex(ttc_plan_t* out, int ndim, const int* perm, const int64_t* sizes,
+                            const int64_t* outer_sizes_A, const int64_t* outer_sizes_B, ttc_dtype dtype_in,
+                            ttc_dtype dtype_out, double alpha_re, double alpha_im, double beta_re,
+                            double beta_im) {
+  return plan_create(out, ndim, perm, sizes, outer_sizes_A, outer_sizes_B, dtype_in, dtype_out, alpha_re,
+                     alpha_im, beta_re, beta_im);
 }
 
 ttc_status ttc_plan_destroy(ttc_plan_t plan) {
@@ -335,7 +366,7 @@ ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info) {
   }
   info->n = c.n;
   const int sa = dtype_size(plan->din), sb = dtype_size(plan->dout);
-  info->algorithmic_bytes = c.n * (sa + (plan->beta != 0.0 ? 2 * sb : sb));
+  info->algorithmic_bytes = c.n * (sa + (plan->beta_nonzero() ? 2 * sb : sb));
   const Candidate& k = plan->cands[plan->sel];
   info->variant = k.rows ? TTC_VARIANT_ROWCOPY : k.variant;
   info->candidate = plan->sel;

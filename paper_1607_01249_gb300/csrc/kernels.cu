@@ -69,62 +69,29 @@ cudaError_t grid_for(const void* fn, int smem, int64_t work, int* grid) {
 }
 
 
-cudaError_t launch_tile_f32_f32(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile_slots_f32_f32(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile2_f32_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_copy_f32_f32(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_rowcopy_f32_f32(const void*, void*, const TileParams&, cudaStream_t);
-cudaError_t launch_tile_f32_f64(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile_slots_f32_f64(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile2_f32_f64(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_copy_f32_f64(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_rowcopy_f32_f64(const void*, void*, const TileParams&, cudaStream_t);
-cudaError_t launch_tile_f32_bf16(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile_slots_f32_bf16(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile2_f32_bf16(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_copy_f32_bf16(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_rowcopy_f32_bf16(const void*, void*, const TileParams&, cudaStream_t);
-cudaError_t launch_tile_f32_e4m3(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile_slots_f32_e4m3(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile2_f32_e4m3(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_copy_f32_e4m3(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_rowcopy_f32_e4m3(const void*, void*, const TileParams&, cudaStream_t);
-cudaError_t launch_tile_f64_f64(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile_slots_f64_f64(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile2_f64_f64(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_copy_f64_f64(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_rowcopy_f64_f64(const void*, void*, const TileParams&, cudaStream_t);
-cudaError_t launch_tile_f64_f32(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile_slots_f64_f32(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile2_f64_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_copy_f64_f32(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_rowcopy_f64_f32(const void*, void*, const TileParams&, cudaStream_t);
-cudaError_t launch_tile_bf16_bf16(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile_slots_bf16_bf16(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile2_bf16_bf16(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_copy_bf16_bf16(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_rowcopy_bf16_bf16(const void*, void*, const TileParams&, cudaStream_t);
-cudaError_t launch_tile_bf16_f32(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile_slots_bf16_f32(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile2_bf16_f32(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_copy_bf16_f32(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_rowcopy_bf16_f32(const void*, void*, const TileParams&, cudaStream_t);
-cudaError_t launch_tile_bf16_e4m3(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile_slots_bf16_e4m3(const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_tile2_bf16_e4m3(int, int, const void*, void*, const TileParams&, int, cudaStream_t);
-cudaError_t launch_copy_bf16_e4m3(int, const void*, void*, const RowParams&, cudaStream_t);
-cudaError_t launch_rowcopy_bf16_e4m3(const void*, void*, const TileParams&, cudaStream_t);
+// The dtype pairs with kernels (one kern_<in>_<out>.cu each): the paper's
+// s, d, sd, ds, c, z, cz, zc (section 2.1) plus the BF16 and FP8 downcasts.
+#define TTC_PAIRS(X)                                                                                      \
+  X(DT_F32, DT_F32, f32_f32) X(DT_F32, DT_F64, f32_f64) X(DT_F32, DT_BF16, f32_bf16)                     \
+  X(DT_F32, DT_E4M3, f32_e4m3) X(DT_F64, DT_F64, f64_f64) X(DT_F64, DT_F32, f64_f32)                     \
+  X(DT_BF16, DT_BF16, bf16_bf16) X(DT_BF16, DT_F32, bf16_f32) X(DT_BF16, DT_E4M3, bf16_e4m3)             \
+  X(DT_C64, DT_C64, c64_c64) X(DT_C128, DT_C128, c128_c128) X(DT_C64, DT_C128, c64_c128)                 \
+  X(DT_C128, DT_C64, c128_c64)
+
+#define TTC_DECLARE(I, O, P)                                                                              \
+  cudaError_t launch_tile_##P(const void*, void*, const TileParams&, int, cudaStream_t);                  \
+  cudaError_t launch_tile_slots_##P(const void*, void*, const TileParams&, int, cudaStream_t);            \
+  cudaError_t launch_tile2_##P(int, int, const void*, void*, const TileParams&, int, cudaStream_t);       \
+  cudaError_t launch_copy_##P(int, const void*, void*, const RowParams&, cudaStream_t);                   \
+  cudaError_t launch_rowcopy_##P(const void*, void*, const TileParams&, cudaStream_t);
+TTC_PAIRS(TTC_DECLARE)
+#undef TTC_DECLARE
 
 bool pair_supported(int din, int dout) {
-  if (din == DT_F32 && dout == DT_F32) return true;
-  if (din == DT_F32 && dout == DT_F64) return true;
-  if (din == DT_F32 && dout == DT_BF16) return true;
-  if (din == DT_F32 && dout == DT_E4M3) return true;
-  if (din == DT_F64 && dout == DT_F64) return true;
-  if (din == DT_F64 && dout == DT_F32) return true;
-  if (din == DT_BF16 && dout == DT_BF16) return true;
-  if (din == DT_BF16 && dout == DT_F32) return true;
-  if (din == DT_BF16 && dout == DT_E4M3) return true;
+#define TTC_IS(I, O, P) \
+  if (din == I && dout == O) return true;
+  TTC_PAIRS(TTC_IS)
+#undef TTC_IS
   return false;
 }
 
@@ -137,70 +104,45 @@ int copy_vec_width(int din, int dout) {
 
 cudaError_t launch_tile_slots(int din, int dout, const void* A, void* B, const TileParams& p, int smem,
                               cudaStream_t s) {
-  if (din == DT_F32 && dout == DT_F32) return launch_tile_slots_f32_f32(A, B, p, smem, s);
-  if (din == DT_F32 && dout == DT_F64) return launch_tile_slots_f32_f64(A, B, p, smem, s);
-  if (din == DT_F32 && dout == DT_BF16) return launch_tile_slots_f32_bf16(A, B, p, smem, s);
-  if (din == DT_F32 && dout == DT_E4M3) return launch_tile_slots_f32_e4m3(A, B, p, smem, s);
-  if (din == DT_F64 && dout == DT_F64) return launch_tile_slots_f64_f64(A, B, p, smem, s);
-  if (din == DT_F64 && dout == DT_F32) return launch_tile_slots_f64_f32(A, B, p, smem, s);
-  if (din == DT_BF16 && dout == DT_BF16) return launch_tile_slots_bf16_bf16(A, B, p, smem, s);
-  if (din == DT_BF16 && dout == DT_F32) return launch_tile_slots_bf16_f32(A, B, p, smem, s);
-  if (din == DT_BF16 && dout == DT_E4M3) return launch_tile_slots_bf16_e4m3(A, B, p, smem, s);
+#define TTC_GO(I, O, P) \
+  if (din == I && dout == O) return launch_tile_slots_##P(A, B, p, smem, s);
+  TTC_PAIRS(TTC_GO)
+#undef TTC_GO
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tile(int din, int dout, const void* A, void* B, const TileParams& p, int smem,
                         cudaStream_t s) {
-  if (din == DT_F32 && dout == DT_F32) return launch_tile_f32_f32(A, B, p, smem, s);
-  if (din == DT_F32 && dout == DT_F64) return launch_tile_f32_f64(A, B, p, smem, s);
-  if (din == DT_F32 && dout == DT_BF16) return launch_tile_f32_bf16(A, B, p, smem, s);
-  if (din == DT_F32 && dout == DT_E4M3) return launch_tile_f32_e4m3(A, B, p, smem, s);
-  if (din == DT_F64 && dout == DT_F64) return launch_tile_f64_f64(A, B, p, smem, s);
-  if (din == DT_F64 && dout == DT_F32) return launch_tile_f64_f32(A, B, p, smem, s);
-  if (din == DT_BF16 && dout == DT_BF16) return launch_tile_bf16_bf16(A, B, p, smem, s);
-  if (din == DT_BF16 && dout == DT_F32) return launch_tile_bf16_f32(A, B, p, smem, s);
-  if (din == DT_BF16 && dout == DT_E4M3) return launch_tile_bf16_e4m3(A, B, p, smem, s);
+#define TTC_GO(I, O, P) \
+  if (din == I && dout == O) return launch_tile_##P(A, B, p, smem, s);
+  TTC_PAIRS(TTC_GO)
+#undef TTC_GO
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tile2(int din, int dout, int ju, int jw, const void* A, void* B, const TileParams& p,
                          int smem, cudaStream_t s) {
-  if (din == DT_F32 && dout == DT_F32) return launch_tile2_f32_f32(ju, jw, A, B, p, smem, s);
-  if (din == DT_F32 && dout == DT_F64) return launch_tile2_f32_f64(ju, jw, A, B, p, smem, s);
-  if (din == DT_F32 && dout == DT_BF16) return launch_tile2_f32_bf16(ju, jw, A, B, p, smem, s);
-  if (din == DT_F32 && dout == DT_E4M3) return launch_tile2_f32_e4m3(ju, jw, A, B, p, smem, s);
-  if (din == DT_F64 && dout == DT_F64) return launch_tile2_f64_f64(ju, jw, A, B, p, smem, s);
-  if (din == DT_F64 && dout == DT_F32) return launch_tile2_f64_f32(ju, jw, A, B, p, smem, s);
-  if (din == DT_BF16 && dout == DT_BF16) return launch_tile2_bf16_bf16(ju, jw, A, B, p, smem, s);
-  if (din == DT_BF16 && dout == DT_F32) return launch_tile2_bf16_f32(ju, jw, A, B, p, smem, s);
-  if (din == DT_BF16 && dout == DT_E4M3) return launch_tile2_bf16_e4m3(ju, jw, A, B, p, smem, s);
+#define TTC_GO(I, O, P) \
+  if (din == I && dout == O) return launch_tile2_##P(ju, jw, A, B, p, smem, s);
+  TTC_PAIRS(TTC_GO)
+#undef TTC_GO
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_copy(int din, int dout, int vec, const void* A, void* B, const RowParams& p,
                         cudaStream_t s) {
-  if (din == DT_F32 && dout == DT_F32) return launch_copy_f32_f32(vec, A, B, p, s);
-  if (din == DT_F32 && dout == DT_F64) return launch_copy_f32_f64(vec, A, B, p, s);
-  if (din == DT_F32 && dout == DT_BF16) return launch_copy_f32_bf16(vec, A, B, p, s);
-  if (din == DT_F32 && dout == DT_E4M3) return launch_copy_f32_e4m3(vec, A, B, p, s);
-  if (din == DT_F64 && dout == DT_F64) return launch_copy_f64_f64(vec, A, B, p, s);
-  if (din == DT_F64 && dout == DT_F32) return launch_copy_f64_f32(vec, A, B, p, s);
-  if (din == DT_BF16 && dout == DT_BF16) return launch_copy_bf16_bf16(vec, A, B, p, s);
-  if (din == DT_BF16 && dout == DT_F32) return launch_copy_bf16_f32(vec, A, B, p, s);
-  if (din == DT_BF16 && dout == DT_E4M3) return launch_copy_bf16_e4m3(vec, A, B, p, s);
+#define TTC_GO(I, O, P) \
+  if (din == I && dout == O) return launch_copy_##P(vec, A, B, p, s);
+  TTC_PAIRS(TTC_GO)
+#undef TTC_GO
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_rowcopy(int din, int dout, const void* A, void* B, const TileParams& p, cudaStream_t s) {
-  if (din == DT_F32 && dout == DT_F32) return launch_rowcopy_f32_f32(A, B, p, s);
-  if (din == DT_F32 && dout == DT_F64) return launch_rowcopy_f32_f64(A, B, p, s);
-  if (din == DT_F32 && dout == DT_BF16) return launch_rowcopy_f32_bf16(A, B, p, s);
-  if (din == DT_F32 && dout == DT_E4M3) return launch_rowcopy_f32_e4m3(A, B, p, s);
-  if (din == DT_F64 && dout == DT_F64) return launch_rowcopy_f64_f64(A, B, p, s);
-  if (din == DT_F64 && dout == DT_F32) return launch_rowcopy_f64_f32(A, B, p, s);
-  if (din == DT_BF16 && dout == DT_BF16) return launch_rowcopy_bf16_bf16(A, B, p, s);
-  if (din == DT_BF16 && dout == DT_F32) return launch_rowcopy_bf16_f32(A, B, p, s);
-  if (din == DT_BF16 && dout == DT_E4M3) return launch_rowcopy_bf16_e4m3(A, B, p, s);
+#define TTC_GO(I, O, P) \
+  if (din == I && dout == O) return launch_rowcopy_##P(A, B, p, s);
+  TTC_PAIRS(TTC_GO)
+#undef TTC_GO
   return cudaErrorInvalidValue;
 }
 

@@ -19,9 +19,13 @@ template <> struct Store<DT_F32> { using T = float; };
 template <> struct Store<DT_F64> { using T = double; };
 template <> struct Store<DT_BF16> { using T = uint16_t; };
 template <> struct Store<DT_E4M3> { using T = uint8_t; };
+template <> struct Store<DT_C64> { using T = float2; };     // (real, imaginary)
+template <> struct Store<DT_C128> { using T = double2; };
 
 template <int DT> struct Stage { using T = float; };
 template <> struct Stage<DT_F64> { using T = double; };
+template <> struct Stage<DT_C64> { using T = float2; };
+template <> struct Stage<DT_C128> { using T = double2; };
 
 template <int DT> using store_t = typename Store<DT>::T;
 template <int DT> using stage_t = typename Stage<DT>::T;
@@ -93,6 +97,52 @@ __device__ __forceinline__ store_t<DOUT> epilogue(stage_t<DIN> a, store_t<DOUT> 
 // r = alpha*a, EK_AXPBY r = fma(beta, b, alpha*a), EK_FP8 the scaled E4M3 code.
 enum EpiKind : int { EK_COPY = 0, EK_SCALE = 1, EK_AXPBY = 2, EK_FP8 = 3 };
 
+// Complex update (the paper's c, z, cz, zc types), in double-complex when
+// either side is double-complex, else in single-complex, with this fixed
+// sequence of roundings (ar, ai = alpha; br, bi = beta; (x, y) = a; (u, v) = b):
+//   re = fl(ar*x), im = fl(ar*y); if ai != 0: re = fma(-ai, y, re), im = fma(ai, x, im)
+//   EK_AXPBY: re = fma(br, u, re), im = fma(br, v, im);
+//             if bi != 0: re = fma(-bi, v, re), im = fma(bi, u, im)
+// then one rounding per part to B's type.  With real scalars the cross terms
+// are skipped, so each part is updated exactly as a real tensor would be.
+template <int DIN, int DOUT, int EK>
+__device__ __forceinline__ store_t<DOUT> epilogue_complex(stage_t<DIN> a, store_t<DOUT> b, const Epilogue& e) {
+  if constexpr (DIN == DT_C128 || DOUT == DT_C128) {
+    const double x = a.x, y = a.y;      // single-complex widens exactly
+    double re = __dmul_rn(e.alpha_d, x), im = __dmul_rn(e.alpha_d, y);
+    if (e.alpha_di != 0.0) {
+      re = __fma_rn(-e.alpha_di, y, re);
+      im = __fma_rn(e.alpha_di, x, im);
+    }
+    if constexpr (EK == EK_AXPBY) {
+      const double u = b.x, v = b.y;
+      re = __fma_rn(e.beta_d, u, re);
+      im = __fma_rn(e.beta_d, v, im);
+      if (e.beta_di != 0.0) {
+        re = __fma_rn(-e.beta_di, v, re);
+        im = __fma_rn(e.beta_di, u, im);
+      }
+    }
+    if constexpr (DOUT == DT_C128) return make_double2(re, im);
+    else return make_float2(__double2float_rn(re), __double2float_rn(im));
+  } else {
+    float re = __fmul_rn(e.alpha_f, a.x), im = __fmul_rn(e.alpha_f, a.y);
+    if (e.alpha_fi != 0.f) {
+      re = __fmaf_rn(-e.alpha_fi, a.y, re);
+      im = __fmaf_rn(e.alpha_fi, a.x, im);
+    }
+    if constexpr (EK == EK_AXPBY) {
+      re = __fmaf_rn(e.beta_f, b.x, re);
+      im = __fmaf_rn(e.beta_f, b.y, im);
+      if (e.beta_fi != 0.f) {
+        re = __fmaf_rn(-e.beta_fi, b.y, re);
+        im = __fmaf_rn(e.beta_fi, b.x, im);
+      }
+    }
+    return make_float2(re, im);
+  }
+}
+
 template <int DIN, int DOUT, int EK>
 __device__ __forceinline__ store_t<DOUT> epilogue_k(stage_t<DIN> a, store_t<DOUT> b, const Epilogue& e,
                                                     float scale) {
@@ -102,6 +152,8 @@ __device__ __forceinline__ store_t<DOUT> epilogue_k(stage_t<DIN> a, store_t<DOUT
   } else if constexpr (EK == EK_COPY) {
     if constexpr (DIN == DT_BF16 && DOUT == DT_BF16) return store_t<DOUT>(__float_as_uint(a) >> 16);
     else return a;
+  } else if constexpr (is_complex(DIN)) {
+    return epilogue_complex<DIN, DOUT, EK>(a, b, e);
   } else if constexpr (ComputeIsF64<DIN, DOUT>::value) {
     double r = __dmul_rn(e.alpha_d, double(a));
     if constexpr (EK == EK_AXPBY) r = __fma_rn(e.beta_d, double(b), r);

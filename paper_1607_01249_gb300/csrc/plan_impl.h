@@ -43,6 +43,8 @@ struct ttc_plan_s {
   int64_t sizes0[ttc::kMaxDim] = {}, outerA0[ttc::kMaxDim] = {}, outerB0[ttc::kMaxDim] = {};
   int din = 0, dout = 0;
   double alpha = 1.0, beta = 0.0;
+  double alpha_im = 0.0, beta_im = 0.0;   // imaginary parts (complex dtypes only)
+  bool beta_nonzero() const { return beta != 0.0 || beta_im != 0.0; }
   ttc::Canon canon;
   std::vector<ttc::Candidate> cands;
   int sel = 0;

@@ -212,11 +212,11 @@ std::vector<int> cut_options(int64_t s, int64_t cap) {
   return std::vector<int>(o.begin(), o.end());
 }
 
-int stage_bytes(int din) { return din == DT_F64 ? 8 : 4; }
+int stage_bytes(int din) { return stage_bytes_of(din); }
 
 // shared-memory pitch (elements) of one lb row; see ttc_internal.h
 int pick_pitch(int U, int LC, int LB, int din, int smem_cap) {
-  const int banks = din == DT_F64 ? 16 : 32;
+  const int banks = 128 / stage_bytes(din);      // 4-byte banks, counted in elements
   int P;
   if (LC <= 1) P = U | 1;
   else P = U + (((LC - U) % banks) + banks) % banks;
@@ -318,7 +318,7 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
   // ---- multi-row copy: perm keeps index 0 with short runs; G consecutive
   // indices of A's next index make one contiguous block of A per tile
   if (c.perm[0] == 0 && c.N >= 2 && c.sa[0] == 1 && c.sb[0] == 1 && c.sa[1] == c.s[0]) {
-    const int Kt = tile_k_for(din == DT_F64 ? 8 : 4);
+    const int Kt = tile_k_for(stage_bytes(din));
     const int64_t vcap = vmax > 0 ? std::min<int64_t>(vmax, int64_t(kThreads) * Kt) : int64_t(kThreads) * Kt;
     const int64_t cap = vcap / c.s[0];
     if (cap >= 2) {
@@ -360,7 +360,7 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
   const bool hc = c.perm[0] == 0;
   const int c0 = hc ? 1 : 0;
   const int64_t LC = hc ? c.s[0] : 1;
-  const int Kt = tile_k_for(din == DT_F64 ? 8 : 4);
+  const int Kt = tile_k_for(stage_bytes(din));
   const int Vmax = vmax > 0 ? std::min(vmax, kThreads * Kt) : kThreads * Kt;
   std::vector<Candidate> tiles;
   if (!(hc && c.N == 1) && LC * 2 <= Vmax) {
@@ -775,8 +775,10 @@ int build_slot_tables(const TileParams& p, int din, const std::vector<int32_t>& 
                       const std::vector<int32_t>& tabB, std::vector<int32_t>* out) {
   out->assign(slot_table_ints(din), 0);
   int elems = 0;
-  if (tile_k_for(stage_bytes(din)) == 16) slot_tables_k<16>(p, stage_bytes(din) / 4, tabA, tabB, out, &elems);
-  else slot_tables_k<8>(p, stage_bytes(din) / 4, tabA, tabB, out, &elems);
+  const int K = tile_k_for(stage_bytes(din));
+  if (K == 16) slot_tables_k<16>(p, stage_bytes(din) / 4, tabA, tabB, out, &elems);
+  else if (K == 8) slot_tables_k<8>(p, stage_bytes(din) / 4, tabA, tabB, out, &elems);
+  else slot_tables_k<4>(p, stage_bytes(din) / 4, tabA, tabB, out, &elems);
   return elems * stage_bytes(din);
 }
 

@@ -502,7 +502,7 @@ ttc_status ttc_server_submit(ttc_server_t S, ttc_plan_t plan, const void* A, voi
   r.B = B;
   const int sa = dtype_size(plan->din), sb = dtype_size(plan->dout);
   r.bytes = plan->canon.spanA * sa + plan->canon.spanB * sb;
-  r.alg_bytes = plan->canon.n * (sa + (plan->beta != 0.0 ? 2 * sb : sb));
+  r.alg_bytes = plan->canon.n * (sa + (plan->beta_nonzero() ? 2 * sb : sb));
   if (r.bytes > S->budget) return fail(TTC_ERR_BUDGET, "request larger than the server's memory budget");
   if (plan->canon.n > 0) {
     if (!A || !B) return fail(TTC_ERR_INVALID_ARG, "A or B is NULL");
@@ -512,7 +512,9 @@ ttc_status ttc_server_submit(ttc_server_t S, ttc_plan_t plan, const void* A, voi
       return fail(TTC_ERR_ALIAS, "the byte ranges of A and B overlap");
   }
   r.tiles = -1;
-  if (S->small_tiles > 0 && plan->dout != DT_E4M3 && plan->canon.n > 0) r.tiles = batch_tiles(plan);
+  // FP8 (grid-wide amax) and complex requests are never batched
+  if (S->small_tiles > 0 && plan->dout != DT_E4M3 && !is_complex(plan->din) && plan->canon.n > 0)
+    r.tiles = batch_tiles(plan);
   if (plan->canon.n > 0) {
     // the plan's device scratch and tables are set up here, on the caller's
     // thread, the first time the plan meets this device: done by the

@@ -113,8 +113,10 @@ struct Checker {
   }
 
   bool tile(const Candidate& k) {
-    if (p->din == DT_F64) return tile_k<tile_k_for(8)>(k);
-    return tile_k<tile_k_for(4)>(k);
+    const int K = tile_k_for(stage_bytes_of(p->din));
+    if (K == 4) return tile_k<4>(k);
+    if (K == 8) return tile_k<8>(k);
+    return tile_k<16>(k);
   }
 
   // the batch body's tiles (half the slots per thread)
@@ -134,7 +136,7 @@ struct Checker {
     std::vector<int32_t> slots;
     int sbytes = 0;
     if (k.slots) sbytes = build_slot_tables(tp, p->din, ta, tb, &slots);
-    const int ncap = k.slots ? sbytes / (p->din == DT_F64 ? 8 : 4) : tp.P * tp.LB;
+    const int ncap = k.slots ? sbytes / stage_bytes_of(p->din) : tp.P * tp.LB;
     if (k.slots && sbytes > 200 * 1024) return fail("shared memory over budget", sbytes, 0);
     std::vector<int64_t> posA(static_cast<size_t>(ncap));
     std::vector<uint8_t> used(static_cast<size_t>(ncap));
@@ -275,7 +277,7 @@ extern "C" ttc_status ttc_debug_verify_schedule(ttc_plan_t plan, int candidate, 
   bool batch = candidate == -1;
   if (batch) {
     // the schedule the batch body (ttc_batch_*, the server) runs for this plan
-    if (plan->dout == DT_E4M3) return TTC_OK;
+    if (plan->dout == DT_E4M3 || is_complex(plan->din)) return TTC_OK;    // never batched
     k = make_candidates(plan->canon, plan->din, plan->dout, plan->beta, 4,
                         kThreads * batch_k_for(plan->din == DT_F64 ? 8 : 4)).front();
     if (k.variant == VAR_COPY) k.chunk = kBatchCopyChunk / (plan->din == DT_F64 ? 2 : 1);

@@ -40,11 +40,19 @@ constexpr int kTileK = 16;             // elements per thread per phase (tile ke
 constexpr int kTileVmax = kThreads * kTileK;
 // elements per thread per phase for a stage type of `stage_bytes` bytes:
 // 64 bytes of staged data per thread per phase
-constexpr int tile_k_for(int stage_bytes) { return stage_bytes == 8 ? 8 : 16; }
+constexpr int tile_k_for(int stage_bytes) { return stage_bytes == 16 ? 4 : stage_bytes == 8 ? 8 : 16; }
 
-enum DType : int { DT_F32 = 0, DT_F64 = 1, DT_BF16 = 2, DT_E4M3 = 3 };
+// DT_C64 / DT_C128: single- and double-complex (the paper's "c" and "z",
+// section 2.1), stored as (real, imaginary) pairs of binary32 / binary64
+enum DType : int { DT_F32 = 0, DT_F64 = 1, DT_BF16 = 2, DT_E4M3 = 3, DT_C64 = 4, DT_C128 = 5 };
+constexpr int kNumDTypes = 6;
 
-constexpr int dtype_size(int dt) { return dt == DT_F64 ? 8 : dt == DT_F32 ? 4 : dt == DT_BF16 ? 2 : 1; }
+constexpr int dtype_size(int dt) {
+  return dt == DT_C128 ? 16 : (dt == DT_F64 || dt == DT_C64) ? 8 : dt == DT_F32 ? 4 : dt == DT_BF16 ? 2 : 1;
+}
+constexpr bool is_complex(int dt) { return dt == DT_C64 || dt == DT_C128; }
+// bytes of one element of A staged in shared memory (bf16 is widened to f32)
+constexpr int stage_bytes_of(int din) { return din == DT_BF16 ? 4 : dtype_size(din); }
 
 // Epilogue modes (the alpha/beta update of Eq. 1 fused into the store).
 enum Mode : int {
@@ -92,12 +100,15 @@ struct GridDim {
   int32_t pad;
 };
 
-// Epilogue scalars, shared by all kernels.
+// Epilogue scalars, shared by all kernels.  Complex dtypes also use the
+// imaginary parts alpha_*i, beta_*i (zero for real scalars).
 struct Epilogue {
   int mode;
   int beta_nz;         // beta != 0: B is read
   float alpha_f, beta_f;
   double alpha_d, beta_d;
+  float alpha_fi, beta_fi;
+  double alpha_di, beta_di;
   const float* scale_in;       // FP8: caller-supplied scale (device) or null
   const uint32_t* amax_bits;   // FP8: amax as float bits (device scratch) when scale_in is null
   float* scale_out;            // FP8: where block 0 records the scale used

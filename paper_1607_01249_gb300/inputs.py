@@ -19,6 +19,9 @@ is not available, so these synthetic families stand in for it):
 * ``batch_problems`` -- thousands of uneven transposes (N 2..5, element counts
   log-uniform 1Ki..4Mi, FP32/BF16, beta in {0, 0.5}).
 * ``serving_requests`` -- a Poisson arrival stream of mixed requests.
+* ``complex_cases`` -- the paper's complex types (section 2.1: c, z and the
+  mixed cz, zc), N = 2..6, 256 MiB per single-complex input tensor, complex
+  alpha, beta in {0, complex}.
 """
 from __future__ import annotations
 
@@ -28,7 +31,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-DTYPE_BYTES = {"f32": 4, "f64": 8, "bf16": 2, "e4m3": 1}
+DTYPE_BYTES = {"f32": 4, "f64": 8, "bf16": 2, "e4m3": 1, "c64": 8, "c128": 16}
 
 
 @dataclass
@@ -37,8 +40,8 @@ class Problem:
     sizes: tuple
     dtype_in: str = "f32"
     dtype_out: str = "f32"
-    alpha: float = 1.0
-    beta: float = 0.0
+    alpha: float | complex = 1.0
+    beta: float | complex = 0.0
     outer_a: tuple | None = None
     outer_b: tuple | None = None
     tag: str = ""
@@ -180,6 +183,25 @@ def packing_cases(out_dtypes=("bf16", "e4m3")) -> list:
     return cases
 
 
+def complex_cases(seed: int = 5, target: int = 1 << 25, Ns=(2, 3, 4, 5, 6), perms_per_n=2,
+                  pairs=(("c64", "c64"), ("c128", "c128"), ("c64", "c128"), ("c128", "c64")),
+                  alpha=complex(1.7, -0.6), beta=complex(0.4, 0.25)) -> list:
+    """Complex transposes (section 2.1: single- and double-complex, and the
+    mixed cz / zc): near-equal random sizes with `target` elements (+-1 %),
+    perms_per_n seeded perms per N (one keeping index 0 when N >= 3), every
+    dtype pair, beta = 0 and beta = `beta` alternating over the pairs."""
+    g = rng(seed)
+    cases = []
+    for N in Ns:
+        for pi, perm in enumerate(sweep_perms(N, g, perms_per_n)):
+            sizes = near_equal_sizes(N, target, g)
+            for qi, (di, do) in enumerate(pairs):
+                b = beta if (qi + pi) % 2 else 0.0
+                cases.append(Problem(perm=perm, sizes=sizes, dtype_in=di, dtype_out=do, alpha=alpha, beta=b,
+                                     tag=f"C{N}p{pi}"))
+    return cases
+
+
 def batch_problems(count: int = 4096, seed: int = 3, lo_log2=10, hi_log2=22,
                    Nmin=2, Nmax=5) -> list:
     g = rng(seed)
@@ -254,7 +276,12 @@ def tensor_for(dtype: str, n: int, seed: int, dist="uniform") -> np.ndarray:
         return bf16_bits_from_f32_trunc(x)
     if dtype == "e4m3":
         return rng(seed).integers(0, 256, size=n, dtype=np.uint8)
+    if dtype in ("c64", "c128"):
+        # (real, imaginary) pairs, both parts from the same distribution
+        parts = (uniform(2 * n, seed, np.float64) if dist == "uniform" else normal(2 * n, seed, np.float64))
+        return parts.astype(np.float32 if dtype == "c64" else np.float64).view(STORAGE[dtype])
     raise ValueError(dtype)
 
 
-STORAGE = {"f32": np.float32, "f64": np.float64, "bf16": np.uint16, "e4m3": np.uint8}
+STORAGE = {"f32": np.float32, "f64": np.float64, "bf16": np.uint16, "e4m3": np.uint8, "c64": np.complex64,
+           "c128": np.complex128}

@@ -17,8 +17,9 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libttc.so")
 
-DTYPES = {"f32": 0, "f64": 1, "bf16": 2, "e4m3": 3}
-DTYPE_BYTES = {"f32": 4, "f64": 8, "bf16": 2, "e4m3": 1}
+DTYPES = {"f32": 0, "f64": 1, "bf16": 2, "e4m3": 3, "c64": 4, "c128": 5}
+DTYPE_BYTES = {"f32": 4, "f64": 8, "bf16": 2, "e4m3": 1, "c64": 8, "c128": 16}
+COMPLEX_DTYPES = ("c64", "c128")
 MAX_DIM = 16
 STATUS = {0: "TTC_OK", 1: "TTC_ERR_INVALID_PERM", 2: "TTC_ERR_INVALID_SIZE", 3: "TTC_ERR_INVALID_OUTER",
           4: "TTC_ERR_UNSUPPORTED_DTYPE", 5: "TTC_ERR_ALIAS", 6: "TTC_ERR_ALIGN", 7: "TTC_ERR_OOM",
@@ -60,6 +61,8 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 SIGNATURES = {
     "ttc_plan": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i64p,
                                 _i64p, _i64p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+    "ttc_plan_complex": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i64p,
+                                        _i64p, _i64p, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4),
     "ttc_execute": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "ttc_plan_destroy": (ctypes.c_int, [_vp]),
     "ttc_plan_set_fp8_scale": (ctypes.c_int, [_vp, _vp]),
@@ -150,7 +153,8 @@ def _i64arr(vals):
 
 
 class Plan:
-    """A planned permute-scale-add B <- alpha*A + beta*B under `perm` (Eq. 1)."""
+    """A planned permute-scale-add B <- alpha*A + beta*B under `perm` (Eq. 1).
+    For the complex dtypes alpha and beta may be complex numbers."""
 
     def __init__(self, perm, sizes, dtype_in="f32", dtype_out=None, alpha=1.0, beta=0.0,
                  outer_a=None, outer_b=None):
@@ -158,16 +162,21 @@ class Plan:
         self.perm = tuple(int(p) for p in perm)
         self.sizes = tuple(int(s) for s in sizes)
         self.dtype_in, self.dtype_out = dtype_in, dtype_out
-        self.alpha, self.beta = float(alpha), float(beta)
+        a, b = complex(alpha), complex(beta)
+        cplx = dtype_in in COMPLEX_DTYPES or a.imag != 0 or b.imag != 0
+        self.alpha, self.beta = (a, b) if cplx else (a.real, b.real)
         self.outer_a = tuple(outer_a) if outer_a is not None else None
         self.outer_b = tuple(outer_b) if outer_b is not None else None
         h = ctypes.c_void_p()
         n = len(self.perm)
         if len(self.sizes) != n:
             raise ValueError("perm and sizes differ in length")
-        _check(lib().ttc_plan(ctypes.byref(h), n, (ctypes.c_int * n)(*self.perm), _i64arr(self.sizes),
-                              _i64arr(self.outer_a), _i64arr(self.outer_b), DTYPES[dtype_in],
-                              DTYPES[dtype_out], self.alpha, self.beta))
+        args = (ctypes.byref(h), n, (ctypes.c_int * n)(*self.perm), _i64arr(self.sizes), _i64arr(self.outer_a),
+                _i64arr(self.outer_b), DTYPES[dtype_in], DTYPES[dtype_out])
+        if cplx:
+            _check(lib().ttc_plan_complex(*args, a.real, a.imag, b.real, b.imag))
+        else:
+            _check(lib().ttc_plan(*args, a.real, b.real))
         self._h = h
 
     @property

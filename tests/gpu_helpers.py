@@ -11,7 +11,10 @@ import oracle
 from paper_1607_01249_gb300 import inputs
 from paper_1607_01249_gb300 import ttc
 
-ODT = {"f32": oracle.F32, "f64": oracle.F64, "bf16": oracle.BF16, "e4m3": oracle.E4M3}
+ODT = {"f32": oracle.F32, "f64": oracle.F64, "bf16": oracle.BF16, "e4m3": oracle.E4M3, "c64": oracle.C64,
+       "c128": oracle.C128}
+COMPLEX = ("c64", "c128")
+PART = {"c64": "f32", "c128": "f64"}       # the type of one part of a complex element
 
 
 def torch_dtype(dt):
@@ -61,6 +64,10 @@ def run_gpu(p: inputs.Problem, A: np.ndarray, B0: np.ndarray, plan=None, stream=
 
 def oracle_mirror(p: inputs.Problem, A, B0, scale=None):
     Bm = B0.copy()
+    if p.dtype_in in COMPLEX:
+        oracle.permute_complex(p.perm, p.sizes, A, Bm, p.alpha, p.beta, ODT[p.dtype_in], ODT[p.dtype_out],
+                               p.outer_a, p.outer_b)
+        return Bm, None
     if p.dtype_out == "e4m3" and scale is None:
         scale, _ = oracle.fp8_scale(p.sizes, A, p.alpha, ODT[p.dtype_in], p.outer_a)
     oracle.permute(p.perm, p.sizes, A, Bm, p.alpha, p.beta, ODT[p.dtype_in], ODT[p.dtype_out],
@@ -77,9 +84,13 @@ def as_float(x: np.ndarray, dt: str) -> np.ndarray:
 
 
 def compare_bits(got: np.ndarray, want: np.ndarray, dt: str, nan_as_nan: bool):
-    """Bitwise equality; with nan_as_nan, NaN compares equal to any NaN."""
+    """Bitwise equality; with nan_as_nan, NaN compares equal to any NaN.
+    Complex elements compare part by part."""
     if got.dtype != want.dtype or got.shape != want.shape:
         return False, "dtype/shape"
+    if dt in COMPLEX:
+        pt = np.float32 if dt == "c64" else np.float64
+        return compare_bits(got.view(pt), want.view(pt), PART[dt], nan_as_nan)
     if not nan_as_nan:
         eq = got.view(np.uint8).reshape(got.size, -1) == want.view(np.uint8).reshape(want.size, -1)
         bad = np.flatnonzero(~eq.all(axis=1))
@@ -101,6 +112,8 @@ def tolerance_check(p: inputs.Problem, A, B0, got: np.ndarray):
     FP64 data: 1e-15 relative at that scale; BF16 output: 1 BF16 ulp."""
     if p.dtype_out == "e4m3":
         return True, ""
+    if p.dtype_in in COMPLEX:
+        return complex_tolerance_check(p, A, B0, got)
     R, S = oracle.permute_exact(p.perm, p.sizes, A, B0.copy(), p.alpha, p.beta, ODT[p.dtype_in],
                                 ODT[p.dtype_out], p.outer_a, p.outer_b)
     mask = ~np.isnan(S)
@@ -126,6 +139,27 @@ def tolerance_check(p: inputs.Problem, A, B0, got: np.ndarray):
     if np.any(bad):
         i = int(np.flatnonzero(bad)[0])
         return False, f"{int(bad.sum())} beyond tolerance; first err {err[i]} tol {tol[i]}"
+    return True, ""
+
+
+def complex_tolerance_check(p: inputs.Problem, A, B0, got: np.ndarray):
+    """Complex data: each part within the error bound of its rounding
+    sequence, 4 roundings in the compute type at the part's scale (the sum of
+    the absolute values of its products) plus one rounding to B's type."""
+    R, S = oracle.permute_complex_exact(p.perm, p.sizes, A, B0.copy(), p.alpha, p.beta, ODT[p.dtype_in],
+                                        ODT[p.dtype_out], p.outer_a, p.outer_b)
+    mask = ~np.isnan(S[:, 0])
+    eps_c = 2.0 ** -53 if "c128" in (p.dtype_in, p.dtype_out) else 2.0 ** -24
+    eps_o = 2.0 ** -24 if p.dtype_out == "c64" else 2.0 ** -53
+    tiny = 2.0 ** -149 if p.dtype_out == "c64" else 2.0 ** -1074
+    g = got.astype(np.complex128)[mask]
+    for k, (gp, rp) in enumerate(((g.real, R.real[mask]), (g.imag, R.imag[mask]))):
+        err = np.abs(gp - rp)
+        tol = np.maximum(4 * eps_c * S[mask, k] + eps_o * np.abs(rp), tiny)
+        bad = err > tol
+        if np.any(bad):
+            i = int(np.flatnonzero(bad)[0])
+            return False, f"{int(bad.sum())} parts beyond tolerance; first err {err[i]} tol {tol[i]}"
     return True, ""
 
 

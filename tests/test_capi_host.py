@@ -70,8 +70,53 @@ def test_plan_validation_ndim_and_dtypes():
         ttc.Plan((1, 0), (4, 4), "f32", "e4m3", beta=0.5)
     assert ei.value.name == "TTC_ERR_UNSUPPORTED_DTYPE"
     for din, dout in [("f32", "f32"), ("f32", "f64"), ("f32", "bf16"), ("f32", "e4m3"), ("f64", "f64"),
-                      ("f64", "f32"), ("bf16", "bf16"), ("bf16", "f32"), ("bf16", "e4m3")]:
+                      ("f64", "f32"), ("bf16", "bf16"), ("bf16", "f32"), ("bf16", "e4m3"), ("c64", "c64"),
+                      ("c128", "c128"), ("c64", "c128"), ("c128", "c64")]:
         ttc.Plan((1, 0), (4, 4), din, dout)
+
+
+def test_complex_plan_validation():
+    """Complex types pair only with complex types; complex scalars need
+    complex tensors; every part of alpha and beta must be finite."""
+    for din, dout in [("c64", "f32"), ("f64", "c128"), ("c64", "bf16"), ("c128", "e4m3"), ("bf16", "c64")]:
+        with pytest.raises(ttc.TTCError) as ei:
+            ttc.Plan((1, 0), (4, 4), din, dout)
+        assert ei.value.name == "TTC_ERR_UNSUPPORTED_DTYPE"
+    for din in ("f32", "f64", "bf16"):
+        with pytest.raises(ttc.TTCError) as ei:
+            ttc.Plan((1, 0), (4, 4), din, din, alpha=1 + 1j)
+        assert ei.value.name == "TTC_ERR_UNSUPPORTED_DTYPE"
+    with pytest.raises(ttc.TTCError) as ei:
+        ttc.Plan((1, 0), (4, 4), "c64", "c64", alpha=complex(1.0, float("inf")))
+    assert ei.value.name == "TTC_ERR_INVALID_ARG"
+    p = ttc.Plan((2, 0, 1), (5, 6, 7), "c128", "c64", alpha=0.5j, beta=-1j)
+    assert p.info()["algorithmic_bytes"] == 210 * (16 + 2 * 8)     # beta != 0: B read and written
+    p = ttc.Plan((2, 0, 1), (5, 6, 7), "c64", "c128", alpha=0.5j)
+    assert p.info()["algorithmic_bytes"] == 210 * (8 + 16)
+    # not batched: the persistent kernel covers the real pairs only
+    b = ttc.Batch()
+    with pytest.raises(ttc.TTCError) as ei:
+        b.add(ttc.Plan((1, 0), (8, 8), "c64", "c64"), 1 << 20, 2 << 20)
+    assert ei.value.name == "TTC_ERR_UNSUPPORTED_DTYPE"
+    b.close()
+
+
+def test_complex_schedules_are_sound():
+    """Every candidate of complex problems (8- and 16-byte elements, so 8 and
+    4 slots per thread): the kernels' index walks and slot tables put every A
+    element at its Eq. 1 position in B."""
+    g = inputs.rng(32)
+    pairs = [("c64", "c64"), ("c128", "c128"), ("c64", "c128"), ("c128", "c64")]
+    for trial in range(60):
+        N = int(g.integers(1, 6))
+        sizes = tuple(int(x) for x in g.integers(1, 12 if N > 3 else 70, size=N))
+        perm = tuple(int(x) for x in g.permutation(N))
+        oa = tuple(s + int(g.integers(0, 3)) for s in sizes) if g.random() < 0.4 else None
+        din, dout = pairs[trial % 4]
+        plan = ttc.Plan(perm, sizes, din, dout, alpha=1.5 - 0.5j, beta=(0.5j if trial % 3 else 0.0), outer_a=oa)
+        _verify_all(plan, (perm, sizes, oa, din, dout))
+    for c in inputs.complex_cases(target=1 << 16):
+        _verify_all(ttc.Plan(c.perm, c.sizes, c.dtype_in, c.dtype_out, c.alpha, c.beta), (c.tag, c.dtype_in))
 
 
 def test_merge_examples_from_the_paper():
