@@ -158,6 +158,7 @@ Epilogue make_epilogue(const ttc_plan_s* p, const DevRes* r) {
   e.beta_fi = float(p->beta_im);
   e.alpha_di = p->alpha_im;
   e.beta_di = p->beta_im;
+  e.alpha_k = make_dmul_const(p->alpha);
   e.scale_in = p->user_scale;
   e.amax_bits = r ? r->amax : nullptr;
   e.scale_out = r ? r->scale : nullptr;

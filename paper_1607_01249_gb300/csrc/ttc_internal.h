@@ -24,6 +24,8 @@
 
 #include <cstdint>
 
+#include "fpint.h"
+
 struct int4;   // CUDA vector type (vector_types.h); only pointers to it appear here
 
 #if defined(__CUDACC__)
@@ -109,6 +111,7 @@ struct Epilogue {
   double alpha_d, beta_d;
   float alpha_fi, beta_fi;
   double alpha_di, beta_di;
+  DMulConst alpha_k;           // alpha_d prepared for the integer product (fpint.h)
   const float* scale_in;       // FP8: caller-supplied scale (device) or null
   const uint32_t* amax_bits;   // FP8: amax as float bits (device scratch) when scale_in is null
   float* scale_out;            // FP8: where block 0 records the scale used

@@ -241,6 +241,77 @@ int main() {
     assert r.returncode == 0, r.stdout
 
 
+def test_integer_float_conversions_match_ieee_casts(tmp_path):
+    """The kernels' binary32 <-> binary64 conversions and binary64 product
+    (integer operations, no FP64 instruction) against the host's IEEE
+    arithmetic: widening on every one of the 2^32 binary32 values, narrowing
+    on exponents across and beyond the binary32 range, exact ties and rounding
+    carries, and arbitrary bit patterns (NaN only has to stay NaN); the
+    product on random operands of every exponent for several constants."""
+    src = tmp_path / "conv.cpp"
+    src.write_text(r'''
+#include "fpint.h"
+#include <cmath>
+#include <cstdio>
+using namespace ttc;
+int main() {
+  unsigned long long bad = 0, n = 0;
+  for (unsigned long long u = 0; u < (1ull << 32); ++u) {
+    const float f = fp_float((uint32_t)u);
+    const double a = widen_f32(f), b = (double)f;
+    ++n;
+    if (std::isnan(b) ? !std::isnan(a) : fp_bits(a) != fp_bits(b)) ++bad;
+  }
+  unsigned long long x = 88172645463325252ull;
+  auto rnd = [&]() { x ^= x << 13; x ^= x >> 7; x ^= x << 17; return x; };
+  auto check = [&](unsigned long long bits) {
+    const double d = fp_double((uint32_t)(bits >> 32), (uint32_t)bits);
+    const float a = narrow_f64_rn(d), b = (float)d;
+    ++n;
+    if (std::isnan(b) ? !std::isnan(a) : fp_bits(a) != fp_bits(b)) ++bad;
+  };
+  for (int i = 0; i < 20000000; ++i) {
+    const unsigned long long r = rnd();
+    const unsigned long long bits = (r & (1ull << 63)) | ((850 + (r >> 20) % 330) << 52) | (rnd() & 0xfffffffffffffull);
+    check(bits);
+    check((bits & ~0x1fffffffull) | 0x10000000ull);
+    check(bits | 0x1fffffffull);
+  }
+  for (unsigned long long e = 0; e < 2048; ++e)
+    for (unsigned long long k = 0; k < 53; ++k) {
+      const unsigned long long frac = ((1ull << k) - 1) << (52 - k);
+      check((e << 52) | frac);
+      check((1ull << 63) | (e << 52) | frac);
+      check((e << 52) | (1ull << 28) | ((k & 1) << 29));
+    }
+  for (int i = 0; i < 5000000; ++i) check(rnd());
+  // the integer product fl64(c * a): wherever it claims a result, the host's
+  // multiplication gives the same bits
+  const double cs[] = {1.7, 0.4, -1.7, 1.0, 0.5, 3.141592653589793, 1e-300, 1e300, 0.1, 1.9999999999999998};
+  for (double c : cs) {
+    const DMulConst k = make_dmul_const(c);
+    for (int i = 0; i < 3000000; ++i) {
+      const unsigned long long r = rnd();
+      const unsigned long long e = (i & 3) ? 1003 + (r >> 20) % 40 : (r >> 20) % 2048;
+      unsigned long long bits = (r & (1ull << 63)) | (e << 52) | (rnd() & 0xfffffffffffffull);
+      if (i % 5 == 1) bits &= ~0xffffffffull;
+      const double a = fp_double((uint32_t)(bits >> 32), (uint32_t)bits);
+      double got;
+      ++n;
+      if (dmul_normal(k, a, &got) && fp_bits(got) != fp_bits(c * a)) ++bad;
+    }
+  }
+  printf("%llu %llu\n", bad, n);
+  return bad != 0;
+}
+''')
+    exe = tmp_path / "conv"
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-I", os.path.join(ROOT, "paper_1607_01249_gb300", "csrc"),
+                           str(src), "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout
+
+
 def _verify_all(plan, label):
     for i in range(plan.info()["ncandidates"]):
         msg = plan.verify_schedule(i)

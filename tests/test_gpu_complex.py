@@ -182,3 +182,58 @@ def test_full_size_complex_case_sampled(case):
     want, _ = H.oracle_mirror(sub, np.ascontiguousarray(A[offA]), np.ascontiguousarray(B0[offs]))
     ok, msg = H.compare_bits(np.ascontiguousarray(got[offs]), want, case.dtype_out, True)
     assert ok, msg
+
+
+def crafted_doubles(n, g):
+    """binary64 values around every case of the binary64 -> binary32 rounding:
+    exponents from the binary32 subnormal range to past its overflow, exact
+    ties (even and odd kept parts), carries into the next binade, the largest
+    finite binary32 and the halfway point above it, zeros, subnormals,
+    infinities and NaN."""
+    e = g.integers(860, 1190, n).astype(np.uint64)
+    frac = g.integers(0, 1 << 52, n, dtype=np.uint64)
+    sign = g.integers(0, 2, n).astype(np.uint64) << np.uint64(63)
+    bits = sign | (e << np.uint64(52)) | frac
+    k = n // 8
+    tie = np.uint64(1 << 28)
+    bits[:k] = (bits[:k] & ~np.uint64((1 << 29) - 1)) | tie                     # exact ties
+    bits[k:2 * k] |= np.uint64((1 << 29) - 1) << np.uint64(0)                    # round up with carries
+    bits[2 * k:2 * k + 8] = np.array([0x47EFFFFFE0000000, 0x47EFFFFFF0000000, 0xC7EFFFFFF0000000,
+                                      0x47EFFFFFEFFFFFFF, 0x3810000000000000, 0x380FFFFFF0000000,
+                                      0x3800000000000000, 0x36A0000000000000], dtype=np.uint64)
+    bits[2 * k + 8:2 * k + 16] = np.array([0, 1 << 63, 1, 0x000FFFFFFFFFFFFF, 0x7FF0000000000000,
+                                           0xFFF0000000000000, 0x7FF8000000000001, 0x7FF0000000000001],
+                                          dtype=np.uint64)
+    return bits.view(np.float64)
+
+
+def crafted_floats(n, g):
+    """binary32 values of every class: normal numbers over the whole exponent
+    range, subnormals, zeros, infinities and NaN payloads."""
+    bits = g.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    bits[:8] = np.array([0, 0x80000000, 1, 0x007FFFFF, 0x00800000, 0x7F7FFFFF, 0x7F800000, 0xFF800000],
+                        dtype=np.uint32)
+    bits[8:12] = np.array([0x7FC00001, 0x7F800123, 0xFFC00000, 0x80000001], dtype=np.uint32)
+    return bits.view(np.float32)
+
+
+@pytest.mark.parametrize("din,dout", [("f64", "f32"), ("c128", "c64"), ("f32", "f64"), ("c64", "c128")])
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (1.7, 0.0), (1.0, 0.5), (1.7 - 0.6j, 0.4 + 0.25j)])
+def test_mixed_type_conversions_on_crafted_values(din, dout, alpha, beta):
+    """The widening and narrowing of the mixed types (the paper's sd, ds, cz,
+    zc) on values of every class, bit for bit against the oracle's IEEE
+    conversions (NaN results compare as NaN)."""
+    if din in ("f32", "f64") and isinstance(alpha, complex):
+        pytest.skip("complex scalars need complex tensors")
+    g = inputs.rng(91)
+    p = Problem(perm=(1, 0), sizes=(96, 80), dtype_in=din, dtype_out=dout, alpha=alpha, beta=beta)
+    npart = p.n * (2 if din in H.COMPLEX else 1)
+    parts = crafted_doubles(npart, g) if din in ("f64", "c128") else crafted_floats(npart, g)
+    A = parts.view(inputs.STORAGE[din])
+    nb = p.n * (2 if dout in H.COMPLEX else 1)
+    bparts = crafted_doubles(nb, g) if dout in ("f64", "c128") else crafted_floats(nb, g)
+    B0 = bparts.view(inputs.STORAGE[dout]).copy()
+    got, _ = H.run_gpu(p, A, B0)
+    want, _ = H.oracle_mirror(p, A, B0)
+    ok, msg = H.compare_bits(got, want, dout, nan_as_nan=True)
+    assert ok, msg
