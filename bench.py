@@ -45,8 +45,9 @@ METRIC = "effective HBM GB/s (frac of ~8 TB/s); served transposes/s + p99 vs per
 # while their hash is the one it was measured with
 KERNEL_SOURCES = {
     "batch": ["paper_1607_01249_gb300/csrc/batch.cu", "paper_1607_01249_gb300/csrc/kernels_impl.cuh",
-              "paper_1607_01249_gb300/csrc/kernels.cuh"],
-    None: ["paper_1607_01249_gb300/csrc/kernels_impl.cuh", "paper_1607_01249_gb300/csrc/kernels.cuh"],
+              "paper_1607_01249_gb300/csrc/kernels.cuh", "paper_1607_01249_gb300/csrc/fpint.h"],
+    None: ["paper_1607_01249_gb300/csrc/kernels_impl.cuh", "paper_1607_01249_gb300/csrc/kernels.cuh",
+           "paper_1607_01249_gb300/csrc/fpint.h"],
 }
 
 
@@ -173,7 +174,11 @@ def workload_problems(name: str, target: int = 1 << 26, only: str = ""):
     if name == "pow2":
         return inputs.pow2_cases()
     if name == "complex":
-        return inputs.complex_cases()
+        probs = inputs.complex_cases(target=target // 2)
+        if only:
+            keep = set(only.split(","))
+            probs = [p for p in probs if p.tag in keep or f"{p.tag}/{p.dtype_in}>{p.dtype_out}" in keep]
+        return probs
     if name == "batch":
         return inputs.batch_problems(4096)
     if name == "serving":
@@ -388,10 +393,43 @@ def run_ours(args, rank, world):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if args.workload == "complex":
+        out["fp64_pipe"] = fp64_roofline(probs, per_case_ms)
     if fp8_supplied:
         out["fp8"] = {"note": "algorithmic bytes n (s_A + s_B) in both columns; the computed scale also reads A "
                               "once more (amax pre-pass)", "cases": fp8_supplied}
     return out
+
+
+# FP64 pipe: nominal 1.25 TFLOP/s dense FP64 on GB300 = 0.625 T fused
+# multiply-adds per second; a dependent-free FMA loop measured 505 G/s
+FP64_FMA_PEAK_G = 625.0
+FP64_FMA_MEASURED_G = 505.0
+
+
+def fp64_fmas_per_element(p) -> int:
+    """FP64-pipe instructions of the double-complex update per element: the
+    products alpha_re * a run as integer code, the cross term of alpha_im and
+    both beta terms are fused multiply-adds (two parts each)."""
+    if "c128" not in (p.dtype_in, p.dtype_out):
+        return 0
+    a, b = complex(p.alpha), complex(p.beta)
+    return 2 * (a.imag != 0) + 2 * (b != 0) + 2 * (b.imag != 0)
+
+
+def fp64_roofline(probs, per_case_ms):
+    """ALU roofline of the cases computed in double-complex: FP64-pipe fused
+    multiply-adds per second against the pipe's peak."""
+    ops = sum(p.n * fp64_fmas_per_element(p) for p in probs)
+    ms = sum(t for p, t in zip(probs, per_case_ms) if fp64_fmas_per_element(p))
+    if not ops or not ms:
+        return None
+    achieved = ops / (ms * 1e-3) / 1e9
+    return {"bound": "alu", "unit": "G FP64 FMA/s", "achieved": round(achieved, 1), "peak": FP64_FMA_PEAK_G,
+            "frac": round(achieved / FP64_FMA_PEAK_G, 4), "frac_of_measured_fma_loop": round(
+                achieved / FP64_FMA_MEASURED_G, 4),
+            "peak_source": "nominal 1.25 TFLOP/s FP64 / 2 per FMA; measured FMA loop 505 G/s",
+            "cases": sum(1 for p in probs if fp64_fmas_per_element(p))}
 
 
 def workload_desc(name, probs):
@@ -846,8 +884,10 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="default workload: skip the serving summary")
     ap.add_argument("--no-complex", action="store_true", help="default workload: skip the complex-types row")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--target", type=int, default=1 << 26, help="elements per tensor of the sweep")
-    ap.add_argument("--only", default="", help="comma-separated case tags of the sweep (e.g. N5p3)")
+    ap.add_argument("--target", type=int, default=1 << 26,
+                    help="elements per tensor of the sweep (the complex workload takes half)")
+    ap.add_argument("--only", default="", help="comma-separated case tags of the sweep or the complex workload "
+                                               "(e.g. N5p3, C2p0/c128>c128)")
     ap.add_argument("--cases-out", default="", help="write per-case timings (JSON) to this file")
     ap.add_argument("--profile-timed", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
@@ -894,7 +934,7 @@ def main():
                 r = run_ours(cx, rank, world)
                 out["complex"] = {"workload": r["config"]["workload"], "GB/s": r["value"], "cases": r["cases"],
                                   "per_variant": r["per_variant"], "roofline_frac": r["roofline"]["frac"],
-                                  "timing": "CUDA events"}
+                                  "fp64_pipe": r.get("fp64_pipe"), "timing": "CUDA events"}
             if not args.no_batch:
                 b = run_batch(sub, rank, world)
                 out["batch"] = {"workload": b["config"]["workload"], "GB/s": b["value"],
