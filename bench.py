@@ -669,6 +669,94 @@ def run_serving(args, rank, world):
     }
 
 
+# FP32 SIMT peak from the unit counts and clock: 152 SMs x 128 FP32 lanes x
+# 2 FLOP per FMA x 2.07 GHz
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def run_contraction(args, rank, world):
+    """TTGT contractions (ttc_contraction_*): each case once with an exact
+    FP32 GEMM and once with BF16 operands packed by the transposes (FP32
+    accumulation); against a cuBLAS GEMM of the same m, n, k on operands that
+    are already matrices (torch.mm), which is what TTGT adds its transposes
+    to."""
+    import torch
+    from paper_1607_01249_gb300 import build as ttc_build
+    from paper_1607_01249_gb300 import ttc
+
+    ttc_build.build()
+    ttc.lib()
+    torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
+    torch.backends.cuda.matmul.allow_tf32 = False
+    stream = torch.cuda.current_stream()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    peak_bf16 = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            peak_bf16 = float(json.load(f)["bf16_tflops"])
+    steps = max(args.steps, 1)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1) / steps, world)
+
+    cases, tot_flop, tot_ms, launches = [], 0.0, 0.0, 0
+    for c in inputs.contraction_cases():
+        ext = c["extents"]
+        sa, sb, sc = (tuple(ext[m] for m in c[k]) for k in ("modes_a", "modes_b", "modes_c"))
+        A = torch.empty(int(np.prod(sa)), device="cuda").uniform_(-1, 1, generator=g)
+        B = torch.empty(int(np.prod(sb)), device="cuda").uniform_(-1, 1, generator=g)
+        C = torch.zeros(int(np.prod(sc)), device="cuda")
+        row = {"case": c["tag"]}
+        for gd in ("f32", "bf16"):
+            con = ttc.Contraction(c["modes_a"], sa, c["modes_b"], sb, c["modes_c"], sc, "f32", gd, 1.0, 0.0)
+            inf = con.info()
+            flop = 2.0 * inf["m"] * inf["n"] * inf["k"]
+            l0 = ttc.launch_count()
+            ms = timed(lambda: con.execute(A, B, C, stream))
+            launches += (ttc.launch_count() - l0) // (steps + max(args.warmup, 3))
+            mt = torch.float32 if gd == "f32" else torch.bfloat16
+            X = torch.empty(inf["m"], inf["k"], device="cuda", dtype=mt).uniform_(-1, 1, generator=g)
+            Y = torch.empty(inf["k"], inf["n"], device="cuda", dtype=mt).uniform_(-1, 1, generator=g)
+            ms_gemm = timed(lambda: torch.mm(X, Y))
+            del X, Y
+            tf = world * flop / (ms * 1e-3) / 1e12
+            peak = FP32_SIMT_PEAK_TFLOPS if gd == "f32" else peak_bf16
+            row[gd] = {"m": inf["m"], "n": inf["n"], "k": inf["k"], "permuted": inf["permuted"],
+                       "ms": round(ms, 4), "TFLOP/s": round(tf, 1), "gemm_only_ms": round(ms_gemm, 4),
+                       "transpose_share": round(max(ms - ms_gemm, 0.0) / ms, 3),
+                       "frac_of_peak": round(tf / world / peak, 3) if peak else None}
+            tot_flop += flop
+            tot_ms += ms
+            con.close()
+        cases.append(row)
+        del A, B, C
+    value = world * tot_flop / (tot_ms * 1e-3) / 1e12
+    return {
+        "metric": "TTGT tensor contraction TFLOP/s (2 m n k per contraction)", "value": round(value, 2),
+        "unit": "TFLOP/s", "n_gpus": world, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": round(tot_ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (exact FP32 GEMM) + f32 packed to bf16 (FP32 accumulation)",
+        "data": "synthetic (uniform[-1,1], torch Philox on the device)",
+        "config": {"workload": "contractions " + ", ".join(c["tag"] for c in inputs.contraction_cases()),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "fp32 SIMT / bf16 tensor", "fp32_peak_tflops": round(FP32_SIMT_PEAK_TFLOPS, 1),
+                     "fp32_peak_source": "152 SMs x 128 lanes x 2 x 2.07 GHz",
+                     "bf16_peak_tflops": peak_bf16, "bf16_peak_source": "MEASURED_PEAKS.json bf16_tflops"},
+        "cases": cases, "gpu_launches": launches,
+    }
+
+
 def run_serving_line(args, rank, world):
     s = run_serving(args, rank, world)
     c = s["continuous"]
@@ -831,6 +919,9 @@ def cpu_baseline(budget_s: float, probs, threads: int):
 
 
 def run_reference(args, rank, world):
+    if args.workload == "contraction":
+        return {"impl": "reference", "unavailable": "the contraction workload has no timed CPU arm (its oracle is "
+                                                    "numpy.einsum in float64, a test reference only)"}
     probs = workload_problems(args.workload, args.target, args.only)
     threads = os.cpu_count() or 1
     import oracle
@@ -867,7 +958,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "pow2", "complex", "single4d", "packing", "batch", "serving"])
+                    choices=["sweep", "pow2", "complex", "single4d", "packing", "batch", "serving", "contraction"])
     ap.add_argument("--serve-count", type=int, default=1500)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
@@ -883,6 +974,7 @@ def main():
     ap.add_argument("--no-pow2", action="store_true", help="default workload: skip the power-of-two-sizes row")
     ap.add_argument("--no-serving", action="store_true", help="default workload: skip the serving summary")
     ap.add_argument("--no-complex", action="store_true", help="default workload: skip the complex-types row")
+    ap.add_argument("--no-contraction", action="store_true", help="default workload: skip the TTGT contraction row")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--target", type=int, default=1 << 26,
                     help="elements per tensor of the sweep (the complex workload takes half)")
@@ -908,6 +1000,8 @@ def main():
         tdist.init_process_group("nccl")
     if args.workload == "batch":
         out = run_batch(args, rank, world)
+    elif args.workload == "contraction":
+        out = run_contraction(args, rank, world)
     elif args.workload == "serving":
         out = run_serving_line(args, rank, world)
     else:
@@ -935,6 +1029,10 @@ def main():
                 out["complex"] = {"workload": r["config"]["workload"], "GB/s": r["value"], "cases": r["cases"],
                                   "per_variant": r["per_variant"], "roofline_frac": r["roofline"]["frac"],
                                   "fp64_pipe": r.get("fp64_pipe"), "timing": "CUDA events"}
+            if not args.no_contraction:
+                ct = run_contraction(sub, rank, world)
+                out["contraction"] = {"workload": ct["config"]["workload"], "TFLOP/s": ct["value"],
+                                      "cases": ct["cases"], "timing": "CUDA events"}
             if not args.no_batch:
                 b = run_batch(sub, rank, world)
                 out["batch"] = {"workload": b["config"]["workload"], "GB/s": b["value"],
@@ -954,7 +1052,7 @@ def main():
                                   "saturated_speedup_vs_per_call": sv["saturated_speedup_vs_per_call"],
                                   "timing": "host steady clock, arrival to detected completion"}
     if rank == 0:
-        if not args.no_cpu and world == 1 and args.workload not in ("batch", "serving"):
+        if not args.no_cpu and world == 1 and args.workload not in ("batch", "serving", "contraction"):
             out["cpu_baseline"] = cpu_baseline(args.cpu_budget,
                                                workload_problems(args.workload, args.target, args.only),
                                                os.cpu_count() or 1)

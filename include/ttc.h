@@ -278,6 +278,51 @@ ttc_status ttc_batch_info(ttc_batch_t batch, int64_t* problems, int64_t* tiles);
 ttc_status ttc_batch_set_direct_threshold(ttc_batch_t batch, int64_t min_elements);
 
 /*
+ * Tensor contraction by Transpose-Transpose-GEMM-Transpose (TTGT; the use of
+ * tensor transpositions that motivates the paper, section 1):
+ *
+ *     C[modes_C] <- alpha * sum over contracted labels of A[modes_A] * B[modes_B]
+ *                   + beta * C[modes_C]
+ *
+ * Tensors are dense and column-major (index 0 stride 1).  A label (any int)
+ * names an index: one in A and B but not C is contracted, one in A and C (or
+ * B and C) is a free index; every label must appear in exactly two of the
+ * three tensors with the same extent (labels in all three, i.e. batched
+ * contractions, and labels in one tensor only are rejected with
+ * TTC_ERR_INVALID_PERM).  Each operand is permuted by this library's kernels
+ * into a column-major matrix unless it already is one (either orientation);
+ * the product is one cuBLAS GEMM; C takes the GEMM's output directly when it
+ * is laid out as [free A labels, free B labels] or the reverse, else it is
+ * permuted from a workspace with the beta update of Eq. 1.
+ *
+ *  ttc_contraction_plan     validate and plan (host only).  dtype: type of A,
+ *                           B and C; gemm_dtype: TTC_F32 (exact FP32 GEMM)
+ *                           or TTC_BF16 (operands packed to bfloat16 by the
+ *                           transposes, round to nearest even, products
+ *                           accumulated in FP32) for dtype TTC_F32;
+ *                           TTC_F64 for dtype TTC_F64.  alpha is applied by
+ *                           the GEMM.  Returns TTC_ERR_INVALID_SIZE for
+ *                           inconsistent extents or a GEMM extent >= 2^31.
+ *  ttc_contraction_execute  enqueue on `stream` (A, B, C device pointers;
+ *                           C must not overlap A or B).  Workspaces (the
+ *                           permuted operands and product) and the cuBLAS
+ *                           handle are created on the first execution on a
+ *                           device and owned by the contraction.
+ *  ttc_contraction_info     GEMM extents m, n, k and which tensors are
+ *                           permuted (bit 0: A, bit 1: B, bit 2: C).
+ *  ttc_contraction_destroy  release (no work using it may be queued).
+ */
+typedef struct ttc_contraction_s* ttc_contraction_t;
+ttc_status ttc_contraction_plan(ttc_contraction_t* out, int nA, const int* modes_A, const int64_t* sizes_A,
+                                int nB, const int* modes_B, const int64_t* sizes_B, int nC, const int* modes_C,
+                                const int64_t* sizes_C, ttc_dtype dtype, ttc_dtype gemm_dtype, double alpha,
+                                double beta);
+ttc_status ttc_contraction_execute(ttc_contraction_t c, const void* A, const void* B, void* C,
+                                   ttc_stream_t stream);
+ttc_status ttc_contraction_info(ttc_contraction_t c, int64_t* m, int64_t* n, int64_t* k, int* transposes);
+ttc_status ttc_contraction_destroy(ttc_contraction_t c);
+
+/*
  * Server: continuous batching of permute-scale-add requests (Eq. 1) that
  * arrive over time.  A scheduler thread admits pending requests in arrival
  * order while the bytes of admitted, unfinished requests (A's and B's

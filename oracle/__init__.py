@@ -214,3 +214,29 @@ def fmaf(a, b, c) -> np.ndarray:
     y = np.empty(a.shape, np.float32)
     lib().oracle_fmaf_n(_ptr(a), _ptr(b), _ptr(c), _ptr(y), a.size)
     return y
+
+
+# ------------------------------------------------------------ contraction
+
+def contract(modes_a, A, sizes_a, modes_b, B, sizes_b, modes_c, C, sizes_c, alpha=1.0, beta=0.0, absolute=False):
+    """Tensor contraction by its definition (section 1: the operation TTGT
+    computes), in float64: C[modes_c] = alpha * sum over the labels of A and B
+    missing from C of A * B + beta * C, every tensor a flat column-major
+    buffer.  numpy.einsum evaluates the sum of products (a library primitive
+    serving as one step).  With absolute=True it returns the same contraction
+    of |A|, |B| with |alpha|, |beta| and |C|: the scale of the GEMM's error
+    bound.  B is read only when beta != 0."""
+    letters = {}
+    for m in list(modes_a) + list(modes_b) + list(modes_c):
+        letters.setdefault(m, "abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ"[len(letters)])
+    spec = "".join(letters[m] for m in modes_a) + "," + "".join(letters[m] for m in modes_b) + "->" + \
+        "".join(letters[m] for m in modes_c)
+    a = np.asarray(A, dtype=np.float64).reshape(tuple(sizes_a), order="F")
+    b = np.asarray(B, dtype=np.float64).reshape(tuple(sizes_b), order="F")
+    if absolute:
+        a, b, alpha, beta = np.abs(a), np.abs(b), abs(alpha), abs(beta)
+    r = alpha * np.einsum(spec, a, b).reshape(-1, order="F")
+    if beta != 0.0:
+        c = np.asarray(C, dtype=np.float64)
+        r = r + beta * (np.abs(c) if absolute else c)
+    return r

@@ -86,7 +86,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
                 print(log)
     objs = [o for o, _ in results]
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-lpthread"]
+    # cuBLAS (the GEMM of the TTGT contractions) from the toolkit's own
+    # library directory, found again at load time through the rpath
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
+    cmd = ([cc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs +
+           ["-L", cuda_lib, "-lcublas", "-Xlinker", "-rpath", "-Xlinker", cuda_lib, "-lpthread"])
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

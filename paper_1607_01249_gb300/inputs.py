@@ -202,6 +202,24 @@ def complex_cases(seed: int = 5, target: int = 1 << 25, Ns=(2, 3, 4, 5, 6), perm
     return cases
 
 
+def contraction_cases() -> list:
+    """Tensor contractions of the kind TTGT serves (section 1): each a dict of
+    integer labels per tensor and one extent per label.
+    * ttgt4d: C[a,b,c,d] = A[a,e,b,f] B[f,c,e,d], all extents 48: both
+      operands and the result need a transpose (interleaved free labels);
+    * ttgt3d: C[a,b,c] = A[d,a,c] B[d,b]: A is already a (transposed) matrix,
+      C's free labels are interleaved;
+    * matrix: C[a,b] = A[a,k] B[k,b], 4096^3: a plain GEMM, no transpose."""
+    return [
+        {"tag": "ttgt4d", "modes_a": (0, 4, 1, 5), "modes_b": (5, 2, 4, 3), "modes_c": (0, 1, 2, 3),
+         "extents": {0: 48, 1: 48, 2: 48, 3: 48, 4: 48, 5: 48}},
+        {"tag": "ttgt3d", "modes_a": (3, 0, 2), "modes_b": (3, 1), "modes_c": (0, 1, 2),
+         "extents": {0: 256, 1: 512, 2: 256, 3: 512}},
+        {"tag": "matrix", "modes_a": (0, 2), "modes_b": (2, 1), "modes_c": (0, 1),
+         "extents": {0: 4096, 1: 4096, 2: 4096}},
+    ]
+
+
 def batch_problems(count: int = 4096, seed: int = 3, lo_log2=10, hi_log2=22,
                    Nmin=2, Nmax=5) -> list:
     g = rng(seed)

@@ -83,6 +83,13 @@ SIGNATURES = {
     "ttc_batch_destroy": (ctypes.c_int, [_vp]),
     "ttc_batch_info": (ctypes.c_int, [_vp, _i64p, _i64p]),
     "ttc_batch_set_direct_threshold": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "ttc_contraction_plan": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i64p,
+                                            ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i64p, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int), _i64p, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_double]),
+    "ttc_contraction_execute": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ttc_contraction_info": (ctypes.c_int, [_vp, _i64p, _i64p, _i64p, ctypes.POINTER(ctypes.c_int)]),
+    "ttc_contraction_destroy": (ctypes.c_int, [_vp]),
     "ttc_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_int, ctypes.c_int64]),
     "ttc_server_submit": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64p]),
     "ttc_server_poll": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64]),
@@ -261,6 +268,54 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             lib().ttc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Contraction:
+    """C[modes_c] <- alpha * sum A[modes_a] * B[modes_b] + beta * C[modes_c]
+    by Transpose-Transpose-GEMM-Transpose (ttc_contraction_*).  Modes are
+    integer labels, sizes the extents of each tensor's indices (column-major).
+    dtype f32 (gemm_dtype f32 or bf16) or f64."""
+
+    def __init__(self, modes_a, sizes_a, modes_b, sizes_b, modes_c, sizes_c, dtype="f32", gemm_dtype=None,
+                 alpha=1.0, beta=0.0):
+        gemm_dtype = gemm_dtype or dtype
+        self.modes = (tuple(modes_a), tuple(modes_b), tuple(modes_c))
+        self.sizes = (tuple(sizes_a), tuple(sizes_b), tuple(sizes_c))
+        self.dtype, self.gemm_dtype, self.alpha, self.beta = dtype, gemm_dtype, float(alpha), float(beta)
+        h = ctypes.c_void_p()
+        args = []
+        for m, sz in zip(self.modes, self.sizes):
+            if len(m) != len(sz):
+                raise ValueError("modes and sizes differ in length")
+            args += [len(m), (ctypes.c_int * max(len(m), 1))(*m), _i64arr(sz) if sz else None]
+        _check(lib().ttc_contraction_plan(ctypes.byref(h), *args, DTYPES[dtype], DTYPES[gemm_dtype], self.alpha,
+                                          self.beta))
+        self._h = h
+
+    def execute(self, A, B, C, stream=None):
+        _check(lib().ttc_contraction_execute(self._h, _ptr(A), _ptr(B), _ptr(C), _stream(stream)))
+        return C
+
+    __call__ = execute
+
+    def info(self) -> dict:
+        m, n, k, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib().ttc_contraction_info(self._h, ctypes.byref(m), ctypes.byref(n), ctypes.byref(k),
+                                          ctypes.byref(t)))
+        return {"m": m.value, "n": n.value, "k": k.value, "permuted": {"A": bool(t.value & 1),
+                                                                       "B": bool(t.value & 2),
+                                                                       "C": bool(t.value & 4)}}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ttc_contraction_destroy(self._h)
             self._h = None
 
     def __del__(self):

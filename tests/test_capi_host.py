@@ -365,3 +365,39 @@ def test_tune_cache_file_round_trip(tmp_path):
     with pytest.raises(ttc.TTCError) as ei:
         ttc.tune_cache_load(str(tmp_path / "missing.txt"))
     assert ei.value.name == "TTC_ERR_INVALID_ARG"
+
+
+def test_contraction_plan_validation_and_layouts():
+    """TTGT planning on the host: label rules, extents, dtypes, and which
+    tensors need a transpose for each layout."""
+    C = ttc.Contraction
+    bad = [
+        (((0, 1), (4, 5), (1, 2), (5, 6), (0, 3), (4, 6)), "TTC_ERR_INVALID_PERM"),     # label 3 only in C
+        (((0, 1), (4, 5), (1, 2), (5, 6), (0, 2, 1), (4, 6, 5)), "TTC_ERR_INVALID_PERM"),  # batched label
+        (((0, 1, 7), (4, 5, 2), (1, 2), (5, 6), (0, 2), (4, 6)), "TTC_ERR_INVALID_PERM"),  # label 7 in A only
+        (((0, 1), (4, 5), (1, 2), (6, 6), (0, 2), (4, 6)), "TTC_ERR_INVALID_SIZE"),      # extent mismatch
+        (((0, 0), (4, 4), (0, 2), (4, 6), (2,), (6,)), "TTC_ERR_INVALID_PERM"),         # repeated label
+    ]
+    for (ma, sa, mb, sb, mc, sc), status in bad:
+        with pytest.raises(ttc.TTCError) as ei:
+            C(ma, sa, mb, sb, mc, sc)
+        assert ei.value.name == status, (ma, mb, mc)
+    for dt, gd in [("f64", "f32"), ("f32", "f64"), ("bf16", "bf16"), ("c64", "c64"), ("f64", "bf16")]:
+        with pytest.raises(ttc.TTCError) as ei:
+            C((0, 1), (4, 5), (1, 2), (5, 6), (0, 2), (4, 6), dt, gd)
+        assert ei.value.name == "TTC_ERR_UNSUPPORTED_DTYPE"
+    # matrix layouts need no transpose in either orientation; a permuted C does
+    assert C((0, 1), (4, 5), (1, 2), (5, 6), (0, 2), (4, 6)).info() == {
+        "m": 4, "n": 6, "k": 5, "permuted": {"A": False, "B": False, "C": False}}
+    assert C((1, 0), (5, 4), (2, 1), (6, 5), (2, 0), (6, 4)).info()["permuted"] == {"A": False, "B": False,
+                                                                                  "C": False}
+    # C = [free B, free A]: the GEMM computes C's transpose directly
+    inf = C((0, 3, 1, 4), (3, 2, 4, 5), (4, 2, 3), (5, 6, 2), (2, 1, 0), (6, 4, 3)).info()
+    assert (inf["m"], inf["n"], inf["k"]) == (12, 6, 10)
+    assert inf["permuted"] == {"A": True, "B": True, "C": False}
+    # free labels interleaved in C: the product goes through a workspace and a transpose
+    inf = C((0, 3, 1, 4), (3, 2, 4, 5), (4, 2, 3), (5, 6, 2), (1, 2, 0), (4, 6, 3)).info()
+    assert inf["permuted"]["C"]
+    # the BF16 GEMM path always packs (downcasts) both operands
+    assert C((0, 1), (4, 5), (1, 2), (5, 6), (0, 2), (4, 6), "f32", "bf16").info()["permuted"] == {
+        "A": True, "B": True, "C": False}
