@@ -323,6 +323,44 @@ ttc_status ttc_contraction_info(ttc_contraction_t c, int64_t* m, int64_t* n, int
 ttc_status ttc_contraction_destroy(ttc_contraction_t c);
 
 /*
+ * GEMM consuming the packing routine (the level-3 BLAS use of sub-tensor
+ * transpositions, section 2.1, Figs. 2-3), on the tensor cores:
+ *
+ *     C = alpha * P * Bm
+ *
+ * P is the BF16 panel that ttc_plan(perm, sizes, outer_sizes_A, TTC_F32 ->
+ * TTC_BF16, alpha 1, beta 0) would write (each element of A's sub-tensor
+ * rounded to nearest even), viewed as a column-major M x K matrix: its first
+ * rank_m indices form the row index m, the others the column index k.  Bm is
+ * a column-major K x N BFloat16 matrix (leading dimension K), C a
+ * column-major M x N FP32 matrix (leading dimension M).  P is never written
+ * to memory: each CTA gathers its slice of P from A, rounds it into shared
+ * memory and multiplies it on the tensor cores (tcgen05.mma, FP32
+ * accumulation in tensor memory); alpha scales the FP32 accumulator.
+ *
+ *  ttc_packed_gemm_plan     validate and plan (host only): perm a
+ *                           permutation, 1 <= rank_m < ndim, sizes >= 1,
+ *                           outer >= size, A's span and M, K below 2^31,
+ *                           K a multiple of 8, 1 <= n < 2^31.
+ *  ttc_packed_gemm_execute  enqueue on `stream`.  A (FP32) 4-byte aligned,
+ *                           B (BF16) 16-byte aligned, C 4-byte aligned; C
+ *                           must not overlap A or B (TTC_ERR_ALIAS).
+ *  ttc_packed_gemm_check    synchronous: TTC_ERR_TIMEOUT if a tensor-core
+ *                           wait of any execution on the current device gave
+ *                           up (its C is then incomplete), else TTC_OK.
+ *  ttc_packed_gemm_info     m, n, k.
+ *  ttc_packed_gemm_destroy  release (no work using it may be queued).
+ */
+typedef struct ttc_packed_gemm_s* ttc_packed_gemm_t;
+ttc_status ttc_packed_gemm_plan(ttc_packed_gemm_t* out, int ndim, const int* perm, const int64_t* sizes,
+                                const int64_t* outer_sizes_A, int rank_m, int64_t n, double alpha);
+ttc_status ttc_packed_gemm_execute(ttc_packed_gemm_t g, const float* A, const void* B, float* C,
+                                   ttc_stream_t stream);
+ttc_status ttc_packed_gemm_check(ttc_packed_gemm_t g);
+ttc_status ttc_packed_gemm_info(ttc_packed_gemm_t g, int64_t* m, int64_t* n, int64_t* k);
+ttc_status ttc_packed_gemm_destroy(ttc_packed_gemm_t g);
+
+/*
  * Server: continuous batching of permute-scale-add requests (Eq. 1) that
  * arrive over time.  A scheduler thread admits pending requests in arrival
  * order while the bytes of admitted, unfinished requests (A's and B's

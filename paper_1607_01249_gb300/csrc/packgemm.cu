@@ -1,0 +1,380 @@
+// packgemm.cu -- a GEMM that consumes the packing routine directly (the
+// level-3 BLAS use of TTC's sub-tensor transpositions, section 2.1, Figs.
+// 2-3): C = alpha * P * Bm, where P is the BF16 panel that the permute plan
+// (perm, sizes, outer sizes of A; FP32 -> BF16, round to nearest even) would
+// write, viewed as an M x K column-major matrix, and Bm is a BF16 K x N
+// column-major matrix.  Instead of writing P to memory and reading it back
+// into a GEMM, every CTA gathers its 128 x 64 slice of P straight from A
+// (per-row and per-column offset tables: the permutation splits into an
+// M part and a K part), rounds it to BF16 into shared memory in the tensor
+// cores' K-major layout, and issues tcgen05.mma (M 128, N 128, K 16) into a
+// TMEM accumulator; the epilogue reads TMEM with tcgen05.ld and writes C.
+//
+// Every wait is bounded: a wait that gives up sets the plan's error word,
+// which ttc_packed_gemm_check reports, and the CTA still frees its TMEM.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ttc.h"
+#include "plan_impl.h"
+
+using namespace ttc;
+
+namespace ttc {
+extern std::atomic<int64_t> g_launches;
+}
+
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kBK = 64;     // CTA tile; one MMA is 128 x 128 x 16
+constexpr int kPgThreads = 256;
+constexpr uint32_t kTmemCols = 128;               // FP32 accumulator: 128 lanes x 128 columns
+// shared-memory operand layout without swizzle, K-major: core matrices of
+// 8 rows x 16 bytes (8 BF16 along K), stored 128 bytes apart along K (the
+// leading byte offset) and kBK / 8 * 128 bytes apart along M or N (the stride
+// byte offset)
+constexpr int kCore = 128;
+constexpr int kLBO = kCore;
+constexpr int kSBO = (kBK / 8) * kCore;
+constexpr int kTileBytes = kBM * kBK * 2;          // 16 KiB per operand tile
+// dynamic shared memory per CTA: two tiles, the barrier and the TMEM address,
+// padded so that at most four CTAs are resident on an SM (four 128-column
+// accumulators fill the SM's 512 TMEM columns: no allocation waits)
+constexpr int kPgSmem = 56 * 1024;
+constexpr uint32_t kWaitLimit = 1u << 22;          // polls of one barrier phase before giving up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+// shared-memory matrix descriptor of a K-major tile without swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = uint64_t((saddr >> 4) & 0x3fffu);
+  d |= uint64_t((kLBO >> 4) & 0x3fff) << 16;
+  d |= uint64_t((kSBO >> 4) & 0x3fff) << 32;
+  d |= uint64_t(1) << 46;                          // descriptor version of this architecture
+  return d;                                        // base offset 0, layout type 0 (no swizzle)
+}
+
+// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M x N
+constexpr uint32_t mma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// byte offset of element (row, k) of a tile
+__device__ __forceinline__ int tile_off(int row, int k) {
+  return (row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ bool barrier_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  return uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(lo))) |
+         (uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(hi))) << 16);
+}
+
+__global__ void __launch_bounds__(kPgThreads, 1)
+    packgemm_kernel(const float* __restrict__ A, const int32_t* __restrict__ rowoff,
+                    const int32_t* __restrict__ coloff, const uint16_t* __restrict__ Bm, float* __restrict__ C,
+                    int M, int N, int K, float alpha, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + kTileBytes;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kTileBytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * kTileBytes + 8);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+  const uint32_t bar_a = smem_addr(bar);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int nk = (K + kBK - 1) / kBK;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int kt = 0; kt < nk; ++kt) {
+    const int k0 = kt * kBK;
+    // P slice: 128 rows x 8 groups of 8 k; lanes run along the rows
+    for (int j = 0; j < (kBM * kBK / 8) / kPgThreads; ++j) {
+      const int i = t + kPgThreads * j;
+      const int r = i % kBM, kg = i / kBM;
+      const int m = m0 + r, kb = k0 + kg * 8;
+      float v[8];
+      const int32_t ro = m < M ? rowoff[m] : 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = kb + e;
+        v[e] = (m < M && k < K) ? __ldg(A + (int64_t(ro) + coloff[k])) : 0.f;
+      }
+      const uint4 q = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                                 pack_bf16x2(v[6], v[7]));
+      *reinterpret_cast<uint4*>(sA + tile_off(r, kg * 8)) = q;
+    }
+    // Bm slice: 128 columns n x 8 groups of 8 k, one 16-byte load each (K % 8 == 0)
+    for (int j = 0; j < (kBN * kBK / 8) / kPgThreads; ++j) {
+      const int i = t + kPgThreads * j;
+      const int kg = i % (kBK / 8), r = i / (kBK / 8);
+      const int n = n0 + r, kb = k0 + kg * 8;
+      uint4 q = make_uint4(0u, 0u, 0u, 0u);
+      if (n < N && kb < K) q = __ldg(reinterpret_cast<const uint4*>(Bm + (int64_t(n) * K + kb)));
+      *reinterpret_cast<uint4*>(sB + tile_off(r, kg * 8)) = q;
+    }
+    // the tiles were written by the generic proxy; the tensor cores read them
+    // through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+#pragma unroll
+      for (int s = 0; s < kBK / 16; ++s) {
+        const uint64_t da = smem_desc(a0 + s * 2 * kLBO), db = smem_desc(b0 + s * 2 * kLBO);
+        const uint32_t accumulate = (kt > 0 || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(mma_idesc(kBM, kBN)), "r"(accumulate)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
+                   : "memory");
+    }
+    // the tiles are overwritten next: wait for this stage's MMAs
+    const bool mine = barrier_wait(bar_a, phase);
+    phase ^= 1;
+    ok = __syncthreads_and(ok && mine) != 0;
+    if (!ok) break;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    // accumulator row m0 + 32 * (warp % 4) + lane; warps 0-3 take columns
+    // 0-63, warps 4-7 columns 64-127
+    const int q = warp & 3, h = warp >> 2;
+    const int m = m0 + 32 * q + lane;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int col = 64 * h + 32 * c;
+      uint32_t r[32];
+      const uint32_t taddr = tmem + (uint32_t(32 * q) << 16) + uint32_t(col);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < M) {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          const int n = n0 + col + e;
+          if (n < N) C[int64_t(n) * M + m] = __fmul_rn(alpha, __uint_as_float(r[e]));
+        }
+      }
+    }
+  } else if (t == 0) {
+    atomicExch(err, 1);
+    // give the MMAs in flight a last bounded chance to finish before the
+    // accumulator is released
+    barrier_wait(bar_a, phase ^ 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+struct PgDev {
+  int32_t* tables = nullptr;   // rowoff[M] | coloff[K] | error word
+  int* err = nullptr;
+};
+
+}  // namespace
+
+struct ttc_packed_gemm_s {
+  std::mutex mu;
+  int64_t M = 0, N = 0, K = 0, spanA = 0;
+  float alpha = 1.f;
+  std::vector<int32_t> rowoff, coloff;
+  std::map<int, PgDev> dev;
+  ~ttc_packed_gemm_s() {
+    int cur = 0;
+    const bool have = cudaGetDevice(&cur) == cudaSuccess;
+    for (auto& kv : dev) {
+      if (have) cudaSetDevice(kv.first);
+      if (kv.second.tables) cudaFree(kv.second.tables);
+    }
+    if (have) cudaSetDevice(cur);
+  }
+};
+
+extern "C" {
+
+ttc_status ttc_packed_gemm_plan(ttc_packed_gemm_t* out, int ndim, const int* perm, const int64_t* sizes,
+                                const int64_t* outer_sizes_A, int rank_m, int64_t n, double alpha) {
+  if (!out) return fail(TTC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (ndim < 1 || ndim > kMaxDim || !perm || !sizes) return fail(TTC_ERR_INVALID_PERM, "bad ndim, perm or sizes");
+  std::vector<int> seen(size_t(ndim), 0);
+  for (int d = 0; d < ndim; ++d) {
+    if (perm[d] < 0 || perm[d] >= ndim || seen[size_t(perm[d])]++) return fail(TTC_ERR_INVALID_PERM, "not a permutation");
+  }
+  if (rank_m < 1 || rank_m >= ndim) return fail(TTC_ERR_INVALID_ARG, "rank_m must split the packed indices");
+  if (!std::isfinite(alpha)) return fail(TTC_ERR_INVALID_ARG, "alpha not finite");
+  std::vector<int64_t> strideA(static_cast<size_t>(ndim));
+  int64_t st = 1, span = 1;
+  for (int k = 0; k < ndim; ++k) {
+    const int64_t o = outer_sizes_A ? outer_sizes_A[k] : sizes[k];
+    if (sizes[k] < 1) return fail(TTC_ERR_INVALID_SIZE, "sizes must be >= 1");
+    if (o < sizes[k]) return fail(TTC_ERR_INVALID_OUTER, "outer size below size");
+    strideA[size_t(k)] = st;
+    span += (sizes[k] - 1) * st;
+    st *= o;
+  }
+  if (span >= (int64_t(1) << 31)) return fail(TTC_ERR_INVALID_SIZE, "A spans 2^31 elements or more");
+  std::unique_ptr<ttc_packed_gemm_s> g(new (std::nothrow) ttc_packed_gemm_s());
+  if (!g) return fail(TTC_ERR_OOM, "host allocation failed");
+  // the packed panel's index d is A's index perm[d]; d < rank_m form the
+  // row (M) index, the rest the column (K) index, both column-major
+  auto offsets = [&](int d0, int d1, std::vector<int32_t>* out_offs) -> int64_t {
+    int64_t cnt = 1;
+    for (int d = d0; d < d1; ++d) cnt *= sizes[perm[d]];
+    if (cnt >= (int64_t(1) << 31)) return -1;
+    out_offs->assign(size_t(cnt), 0);
+    for (int64_t i = 0; i < cnt; ++i) {
+      int64_t r = i, off = 0;
+      for (int d = d0; d < d1; ++d) {
+        const int64_t s = sizes[perm[d]];
+        off += (r % s) * strideA[size_t(perm[d])];
+        r /= s;
+      }
+      (*out_offs)[size_t(i)] = int32_t(off);
+    }
+    return cnt;
+  };
+  g->M = offsets(0, rank_m, &g->rowoff);
+  g->K = offsets(rank_m, ndim, &g->coloff);
+  if (g->M < 0 || g->K < 0) return fail(TTC_ERR_INVALID_SIZE, "a GEMM extent exceeds 2^31 - 1");
+  if (g->K % 8) return fail(TTC_ERR_INVALID_SIZE, "K must be a multiple of 8 (16-byte rows of the BF16 matrix)");
+  if (n < 1 || n >= (int64_t(1) << 31) || g->M * n >= (int64_t(1) << 62))
+    return fail(TTC_ERR_INVALID_SIZE, "bad n");
+  if ((g->M + kBM - 1) / kBM > 2147483647 || (n + kBN - 1) / kBN > 65535)
+    return fail(TTC_ERR_INVALID_SIZE, "too many tiles");
+  g->N = n;
+  g->spanA = span;
+  g->alpha = float(alpha);
+  *out = g.release();
+  return TTC_OK;
+}
+
+ttc_status ttc_packed_gemm_execute(ttc_packed_gemm_t g, const float* A, const void* B, float* C,
+                                   ttc_stream_t stream) {
+  if (!g) return fail(TTC_ERR_INVALID_ARG, "plan is NULL");
+  if (!A || !B || !C) return fail(TTC_ERR_INVALID_ARG, "A, B or C is NULL");
+  if (reinterpret_cast<uintptr_t>(A) % 4 || reinterpret_cast<uintptr_t>(C) % 4 ||
+      reinterpret_cast<uintptr_t>(B) % 16)
+    return fail(TTC_ERR_ALIGN, "A and C need 4-byte, B 16-byte alignment");
+  const uintptr_t a = reinterpret_cast<uintptr_t>(A), c = reinterpret_cast<uintptr_t>(C);
+  const uintptr_t b = reinterpret_cast<uintptr_t>(B);
+  const size_t bytesC = size_t(g->M) * size_t(g->N) * 4, bytesA = size_t(g->spanA) * 4;
+  const size_t bytesB = size_t(g->K) * size_t(g->N) * 2;
+  if ((c < a + bytesA && a < c + bytesC) || (c < b + bytesB && b < c + bytesC))
+    return fail(TTC_ERR_ALIAS, "C overlaps A or B");
+  std::lock_guard<std::mutex> lk(g->mu);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  PgDev& d = g->dev[dev];
+  if (!d.tables) {
+    const size_t ints = g->rowoff.size() + g->coloff.size() + 1;
+    e = cudaMalloc(&d.tables, ints * sizeof(int32_t));
+    if (e != cudaSuccess) {
+      d.tables = nullptr;
+      return e == cudaErrorMemoryAllocation ? fail(TTC_ERR_OOM, "table allocation failed")
+                                            : cuda_fail(e, "cudaMalloc");
+    }
+    e = cudaMemcpy(d.tables, g->rowoff.data(), g->rowoff.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(d.tables + g->rowoff.size(), g->coloff.data(), g->coloff.size() * sizeof(int32_t),
+                     cudaMemcpyHostToDevice);
+    d.err = d.tables + g->rowoff.size() + g->coloff.size();
+    if (e == cudaSuccess) e = cudaMemset(d.err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "table upload");
+    e = cudaFuncSetAttribute(packgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPgSmem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  const dim3 grid(unsigned((g->M + kBM - 1) / kBM), unsigned((g->N + kBN - 1) / kBN));
+  packgemm_kernel<<<grid, kPgThreads, kPgSmem, reinterpret_cast<cudaStream_t>(stream)>>>(
+      A, d.tables, d.tables + g->rowoff.size(), static_cast<const uint16_t*>(B), C, int(g->M), int(g->N),
+      int(g->K), g->alpha, d.err);
+  ++g_launches;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? TTC_OK : cuda_fail(e, "packed GEMM launch");
+}
+
+ttc_status ttc_packed_gemm_check(ttc_packed_gemm_t g) {
+  if (!g) return fail(TTC_ERR_INVALID_ARG, "plan is NULL");
+  std::lock_guard<std::mutex> lk(g->mu);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  auto it = g->dev.find(dev);
+  if (it == g->dev.end() || !it->second.err) return TTC_OK;
+  int flag = 0;
+  e = cudaMemcpy(&flag, it->second.err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "error word read");
+  return flag ? fail(TTC_ERR_TIMEOUT, "a tensor-core wait gave up") : TTC_OK;
+}
+
+ttc_status ttc_packed_gemm_info(ttc_packed_gemm_t g, int64_t* m, int64_t* n, int64_t* k) {
+  if (!g) return fail(TTC_ERR_INVALID_ARG, "plan is NULL");
+  if (m) *m = g->M;
+  if (n) *n = g->N;
+  if (k) *k = g->K;
+  return TTC_OK;
+}
+
+ttc_status ttc_packed_gemm_destroy(ttc_packed_gemm_t g) {
+  if (!g) return fail(TTC_ERR_INVALID_ARG, "plan is NULL");
+  delete g;
+  return TTC_OK;
+}
+
+}  // extern "C"

@@ -90,6 +90,12 @@ SIGNATURES = {
     "ttc_contraction_execute": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "ttc_contraction_info": (ctypes.c_int, [_vp, _i64p, _i64p, _i64p, ctypes.POINTER(ctypes.c_int)]),
     "ttc_contraction_destroy": (ctypes.c_int, [_vp]),
+    "ttc_packed_gemm_plan": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i64p,
+                                            _i64p, ctypes.c_int, ctypes.c_int64, ctypes.c_double]),
+    "ttc_packed_gemm_execute": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ttc_packed_gemm_check": (ctypes.c_int, [_vp]),
+    "ttc_packed_gemm_info": (ctypes.c_int, [_vp, _i64p, _i64p, _i64p]),
+    "ttc_packed_gemm_destroy": (ctypes.c_int, [_vp]),
     "ttc_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_int, ctypes.c_int64]),
     "ttc_server_submit": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64p]),
     "ttc_server_poll": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64]),
@@ -316,6 +322,46 @@ class Contraction:
     def close(self):
         if getattr(self, "_h", None):
             lib().ttc_contraction_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PackedGemm:
+    """C = alpha * P * Bm on the tensor cores, P the BF16 panel of the
+    permutation (perm, sizes, outer_a) viewed as M x K (first rank_m indices
+    form m), Bm a K x N BF16 column-major matrix (ttc_packed_gemm_*)."""
+
+    def __init__(self, perm, sizes, rank_m, n, alpha=1.0, outer_a=None):
+        self.perm, self.sizes = tuple(int(p) for p in perm), tuple(int(s) for s in sizes)
+        self.outer_a = tuple(outer_a) if outer_a is not None else None
+        h = ctypes.c_void_p()
+        k = len(self.perm)
+        _check(lib().ttc_packed_gemm_plan(ctypes.byref(h), k, (ctypes.c_int * k)(*self.perm), _i64arr(self.sizes),
+                                          _i64arr(self.outer_a), int(rank_m), int(n), float(alpha)))
+        self._h = h
+
+    def execute(self, A, B, C, stream=None):
+        _check(lib().ttc_packed_gemm_execute(self._h, _ptr(A), _ptr(B), _ptr(C), _stream(stream)))
+        return C
+
+    __call__ = execute
+
+    def check(self):
+        _check(lib().ttc_packed_gemm_check(self._h))
+
+    def info(self) -> dict:
+        m, n, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().ttc_packed_gemm_info(self._h, ctypes.byref(m), ctypes.byref(n), ctypes.byref(k)))
+        return {"m": m.value, "n": n.value, "k": k.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ttc_packed_gemm_destroy(self._h)
             self._h = None
 
     def __del__(self):

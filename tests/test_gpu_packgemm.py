@@ -1,0 +1,99 @@
+"""GPU parity of the tensor-core GEMM that consumes the packing routine
+(ttc_packed_gemm_*): the panel P must be exactly the oracle's FP32 -> BF16
+permutation (round to nearest even) of A's sub-tensor, and C = alpha * P * Bm
+within the FP32-accumulation bound gamma_(K+1) * |alpha| |P| |Bm| (taken with
+a unit roundoff of 2^-23, one bit more than round-to-nearest, since the
+tensor cores' internal accumulation order and rounding are not specified)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1607_01249_gb300 import build as ttc_build
+from paper_1607_01249_gb300 import inputs
+from paper_1607_01249_gb300 import ttc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    ttc_build.build()
+    ttc.lib()
+
+
+def bf16_to_f64(bits):
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def run(perm, sizes, rank_m, n, alpha=1.0, outer=None, seed=0):
+    g = inputs.rng(seed)
+    oa = outer or sizes
+    A = g.uniform(-1, 1, int(np.prod(oa, dtype=np.int64))).astype(np.float32)
+    gemm = ttc.PackedGemm(perm, sizes, rank_m, n, alpha, outer)
+    inf = gemm.info()
+    M, K = inf["m"], inf["k"]
+    Bm = oracle.bf16_from_f32(g.uniform(-1, 1, K * n).astype(np.float32))
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(Bm.view(np.int16)).cuda()
+    dC = torch.full((M * n,), float("nan"), device="cuda")
+    gemm.execute(dA, dB, dC)
+    torch.cuda.synchronize()
+    gemm.check()
+    got = dC.cpu().numpy().astype(np.float64).reshape(n, M).T          # column-major M x N
+    # P: the oracle's permutation with the BF16 downcast, as an M x K column-major matrix
+    sB = [sizes[p] for p in perm]
+    P = np.zeros(int(np.prod(sB, dtype=np.int64)), np.uint16)
+    oracle.permute(perm, sizes, A, P, 1.0, 0.0, oracle.F32, oracle.BF16, outer, None)
+    Pm = bf16_to_f64(P).reshape(K, M).T
+    Bmm = bf16_to_f64(Bm).reshape(n, K).T
+    want = alpha * (Pm @ Bmm)
+    scale = abs(alpha) * (np.abs(Pm) @ np.abs(Bmm))
+    u = 2.0 ** -23
+    gamma = (K + 1) * u / (1 - (K + 1) * u)
+    err = np.abs(got - want)
+    bad = ~(err <= gamma * scale + 1e-30)
+    assert not bad.any(), (perm, sizes, rank_m, n, int(bad.sum()), float(np.nanmax(err)))
+    return gemm
+
+
+def test_packed_gemm_plain_matrix_one_tile():
+    run((0, 1), (128, 64), 1, 128, seed=1)
+
+
+def test_packed_gemm_ragged_edges_and_transposed_operand():
+    # A stored K x M: the panel is its transpose; M, N and K all ragged
+    run((1, 0), (72, 200), 1, 150, alpha=1.5, seed=2)
+
+
+def test_packed_gemm_permuted_4d_operand():
+    # A[a, e, b, f] contracted over (e, f): M = a * b, K = e * f (the TTGT layout)
+    run((0, 2, 1, 3), (20, 8, 13, 9), 2, 96, alpha=-0.75, seed=3)
+
+
+def test_packed_gemm_sub_block_with_outer_sizes():
+    # a 300 x 136 block of a larger 320 x 160 matrix (the packing of section 2.1, Fig. 2)
+    run((0, 1), (300, 136), 1, 257, outer=(320, 160), seed=4)
+
+
+def test_packed_gemm_several_k_stages_and_tiles():
+    run((1, 0, 2), (16, 40, 24), 2, 300, seed=5)          # M = 640, K = 24
+    run((2, 0, 1), (32, 24, 16), 1, 200, seed=6)          # M = 16, K = 768 (12 stages)
+
+
+def test_packed_gemm_host_checks():
+    with pytest.raises(ttc.TTCError) as ei:
+        ttc.PackedGemm((0, 1), (64, 60), 1, 64)           # K = 60 is not a multiple of 8
+    assert ei.value.name == "TTC_ERR_INVALID_SIZE"
+    with pytest.raises(ttc.TTCError) as ei:
+        ttc.PackedGemm((0, 1), (64, 64), 0, 64)
+    assert ei.value.name == "TTC_ERR_INVALID_ARG"
+    g = ttc.PackedGemm((0, 1), (64, 64), 1, 64)
+    A = torch.zeros(64 * 64, device="cuda")
+    B = torch.zeros(64 * 64, dtype=torch.int16, device="cuda")
+    with pytest.raises(ttc.TTCError) as ei:
+        g.execute(A, B, A)
+    assert ei.value.name == "TTC_ERR_ALIAS"
