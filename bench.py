@@ -757,6 +757,99 @@ def run_contraction(args, rank, world):
     }
 
 
+def run_packed_gemm(args, rank, world):
+    """The GEMM that consumes the packing routine (ttc_packed_gemm_*: gather,
+    BF16 rounding and tcgen05.mma in one kernel) against the unfused path:
+    the permute plan writes the BF16 panel to memory, then a cuBLAS BF16
+    GEMM (torch.mm) reads it."""
+    import torch
+    from paper_1607_01249_gb300 import build as ttc_build
+    from paper_1607_01249_gb300 import ttc
+
+    ttc_build.build()
+    ttc.lib()
+    torch.cuda.set_device(rank % max(torch.cuda.device_count(), 1))
+    stream = torch.cuda.current_stream()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    peak = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    steps = max(args.steps, 1)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1) / steps, world)
+
+    cases, tot_flop, tot_ms, launches = [], 0.0, 0.0, 0
+    for c in inputs.packed_gemm_cases():
+        oa = c["outer"] or c["sizes"]
+        A = torch.empty(int(np.prod(oa)), device="cuda").uniform_(-1, 1, generator=g)
+        gemm = ttc.PackedGemm(c["perm"], c["sizes"], c["rank_m"], c["n"], 1.0, c["outer"])
+        inf = gemm.info()
+        M, N, K = inf["m"], inf["n"], inf["k"]
+        B = torch.empty(K * N, device="cuda").uniform_(-1, 1, generator=g).to(torch.bfloat16)
+        C = torch.empty(M * N, device="cuda")
+        l0 = ttc.launch_count()
+        ms = timed(lambda: gemm.execute(A, B, C, stream))
+        launches += (ttc.launch_count() - l0) // (steps + max(args.warmup, 3))
+        gemm.check()
+        plan = ttc.Plan(c["perm"], c["sizes"], "f32", "bf16", outer_a=c["outer"])
+        P = torch.empty(M * K, device="cuda", dtype=torch.bfloat16)
+        Bt, Pt = B.view(N, K), P.view(K, M)
+        # cuBLAS with an FP32 result where this torch has it, else a BF16 result
+        # (half the result bytes: favours the unfused path)
+        try:
+            torch.mm(Bt, Pt, out_dtype=torch.float32)
+            mm_out = "f32"
+        except (TypeError, RuntimeError):
+            mm_out = "bf16"
+
+        def unfused():
+            plan.execute(A, P, stream)
+            if mm_out == "f32":
+                torch.mm(Bt, Pt, out_dtype=torch.float32)
+            else:
+                torch.mm(Bt, Pt)
+
+        ms_unfused = timed(unfused)
+        ms_pack = timed(lambda: plan.execute(A, P, stream))
+        flop = 2.0 * M * N * K
+        tf = world * flop / (ms * 1e-3) / 1e12
+        cases.append({"case": c["tag"], "m": M, "n": N, "k": K, "fused_ms": round(ms, 4),
+                      "fused_TFLOP/s": round(tf, 1), "unfused_ms": round(ms_unfused, 4),
+                      "unfused_pack_ms": round(ms_pack, 4), "unfused_gemm_result": mm_out,
+                      "unfused_TFLOP/s": round(world * flop / (ms_unfused * 1e-3) / 1e12, 1),
+                      "speedup_vs_unfused": round(ms_unfused / ms, 3),
+                      "frac_of_bf16_peak": round(tf / world / peak, 3) if peak else None})
+        tot_flop += flop
+        tot_ms += ms
+        del A, B, C, P
+        gemm.close()
+    value = world * tot_flop / (tot_ms * 1e-3) / 1e12
+    return {"metric": "packed-operand GEMM TFLOP/s (2 m n k)", "value": round(value, 2), "unit": "TFLOP/s",
+            "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": round(tot_ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 operands (f32 A packed on the fly), f32 accumulation",
+            "data": "synthetic (uniform[-1,1], torch Philox on the device)",
+            "config": {"workload": "packed GEMM " + ", ".join(c["tag"] for c in inputs.packed_gemm_cases()),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "tensor", "peak": peak, "unit": "TFLOP/s",
+                         "achieved": round(value / world, 1), "frac": round(value / world / peak, 4) if peak else None,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"},
+            "cases": cases, "gpu_launches": launches}
+
+
 def run_serving_line(args, rank, world):
     s = run_serving(args, rank, world)
     c = s["continuous"]
@@ -919,9 +1012,9 @@ def cpu_baseline(budget_s: float, probs, threads: int):
 
 
 def run_reference(args, rank, world):
-    if args.workload == "contraction":
-        return {"impl": "reference", "unavailable": "the contraction workload has no timed CPU arm (its oracle is "
-                                                    "numpy.einsum in float64, a test reference only)"}
+    if args.workload in ("contraction", "packgemm"):
+        return {"impl": "reference", "unavailable": "the GEMM workloads have no timed CPU arm (their oracles are "
+                                                    "numpy contractions in float64, test references only)"}
     probs = workload_problems(args.workload, args.target, args.only)
     threads = os.cpu_count() or 1
     import oracle
@@ -958,7 +1051,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "pow2", "complex", "single4d", "packing", "batch", "serving", "contraction"])
+                    choices=["sweep", "pow2", "complex", "single4d", "packing", "batch", "serving", "contraction",
+                             "packgemm"])
     ap.add_argument("--serve-count", type=int, default=1500)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
@@ -1002,6 +1096,8 @@ def main():
         out = run_batch(args, rank, world)
     elif args.workload == "contraction":
         out = run_contraction(args, rank, world)
+    elif args.workload == "packgemm":
+        out = run_packed_gemm(args, rank, world)
     elif args.workload == "serving":
         out = run_serving_line(args, rank, world)
     else:
@@ -1030,6 +1126,9 @@ def main():
                                   "per_variant": r["per_variant"], "roofline_frac": r["roofline"]["frac"],
                                   "fp64_pipe": r.get("fp64_pipe"), "timing": "CUDA events"}
             if not args.no_contraction:
+                pg = run_packed_gemm(sub, rank, world)
+                out["packed_gemm"] = {"workload": pg["config"]["workload"], "TFLOP/s": pg["value"],
+                                      "roofline": pg["roofline"], "cases": pg["cases"], "timing": "CUDA events"}
                 ct = run_contraction(sub, rank, world)
                 out["contraction"] = {"workload": ct["config"]["workload"], "TFLOP/s": ct["value"],
                                       "cases": ct["cases"], "timing": "CUDA events"}
@@ -1052,7 +1151,7 @@ def main():
                                   "saturated_speedup_vs_per_call": sv["saturated_speedup_vs_per_call"],
                                   "timing": "host steady clock, arrival to detected completion"}
     if rank == 0:
-        if not args.no_cpu and world == 1 and args.workload not in ("batch", "serving", "contraction"):
+        if not args.no_cpu and world == 1 and args.workload not in ("batch", "serving", "contraction", "packgemm"):
             out["cpu_baseline"] = cpu_baseline(args.cpu_budget,
                                                workload_problems(args.workload, args.target, args.only),
                                                os.cpu_count() or 1)

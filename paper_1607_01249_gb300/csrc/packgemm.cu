@@ -46,10 +46,11 @@ constexpr int kCore = 128;
 constexpr int kLBO = kCore;
 constexpr int kSBO = (kBK / 8) * kCore;
 constexpr int kTileBytes = kBM * kBK * 2;          // 16 KiB per operand tile
-// dynamic shared memory per CTA: two tiles, the barrier and the TMEM address,
-// padded so that at most four CTAs are resident on an SM (four 128-column
-// accumulators fill the SM's 512 TMEM columns: no allocation waits)
-constexpr int kPgSmem = 56 * 1024;
+// dynamic shared memory per CTA: two buffers of two tiles, two barriers and
+// the TMEM address, padded so that at most three CTAs are resident on an SM
+// (three 128-column accumulators fit the SM's 512 TMEM columns: no
+// allocation waits)
+constexpr int kPgSmem = 72 * 1024;
 constexpr uint32_t kWaitLimit = 1u << 22;          // polls of one barrier phase before giving up
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -94,18 +95,83 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
          (uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(hi))) << 16);
 }
 
-__global__ void __launch_bounds__(kPgThreads, 1)
+// One stage's operand slices, staged in registers between the global loads
+// and the shared-memory stores, so that the next stage's loads are in flight
+// while the tensor cores work on the current one.
+struct StageRegs {
+  float a[4][8];   // four (row, 8 k) items of P
+  uint4 b[4];      // four (column, 8 k) items of Bm
+};
+
+// KVEC: A's stride-1 index lies among the K indices (each group of 8 k is 8
+// consecutive, 16-byte aligned floats of A): lanes run along k with two
+// 16-byte loads per item; else lanes run along the rows with 8 scalar loads.
+template <bool KVEC>
+__device__ __forceinline__ void load_stage(StageRegs& R, int t, int m0, int n0, int k0, const float* __restrict__ A,
+                                           const int32_t* __restrict__ rowoff, const int32_t* __restrict__ coloff,
+                                           const uint16_t* __restrict__ Bm, int M, int N, int K) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i = t + kPgThreads * j;
+    const int r = KVEC ? i / (kBK / 8) : i % kBM, kg = KVEC ? i % (kBK / 8) : i / kBM;
+    const int m = m0 + r, kb = k0 + kg * 8;
+    if (KVEC) {
+      float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+      if (m < M && kb < K) {
+        const float4* p = reinterpret_cast<const float4*>(A + (int64_t(rowoff[m]) + coloff[kb]));
+        lo = __ldg(p);
+        hi = __ldg(p + 1);
+      }
+      R.a[j][0] = lo.x; R.a[j][1] = lo.y; R.a[j][2] = lo.z; R.a[j][3] = lo.w;
+      R.a[j][4] = hi.x; R.a[j][5] = hi.y; R.a[j][6] = hi.z; R.a[j][7] = hi.w;
+    } else {
+      const int32_t ro = m < M ? rowoff[m] : 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = kb + e;
+        R.a[j][e] = (m < M && k < K) ? __ldg(A + (int64_t(ro) + coloff[k])) : 0.f;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i = t + kPgThreads * j;
+    const int kg = i % (kBK / 8), r = i / (kBK / 8);
+    const int n = n0 + r, kb = k0 + kg * 8;
+    R.b[j] = (n < N && kb < K) ? __ldg(reinterpret_cast<const uint4*>(Bm + (int64_t(n) * K + kb)))
+                               : make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+template <bool KVEC>
+__device__ __forceinline__ void store_stage(const StageRegs& R, int t, uint8_t* sA, uint8_t* sB) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i = t + kPgThreads * j;
+    const int r = KVEC ? i / (kBK / 8) : i % kBM, kg = KVEC ? i % (kBK / 8) : i / kBM;
+    *reinterpret_cast<uint4*>(sA + tile_off(r, kg * 8)) =
+        make_uint4(pack_bf16x2(R.a[j][0], R.a[j][1]), pack_bf16x2(R.a[j][2], R.a[j][3]),
+                   pack_bf16x2(R.a[j][4], R.a[j][5]), pack_bf16x2(R.a[j][6], R.a[j][7]));
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i = t + kPgThreads * j;
+    *reinterpret_cast<uint4*>(sB + tile_off(i / (kBK / 8), (i % (kBK / 8)) * 8)) = R.b[j];
+  }
+}
+
+template <bool KVEC>
+__global__ void __launch_bounds__(kPgThreads, 3)
     packgemm_kernel(const float* __restrict__ A, const int32_t* __restrict__ rowoff,
                     const int32_t* __restrict__ coloff, const uint16_t* __restrict__ Bm, float* __restrict__ C,
                     int M, int N, int K, float alpha, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + kTileBytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kTileBytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * kTileBytes + 8);
+  // two buffers of (A slice, B slice), one barrier each
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * kTileBytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 4 * kTileBytes + 16);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
-  const uint32_t bar_a = smem_addr(bar);
+  const uint32_t bar0 = smem_addr(bars);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
@@ -114,7 +180,8 @@ __global__ void __launch_bounds__(kPgThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -123,37 +190,24 @@ __global__ void __launch_bounds__(kPgThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   const int nk = (K + kBK - 1) / kBK;
-  uint32_t phase = 0;
   bool ok = true;
+  int issued = -1;   // last stage whose MMAs were committed
+  StageRegs R;
+  load_stage<KVEC>(R, t, m0, n0, 0, A, rowoff, coloff, Bm, M, N, K);
   for (int kt = 0; kt < nk; ++kt) {
-    const int k0 = kt * kBK;
-    // P slice: 128 rows x 8 groups of 8 k; lanes run along the rows
-    for (int j = 0; j < (kBM * kBK / 8) / kPgThreads; ++j) {
-      const int i = t + kPgThreads * j;
-      const int r = i % kBM, kg = i / kBM;
-      const int m = m0 + r, kb = k0 + kg * 8;
-      float v[8];
-      const int32_t ro = m < M ? rowoff[m] : 0;
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int k = kb + e;
-        v[e] = (m < M && k < K) ? __ldg(A + (int64_t(ro) + coloff[k])) : 0.f;
-      }
-      const uint4 q = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                                 pack_bf16x2(v[6], v[7]));
-      *reinterpret_cast<uint4*>(sA + tile_off(r, kg * 8)) = q;
+    const int buf = kt & 1;
+    uint8_t* sA = smem + buf * 2 * kTileBytes;
+    uint8_t* sB = sA + kTileBytes;
+    // this buffer was last read by the MMAs of stage kt - 2 (the j-th use of
+    // a buffer completes its barrier's phase j)
+    if (kt >= 2) {
+      const bool mine = barrier_wait(bar0 + 8 * buf, uint32_t((kt - 2) >> 1) & 1u);
+      ok = __syncthreads_and(ok && mine) != 0;
+      if (!ok) break;
     }
-    // Bm slice: 128 columns n x 8 groups of 8 k, one 16-byte load each (K % 8 == 0)
-    for (int j = 0; j < (kBN * kBK / 8) / kPgThreads; ++j) {
-      const int i = t + kPgThreads * j;
-      const int kg = i % (kBK / 8), r = i / (kBK / 8);
-      const int n = n0 + r, kb = k0 + kg * 8;
-      uint4 q = make_uint4(0u, 0u, 0u, 0u);
-      if (n < N && kb < K) q = __ldg(reinterpret_cast<const uint4*>(Bm + (int64_t(n) * K + kb)));
-      *reinterpret_cast<uint4*>(sB + tile_off(r, kg * 8)) = q;
-    }
-    // the tiles were written by the generic proxy; the tensor cores read them
-    // through the async proxy
+    store_stage<KVEC>(R, t, sA, sB);
+    // the slices were written by the generic proxy; the tensor cores read
+    // them through the async proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (t == 0) {
@@ -170,14 +224,16 @@ __global__ void __launch_bounds__(kPgThreads, 1)
             "l"(da), "l"(db), "r"(mma_idesc(kBM, kBN)), "r"(accumulate)
             : "memory");
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar0 + 8 * buf)
                    : "memory");
     }
-    // the tiles are overwritten next: wait for this stage's MMAs
-    const bool mine = barrier_wait(bar_a, phase);
-    phase ^= 1;
-    ok = __syncthreads_and(ok && mine) != 0;
-    if (!ok) break;
+    issued = kt;
+    if (kt + 1 < nk) load_stage<KVEC>(R, t, m0, n0, (kt + 1) * kBK, A, rowoff, coloff, Bm, M, N, K);
+  }
+  // the last commit completes when every MMA before it has completed
+  if (ok && issued >= 0) {
+    const bool mine = barrier_wait(bar0 + 8 * (issued & 1), uint32_t(issued >> 1) & 1u);
+    ok = __syncthreads_and(mine) != 0;
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
@@ -212,7 +268,7 @@ __global__ void __launch_bounds__(kPgThreads, 1)
     atomicExch(err, 1);
     // give the MMAs in flight a last bounded chance to finish before the
     // accumulator is released
-    barrier_wait(bar_a, phase ^ 1);
+    if (issued >= 0) barrier_wait(bar0 + 8 * (issued & 1), uint32_t(issued >> 1) & 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -232,6 +288,7 @@ struct ttc_packed_gemm_s {
   std::mutex mu;
   int64_t M = 0, N = 0, K = 0, spanA = 0;
   float alpha = 1.f;
+  bool kvec = false;   // every group of 8 k is 8 consecutive floats of A, 16-byte aligned relative to A
   std::vector<int32_t> rowoff, coloff;
   std::map<int, PgDev> dev;
   ~ttc_packed_gemm_s() {
@@ -300,6 +357,14 @@ ttc_status ttc_packed_gemm_plan(ttc_packed_gemm_t* out, int ndim, const int* per
   g->N = n;
   g->spanA = span;
   g->alpha = float(alpha);
+  g->kvec = true;
+  for (int64_t k = 0; k < g->K && g->kvec; k += 8) {
+    if (g->coloff[size_t(k)] % 4) g->kvec = false;
+    for (int e = 1; e < 8 && g->kvec; ++e)
+      if (g->coloff[size_t(k + e)] != g->coloff[size_t(k)] + e) g->kvec = false;
+  }
+  for (int64_t m = 0; m < g->M && g->kvec; ++m)
+    if (g->rowoff[size_t(m)] % 4) g->kvec = false;
   *out = g.release();
   return TTC_OK;
 }
@@ -337,13 +402,21 @@ ttc_status ttc_packed_gemm_execute(ttc_packed_gemm_t g, const float* A, const vo
     d.err = d.tables + g->rowoff.size() + g->coloff.size();
     if (e == cudaSuccess) e = cudaMemset(d.err, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "table upload");
-    e = cudaFuncSetAttribute(packgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPgSmem);
+    e = cudaFuncSetAttribute(packgemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPgSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(packgemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPgSmem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   }
   const dim3 grid(unsigned((g->M + kBM - 1) / kBM), unsigned((g->N + kBN - 1) / kBN));
-  packgemm_kernel<<<grid, kPgThreads, kPgSmem, reinterpret_cast<cudaStream_t>(stream)>>>(
-      A, d.tables, d.tables + g->rowoff.size(), static_cast<const uint16_t*>(B), C, int(g->M), int(g->N),
-      int(g->K), g->alpha, d.err);
+  const int32_t* rows = d.tables;
+  const int32_t* cols = d.tables + g->rowoff.size();
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (g->kvec && reinterpret_cast<uintptr_t>(A) % 16 == 0)
+    packgemm_kernel<true><<<grid, kPgThreads, kPgSmem, s>>>(A, rows, cols, static_cast<const uint16_t*>(B), C,
+                                                             int(g->M), int(g->N), int(g->K), g->alpha, d.err);
+  else
+    packgemm_kernel<false><<<grid, kPgThreads, kPgSmem, s>>>(A, rows, cols, static_cast<const uint16_t*>(B), C,
+                                                              int(g->M), int(g->N), int(g->K), g->alpha, d.err);
   ++g_launches;
   e = cudaGetLastError();
   return e == cudaSuccess ? TTC_OK : cuda_fail(e, "packed GEMM launch");

@@ -220,6 +220,19 @@ def contraction_cases() -> list:
     ]
 
 
+def packed_gemm_cases() -> list:
+    """GEMMs whose left operand is a packed (permuted, sub-tensor, BF16)
+    panel of an FP32 tensor (section 2.1, Figs. 2-3):
+    * subblock: a 4096 x 2048 block of an 8192 x 8192 matrix, N = 4096;
+    * transposed: the same extents with A stored K x M;
+    * ttgt4d: A[a,e,b,f], all extents 48, packed as (a b) x (e f), N = 2304."""
+    return [
+        {"tag": "subblock", "perm": (0, 1), "sizes": (4096, 2048), "outer": (8192, 8192), "rank_m": 1, "n": 4096},
+        {"tag": "transposed", "perm": (1, 0), "sizes": (2048, 4096), "outer": None, "rank_m": 1, "n": 4096},
+        {"tag": "ttgt4d", "perm": (0, 2, 1, 3), "sizes": (48, 48, 48, 48), "outer": None, "rank_m": 2, "n": 2304},
+    ]
+
+
 def batch_problems(count: int = 4096, seed: int = 3, lo_log2=10, hi_log2=22,
                    Nmin=2, Nmax=5) -> list:
     g = rng(seed)
