@@ -38,13 +38,15 @@ namespace {
 constexpr int kBM = 128, kBN = 128, kBK = 64;     // CTA tile; one MMA is 128 x 128 x 16
 constexpr int kPgThreads = 256;
 constexpr uint32_t kTmemCols = 128;               // FP32 accumulator: 128 lanes x 128 columns
-// shared-memory operand layout without swizzle, K-major: core matrices of
-// 8 rows x 16 bytes (8 BF16 along K), stored 128 bytes apart along K (the
-// leading byte offset) and kBK / 8 * 128 bytes apart along M or N (the stride
-// byte offset)
-constexpr int kCore = 128;
-constexpr int kLBO = kCore;
-constexpr int kSBO = (kBK / 8) * kCore;
+// shared-memory operand layout: K-major with the 128-byte swizzle.  A row of
+// a tile is its kBK = 64 BF16 (128 bytes) along K; 8 rows form a 1024-byte
+// atom (the stride byte offset between 8-row groups), and inside an atom the
+// 16-byte chunk c of row r sits at chunk c ^ r, so that 8 lanes storing
+// either 8 chunks of one row or one chunk of 8 rows hit 32 distinct banks.
+// One MMA (K = 16) reads 32 bytes of every row: its descriptor starts 32
+// bytes further per K step, and the hardware applies the same XOR.
+constexpr int kSBO = 8 * kBK * 2;
+constexpr uint64_t kSwizzle128B = 2;               // descriptor layout type
 constexpr int kTileBytes = kBM * kBK * 2;          // 16 KiB per operand tile
 // dynamic shared memory per CTA: two buffers of two tiles, two barriers and
 // the TMEM address, padded so that at most three CTAs are resident on an SM
@@ -55,13 +57,16 @@ constexpr uint32_t kWaitLimit = 1u << 22;          // polls of one barrier phase
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
-// shared-memory matrix descriptor of a K-major tile without swizzle
+// shared-memory matrix descriptor of a K-major tile with the 128-byte
+// swizzle (atoms 1024-byte aligned: base offset 0; the leading byte offset
+// is unused when one MMA's K lies inside a row, and is set to 16 bytes)
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = uint64_t((saddr >> 4) & 0x3fffu);
-  d |= uint64_t((kLBO >> 4) & 0x3fff) << 16;
+  d |= uint64_t(1) << 16;
   d |= uint64_t((kSBO >> 4) & 0x3fff) << 32;
   d |= uint64_t(1) << 46;                          // descriptor version of this architecture
-  return d;                                        // base offset 0, layout type 0 (no swizzle)
+  d |= kSwizzle128B << 61;
+  return d;
 }
 
 // instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
@@ -70,9 +75,10 @@ constexpr uint32_t mma_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
-// byte offset of element (row, k) of a tile
+// byte offset of element (row, k) of a tile (k a multiple of 8: the start of
+// a 16-byte chunk)
 __device__ __forceinline__ int tile_off(int row, int k) {
-  return (row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2;
+  return (row >> 3) * kSBO + (row & 7) * (kBK * 2) + ((((k >> 3) ^ row) & 7) << 4);
 }
 
 __device__ __forceinline__ bool barrier_wait(uint32_t bar, uint32_t parity) {
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(kPgThreads, 3)
       const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
 #pragma unroll
       for (int s = 0; s < kBK / 16; ++s) {
-        const uint64_t da = smem_desc(a0 + s * 2 * kLBO), db = smem_desc(b0 + s * 2 * kLBO);
+        const uint64_t da = smem_desc(a0 + s * 32), db = smem_desc(b0 + s * 32);
         const uint32_t accumulate = (kt > 0 || s > 0) ? 1u : 0u;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
