@@ -4,10 +4,10 @@
 // (perm, sizes, outer sizes of A; FP32 -> BF16, round to nearest even) would
 // write, viewed as an M x K column-major matrix, and Bm is a BF16 K x N
 // column-major matrix.  Instead of writing P to memory and reading it back
-// into a GEMM, every CTA gathers its 128 x 64 slice of P straight from A
+// into a GEMM, every CTA gathers its 128 x 64 slices of P straight from A
 // (per-row and per-column offset tables: the permutation splits into an
 // M part and a K part), rounds it to BF16 into shared memory in the tensor
-// cores' K-major layout, and issues tcgen05.mma (M 128, N 128, K 16) into a
+// cores' K-major layout, and issues tcgen05.mma (M 128, N 256, K 16) into a
 // TMEM accumulator; the epilogue reads TMEM with tcgen05.ld and writes C.
 //
 // Every wait is bounded: a wait that gives up sets the plan's error word,
@@ -35,9 +35,9 @@ extern std::atomic<int64_t> g_launches;
 
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 64;     // CTA tile; one MMA is 128 x 128 x 16
+constexpr int kBM = 128, kBN = 256, kBK = 64;     // CTA tile; one MMA is 128 x 256 x 16
 constexpr int kPgThreads = 256;
-constexpr uint32_t kTmemCols = 128;               // FP32 accumulator: 128 lanes x 128 columns
+constexpr uint32_t kTmemCols = 256;               // FP32 accumulator: 128 lanes x 256 columns
 // shared-memory operand layout: K-major with the 128-byte swizzle.  A row of
 // a tile is its kBK = 64 BF16 (128 bytes) along K; 8 rows form a 1024-byte
 // atom (the stride byte offset between 8-row groups), and inside an atom the
@@ -47,12 +47,14 @@ constexpr uint32_t kTmemCols = 128;               // FP32 accumulator: 128 lanes
 // bytes further per K step, and the hardware applies the same XOR.
 constexpr int kSBO = 8 * kBK * 2;
 constexpr uint64_t kSwizzle128B = 2;               // descriptor layout type
-constexpr int kTileBytes = kBM * kBK * 2;          // 16 KiB per operand tile
+constexpr int kTileA = kBM * kBK * 2;              // 16 KiB: the slice of P
+constexpr int kTileB = kBN * kBK * 2;              // 32 KiB: the slice of Bm
+constexpr int kStage = kTileA + kTileB;
 // dynamic shared memory per CTA: two buffers of two tiles, two barriers and
-// the TMEM address, padded so that at most three CTAs are resident on an SM
-// (three 128-column accumulators fit the SM's 512 TMEM columns: no
+// the TMEM address, padded so that at most two CTAs are resident on an SM
+// (two 256-column accumulators fill the SM's 512 TMEM columns: no
 // allocation waits)
-constexpr int kPgSmem = 72 * 1024;
+constexpr int kPgSmem = 100 * 1024;
 constexpr uint32_t kWaitLimit = 1u << 22;          // polls of one barrier phase before giving up
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -106,7 +108,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // while the tensor cores work on the current one.
 struct StageRegs {
   float a[4][8];   // four (row, 8 k) items of P
-  uint4 b[4];      // four (column, 8 k) items of Bm
+  uint4 b[8];      // eight (column, 8 k) items of Bm
 };
 
 // KVEC: A's stride-1 index lies among the K indices (each group of 8 k is 8
@@ -140,7 +142,7 @@ __device__ __forceinline__ void load_stage(StageRegs& R, int t, int m0, int n0, 
     }
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < (kBN * kBK / 8) / kPgThreads; ++j) {
     const int i = t + kPgThreads * j;
     const int kg = i % (kBK / 8), r = i / (kBK / 8);
     const int n = n0 + r, kb = k0 + kg * 8;
@@ -160,21 +162,21 @@ __device__ __forceinline__ void store_stage(const StageRegs& R, int t, uint8_t* 
                    pack_bf16x2(R.a[j][4], R.a[j][5]), pack_bf16x2(R.a[j][6], R.a[j][7]));
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < (kBN * kBK / 8) / kPgThreads; ++j) {
     const int i = t + kPgThreads * j;
     *reinterpret_cast<uint4*>(sB + tile_off(i / (kBK / 8), (i % (kBK / 8)) * 8)) = R.b[j];
   }
 }
 
 template <bool KVEC>
-__global__ void __launch_bounds__(kPgThreads, 3)
+__global__ void __launch_bounds__(kPgThreads, 2)
     packgemm_kernel(const float* __restrict__ A, const int32_t* __restrict__ rowoff,
                     const int32_t* __restrict__ coloff, const uint16_t* __restrict__ Bm, float* __restrict__ C,
                     int M, int N, int K, float alpha, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   // two buffers of (A slice, B slice), one barrier each
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * kTileBytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 4 * kTileBytes + 16);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kStage);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * kStage + 16);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
   const uint32_t bar0 = smem_addr(bars);
@@ -202,8 +204,8 @@ __global__ void __launch_bounds__(kPgThreads, 3)
   load_stage<KVEC>(R, t, m0, n0, 0, A, rowoff, coloff, Bm, M, N, K);
   for (int kt = 0; kt < nk; ++kt) {
     const int buf = kt & 1;
-    uint8_t* sA = smem + buf * 2 * kTileBytes;
-    uint8_t* sB = sA + kTileBytes;
+    uint8_t* sA = smem + buf * kStage;
+    uint8_t* sB = sA + kTileA;
     // this buffer was last read by the MMAs of stage kt - 2 (the j-th use of
     // a buffer completes its barrier's phase j)
     if (kt >= 2) {
@@ -243,13 +245,13 @@ __global__ void __launch_bounds__(kPgThreads, 3)
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
-    // accumulator row m0 + 32 * (warp % 4) + lane; warps 0-3 take columns
-    // 0-63, warps 4-7 columns 64-127
+    // accumulator row m0 + 32 * (warp % 4) + lane; warps 0-3 take the first
+    // half of the columns, warps 4-7 the second
     const int q = warp & 3, h = warp >> 2;
     const int m = m0 + 32 * q + lane;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int col = 64 * h + 32 * c;
+#pragma unroll 1
+    for (int c = 0; c < kBN / 64; ++c) {
+      const int col = (kBN / 2) * h + 32 * c;
       uint32_t r[32];
       const uint32_t taddr = tmem + (uint32_t(32 * q) << 16) + uint32_t(col);
       asm volatile(
