@@ -401,3 +401,33 @@ def test_contraction_plan_validation_and_layouts():
     # the BF16 GEMM path always packs (downcasts) both operands
     assert C((0, 1), (4, 5), (1, 2), (5, 6), (0, 2), (4, 6), "f32", "bf16").info()["permuted"] == {
         "A": True, "B": True, "C": False}
+
+
+def test_packed_gemm_plan_on_the_host():
+    """ttc_packed_gemm_plan validates and splits the packed panel on the host
+    (no device work): M is the product of the first rank_m packed indices, K
+    of the rest."""
+    g = ttc.PackedGemm((0, 2, 1, 3), (20, 8, 13, 9), 2, 96)
+    assert g.info() == {"m": 20 * 13, "n": 96, "k": 8 * 9}
+    g = ttc.PackedGemm((0, 1), (4096, 2048), 1, 4096, outer_a=(8192, 8192))
+    assert g.info() == {"m": 4096, "n": 4096, "k": 2048}
+    for args, status in [(((0, 1), (64, 60), 1, 64), "TTC_ERR_INVALID_SIZE"),      # K not a multiple of 8
+                         (((0, 1), (64, 64), 0, 64), "TTC_ERR_INVALID_ARG"),       # rank_m must split
+                         (((0, 1), (64, 64), 2, 64), "TTC_ERR_INVALID_ARG"),
+                         (((0, 0), (64, 64), 1, 64), "TTC_ERR_INVALID_PERM"),
+                         (((0, 1), (64, 64), 1, 0), "TTC_ERR_INVALID_SIZE"),       # n >= 1
+                         (((0, 1), (0, 64), 1, 64), "TTC_ERR_INVALID_SIZE")]:
+        with pytest.raises(ttc.TTCError) as ei:
+            ttc.PackedGemm(*args)
+        assert ei.value.name == status, args
+    with pytest.raises(ttc.TTCError) as ei:
+        ttc.PackedGemm((0, 1), (64, 64), 1, 64, outer_a=(32, 64))
+    assert ei.value.name == "TTC_ERR_INVALID_OUTER"
+    # execute checks come before any device work
+    g = ttc.PackedGemm((0, 1), (64, 64), 1, 64)
+    with pytest.raises(ttc.TTCError) as ei:
+        g.execute(0x100000, 0x200008, 0x300000)     # B not 16-byte aligned
+    assert ei.value.name == "TTC_ERR_ALIGN"
+    with pytest.raises(ttc.TTCError) as ei:
+        g.execute(0x100000, 0x200000, 0x100000 + 64)  # C inside A
+    assert ei.value.name == "TTC_ERR_ALIAS"
