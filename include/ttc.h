@@ -346,8 +346,9 @@ ttc_status ttc_contraction_destroy(ttc_contraction_t c);
  *                           B (BF16) 16-byte aligned, C 4-byte aligned; C
  *                           must not overlap A or B (TTC_ERR_ALIAS).
  *  ttc_packed_gemm_check    synchronous: TTC_ERR_TIMEOUT if a tensor-core
- *                           wait of any execution on the current device gave
- *                           up (its C is then incomplete), else TTC_OK.
+ *                           wait of an execution on the current device gave
+ *                           up since the last check (that C is incomplete;
+ *                           the error is reported once), else TTC_OK.
  *  ttc_packed_gemm_info     m, n, k.
  *  ttc_packed_gemm_destroy  release (no work using it may be queued).
  */

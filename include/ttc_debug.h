@@ -56,6 +56,16 @@ ttc_status ttc_debug_slot_tables(ttc_plan_t plan, int candidate, int32_t* out, i
 ttc_status ttc_debug_server_set_watchdog(ttc_server_t server, double seconds);
 ttc_status ttc_debug_server_submit_delay(ttc_server_t server, int64_t microseconds, int64_t* ticket);
 
+/*
+ * Failure detection of the packed GEMM's bounded waits without a GPU fault:
+ * with skip != 0 the plan's next executions issue no tensor-core MMA and
+ * commit nothing, so every mbarrier wait runs out (after 2^12 polls under
+ * this hook); the kernel records the error word, frees its tensor memory and
+ * returns without writing C, and ttc_packed_gemm_check reports
+ * TTC_ERR_TIMEOUT (once).  skip = 0 restores normal executions.
+ */
+ttc_status ttc_debug_packed_gemm_skip_mma(ttc_packed_gemm_t g, int skip);
+
 #ifdef __cplusplus
 }
 #endif

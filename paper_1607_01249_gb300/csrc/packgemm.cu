@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "../../include/ttc.h"
+#include "../../include/ttc_debug.h"
 #include "plan_impl.h"
 
 using namespace ttc;
@@ -56,6 +57,7 @@ constexpr int kStage = kTileA + kTileB;
 // allocation waits)
 constexpr int kPgSmem = 100 * 1024;
 constexpr uint32_t kWaitLimit = 1u << 22;          // polls of one barrier phase before giving up
+constexpr uint32_t kTestWaitLimit = 1u << 12;      // the same under the testing hook that skips the MMAs
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
@@ -83,8 +85,8 @@ __device__ __forceinline__ int tile_off(int row, int k) {
   return (row >> 3) * kSBO + (row & 7) * (kBK * 2) + ((((k >> 3) ^ row) & 7) << 4);
 }
 
-__device__ __forceinline__ bool barrier_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+__device__ __forceinline__ bool barrier_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -172,8 +174,11 @@ template <bool KVEC>
 __global__ void __launch_bounds__(kPgThreads, 2)
     packgemm_kernel(const float* __restrict__ A, const int32_t* __restrict__ rowoff,
                     const int32_t* __restrict__ coloff, const uint16_t* __restrict__ Bm, float* __restrict__ C,
-                    int M, int N, int K, float alpha, int* err) {
+                    int M, int N, int K, float alpha, int* err, int skip_mma) {
   extern __shared__ __align__(1024) uint8_t smem[];
+  // skip_mma (testing hook): no MMA is issued or committed, so every wait
+  // runs out and takes the error path
+  const uint32_t wait_limit = skip_mma ? kTestWaitLimit : kWaitLimit;
   // two buffers of (A slice, B slice), one barrier each
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kStage);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * kStage + 16);
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(kPgThreads, 2)
     // this buffer was last read by the MMAs of stage kt - 2 (the j-th use of
     // a buffer completes its barrier's phase j)
     if (kt >= 2) {
-      const bool mine = barrier_wait(bar0 + 8 * buf, uint32_t((kt - 2) >> 1) & 1u);
+      const bool mine = barrier_wait(bar0 + 8 * buf, uint32_t((kt - 2) >> 1) & 1u, wait_limit);
       ok = __syncthreads_and(ok && mine) != 0;
       if (!ok) break;
     }
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(kPgThreads, 2)
     // them through the async proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (t == 0) {
+    if (t == 0 && !skip_mma) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
 #pragma unroll
@@ -235,12 +240,12 @@ __global__ void __launch_bounds__(kPgThreads, 2)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar0 + 8 * buf)
                    : "memory");
     }
-    issued = kt;
+    if (!skip_mma) issued = kt;
     if (kt + 1 < nk) load_stage<KVEC>(R, t, m0, n0, (kt + 1) * kBK, A, rowoff, coloff, Bm, M, N, K);
   }
   // the last commit completes when every MMA before it has completed
-  if (ok && issued >= 0) {
-    const bool mine = barrier_wait(bar0 + 8 * (issued & 1), uint32_t(issued >> 1) & 1u);
+  if (ok) {
+    const bool mine = issued >= 0 && barrier_wait(bar0 + 8 * (issued & 1), uint32_t(issued >> 1) & 1u, wait_limit);
     ok = __syncthreads_and(mine) != 0;
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(kPgThreads, 2)
     atomicExch(err, 1);
     // give the MMAs in flight a last bounded chance to finish before the
     // accumulator is released
-    if (issued >= 0) barrier_wait(bar0 + 8 * (issued & 1), uint32_t(issued >> 1) & 1u);
+    if (issued >= 0) barrier_wait(bar0 + 8 * (issued & 1), uint32_t(issued >> 1) & 1u, wait_limit);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -297,6 +302,7 @@ struct ttc_packed_gemm_s {
   int64_t M = 0, N = 0, K = 0, spanA = 0;
   float alpha = 1.f;
   bool kvec = false;   // every group of 8 k is 8 consecutive floats of A, 16-byte aligned relative to A
+  int skip_mma = 0;    // testing hook (ttc_debug_packed_gemm_skip_mma)
   std::vector<int32_t> rowoff, coloff;
   std::map<int, PgDev> dev;
   ~ttc_packed_gemm_s() {
@@ -421,10 +427,12 @@ ttc_status ttc_packed_gemm_execute(ttc_packed_gemm_t g, const float* A, const vo
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (g->kvec && reinterpret_cast<uintptr_t>(A) % 16 == 0)
     packgemm_kernel<true><<<grid, kPgThreads, kPgSmem, s>>>(A, rows, cols, static_cast<const uint16_t*>(B), C,
-                                                             int(g->M), int(g->N), int(g->K), g->alpha, d.err);
+                                                             int(g->M), int(g->N), int(g->K), g->alpha, d.err,
+                                                             g->skip_mma);
   else
     packgemm_kernel<false><<<grid, kPgThreads, kPgSmem, s>>>(A, rows, cols, static_cast<const uint16_t*>(B), C,
-                                                              int(g->M), int(g->N), int(g->K), g->alpha, d.err);
+                                                              int(g->M), int(g->N), int(g->K), g->alpha, d.err,
+                                                              g->skip_mma);
   ++g_launches;
   e = cudaGetLastError();
   return e == cudaSuccess ? TTC_OK : cuda_fail(e, "packed GEMM launch");
@@ -441,7 +449,10 @@ ttc_status ttc_packed_gemm_check(ttc_packed_gemm_t g) {
   int flag = 0;
   e = cudaMemcpy(&flag, it->second.err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "error word read");
-  return flag ? fail(TTC_ERR_TIMEOUT, "a tensor-core wait gave up") : TTC_OK;
+  if (!flag) return TTC_OK;
+  e = cudaMemset(it->second.err, 0, sizeof(int));      // reported once
+  if (e != cudaSuccess) return cuda_fail(e, "error word reset");
+  return fail(TTC_ERR_TIMEOUT, "a tensor-core wait gave up");
 }
 
 ttc_status ttc_packed_gemm_info(ttc_packed_gemm_t g, int64_t* m, int64_t* n, int64_t* k) {
@@ -449,6 +460,13 @@ ttc_status ttc_packed_gemm_info(ttc_packed_gemm_t g, int64_t* m, int64_t* n, int
   if (m) *m = g->M;
   if (n) *n = g->N;
   if (k) *k = g->K;
+  return TTC_OK;
+}
+
+ttc_status ttc_debug_packed_gemm_skip_mma(ttc_packed_gemm_t g, int skip) {
+  if (!g) return fail(TTC_ERR_INVALID_ARG, "plan is NULL");
+  std::lock_guard<std::mutex> lk(g->mu);
+  g->skip_mma = skip ? 1 : 0;
   return TTC_OK;
 }
 

@@ -108,6 +108,7 @@ SIGNATURES = {
     "ttc_debug_describe_candidate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
     "ttc_debug_slot_tables": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
                                              _i64p]),
+    "ttc_debug_packed_gemm_skip_mma": (ctypes.c_int, [_vp, ctypes.c_int]),
     "ttc_debug_server_set_watchdog": (ctypes.c_int, [_vp, ctypes.c_double]),
     "ttc_debug_server_submit_delay": (ctypes.c_int, [_vp, ctypes.c_int64, _i64p]),
 }
@@ -353,6 +354,11 @@ class PackedGemm:
 
     def check(self):
         _check(lib().ttc_packed_gemm_check(self._h))
+
+    def skip_mma(self, skip: bool = True):
+        """Testing hook: executions issue no MMA, so their bounded waits run
+        out and check() reports TTC_ERR_TIMEOUT."""
+        _check(lib().ttc_debug_packed_gemm_skip_mma(self._h, int(bool(skip))))
 
     def info(self) -> dict:
         m, n, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -97,3 +97,28 @@ def test_packed_gemm_host_checks():
     with pytest.raises(ttc.TTCError) as ei:
         g.execute(A, B, A)
     assert ei.value.name == "TTC_ERR_ALIAS"
+
+
+def test_packed_gemm_wait_limit_reports_timeout_and_keeps_the_context():
+    """Failure detection without a GPU fault: under the testing hook no MMA
+    is committed, so the kernel's bounded mbarrier waits run out; it records
+    the error word, frees its tensor memory and returns without writing C.
+    The host reads TTC_ERR_TIMEOUT once, and the context keeps working."""
+    g = ttc.PackedGemm((0, 1), (128, 192), 1, 256)           # one CTA, three k stages
+    A = torch.ones(128 * 192, device="cuda")
+    B = torch.zeros(192 * 256, dtype=torch.int16, device="cuda")
+    C = torch.full((128 * 256,), 7.0, device="cuda")
+    g.skip_mma(True)
+    g.execute(A, B, C)
+    torch.cuda.synchronize()
+    with pytest.raises(ttc.TTCError) as ei:
+        g.check()
+    assert ei.value.name == "TTC_ERR_TIMEOUT"
+    assert bool((C == 7.0).all())                             # C untouched
+    g.check()                                                 # reported once
+    g.skip_mma(False)
+    g.execute(A, B, C)                                        # the same plan works again
+    torch.cuda.synchronize()
+    g.check()
+    assert bool((C == 0.0).all())                             # Bm = 0
+    run((0, 1), (128, 192), 1, 256, seed=7)                  # and a fresh plan matches the oracle
