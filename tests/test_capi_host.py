@@ -1,6 +1,7 @@
 """Host-side tests of libttc (no GPU): exports, validation, canonicalisation,
 schedule choice, and the checks ttc_execute makes before touching the device."""
 import ctypes
+import math
 import os
 import re
 import subprocess
@@ -431,3 +432,43 @@ def test_packed_gemm_plan_on_the_host():
     with pytest.raises(ttc.TTCError) as ei:
         g.execute(0x100000, 0x200000, 0x100000 + 64)  # C inside A
     assert ei.value.name == "TTC_ERR_ALIAS"
+
+
+def test_contraction_planner_decisions_on_random_layouts():
+    """Random contractions (host only): the GEMM extents are the products of
+    the free and contracted extents, and an operand is permuted exactly when
+    it is not already a matrix in either orientation ([free, contracted] or
+    [contracted, free]); C is permuted exactly when it is neither [free A,
+    free B] nor [free B, free A] in C's own label order."""
+    g = inputs.rng(77)
+    for trial in range(200):
+        labels = list(range(int(g.integers(2, 7))))
+        roles = {}
+        for lab in labels:
+            roles[lab] = ["k", "a", "b"][int(g.integers(0, 3))]
+        ka = [lab for lab in labels if roles[lab] in "ka"]
+        kb = [lab for lab in labels if roles[lab] in "kb"]
+        kc = [lab for lab in labels if roles[lab] in "ab"]
+        if not ka or not kb or not kc:
+            continue
+        ma = tuple(int(x) for x in g.permutation(ka))
+        mb = tuple(int(x) for x in g.permutation(kb))
+        mc = tuple(int(x) for x in g.permutation(kc))
+        ext = {lab: int(g.integers(1, 6)) for lab in labels}
+        c = ttc.Contraction(ma, [ext[m] for m in ma], mb, [ext[m] for m in mb], mc, [ext[m] for m in mc])
+        inf = c.info()
+        contracted = [m for m in ma if roles[m] == "k"]
+        fa_c = [m for m in mc if roles[m] == "a"]
+        fb_c = [m for m in mc if roles[m] == "b"]
+        prod = lambda ls: math.prod(ext[m] for m in ls)
+        assert (inf["m"], inf["n"], inf["k"]) == (prod(fa_c), prod(fb_c), prod(contracted)), (ma, mb, mc)
+        c_direct = list(mc) in (fa_c + fb_c, fb_c + fa_c)
+        assert inf["permuted"]["C"] == (not c_direct), (ma, mb, mc)
+        # the free indices of an operand follow C's order when C is a GEMM
+        # output layout, else the operand's own order
+        fa = fa_c if c_direct else [m for m in ma if roles[m] == "a"]
+        fb = fb_c if c_direct else [m for m in mb if roles[m] == "b"]
+        a_matrix = list(ma) in (fa + contracted, contracted + fa)
+        b_matrix = list(mb) in (contracted + fb, fb + contracted)
+        assert inf["permuted"]["A"] == (not a_matrix), (ma, mb, mc)
+        assert inf["permuted"]["B"] == (not b_matrix), (ma, mb, mc)
