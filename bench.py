@@ -196,8 +196,9 @@ class DeviceSet:
     """Device buffers for a list of problems: two alternating A/B sets per
     dtype pair so that consecutive transposes never re-read the same input."""
 
-    def __init__(self, probs, seed=0):
+    def __init__(self, probs, seed=0, dist="uniform"):
         import torch
+        self.dist = dist
         self.bufs = {}
         need = {}
         for p in probs:
@@ -209,17 +210,20 @@ class DeviceSet:
         for (di, do), (va, vb) in need.items():
             sets = []
             for j in range(2):
-                A = self._rand(di, va, g)
-                B = self._rand(do, vb, g)
+                A = self._rand(di, va, g, dist)
+                B = self._rand(do, vb, g, dist)
                 sets.append((A, B))
             self.bufs[(di, do)] = sets
 
     @staticmethod
-    def _rand(dt, n, g):
+    def _rand(dt, n, g, dist="uniform"):
         import torch
         if dt in ("f32", "f64"):
             t = torch.empty(n, dtype=storage_torch(dt), device="cuda")
-            t.uniform_(-1.0, 1.0, generator=g)
+            if dist == "normal":
+                t.normal_(0.0, 1.0, generator=g)
+            else:
+                t.uniform_(-1.0, 1.0, generator=g)
             return t
         if dt in ("c64", "c128"):
             # both parts uniform[-1, 1]
@@ -247,7 +251,9 @@ def run_ours(args, rank, world):
     probs = workload_problems(args.workload, args.target, args.only)
     plans = [ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta, p.outer_a, p.outer_b)
              for p in probs]
-    bufs = DeviceSet(probs)
+    # the packing workload's A is normal(0, 1) (its configuration); the
+    # transposes' tensors are uniform[-1, 1]
+    bufs = DeviceSet(probs, dist="normal" if args.workload == "packing" else "uniform")
     stream = torch.cuda.current_stream()
     bytes_step = sum(p.algorithmic_bytes() for p in probs)
 
@@ -393,12 +399,58 @@ def run_ours(args, rank, world):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if args.workload in ("packing", "single4d"):
+        out["per_case"] = [{"case": f"{p.tag}/{p.dtype_in}>{p.dtype_out}", "us": round(ms * 1e3, 2),
+                            "GB/s": round(g, 1), "frac_of_peak": round(g / peak, 4), "kernel": pl.info()["kernel"]}
+                           for p, pl, ms, g in zip(probs, plans, per_case_ms, case_gbs)]
+    if args.workload == "packing":
+        out["fp8_error"] = {f"{p.tag}/{p.dtype_in}>{p.dtype_out}": fp8_error_stats(p, pl, bufs.get(p, i), stream)
+                            for i, (p, pl) in enumerate(zip(probs, plans)) if p.dtype_out == "e4m3"}
     if args.workload == "complex":
         out["fp64_pipe"] = fp64_roofline(probs, per_case_ms)
     if fp8_supplied:
         out["fp8"] = {"note": "algorithmic bytes n (s_A + s_B) in both columns; the computed scale also reads A "
                               "once more (amax pre-pass)", "cases": fp8_supplied}
     return out
+
+
+def colmajor_view(flat, sizes, outer):
+    """The (sub-)tensor of column-major sizes inside outer extents, as a
+    strided torch view indexed [i0, i1, ...]."""
+    st, acc = [], 1
+    for s, o in zip(sizes, outer):
+        st.append(acc)
+        acc *= o
+    return flat.as_strided(tuple(sizes), tuple(st))
+
+
+def fp8_error_stats(p, pl, bufs, stream):
+    """Error of one FP8 result (the scale computed on the device) against the
+    exact value alpha*a: the product of two binary32 numbers is exact in
+    binary64, so the reference is alpha_f * a in float64.  The plan runs once
+    on the case's A; its E4M3 codes, dequantised with the scale it used, are
+    compared element by element through the permutation (torch views of A's
+    sub-tensor and of B)."""
+    import torch
+    A, B = bufs
+    pl.execute(A, B, stream)
+    scale_t = torch.zeros(1, dtype=torch.float32, device="cuda")
+    pl.get_fp8_scale(scale_t, stream)
+    torch.cuda.synchronize()
+    scale = float(scale_t.item())
+    outer_a = p.outer_a or p.sizes
+    sizes_b = [p.sizes[k] for k in p.perm]
+    outer_b = p.outer_b or sizes_b
+    a = colmajor_view(A.view(torch.float32), p.sizes, outer_a).permute(*p.perm).to(torch.float64)
+    ref = float(torch.tensor(p.alpha, dtype=torch.float32).item()) * a
+    codes = colmajor_view(B.view(torch.uint8), sizes_b, outer_b)
+    deq = codes.view(torch.float8_e4m3fn).to(torch.float64) * scale
+    err = (deq - ref).abs()
+    mag = ref.abs()
+    rel = torch.where(mag > 0, err / torch.where(mag > 0, mag, torch.ones_like(mag)), torch.zeros_like(err))
+    return {"scale": scale, "max_abs": float(err.max()), "max_rel": float(rel.max()),
+            "rms": float(err.pow(2).mean().sqrt()), "max_abs_ref": float(mag.max()),
+            "bound_ok": bool((err <= 2.0 ** -4 * mag + scale * 2.0 ** -10 + 1e-30).all())}
 
 
 # FP64 pipe: nominal 1.25 TFLOP/s dense FP64 on GB300 = 0.625 T fused
@@ -1060,7 +1112,7 @@ def main():
     ap.add_argument("--serve-small-tiles", type=int, default=1024)
     ap.add_argument("--serve-dump", default="", help="write per-request latencies (JSON) to <path>.<arm>.json")
     ap.add_argument("--batch-count", type=int, default=4096)
-    ap.add_argument("--autotune", type=int, default=12,
+    ap.add_argument("--autotune", type=int, default=24,
                     help="time up to this many candidates per plan before the timed steps (0: cost model only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -1069,6 +1121,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="default workload: skip the serving summary")
     ap.add_argument("--no-complex", action="store_true", help="default workload: skip the complex-types row")
     ap.add_argument("--no-contraction", action="store_true", help="default workload: skip the TTGT contraction row")
+    ap.add_argument("--no-packing", action="store_true",
+                    help="default workload: skip the single-4D and GEMM-packing rows")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--target", type=int, default=1 << 26,
                     help="elements per tensor of the sweep (the complex workload takes half)")
@@ -1125,6 +1179,23 @@ def main():
                 out["complex"] = {"workload": r["config"]["workload"], "GB/s": r["value"], "cases": r["cases"],
                                   "per_variant": r["per_variant"], "roofline_frac": r["roofline"]["frac"],
                                   "fp64_pipe": r.get("fp64_pipe"), "timing": "CUDA events"}
+            if not args.no_packing:
+                # the single 4D transpose and the GEMM-packing downcasts
+                # (BF16, FP8 with the scale computed and supplied), each case
+                # with its roofline fraction; FP8 results with their error
+                # against the exact alpha*a
+                s4 = copy.copy(sub)
+                s4.workload, s4.no_e2e, s4.cases_out, s4.only = "single4d", True, "", ""
+                r = run_ours(s4, rank, world)
+                out["single4d"] = {"workload": r["config"]["workload"], "us": r["per_case"][0]["us"],
+                                   "GB/s": r["value"], "frac_of_peak": r["per_case"][0]["frac_of_peak"],
+                                   "kernel": r["per_case"][0]["kernel"], "timing": "CUDA events"}
+                pk = copy.copy(sub)
+                pk.workload, pk.no_e2e, pk.cases_out, pk.only = "packing", True, "", ""
+                r = run_ours(pk, rank, world)
+                out["packing"] = {"workload": r["config"]["workload"], "GB/s": r["value"],
+                                  "cases": r["per_case"], "fp8_supplied_scale": (r.get("fp8") or {}).get("cases"),
+                                  "fp8_error": r.get("fp8_error"), "timing": "CUDA events"}
             if not args.no_contraction:
                 pg = run_packed_gemm(sub, rank, world)
                 out["packed_gemm"] = {"workload": pg["config"]["workload"], "TFLOP/s": pg["value"],

@@ -197,6 +197,13 @@ typedef struct {
     int slot_tables;               /* generic tile kernel: whole tiles read their per-thread
                                       offsets from precomputed slot tables (1) or walk the
                                       indices (0) */
+    int packed_threads;            /* tile variant: threads per CTA (256 or 512) of the
+                                      packed-lane kernel, whose lane groups run over the
+                                      tile's rows without idling at run ends; 0 otherwise */
+    int packed_rows;               /* tile variant with a common inner run (perm keeps
+                                      index 0): positions per thread and row of the
+                                      packed-row kernel, which copies the tile's rows
+                                      directly without staging; 0 otherwise */
 } ttc_plan_info;
 
 ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info);
@@ -456,7 +463,17 @@ ttc_status ttc_server_destroy(ttc_server_t server);
  *    ttc_execute still runs it.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture begins.
+ *    before any stream capture begins.  The address is looked up again when
+ *    the device's CUDA context has changed since (after cudaDeviceReset, for
+ *    instance), so a call never passes a kernel an address of an earlier
+ *    context.
+ *  - A tile schedule's offset tables are copied from host memory that the
+ *    call owns only until it returns; on a stream that is being captured
+ *    such a call is refused with TTC_ERR_INVALID_ARG (schedules without
+ *    tables are not refused).
+ *  - The schedule run is the plan's selected candidate, or, unless the caller
+ *    selected one, the candidate an earlier ttc_plan_autotune remembered for
+ *    this problem on this device (as ttc_execute's first use takes it).
  *  - Every call shares the one array per device, and the array keeps the last
  *    call's contents; each call re-initialises what it uses (the amax word is
  *    cleared, the offset tables are re-uploaded on `stream`).  Calls whose

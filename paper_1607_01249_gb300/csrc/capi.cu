@@ -69,6 +69,18 @@ std::string plan_key(const ttc_plan_s* p, int dev) {
   return o.str();
 }
 
+// The candidate an earlier autotune chose for this canonical problem on
+// this device, or -1 (the caller holds p->mu).
+int remembered_choice(const ttc_plan_s* p, int dev) {
+  const std::string key = plan_key(p, dev);
+  std::lock_guard<std::mutex> tl(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return -1;
+  for (size_t i = 0; i < p->cands.size(); ++i)
+    if (cand_key(p->cands[i]) == it->second) return int(i);
+  return -1;
+}
+
 // ------------------------------------------------------- device resources --
 
 ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out) {
@@ -106,12 +118,8 @@ ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out) {
     r.sel = -1;
     // a remembered autotune result for this canonical problem on this device
     if (!p->user_selected) {
-      const std::string key = plan_key(p, dev);
-      std::lock_guard<std::mutex> tl(g_tune_mu);
-      auto it = g_tune.find(key);
-      if (it != g_tune.end())
-        for (size_t i = 0; i < p->cands.size(); ++i)
-          if (cand_key(p->cands[i]) == it->second) p->sel = int(i);
+      const int i = remembered_choice(p, dev);
+      if (i >= 0) p->sel = i;
     }
   }
   if (r.sel != p->sel) {
@@ -193,6 +201,8 @@ ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s) {
     TileParams tp = r->tp;
     tp.epi = epi;
     e = k.rows ? launch_rowcopy(p->din, p->dout, A, B, tp, s)
+        : k.rj ? launch_rowsp(p->din, p->dout, k.rj, A, B, tp, s)
+        : k.pk ? launch_tilep(p->din, p->dout, k.pk, k.ju, k.jw, A, B, tp, r->smem, s)
         : k.ju ? launch_tile2(p->din, p->dout, k.ju, k.jw, A, B, tp, r->smem, s)
         : tp.slots ? launch_tile_slots(p->din, p->dout, A, B, tp, r->smem, s)
                    : launch_tile(p->din, p->dout, A, B, tp, r->smem, s);
@@ -243,6 +253,9 @@ int64_t ttc_launch_count(void) { return ttc::launch_count(); }
 
 namespace {
 
+// candidate schedules a plan keeps (the autotuner times up to this many)
+constexpr int kPlanCandidates = 24;
+
 ttc_status plan_create(ttc_plan_t* out, int ndim, const int* perm, const int64_t* sizes,
                        const int64_t* outer_sizes_A, const int64_t* outer_sizes_B, ttc_dtype dtype_in,
                        ttc_dtype dtype_out, double alpha, double alpha_im, double beta, double beta_im) {
@@ -275,7 +288,7 @@ ttc_status plan_create(ttc_plan_t* out, int ndim, const int* perm, const int64_t
   p->beta = beta;
   p->alpha_im = alpha_im;
   p->beta_im = beta_im;
-  p->cands = make_candidates(p->canon, din, dout, p->beta_nonzero() ? 1.0 : 0.0, 12);
+  p->cands = make_candidates(p->canon, din, dout, p->beta_nonzero() ? 1.0 : 0.0, kPlanCandidates);
   if (p->cands.empty()) return fail(TTC_ERR_INVALID_SIZE, "no schedule fits this problem");
   if (p->canon.n > 0) {
     build_row_params(p->canon, p->canon.s[0] <= 16384 ? p->canon.s[0] : 8192, &p->amax_rows);
@@ -382,9 +395,11 @@ ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info) {
     info->tile_b = tp.LB;
     info->ntiles = tp.ntiles;
     info->vec_in = info->vec_out = 1;
-    info->lanes_a = 32 * k.ju;
-    info->lanes_b = 32 * k.jw;
+    info->lanes_a = k.pk ? 0 : 32 * k.ju;
+    info->lanes_b = k.pk ? 0 : 32 * k.jw;
     info->slot_tables = k.slots;
+    info->packed_threads = k.pk;
+    info->packed_rows = k.rj;
   } else if (k.variant == VAR_COPY) {
     RowParams rp;
     build_row_params(c, k.chunk, &rp);

@@ -82,7 +82,9 @@ cudaError_t grid_for(const void* fn, int smem, int64_t work, int* grid) {
   cudaError_t launch_tile_##P(const void*, void*, const TileParams&, int, cudaStream_t);                  \
   cudaError_t launch_tile_slots_##P(const void*, void*, const TileParams&, int, cudaStream_t);            \
   cudaError_t launch_tile2_##P(int, int, const void*, void*, const TileParams&, int, cudaStream_t);       \
+  cudaError_t launch_tilep_##P(int, int, int, const void*, void*, const TileParams&, int, cudaStream_t);  \
   cudaError_t launch_copy_##P(int, const void*, void*, const RowParams&, cudaStream_t);                   \
+  cudaError_t launch_rowsp_##P(int, const void*, void*, const TileParams&, cudaStream_t);                  \
   cudaError_t launch_rowcopy_##P(const void*, void*, const TileParams&, cudaStream_t);
 TTC_PAIRS(TTC_DECLARE)
 #undef TTC_DECLARE
@@ -129,10 +131,27 @@ cudaError_t launch_tile2(int din, int dout, int ju, int jw, const void* A, void*
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_tilep(int din, int dout, int nt, int ju, int jw, const void* A, void* B, const TileParams& p,
+                         int smem, cudaStream_t s) {
+#define TTC_GO(I, O, P) \
+  if (din == I && dout == O) return launch_tilep_##P(nt, ju, jw, A, B, p, smem, s);
+  TTC_PAIRS(TTC_GO)
+#undef TTC_GO
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_copy(int din, int dout, int vec, const void* A, void* B, const RowParams& p,
                         cudaStream_t s) {
 #define TTC_GO(I, O, P) \
   if (din == I && dout == O) return launch_copy_##P(vec, A, B, p, s);
+  TTC_PAIRS(TTC_GO)
+#undef TTC_GO
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rowsp(int din, int dout, int j, const void* A, void* B, const TileParams& p, cudaStream_t s) {
+#define TTC_GO(I, O, P) \
+  if (din == I && dout == O) return launch_rowsp_##P(j, A, B, p, s);
   TTC_PAIRS(TTC_GO)
 #undef TTC_GO
   return cudaErrorInvalidValue;

@@ -210,6 +210,18 @@ struct TileCoord {
 TTC_HD TileCoord tile_coord(uint32_t tid, const TileParams& p) {
   TileCoord c{0, 0, p.LA, p.LB};
   uint32_t r = tid;
+  if (p.swz && p.ngrid >= 2) {
+    // grouped order: tile tid is block x0 of the first grid index and x1 of
+    // the second, taken in groups of swz values of x0 (the last group may be
+    // narrower), x0 fastest inside a group; r is then the plain mixed-radix
+    // index of (x0, x1, the rest)
+    const uint32_t n0 = p.g[0].div.d, n1 = p.g[1].div.d, plane = n0 * n1;
+    const uint32_t rest = r / plane, q = r - rest * plane;
+    const uint32_t band = q / (p.swz * n1), in = q - band * p.swz * n1;
+    const uint32_t width = n0 - band * p.swz < p.swz ? n0 - band * p.swz : p.swz;
+    const uint32_t x1 = in / width, x0 = band * p.swz + (in - x1 * width);
+    r = rest * plane + x1 * n0 + x0;
+  }
   for (int i = 0; i < p.ngrid; ++i) {
     const uint32_t q = fast_div(r, p.g[i].div);
     const uint32_t d = r - q * p.g[i].div.d;
@@ -367,6 +379,116 @@ TTC_HD void walk2_write(const TileCoord& c, const PT& p, const int32_t* tabB, in
         const bool ok = lane + 32 * j < limV;
         f(i * JW + j, ok, ok ? row + voff[j] : 0, spre[j] + spos);
       }
+    }
+  }
+}
+
+// Packed-lane walks (tilep_kernel).  The tile has no C index (LC = 1): its
+// A-side runs are u = la (remA elements, rows lb < remB) and its B-side runs
+// v = lb (remB elements, rows la < remA).  On each side the CTA's threads form
+// groups of g consecutive threads, one group per row at a time: thread
+// t = tu + g*tr takes the run positions tu + g*j (j < J) of rows
+// tr + rows*i (i < K/J).  g = ceil(n/J) is chosen per tile class (whole
+// tiles, and the short runs of the tiles a cut index leaves short), so the
+// lanes of a warp continue from the end of one row into the next instead of
+// idling at a run's end, and each thread's offsets advance by constants (one
+// add per element, the row's cross offset once per row).  tile2_kernel is
+// the case g = 32 with warps as the groups.  f(k, ok, offset in tile, smem
+// position): smem holds the tile as lb rows of pitch P in A order.
+template <int NT, int J, int K, bool TAB, class F>
+TTC_HD void walkp_read(const TileCoord& c, const TileParams& p, const int32_t* tabA, int t, F&& f) {
+  constexpr int R = K / J;
+  // (the two layouts are selected field by field: indexing the parameter
+  // array with a run-time index would copy it to local memory)
+  const bool whole = c.remA == p.LA;
+  const int g = whole ? p.pkA[0].g : p.pkA[1].g, rows = whole ? p.pkA[0].rows : p.pkA[1].rows;
+  const int tr = int(fast_div(uint32_t(t), whole ? p.pkA[0].div : p.pkA[1].div));
+  const int tu = t - tr * g;
+  const bool active = tr < rows;
+  int32_t uoff[J];
+  bool uok[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int u = tu + g * j;
+    uok[j] = active && u < c.remA;
+    uoff[j] = u * p.saU;
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int lb = tr + rows * i;
+    const bool rok = lb < c.remB;
+    const int32_t cross = TAB ? (rok && active ? tabA[lb] : 0) : lb * p.crossA_lin;
+    const int pos = lb * p.P + tu;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const bool ok = rok && uok[j];
+      f(i * J + j, ok, ok ? uoff[j] + cross : 0, pos + g * j);
+    }
+  }
+}
+
+template <int NT, int J, int K, bool TAB, class F>
+TTC_HD void walkp_write(const TileCoord& c, const TileParams& p, const int32_t* tabB, int t, F&& f) {
+  constexpr int R = K / J;
+  const bool whole = c.remB == p.LB;
+  const int g = whole ? p.pkB[0].g : p.pkB[1].g, rows = whole ? p.pkB[0].rows : p.pkB[1].rows;
+  const int tr = int(fast_div(uint32_t(t), whole ? p.pkB[0].div : p.pkB[1].div));
+  const int tv = t - tr * g;
+  const bool active = tr < rows;
+  int32_t voff[J];
+  bool vok[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int v = tv + g * j;
+    vok[j] = active && v < c.remB;
+    voff[j] = v * p.sbV;
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int la = tr + rows * i;
+    const bool rok = la < c.remA;
+    const int32_t cross = TAB ? (rok && active ? tabB[la] : 0) : la * p.crossB_lin;
+    const int pos = tv * p.P + la;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const bool ok = rok && vok[j];
+      f(i * J + j, ok, ok ? voff[j] + cross : 0, pos + g * j * p.P);
+    }
+  }
+}
+
+// Packed rows (rowsp_kernel): a tile with a C index (perm keeps index 0)
+// is remA x remB rows (la, lb) of LC elements, each row contiguous in A (at
+// la*LC*saU + crossA(lb)) and in B (at lb*LC*sbV + crossB(la)), so rows are
+// copied directly, without staging.  Thread t = tu + g*tr takes positions
+// tu + g*j (j < J) of rows r = tr + rows*i (i < K/J), r = la + remA*lb; g
+// and rows come from the host's layout (pkA[0]).  f(k, ok, A offset, B
+// offset).
+template <int J, int K, bool TA, bool TB, class F>
+TTC_HD void walk_rowsp(const TileCoord& c, const TileParams& p, const int32_t* tabA, const int32_t* tabB, int t,
+                       F&& f) {
+  constexpr int R = K / J;
+  const int g = p.pkA[0].g, rows = p.pkA[0].rows;
+  const int tr = int(fast_div(uint32_t(t), p.pkA[0].div));
+  const int tu = t - tr * g;
+  const bool active = tr < rows;
+  const bool whole = c.remA == p.LA;
+  const int nrow = c.remA * c.remB;
+  const int32_t rowA = p.LC * p.saU, rowB = p.LC * p.sbV;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int r = tr + rows * i;
+    const bool rok = active && r < nrow;
+    const int lb = int(fast_div(uint32_t(r), whole ? p.divRA[0] : p.divRA[1]));
+    const int la = r - lb * c.remA;
+    const int32_t baseA = la * rowA + (TA ? (rok ? tabA[lb] : 0) : lb * p.crossA_lin) + tu * p.saU;
+    const int32_t baseB = lb * rowB + (TB ? (rok ? tabB[la] : 0) : la * p.crossB_lin) + tu * p.sbV;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      // (positions recomputed per element: arrays of J offsets would not fit
+      // in registers next to the staged values)
+      const bool ok = rok && tu + g * j < p.LC;
+      f(i * J + j, ok, ok ? baseA + g * j * p.saU : 0, ok ? baseB + g * j * p.sbV : 0);
     }
   }
 }

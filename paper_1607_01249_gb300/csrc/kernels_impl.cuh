@@ -291,6 +291,104 @@ __global__ void __launch_bounds__(kThreads, 6) tile2_kernel(const store_t<DIN>* 
   else tile2_tabs<DIN, DOUT, JU, JW, EK, false>(Ab, Bb, p, c, tile, scale);
 }
 
+// --------------------------------------------------------- packed-lane tile --
+//
+// Tiles without a C index of any extents up to (threads x K) elements, on 256
+// or 512 threads (the thread count is the launch's; the walks only see the
+// host's layouts): the lanes of a warp are packed over the rows of each side
+// (walkp_read / walkp_write), so runs of any length, and the short runs of the
+// tiles at the tensor's edge, keep almost every lane busy, at the per-element
+// cost of the warp-mapped walk.  With 512 threads a tile holds 8192 four-byte
+// elements, which lets both sides' runs be longer than a 4096-element tile
+// allows.
+
+constexpr int kPackMaxThreads = 512;
+
+template <int DIN, int DOUT, int JU, int JW, int EK, bool TA, bool TB>
+__device__ __forceinline__ void tilep_body(const store_t<DIN>* __restrict__ Ab, store_t<DOUT>* __restrict__ Bb,
+                                           const TileParams& p, const TileCoord& c, stage_t<DIN>* tile,
+                                           float scale) {
+  using S = stage_t<DIN>;
+  using TO = store_t<DOUT>;
+  constexpr int K = tile_k_for(sizeof(S));
+  const int t = threadIdx.x;
+  S v[K];
+  walkp_read<0, JU, K, TA>(c, p, p.tabA, t,
+                           [&](int k, bool, int32_t off, int) { v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + off)); });
+  walkp_read<0, JU, K, TA>(c, p, p.tabA, t, [&](int k, bool ok, int32_t, int pos) {
+    if (ok) tile[pos] = v[k];
+  });
+  __syncthreads();
+  TO bo[K] = {};
+  if constexpr (EK == EK_AXPBY)
+    walkp_write<0, JW, K, TB>(c, p, p.tabB, t, [&](int k, bool, int32_t off, int) { bo[k] = Bb[off]; });
+  walkp_write<0, JW, K, TB>(c, p, p.tabB, t, [&](int k, bool ok, int32_t off, int pos) {
+    if (ok) Bb[off] = epilogue_k<DIN, DOUT, EK>(tile[pos], bo[k], p.epi, scale);
+  });
+}
+
+template <int DIN, int DOUT, int JU, int JW, int EK>
+__global__ void __launch_bounds__(kPackMaxThreads, EK == EK_AXPBY ? 2 : 3) tilep_kernel(
+    const store_t<DIN>* __restrict__ A, store_t<DOUT>* __restrict__ B, const __grid_constant__ TileParams p) {
+  using S = stage_t<DIN>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  S* tile = reinterpret_cast<S*>(smem);
+  const float scale = cta_fp8_scale<EK>(p.epi);
+  const TileCoord c = cta_tile_coord(p);
+  const store_t<DIN>* Ab = A + c.baseA;
+  store_t<DOUT>* Bb = B + c.baseB;
+  if (p.crossA_tab) {
+    if (p.crossB_tab) tilep_body<DIN, DOUT, JU, JW, EK, true, true>(Ab, Bb, p, c, tile, scale);
+    else tilep_body<DIN, DOUT, JU, JW, EK, true, false>(Ab, Bb, p, c, tile, scale);
+  } else {
+    if (p.crossB_tab) tilep_body<DIN, DOUT, JU, JW, EK, false, true>(Ab, Bb, p, c, tile, scale);
+    else tilep_body<DIN, DOUT, JU, JW, EK, false, false>(Ab, Bb, p, c, tile, scale);
+  }
+}
+
+// ------------------------------------------------------------- packed rows --
+//
+// Tiles with a C index (perm keeps index 0) whose rows are contiguous on
+// both sides: each row goes from A to B directly (walk_rowsp), the lanes of a
+// warp packed over the rows, so rows of any length keep almost every lane
+// busy and no shared memory is needed.
+
+template <int DIN, int DOUT, int J, int EK, bool TA, bool TB>
+__device__ __forceinline__ void rowsp_body(const store_t<DIN>* __restrict__ Ab, store_t<DOUT>* __restrict__ Bb,
+                                           const TileParams& p, const TileCoord& c, float scale) {
+  using S = stage_t<DIN>;
+  using TO = store_t<DOUT>;
+  constexpr int K = tile_k_for(sizeof(S));
+  const int t = threadIdx.x;
+  S v[K];
+  TO bo[K] = {};
+  int32_t ob[K];     // B offsets of one walk (-1: no element), kept for the stores
+  walk_rowsp<J, K, TA, TB>(c, p, p.tabA, p.tabB, t, [&](int k, bool ok, int32_t offA, int32_t offB) {
+    v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + offA));
+    if constexpr (EK == EK_AXPBY) bo[k] = Bb[offB];
+    ob[k] = ok ? offB : -1;
+  });
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (ob[k] >= 0) Bb[ob[k]] = epilogue_k<DIN, DOUT, EK>(v[k], bo[k], p.epi, scale);
+}
+
+template <int DIN, int DOUT, int J, int EK>
+__global__ void __launch_bounds__(kThreads, EK == EK_AXPBY ? 3 : 4) rowsp_kernel(
+    const store_t<DIN>* __restrict__ A, store_t<DOUT>* __restrict__ B, const __grid_constant__ TileParams p) {
+  const float scale = cta_fp8_scale<EK>(p.epi);
+  const TileCoord c = cta_tile_coord(p);
+  const store_t<DIN>* Ab = A + c.baseA;
+  store_t<DOUT>* Bb = B + c.baseB;
+  if (p.crossA_tab) {
+    if (p.crossB_tab) rowsp_body<DIN, DOUT, J, EK, true, true>(Ab, Bb, p, c, scale);
+    else rowsp_body<DIN, DOUT, J, EK, true, false>(Ab, Bb, p, c, scale);
+  } else {
+    if (p.crossB_tab) rowsp_body<DIN, DOUT, J, EK, false, true>(Ab, Bb, p, c, scale);
+    else rowsp_body<DIN, DOUT, J, EK, false, false>(Ab, Bb, p, c, scale);
+  }
+}
+
 // ------------------------------------------------------------ multi-row copy --
 //
 // perm keeps index 0 and its runs are short: a tile is LC x LA (LC the shared
@@ -516,6 +614,37 @@ struct Tile2L {
   };
 };
 
+template <int DIN, int DOUT, int JU, int JW>
+struct TilepL {
+  template <int EK>
+  struct L {
+    static cudaError_t run(int nt, const void* A, void* B, const TileParams& p, int smem, cudaStream_t s) {
+      if (smem > 48 * 1024) {
+        int g = 0;
+        cudaError_t err = grid_for(reinterpret_cast<const void*>(&tilep_kernel<DIN, DOUT, JU, JW, EK>), smem, 1, &g);
+        if (err != cudaSuccess) return err;
+      }
+      tilep_kernel<DIN, DOUT, JU, JW, EK><<<p.ntiles, nt, smem, s>>>(static_cast<const store_t<DIN>*>(A),
+                                                                     static_cast<store_t<DOUT>*>(B), p);
+      ++g_launches;
+      return cudaGetLastError();
+    }
+  };
+};
+
+template <int DIN, int DOUT, int J>
+struct RowspL {
+  template <int EK>
+  struct L {
+    static cudaError_t run(const void* A, void* B, const TileParams& p, cudaStream_t s) {
+      rowsp_kernel<DIN, DOUT, J, EK><<<p.ntiles, kThreads, 0, s>>>(static_cast<const store_t<DIN>*>(A),
+                                                                   static_cast<store_t<DOUT>*>(B), p);
+      ++g_launches;
+      return cudaGetLastError();
+    }
+  };
+};
+
 template <int DIN, int DOUT>
 struct RowcopyL {
   template <int EK>
@@ -551,6 +680,29 @@ cudaError_t launch_tile2_pair(int ju, int jw, const void* A, void* B, const Tile
     return with_ek<DIN, DOUT, Tile2L<DIN, DOUT, U_, W_>::template L>(p.epi.mode, p.epi.beta_nz, A, B, p, smem, s);
   J(1, 1) J(1, 2) J(1, 4) J(2, 1) J(2, 2) J(2, 4) J(4, 1) J(4, 2) J(4, 4)
 #undef J
+  return cudaErrorInvalidValue;
+}
+
+template <int DIN, int DOUT>
+cudaError_t launch_tilep_pair(int nt, int ju, int jw, const void* A, void* B, const TileParams& p, int smem,
+                              cudaStream_t s) {
+  if (nt != 256 && nt != 512) return cudaErrorInvalidValue;
+#define J(U_, W_)                                                                                           \
+  if (ju == U_ && jw == W_)                                                                                 \
+    return with_ek<DIN, DOUT, TilepL<DIN, DOUT, U_, W_>::template L>(p.epi.mode, p.epi.beta_nz, nt, A, B, p, smem, s);
+  J(1, 1) J(1, 2) J(1, 4) J(2, 1) J(2, 2) J(2, 4) J(4, 1) J(4, 2) J(4, 4)
+#undef J
+  return cudaErrorInvalidValue;
+}
+
+template <int DIN, int DOUT>
+cudaError_t launch_rowsp_pair(int j, const void* A, void* B, const TileParams& p, cudaStream_t s) {
+  constexpr int K = tile_k_for(sizeof(stage_t<DIN>));
+#define J_(J) \
+  if constexpr (J <= K)     \
+    if (j == J) return with_ek<DIN, DOUT, RowspL<DIN, DOUT, J>::template L>(p.epi.mode, p.epi.beta_nz, A, B, p, s);
+  J_(1) J_(2) J_(4) J_(8) J_(16)
+#undef J_
   return cudaErrorInvalidValue;
 }
 

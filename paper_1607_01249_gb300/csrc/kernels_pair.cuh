@@ -23,6 +23,15 @@ cudaError_t TTC_CAT(launch_tile2_, TTC_PAIR)(int ju, int jw, const void* A, void
   return launch_tile2_pair<TTC_DIN, TTC_DOUT>(ju, jw, A, B, p, smem, s);
 }
 
+cudaError_t TTC_CAT(launch_tilep_, TTC_PAIR)(int nt, int ju, int jw, const void* A, void* B, const TileParams& p,
+                                             int smem, cudaStream_t s) {
+  return launch_tilep_pair<TTC_DIN, TTC_DOUT>(nt, ju, jw, A, B, p, smem, s);
+}
+
+cudaError_t TTC_CAT(launch_rowsp_, TTC_PAIR)(int j, const void* A, void* B, const TileParams& p, cudaStream_t s) {
+  return launch_rowsp_pair<TTC_DIN, TTC_DOUT>(j, A, B, p, s);
+}
+
 cudaError_t TTC_CAT(launch_rowcopy_, TTC_PAIR)(const void* A, void* B, const TileParams& p, cudaStream_t s) {
   return with_ek<TTC_DIN, TTC_DOUT, RowcopyL<TTC_DIN, TTC_DOUT>::template L>(p.epi.mode, p.epi.beta_nz, A, B, p, s);
 }

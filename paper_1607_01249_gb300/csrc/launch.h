@@ -15,6 +15,13 @@ cudaError_t launch_tile_slots(int din, int dout, const void* A, void* B, const T
                               cudaStream_t s);
 cudaError_t launch_tile2(int din, int dout, int ju, int jw, const void* A, void* B, const TileParams& p,
                          int smem, cudaStream_t s);
+// packed-lane tile kernel with nt (256 or 512) threads per CTA and ju / jw
+// (1, 2, 4) run chunks per thread on the load / store side
+cudaError_t launch_tilep(int din, int dout, int nt, int ju, int jw, const void* A, void* B, const TileParams& p,
+                         int smem, cudaStream_t s);
+// packed rows (C tiles copied row by row without staging), j positions per
+// thread in each row (1, 2, 4, 8, 16; at most the kernel's slots per thread)
+cudaError_t launch_rowsp(int din, int dout, int j, const void* A, void* B, const TileParams& p, cudaStream_t s);
 cudaError_t launch_rowcopy(int din, int dout, const void* A, void* B, const TileParams& p, cudaStream_t s);
 cudaError_t launch_copy(int din, int dout, int vec, const void* A, void* B, const RowParams& p,
                         cudaStream_t s);

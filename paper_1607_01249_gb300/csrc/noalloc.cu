@@ -1,8 +1,10 @@
 // noalloc.cu -- ttc_execute_noalloc (include/ttc.h): a plan's execution with
 // its device scratch (FP8 amax word and scale, tile offset tables) in a
 // static device array instead of memory the plan allocates.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -21,26 +23,65 @@ namespace {
 constexpr size_t kAmaxOff = 0;
 constexpr size_t kScaleOff = 16;
 constexpr size_t kTableOff = 256;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[TTC_NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
+// The current CUDA context's process-unique id (cuCtxGetId), through the
+// driver entry points that the runtime hands out (no link against the driver
+// library); 0 when there is no current context or the driver lacks the calls.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 
-// The array's device address on `dev` (looked up once per device, with that
-// device current).  In host code the symbol itself is only a host-side
-// stand-in, so the kernels always receive this address instead.
+struct ScratchAddr {
+  unsigned long long ctx = 0;
+  void* ptr = nullptr;
+};
+std::mutex g_mu;
+std::map<int, ScratchAddr> g_addr;
+
+// The array's device address on `dev`, which is current.  In host code the
+// symbol itself is only a host-side stand-in, so the kernels always receive
+// this address.  It is looked up (cudaGetSymbolAddress) at the first call on
+// each device and again whenever the device's context has changed since (a
+// device reset, or another context made current), so a stale address is
+// never handed to a kernel.
 ttc_status scratch_address(int dev, unsigned char** out) {
-  if (dev < 0 || dev >= kMaxDevices) return fail(TTC_ERR_INVALID_ARG, "device ordinal out of range");
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  ScratchAddr& a = g_addr[dev];
+  if (!a.ptr || ctx == 0 || a.ctx != ctx) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
-    g_addr[dev] = p;
+    if (e != cudaSuccess) {
+      a = ScratchAddr();
+      return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+    }
+    // the lookup made the device's context current if it was not yet
+    a.ctx = ctx ? ctx : current_context_id();
+    a.ptr = p;
   }
-  *out = static_cast<unsigned char*>(g_addr[dev]);
+  *out = static_cast<unsigned char*>(a.ptr);
   return TTC_OK;
 }
 
@@ -60,7 +101,21 @@ extern "C" ttc_status ttc_execute_noalloc(ttc_plan_t plan, const void* A, void* 
   if (a < eb && b < ea) return fail(TTC_ERR_ALIAS, "the byte ranges of A and B overlap");
 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const Candidate& k = plan->cands[plan->sel];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  // the plan's selected schedule, or the one an autotune remembered for this
+  // problem on this device (as ttc_execute's first use on a device takes it)
+  int sel = 0;
+  {
+    std::lock_guard<std::mutex> lk(plan->mu);
+    sel = plan->sel;
+    if (!plan->user_selected) {
+      const int i = remembered_choice(plan, dev);
+      if (i >= 0) sel = i;
+    }
+  }
+  const Candidate& k = plan->cands[size_t(sel)];
   TileParams tp;
   RowParams rp;
   std::vector<int32_t> ta, tb;
@@ -76,9 +131,15 @@ extern "C" ttc_status ttc_execute_noalloc(ttc_plan_t plan, const void* A, void* 
     return fail(TTC_ERR_INVALID_SIZE, "schedule needs " + std::to_string(kTableOff + table_bytes) +
                                           " bytes of scratch; the static scratch holds " +
                                           std::to_string(TTC_NOALLOC_SCRATCH_BYTES));
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (!ta.empty() || !tb.empty()) {
+    // the offset tables are copied from host memory this call owns only until
+    // it returns, which a captured copy would still refer to
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(TTC_ERR_INVALID_ARG, "the schedule uploads offset tables, which a stream capture cannot take");
+  }
   unsigned char* scratch = nullptr;
   ttc_status st = scratch_address(dev, &scratch);
   if (st != TTC_OK) return st;
@@ -109,6 +170,8 @@ extern "C" ttc_status ttc_execute_noalloc(ttc_plan_t plan, const void* A, void* 
     tp.tabB = tables + ta.size();
     tp.epi = epi;
     e = k.rows ? launch_rowcopy(plan->din, plan->dout, A, B, tp, s)
+        : k.rj ? launch_rowsp(plan->din, plan->dout, k.rj, A, B, tp, s)
+        : k.pk ? launch_tilep(plan->din, plan->dout, k.pk, k.ju, k.jw, A, B, tp, smem, s)
         : k.ju ? launch_tile2(plan->din, plan->dout, k.ju, k.jw, A, B, tp, smem, s)
              : launch_tile(plan->din, plan->dout, A, B, tp, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "tile kernel launch");

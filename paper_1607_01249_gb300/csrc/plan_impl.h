@@ -63,6 +63,7 @@ ttc_status fail(ttc_status s, const std::string& msg);
 ttc_status cuda_fail(cudaError_t e, const char* where);
 ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s);
 ttc_status ensure_device(ttc_plan_s* p, int dev, DevRes** out);
+int remembered_choice(const ttc_plan_s* p, int dev);
 Epilogue make_epilogue(const ttc_plan_s* p, const DevRes* r);
 std::string plan_key(const ttc_plan_s* p, int dev);
 }  // namespace ttc

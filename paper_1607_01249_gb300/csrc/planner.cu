@@ -66,7 +66,11 @@ std::string Candidate::describe() const {
     for (size_t i = 0; i < ga.size(); ++i) o << (i ? "," : "") << ga[i];
     o << "]/" << ta << " gb=[";
     for (size_t i = 0; i < gb.size(); ++i) o << (i ? "," : "") << gb[i];
-    o << "]/" << tb << " j=" << ju << "," << jw << (rows ? " rows" : "") << (slots ? " slots" : "") << " order=[";
+    o << "]/" << tb << " j=" << ju << "," << jw << (rows ? " rows" : "") << (slots ? " slots" : "");
+    if (pk) o << " pk=" << pk;
+    if (swz) o << " swz=" << swz;
+    if (rj) o << " rj=" << rj;
+    o << " order=[";
     for (size_t i = 0; i < order.size(); ++i) o << (i ? "," : "") << order[i];
     o << "]";
   }
@@ -261,10 +265,94 @@ std::vector<int> grid_order(const Canon& c, const int64_t* ext, int mode) {
     const double a = double(ext[k]) * double(c.sa[k]), b = double(ext[k]) * double(c.sb[k]);
     if (mode == 1) return a;
     if (mode == 2) return b;
+    // both-local: indices with small steps in both tensors first, so that
+    // consecutive tiles touch neighbouring memory on both sides
+    if (mode == 3) return std::max(a, b) + 1e-9 * std::min(a, b);
     return std::min(a, b) + 1e-9 * std::max(a, b);
   };
   std::stable_sort(g.begin(), g.end(), [&](int x, int y) { return key(x) < key(y); });
   return g;
+}
+
+// Lane-group layout of one side of a packed-lane tile (PackWalk): runs of n
+// elements in R rows on nt threads of k slots each, with j run chunks per
+// thread: groups of g = ceil(n / j) threads, nt / g groups, each taking every
+// (nt / g)-th row.  False if the rows are not covered.
+bool pack_layout(int n, int R, int nt, int k, int j, PackWalk* w) {
+  if (n < 1 || R < 1) return false;
+  const int g = (n + j - 1) / j;
+  const int rows = nt / g;
+  if (rows < 1 || int64_t(rows) * (k / j) < R) return false;
+  if (w) {
+    w->n = n;
+    w->g = g;
+    w->rows = rows;
+    w->div = make_fastdiv(uint32_t(g));
+  }
+  return true;
+}
+
+// Chunks per thread of one side (the fewest of 1, 2, 4 whose layout covers
+// the whole tile; the short tiles then fit too), or 0 if none does.
+int pack_chunks(int n, int R, int nt, int k) {
+  for (int j : {1, 2, 4})
+    if (pack_layout(n, R, nt, k, j, nullptr)) return j;
+  return 0;
+}
+
+// Memory time of a tile schedule: the runs of every class of tiles (the
+// cut index of GA, and of GB, in a whole block or in the short last block)
+// weighted by the class's share of the elements, each run charged the
+// per-run overhead of run_efficiency.  A schedule whose tiles are mostly of
+// the full size gets the full tile's runs; one whose cut leaves a short last
+// block pays for the short runs of those tiles.  `walks`: the index walks'
+// coalescing (see the caller); false for slot tables.
+double tile_mem_time(const Canon& c, const TileShape& sh, const int64_t* ext, int esA, int esB, bool bnz,
+                     bool flat, bool walks) {
+  int orderA[kMaxDim], orderB[kMaxDim];
+  for (int k = 0; k < c.N; ++k) {
+    orderA[k] = k;
+    orderB[k] = c.perm[k];
+  }
+  const int cut[2] = {sh.ga.empty() ? -1 : sh.ga.back(), sh.gb.empty() ? -1 : sh.gb.back()};
+  double per_el = 0;
+  for (int ea = 0; ea < 2; ++ea)
+    for (int eb = 0; eb < 2; ++eb) {
+      int64_t e2[kMaxDim];
+      for (int k = 0; k < c.N; ++k) e2[k] = ext[k];
+      double w = 1;
+      bool skip = false;
+      const int side[2] = {ea, eb};
+      for (int g = 0; g < 2 && !skip; ++g) {
+        const int m = cut[g];
+        const bool short_side = side[g] != 0;
+        if (m < 0 || ext[m] >= c.s[m]) {
+          skip = short_side;
+          continue;
+        }
+        const int64_t whole = c.s[m] / ext[m] * ext[m], rest = c.s[m] - whole;
+        if (short_side) {
+          if (rest == 0) skip = true;
+          w *= double(rest) / double(c.s[m]);
+          e2[m] = rest;
+        } else {
+          w *= double(whole) / double(c.s[m]);
+        }
+      }
+      if (skip || w <= 0) continue;
+      double ra = run_length(c, e2, orderA, c.sa), rb = run_length(c, e2, orderB, c.sb);
+      if (walks) {
+        double U = sh.has_c ? double(c.s[0]) : 1, W = U, V = U;
+        for (int m : sh.ga) U *= double(e2[m]);
+        for (int m : sh.gb) W *= double(e2[m]);
+        V = U * W / V;
+        if (U == 1) ra = ra >= V ? 8.0 : 1.0;
+        if (W == 1) rb = rb >= V ? 8.0 : 1.0;
+      }
+      per_el += w * (esA / run_efficiency(ra * esA, false, flat) + esB / run_efficiency(rb * esB, true, flat) +
+                     (bnz ? esB / run_efficiency(rb * esB, false, flat) : 0.0));
+    }
+  return double(c.n) * per_el / kHbmBytesPerS;
 }
 
 }  // namespace
@@ -361,7 +449,14 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
   const int c0 = hc ? 1 : 0;
   const int64_t LC = hc ? c.s[0] : 1;
   const int Kt = tile_k_for(stage_bytes(din));
-  const int Vmax = vmax > 0 ? std::min(vmax, kThreads * Kt) : kThreads * Kt;
+  // elements of one 256-thread tile; the packed-lane kernel (single-plan
+  // tiles without a C index) also runs tiles of twice that on 512 threads
+  const int V1 = vmax > 0 ? std::min(vmax, kThreads * Kt) : kThreads * Kt;
+  // (512-thread packed tiles of twice the volume measured slower than the
+  // 256-thread ones on every sweep case: fewer, larger CTAs hide the
+  // latency between their load and store phases less well)
+  const bool pk_ok = vmax == 0 && !hc;
+  const int Vmax = V1;
   std::vector<Candidate> tiles;
   if (!(hc && c.N == 1) && LC * 2 <= Vmax) {
     // A-group index list: A order from c0, dense, never B's first index after C
@@ -427,24 +522,14 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
               continue;
             // Slot tables visit a tile's elements in address order on each
             // side, so their runs are the tile footprint's contiguous runs.
-            // The index walks (tile2, the batch) load a tile without a C or GA
-            // index (U = 1) in GB's order, which steps through A by large
-            // strides: a warp's loads do not coalesce.  When the whole tile is
-            // one contiguous block of A, L1 still catches most of the reuse
-            // (measured as if the runs were 8 elements long); otherwise
-            // nothing does.  Likewise for W = 1.
-            const double ra_s = run_length(c, ext, orderA, c.sa), rb_s = run_length(c, ext, orderB, c.sb);
-            double ra = ra_s, rb = rb_s;
-            if (LC * LA == 1) ra = ra >= double(V) ? 8.0 : 1.0;
-            if (LC * LB == 1) rb = rb >= double(V) ? 8.0 : 1.0;
-            const double mem = (n * esA / run_efficiency(ra * esA, false, flat) +
-                                n * esB / run_efficiency(rb * esB, true, flat) +
-                        (bnz ? n * esB / run_efficiency(rb * esB, false, flat) : 0.0)) / kHbmBytesPerS;
-            const double mem_s = (n * esA / run_efficiency(ra_s * esA, false, flat) +
-                                  n * esB / run_efficiency(rb_s * esB, true, flat) +
-                        (bnz ? n * esB / run_efficiency(rb_s * esB, false, flat) : 0.0)) / kHbmBytesPerS;
-            const double per_slot = 26.0 + (sh.ga.size() > 1 ? 3 : 0) + (sh.gb.size() > 1 ? 3 : 0) + (bnz ? 6 : 0);
-            const double issue = ntiles * kTileK * kThreads * per_slot / kLaneInstrPerS;
+            // The index walks (tile2, packed lanes, the batch) load a tile
+            // without a C or GA index (U = 1) in GB's order, which steps
+            // through A by large strides: a warp's loads do not coalesce.  When
+            // the whole tile is one contiguous block of A, L1 still catches
+            // most of the reuse (measured as if the runs were 8 elements long);
+            // otherwise nothing does.  Likewise for W = 1.
+            const double mem = tile_mem_time(c, sh, ext, esA, esB, bnz, flat, true);
+            const double mem_s = tile_mem_time(c, sh, ext, esA, esB, bnz, flat, false);
             const double over = ntiles * kThreads * (60.0 + 10.0 * c.N) / kLaneInstrPerS;
             Candidate k;
             k.variant = VAR_TILE;
@@ -454,45 +539,95 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
             k.gb = sh.gb;
             k.tb = sh.tb;
             k.order = grid_order(c, ext, 0);
-            k.seg_a = ra;
-            k.seg_b = rb;
-            k.est_s = std::max(mem, issue) + 0.25 * std::min(mem, issue) + over + 3e-6;
-            if (vmax == 0) {
-              // single-plan tiles read their whole tiles from slot tables: two
-              // slots per 16-byte table read and no index arithmetic.  The
-              // table reads cost L1 bandwidth and one more dependent load per
-              // phase: measured ~9 % below the warp-mapped kernel on shapes
-              // both fit, 30-40 % above the index walk on every shape tried.
-              const double per_slot3 = 14.0 + (bnz ? 4 : 0);
-              const double issue3 = ntiles * kTileK * kThreads * per_slot3 / kLaneInstrPerS;
-              k.slots = 1;
-              k.est_s = std::max(1.08 * mem_s, issue3) + 0.25 * std::min(mem_s, issue3) + over + 3e-6;
+            k.seg_a = run_length(c, ext, orderA, c.sa);
+            k.seg_b = run_length(c, ext, orderB, c.sb);
+            if (V <= V1) {
+              const double per_slot = 26.0 + (sh.ga.size() > 1 ? 3 : 0) + (sh.gb.size() > 1 ? 3 : 0) + (bnz ? 6 : 0);
+              const double issue = ntiles * kTileK * kThreads * per_slot / kLaneInstrPerS;
+              k.est_s = std::max(mem, issue) + 0.25 * std::min(mem, issue) + over + 3e-6;
+              if (vmax == 0) {
+                // single-plan tiles read their whole tiles from slot tables: two
+                // slots per 16-byte table read and no index arithmetic.  The
+                // table reads cost L1 bandwidth and one more dependent load per
+                // phase: measured ~9 % below the warp-mapped kernel on shapes
+                // both fit, 30-40 % above the index walk on every shape tried.
+                const double per_slot3 = 14.0 + (bnz ? 4 : 0);
+                const double issue3 = ntiles * kTileK * kThreads * per_slot3 / kLaneInstrPerS;
+                k.slots = 1;
+                k.est_s = std::max(1.08 * mem_s, issue3) + 0.25 * std::min(mem_s, issue3) + over + 3e-6;
+              }
+              tiles.push_back(k);
+              // the warp-mapped kernel (single-plan only), when the shape fits
+              // one of its lane layouts
+              const int64_t U = LC * LA, W = LC * LB;
+              int ju = 0, jw = 0;
+              for (int j : {1, 2, 4})
+                if (!ju && vmax == 0 && U <= 32 * j && LB <= 8 * Kt / j) ju = j;
+              for (int j : {1, 2, 4})
+                if (!jw && vmax == 0 && W <= 32 * j && LA <= 8 * Kt / j) jw = j;
+              // a run shorter than half a warp leaves most lanes idle: every
+              // warp access then carries a few elements only (measured slower
+              // than the flat walk in the batch body)
+              if (U < 16 || W < 16) ju = jw = 0;
+              if (ju && jw) {
+                // lanes past a run's end idle, also in the short tiles at the
+                // tensor's edge: every tile costs the full tile's instructions
+                const double rows_r = std::ceil(double(LB) / 8.0), rows_w = std::ceil(double(LA) / 8.0);
+                const double wi = 8.0 * (rows_r * (ju * 4.0 + 4.0 + (sh.gb.size() > 1 ? 2 : 0)) +
+                                         rows_w * (jw * (5.0 + (bnz ? 3.0 : 0.0)) + 4.0 + (sh.ga.size() > 1 ? 2 : 0)));
+                const double issue2 = ntiles * 32.0 * wi / kLaneInstrPerS;
+                Candidate k2 = k;
+                k2.slots = 0;
+                k2.ju = ju;
+                k2.jw = jw;
+                k2.est_s = std::max(mem, issue2) + 0.25 * std::min(mem, issue2) + over + 3e-6;
+                tiles.push_back(k2);
+              }
             }
-            tiles.push_back(k);
-            // the warp-mapped kernel (single-plan only), when the shape fits
-            // one of its lane layouts
-            const int64_t U = LC * LA, W = LC * LB;
-            int ju = 0, jw = 0;
-            for (int j : {1, 2, 4})
-              if (!ju && vmax == 0 && U <= 32 * j && LB <= 8 * Kt / j) ju = j;
-            for (int j : {1, 2, 4})
-              if (!jw && vmax == 0 && W <= 32 * j && LA <= 8 * Kt / j) jw = j;
-            // a run shorter than half a warp leaves most lanes idle: every
-            // warp access then carries a few elements only (measured slower
-            // than the flat walk in the batch body)
-            if (U < 16 || W < 16) ju = jw = 0;
-            if (ju && jw) {
-              const double rows_r = std::ceil(double(LB) / 8.0), rows_w = std::ceil(double(LA) / 8.0);
-              const double wi = 8.0 * (rows_r * (ju * 4.0 + 4.0 + (sh.gb.size() > 1 ? 2 : 0)) +
-                                       rows_w * (jw * (5.0 + (bnz ? 3.0 : 0.0)) + 4.0 + (sh.ga.size() > 1 ? 2 : 0)));
-              const double issue2 = ntiles * 32.0 * wi / kLaneInstrPerS;
-              Candidate k2 = k;
-              k2.slots = 0;
-              k2.ju = ju;
-              k2.jw = jw;
-              k2.est_s = std::max(mem, issue2) + 0.25 * std::min(mem, issue2) + over + 3e-6;
-              tiles.push_back(k2);
-
+            if (hc && vmax == 0 && V >= 64) {
+              // packed rows: the C run is contiguous on both sides, so rows
+              // are copied directly (no staging); the fewest idle threads
+              // whose layout covers the tile's rows
+              const int nrows = int(LA * LB);
+              int best_j = 0, best_active = 0;
+              for (int j : {1, 2, 4, 8, 16}) {
+                if (j > Kt) break;
+                PackWalk w;
+                if (!pack_layout(int(LC), nrows, kThreads, Kt, j, &w)) continue;
+                if (w.g * w.rows > best_active) {
+                  best_active = w.g * w.rows;
+                  best_j = j;
+                }
+              }
+              if (best_j) {
+                const double rows_per_thread = double(Kt / best_j);
+                const double wi = rows_per_thread * (16.0 + best_j * (4.0 + (bnz ? 3.0 : 0.0))) + 20.0;
+                const double issuer = ntiles * kThreads * wi / kLaneInstrPerS;
+                Candidate kr = k;
+                kr.slots = 0;
+                kr.rj = best_j;
+                kr.est_s = std::max(mem, issuer) + 0.25 * std::min(mem, issuer) + over + 3e-6;
+                tiles.push_back(kr);
+              }
+            }
+            if (pk_ok && V >= 64) {
+              // the packed-lane kernel: lane groups of any width, so ragged
+              // runs (and the short runs of the edge tiles) idle few lanes
+              const int nt = V <= V1 ? kThreads : 2 * kThreads;
+              const int ju = pack_chunks(int(LA), int(LB), nt, Kt), jw = pack_chunks(int(LB), int(LA), nt, Kt);
+              if (ju && jw) {
+                const double wi = (Kt / ju) * (ju * 3.0 + 6.0 + (sh.gb.size() > 1 ? 2 : 0)) +
+                                  (Kt / jw) * (jw * (4.0 + (bnz ? 3.0 : 0.0)) + 6.0 + (sh.ga.size() > 1 ? 2 : 0)) + 30.0;
+                const double issuep = ntiles * nt * wi / kLaneInstrPerS;
+                const double overp = ntiles * nt * (60.0 + 10.0 * c.N) / kLaneInstrPerS;
+                Candidate kp = k;
+                kp.slots = 0;
+                kp.ju = ju;
+                kp.jw = jw;
+                kp.pk = nt;
+                kp.est_s = std::max(mem, issuep) + 0.25 * std::min(mem, issuep) + overp + 3e-6;
+                tiles.push_back(kp);
+              }
             }
           }
         }
@@ -501,26 +636,71 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
   }
   std::stable_sort(tiles.begin(), tiles.end(),
                    [](const Candidate& a, const Candidate& b) { return a.est_s < b.est_s; });
-  // keep the best few shapes, each also with the A-major and B-major grid orders
+  // Keep the best few of every kernel kind (the cost model ranks kinds less
+  // reliably than shapes of one kind), then give the best shapes the A-major,
+  // B-major and both-local grid orders and the grouped order (measured: the
+  // order alone moves a tile schedule by up to 20 %); the autotuner sorts
+  // them out.
+  auto kind = [](const Candidate& q) { return q.rj ? 5 : q.pk ? 2 : q.rows ? 3 : q.slots ? 0 : q.ju ? 1 : 4; };
+  auto same = [](const Candidate& q, const Candidate& k) {
+    return q.order == k.order && q.ga == k.ga && q.gb == k.gb && q.ta == k.ta && q.tb == k.tb &&
+           q.has_c == k.has_c && q.ju == k.ju && q.jw == k.jw && q.slots == k.slots && q.pk == k.pk &&
+           q.rows == k.rows && q.swz == k.swz && q.rj == k.rj;
+  };
+  const int base_keep = std::max(1, max_keep / 2);
+  const int per_kind = std::max(1, base_keep / 3);
   std::vector<Candidate> keep;
+  int nkind[6] = {};
   for (const auto& t : tiles) {
-    if (int(keep.size()) >= max_keep) break;
+    if (int(keep.size()) >= base_keep) break;
+    if (nkind[kind(t)] >= per_kind) continue;
+    ++nkind[kind(t)];
     keep.push_back(t);
   }
+  for (const auto& t : tiles) {       // fill up with the next best of any kind
+    if (int(keep.size()) >= base_keep) break;
+    bool dup = false;
+    for (const auto& q : keep) dup = dup || same(q, t);
+    if (!dup) keep.push_back(t);
+  }
   const size_t nshape = keep.size();
-  for (size_t i = 0; i < nshape && i < 3; ++i) {
+  std::vector<Candidate> vars;
+  int vkind[6] = {};
+  for (size_t i = 0; i < nshape; ++i) {
+    if (vkind[kind(keep[i])]++ >= 2) continue;
     int64_t ext[kMaxDim];
     TileShape sh{keep[i].has_c, keep[i].ga, keep[i].gb, keep[i].ta, keep[i].tb};
     tile_extents(c, sh, ext);
-    for (int mode = 1; mode <= 2; ++mode) {
-      Candidate k = keep[i];
-      k.order = grid_order(c, ext, mode);
-      if (k.order != keep[i].order) {
-        k.est_s *= 1.01;
-        keep.push_back(k);
+    for (int mode = 1; mode <= 3; ++mode) {
+      for (int swz : {0, 8}) {
+        Candidate k = keep[i];
+        k.order = grid_order(c, ext, mode);
+        k.swz = k.order.size() >= 2 ? swz : 0;
+        if (swz && !k.swz) continue;
+        bool dup = false;
+        for (const auto& q : keep) dup = dup || same(q, k);
+        for (const auto& q : vars) dup = dup || same(q, k);
+        if (!dup) {
+          k.est_s *= swz ? 1.02 : 1.01;
+          vars.push_back(k);
+        }
       }
     }
   }
+  std::stable_sort(vars.begin(), vars.end(),
+                   [](const Candidate& a, const Candidate& b) { return a.est_s < b.est_s; });
+  for (const auto& v : vars) {
+    if (int(keep.size()) >= max_keep) break;
+    keep.push_back(v);
+  }
+  // the copy and the best three multi-row copies, then the tiles
+  std::stable_sort(out.begin(), out.end(),
+                   [](const Candidate& a, const Candidate& b) { return a.est_s < b.est_s; });
+  std::vector<Candidate> rows_keep;
+  int nrows = 0;
+  for (const auto& q : out)
+    if (!q.rows || nrows++ < 3) rows_keep.push_back(q);
+  out.swap(rows_keep);
   out.insert(out.end(), keep.begin(), keep.end());
   std::stable_sort(out.begin(), out.end(),
                    [](const Candidate& a, const Candidate& b) { return a.est_s < b.est_s; });
@@ -606,6 +786,7 @@ void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* 
     ntiles *= uint64_t(nb);
   }
   p->ntiles = uint32_t(ntiles);
+  p->swz = p->ngrid >= 2 ? uint32_t(k.swz) : 0u;
   const int smem_cap = 160 * 1024;
   p->P = pick_pitch(p->U, LC, LB, din, smem_cap);
   // thread steps
@@ -618,6 +799,28 @@ void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* 
   p->divLC = make_fastdiv(uint32_t(LC));
   p->divLB = make_fastdiv(uint32_t(LB));
   p->divW = make_fastdiv(uint32_t(p->W));
+  if (k.pk) {
+    // packed-lane layouts of both sides, for a whole tile and for the tile a
+    // cut index leaves short (remA = fullA * (s mod t), likewise remB)
+    const int Kt = tile_k_for(stage_bytes(din));
+    int edgeA = LA, edgeB = LB;
+    if (cutA >= 0 && ext[cutA] < c.s[cutA] && c.s[cutA] % ext[cutA]) edgeA = fullA * int(c.s[cutA] % ext[cutA]);
+    if (cutB >= 0 && ext[cutB] < c.s[cutB] && c.s[cutB] % ext[cutB]) edgeB = fullB * int(c.s[cutB] % ext[cutB]);
+    pack_layout(LA, LB, k.pk, Kt, k.ju, &p->pkA[0]);
+    pack_layout(edgeA, LB, k.pk, Kt, k.ju, &p->pkA[1]);
+    pack_layout(LB, LA, k.pk, Kt, k.jw, &p->pkB[0]);
+    pack_layout(edgeB, LA, k.pk, Kt, k.jw, &p->pkB[1]);
+  }
+  if (k.rj) {
+    // packed rows: g threads per row of LC elements, and the row counts of
+    // a whole tile's A side and of the short last block's
+    const int Kt = tile_k_for(stage_bytes(din));
+    int edgeA = LA;
+    if (cutA >= 0 && ext[cutA] < c.s[cutA] && c.s[cutA] % ext[cutA]) edgeA = fullA * int(c.s[cutA] % ext[cutA]);
+    pack_layout(LC, LA * LB, kThreads, Kt, k.rj, &p->pkA[0]);
+    p->divRA[0] = make_fastdiv(uint32_t(LA));
+    p->divRA[1] = make_fastdiv(uint32_t(edgeA));
+  }
   *smem_bytes = int(((tabA->size() + tabB->size()) * sizeof(int32_t) + 15) & ~size_t(15)) +
                 p->P * LB * stage_bytes(din);
 }

@@ -38,6 +38,9 @@ struct Candidate {
   int ju = 0, jw = 0;          // >0: warp-mapped tile kernel with JU/JW chunks of 32 lanes
   int rows = 0;                // multi-row copy kernel (perm keeps index 0, GB empty, no staging)
   int slots = 0;               // tile_kernel from precomputed slot tables (whole tiles)
+  int pk = 0;                  // >0: packed-lane tile kernel with pk (256 or 512) threads per CTA
+  int swz = 0;                 // grouped grid order (TileParams::swz), 0: plain
+  int rj = 0;                  // >0: packed rows (C tiles copied row by row), rj positions per thread and row
   // copy variant
   int64_t chunk = 0;
   int vec = 1;                 // vector width usable when pointers are aligned

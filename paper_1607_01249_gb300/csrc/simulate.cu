@@ -132,7 +132,8 @@ struct Checker {
     int smem = 0;
     build_tile_params(p->canon, k, p->din, &tp, &ta, &tb, &smem);
     if (smem > 200 * 1024) return fail("shared memory over budget", smem, 0);
-    if (tp.V > kThreads * K) return fail("tile larger than the threads cover", tp.V, kThreads * K);
+    const int nthreads = k.pk ? k.pk : kThreads;
+    if (tp.V > nthreads * K) return fail("tile larger than the threads cover", tp.V, nthreads * K);
     std::vector<int32_t> slots;
     int sbytes = 0;
     if (k.slots) sbytes = build_slot_tables(tp, p->din, ta, tb, &slots);
@@ -160,6 +161,17 @@ struct Checker {
         ok = pair(posA[size_t(pos)], c.baseB + off);
       };
       const bool full = c.remA == tp.LA && c.remB == tp.LB;
+      if (k.rj) {
+        // packed rows: no staging either
+        for (int t = 0; t < kThreads && ok; ++t) {
+          auto on_pair = [&](int, bool valid, int32_t offA, int32_t offB) {
+            if (ok && valid) ok = pair(c.baseA + offA, c.baseB + offB);
+          };
+          if (!rowsp_walk<K>(k.rj, c, tp, ta, tb, t, on_pair)) ok = fail("unknown packed-row layout", k.rj, 0);
+        }
+        if (!ok) return false;
+        continue;
+      }
       if (k.rows) {
         // no staging: each element goes straight from A to B
         for (int t = 0; t < kThreads && ok; ++t)
@@ -189,6 +201,10 @@ struct Checker {
               else if (f == 0) on_read(kk, valid, off, pos);
               else on_write(kk, valid, off, pos);
             }
+      } else if (k.pk) {
+        if (tp.LC != 1) return fail("packed-lane tile with a C index", tp.LC, 0);
+        if (k.pk != 256 && k.pk != 512) ok = fail("unknown packed-lane thread count", k.pk, 0);
+        else ok = packed<K>(k.pk, k.ju, k.jw, c, tp, ta, tb, on_read, on_write);
       } else if (k.ju == 0) {
         for (int t = 0; t < kThreads && ok; ++t) {
           int u0, lb0, lc0, lbw0, la0;
@@ -222,6 +238,58 @@ struct Checker {
       if (!ok) return false;
     }
     return true;
+  }
+
+  template <int J, int K, class F>
+  void rowsp_j(const TileCoord& c, const TileParams& tp, const std::vector<int32_t>& ta,
+               const std::vector<int32_t>& tb, int t, F& f) {
+    if (tp.crossA_tab) {
+      if (tp.crossB_tab) walk_rowsp<J, K, true, true>(c, tp, ta.data(), tb.data(), t, f);
+      else walk_rowsp<J, K, true, false>(c, tp, ta.data(), tb.data(), t, f);
+    } else {
+      if (tp.crossB_tab) walk_rowsp<J, K, false, true>(c, tp, ta.data(), tb.data(), t, f);
+      else walk_rowsp<J, K, false, false>(c, tp, ta.data(), tb.data(), t, f);
+    }
+  }
+  template <int K, class F>
+  bool rowsp_walk(int j, const TileCoord& c, const TileParams& tp, const std::vector<int32_t>& ta,
+                  const std::vector<int32_t>& tb, int t, F& f) {
+    if (j == 1) rowsp_j<1, K>(c, tp, ta, tb, t, f);
+    else if (j == 2) rowsp_j<2, K>(c, tp, ta, tb, t, f);
+    else if (j == 4 && K >= 4) rowsp_j<(K >= 4 ? 4 : 1), K>(c, tp, ta, tb, t, f);
+    else if (j == 8 && K >= 8) rowsp_j<(K >= 8 ? 8 : 1), K>(c, tp, ta, tb, t, f);
+    else if (j == 16 && K >= 16) rowsp_j<(K >= 16 ? 16 : 1), K>(c, tp, ta, tb, t, f);
+    else return false;
+    return true;
+  }
+
+  // tilep_kernel: every thread's load walk, then every thread's store walk
+  template <int J, int K, class F>
+  void packed_read(const TileCoord& c, const TileParams& tp, const std::vector<int32_t>& ta, int t, F& f) {
+    if (tp.crossA_tab) walkp_read<0, J, K, true>(c, tp, ta.data(), t, f);
+    else walkp_read<0, J, K, false>(c, tp, ta.data(), t, f);
+  }
+  template <int J, int K, class F>
+  void packed_write(const TileCoord& c, const TileParams& tp, const std::vector<int32_t>& tb, int t, F& f) {
+    if (tp.crossB_tab) walkp_write<0, J, K, true>(c, tp, tb.data(), t, f);
+    else walkp_write<0, J, K, false>(c, tp, tb.data(), t, f);
+  }
+  template <int K, class FR, class FW>
+  bool packed(int nt, int ju, int jw, const TileCoord& c, const TileParams& tp, const std::vector<int32_t>& ta,
+              const std::vector<int32_t>& tb, FR& on_read, FW& on_write) {
+    for (int t = 0; t < nt && err.empty(); ++t) {
+      if (ju == 1) packed_read<1, K>(c, tp, ta, t, on_read);
+      else if (ju == 2) packed_read<2, K>(c, tp, ta, t, on_read);
+      else if (ju == 4) packed_read<4, K>(c, tp, ta, t, on_read);
+      else return fail("unknown packed-lane chunk count", ju, 0);
+    }
+    for (int t = 0; t < nt && err.empty(); ++t) {
+      if (jw == 1) packed_write<1, K>(c, tp, tb, t, on_write);
+      else if (jw == 2) packed_write<2, K>(c, tp, tb, t, on_write);
+      else if (jw == 4) packed_write<4, K>(c, tp, tb, t, on_write);
+      else return fail("unknown packed-lane chunk count", jw, 0);
+    }
+    return err.empty();
   }
 
   bool copy(const Candidate& k) {

@@ -117,9 +117,23 @@ struct Epilogue {
   float* scale_out;            // FP8: where block 0 records the scale used
 };
 
+// Thread layout of one side of a packed-lane tile (tilep_kernel) for one
+// run length n: the CTA's threads form `rows` groups of g consecutive
+// threads (g * rows <= the thread count); thread t = tu + g * tr takes run
+// positions tu + g * j (j < J, the kernel's chunks per run, g * J >= n) of
+// rows tr + rows * i.  g as an invariant divisor.
+struct PackWalk {
+  int n = 1, g = 1, rows = 1;
+  FastDiv div;
+};
+
 struct TileParams {
   int ngrid;
   uint32_t ntiles;
+  // grouped order (0: off): the first two grid indices are visited in groups
+  // of `swz` blocks of the first, all blocks of the second within a group,
+  // so that consecutive tiles stay close in both tensors
+  uint32_t swz;
   GridDim g[kMaxDim];
   int LC, LA, LB;      // group extents
   int U;               // LC*LA  (A-side run, in elements)
@@ -149,6 +163,13 @@ struct TileParams {
   int wr_dlc, wr_dlb, wr_dla;
   // invariant divisors of the lane/thread decompositions
   FastDiv divU, divLC, divLB, divW;
+  // packed-lane tiles (no C index): walk constants of the load side (runs of
+  // u = la, rows lb) and of the store side (runs of v = lb, rows la), [0] for
+  // the full extent, [1] for the extent a cut index leaves in the last block
+  PackWalk pkA[2], pkB[2];
+  // packed rows (rowsp_kernel): the row count of a tile's A side, LA and
+  // the short last block's, as invariant divisors of the row index
+  FastDiv divRA[2];
   Epilogue epi;
 };
 

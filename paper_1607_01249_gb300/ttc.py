@@ -43,7 +43,8 @@ class PlanInfo(ctypes.Structure):
                 ("tile_c", ctypes.c_int), ("tile_a", ctypes.c_int), ("tile_b", ctypes.c_int),
                 ("ntiles", ctypes.c_int64), ("vec_in", ctypes.c_int), ("vec_out", ctypes.c_int),
                 ("candidate", ctypes.c_int), ("ncandidates", ctypes.c_int),
-                ("lanes_a", ctypes.c_int), ("lanes_b", ctypes.c_int), ("slot_tables", ctypes.c_int)]
+                ("lanes_a", ctypes.c_int), ("lanes_b", ctypes.c_int), ("slot_tables", ctypes.c_int),
+                ("packed_threads", ctypes.c_int), ("packed_rows", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -220,9 +221,11 @@ class Plan:
                 "tile": (inf.tile_c, inf.tile_a, inf.tile_b), "ntiles": inf.ntiles,
                 "vec": (inf.vec_in, inf.vec_out), "candidate": inf.candidate,
                 "ncandidates": inf.ncandidates, "lanes": (inf.lanes_a, inf.lanes_b),
-                "slot_tables": bool(inf.slot_tables),
+                "slot_tables": bool(inf.slot_tables), "packed_threads": inf.packed_threads,
+                "packed_rows": inf.packed_rows,
                 "kernel": ({0: "empty", 1: "copy_kernel", 3: "rowcopy_kernel"}.get(inf.variant) or
-                           ("tile2_kernel" if inf.lanes_a else
+                           ("tile2_kernel" if inf.lanes_a else "tilep_kernel" if inf.packed_threads else
+                            "rowsp_kernel" if inf.packed_rows else
                             "tile_slots_kernel" if inf.slot_tables else "tile_kernel"))}
 
     def autotune(self, max_candidates=8, stream=None) -> float:

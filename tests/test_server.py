@@ -167,25 +167,33 @@ def test_server_watchdog_gives_up_an_epoch_and_keeps_serving():
     import torch
     from tests import gpu_helpers as H
     srv = ttc.Server(1 << 30, 2, 4096)
+    probs = [Problem(perm=(1, 0), sizes=(300, 200)), Problem(perm=(2, 0, 1), sizes=(64, 50, 70), alpha=1.5)]
+
+    def serve_all():
+        data = []
+        for i, p in enumerate(probs):
+            plan = ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta)
+            A, B0 = H.make_inputs(p, 40 + i)
+            dA, dB = H.to_device(A, p.dtype_in), H.to_device(B0, p.dtype_out)
+            data.append((p, A, B0, dB, srv.submit(plan, dA, dB)))
+        for p, A, B0, dB, t in data:
+            assert srv.poll(t, 5_000_000)
+            torch.cuda.synchronize()
+            want, _ = H.oracle_mirror(p, A, B0)
+            assert H.compare_bits(H.to_host(dB, p.dtype_out), want, p.dtype_out, True)[0]
+
+    # once under the default watchdog: the first launches of the serving
+    # kernels (whose code the driver may load then) are not what the short
+    # watchdog below is about
+    serve_all()
     srv.set_watchdog(0.1)
     t_slow = srv.submit_delay(400_000)
     with pytest.raises(ttc.TTCError) as ei:
         srv.poll(t_slow, 3_000_000)
     assert ei.value.name == "TTC_ERR_TIMEOUT"
-    probs = [Problem(perm=(1, 0), sizes=(300, 200)), Problem(perm=(2, 0, 1), sizes=(64, 50, 70), alpha=1.5)]
-    data = []
-    for i, p in enumerate(probs):
-        plan = ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta)
-        A, B0 = H.make_inputs(p, 40 + i)
-        dA, dB = H.to_device(A, p.dtype_in), H.to_device(B0, p.dtype_out)
-        data.append((p, A, B0, dB, srv.submit(plan, dA, dB)))
-    for p, A, B0, dB, t in data:
-        assert srv.poll(t, 5_000_000)
-        torch.cuda.synchronize()
-        want, _ = H.oracle_mirror(p, A, B0)
-        assert H.compare_bits(H.to_host(dB, p.dtype_out), want, p.dtype_out, True)[0]
+    serve_all()
     st = srv.stats()
-    assert st["failed"] == 1 and st["completed"] == len(probs)
+    assert st["failed"] == 1 and st["completed"] == 2 * len(probs)
     t0 = time.time()
     srv.close()
     assert time.time() - t0 < 5.0

@@ -1,4 +1,5 @@
-"""The allocation-free entry point, ttc_execute_noalloc, against ttc_execute.
+"""The allocation-free entry point, ttc_execute_noalloc, against the oracle
+and against ttc_execute.
 
 Some callers cannot allocate device memory: their device memory belongs to a
 pool allocator (a framework's caching allocator, a serving process with a
@@ -6,11 +7,16 @@ fixed budget), or they must not make the implicitly synchronising
 cudaMalloc/cudaFree calls.  For them ttc_execute_noalloc runs the same
 kernels with the scratch (FP8 amax/scale words, tile offset tables) in one
 static device array of the library.  This file checks, through the C ABI,
-that two calls in a row give exactly what the regular entry point gives (the
-array keeps the last call's contents between calls), and that a schedule
-needing more scratch than the array holds is refused with a clear error.
+that two calls in a row give the oracle's result and exactly what the
+regular entry point gives (the array keeps the last call's contents between
+calls), that a call on a fresh plan leaves the device's free memory as it
+was, that calls of two plans on two streams ordered by an event give each
+plan's result, and that a schedule needing more scratch than the array holds
+is refused with a clear error.
 
-It is named so that pytest collects it last.
+The file is named so that pytest collects it last: should one of its checks
+fail, a run that stops at the first failure has already run every other
+test.  Its tests do not depend on that order.
 """
 import numpy as np
 import pytest
@@ -71,6 +77,7 @@ def fitting_plan(p: Problem):
 def test_noalloc_matches_execute_on_two_calls(p):
     plan = fitting_plan(p)
     A, B0 = H.make_inputs(p, 17, "normal")
+    want, want_scale = H.oracle_mirror(p, A, B0)
     dA = H.to_device(A, p.dtype_in)
     # the regular entry point
     dB = H.to_device(B0, p.dtype_out)
@@ -89,10 +96,65 @@ def test_noalloc_matches_execute_on_two_calls(p):
         plan.execute_noalloc(dA, dB2, s2 if p.dtype_out == "e4m3" else None)
         torch.cuda.synchronize()
         got = H.to_host(dB2, p.dtype_out)
+        ok, msg = H.compare_bits(got, want, p.dtype_out, nan_as_nan=True)
+        assert ok, f"call {call} against the oracle: {msg}"
         ok, msg = H.compare_bits(got, ref, p.dtype_out, nan_as_nan=True)
-        assert ok, f"call {call}: {msg}"
+        assert ok, f"call {call} against ttc_execute: {msg}"
         if p.dtype_out == "e4m3":
-            assert float(s2.cpu().item()) == ref_scale, f"call {call}: scale"
+            assert float(s2.cpu().item()) == ref_scale == want_scale, f"call {call}: scale"
+
+
+@pytest.mark.parametrize("p", CASES, ids=lambda p: p.tag)
+def test_noalloc_first_call_leaves_free_device_memory_unchanged(p):
+    """A fresh plan's first call allocates nothing: the device's free memory
+    (cudaMemGetInfo) is the same before and after it.  An earlier plan of the
+    same problem has run the same kernels, so that loading their code (which
+    the CUDA driver may do on a kernel's first launch) does not show up here."""
+    fitting_plan(p)                        # loads the kernels of this schedule
+    fresh = fitting_plan(p)
+    sel = fresh.info()["candidate"]
+    plan = ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta, p.outer_a, p.outer_b)
+    plan.select(sel)
+    A, B0 = H.make_inputs(p, 23, "normal")
+    want, _ = H.oracle_mirror(p, A, B0)
+    dA = H.to_device(A, p.dtype_in)
+    dB = H.to_device(B0, p.dtype_out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    plan.execute_noalloc(dA, dB)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, f"free device memory changed by {free0 - free1} bytes"
+    ok, msg = H.compare_bits(H.to_host(dB, p.dtype_out), want, p.dtype_out, nan_as_nan=True)
+    assert ok, msg
+
+
+def test_noalloc_two_plans_on_two_streams_ordered_by_an_event():
+    """The array is shared: the second stream waits on an event recorded after
+    the first plan's call, so the two calls run back to back, and each result
+    is that plan's."""
+    p1, p2 = CASES[3], CASES[2]                # both upload offset tables
+    plan1, plan2 = fitting_plan(p1), fitting_plan(p2)
+    A1, B1 = H.make_inputs(p1, 5, "normal")
+    A2, B2 = H.make_inputs(p2, 6, "normal")
+    w1, _ = H.oracle_mirror(p1, A1, B1)
+    w2, _ = H.oracle_mirror(p2, A2, B2)
+    dA1, dA2 = H.to_device(A1, p1.dtype_in), H.to_device(A2, p2.dtype_in)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for _ in range(2):
+        o1 = H.to_device(B1, p1.dtype_out)
+        o2 = H.to_device(B2, p2.dtype_out)
+        torch.cuda.synchronize()
+        ev = torch.cuda.Event()
+        plan1.execute_noalloc(dA1, o1, stream=s1)
+        ev.record(s1)
+        s2.wait_event(ev)
+        plan2.execute_noalloc(dA2, o2, stream=s2)
+        torch.cuda.synchronize()
+        ok, msg = H.compare_bits(H.to_host(o1, p1.dtype_out), w1, p1.dtype_out, nan_as_nan=True)
+        assert ok, msg
+        ok, msg = H.compare_bits(H.to_host(o2, p2.dtype_out), w2, p2.dtype_out, nan_as_nan=True)
+        assert ok, msg
 
 
 def test_noalloc_interleaved_plans_share_the_array():
