@@ -777,6 +777,12 @@ def run_contraction(args, rank, world):
             l0 = ttc.launch_count()
             ms = timed(lambda: con.execute(A, B, C, stream))
             launches += (ttc.launch_count() - l0) // (steps + max(args.warmup, 3))
+            ms_cublas = None
+            if gd == "bf16":
+                # the timed comparison: the same K-major BF16 operands on cuBLAS
+                con.use_cublas(True)
+                ms_cublas = timed(lambda: con.execute(A, B, C, stream))
+                con.use_cublas(False)
             mt = torch.float32 if gd == "f32" else torch.bfloat16
             X = torch.empty(inf["m"], inf["k"], device="cuda", dtype=mt).uniform_(-1, 1, generator=g)
             Y = torch.empty(inf["k"], inf["n"], device="cuda", dtype=mt).uniform_(-1, 1, generator=g)
@@ -787,7 +793,11 @@ def run_contraction(args, rank, world):
             row[gd] = {"m": inf["m"], "n": inf["n"], "k": inf["k"], "permuted": inf["permuted"],
                        "ms": round(ms, 4), "TFLOP/s": round(tf, 1), "gemm_only_ms": round(ms_gemm, 4),
                        "transpose_share": round(max(ms - ms_gemm, 0.0) / ms, 3),
-                       "frac_of_peak": round(tf / world / peak, 3) if peak else None}
+                       "frac_of_peak": round(tf / world / peak, 3) if peak else None,
+                       "gemm": "tcgen05 (this library)" if gd == "bf16" else "cuBLAS SIMT FP32 (pedantic)"}
+            if ms_cublas:
+                row[gd]["with_cublas_gemm_ms"] = round(ms_cublas, 4)
+                row[gd]["speedup_vs_cublas_gemm"] = round(ms_cublas / ms, 3)
             tot_flop += flop
             tot_ms += ms
             con.close()

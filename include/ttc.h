@@ -296,10 +296,15 @@ ttc_status ttc_batch_set_direct_threshold(ttc_batch_t batch, int64_t min_element
  * B and C) is a free index; every label must appear in exactly two of the
  * three tensors with the same extent (labels in all three, i.e. batched
  * contractions, and labels in one tensor only are rejected with
- * TTC_ERR_INVALID_PERM).  Each operand is permuted by this library's kernels
- * into a column-major matrix unless it already is one (either orientation);
- * the product is one cuBLAS GEMM; C takes the GEMM's output directly when it
- * is laid out as [free A labels, free B labels] or the reverse, else it is
+ * TTC_ERR_INVALID_PERM).  The product is one GEMM.  With gemm_dtype TTC_BF16
+ * both operands are permuted by this library's kernels into K-major BF16
+ * matrices (contracted labels fastest, row pitch rounded up to 8 elements)
+ * and the GEMM is this library's tensor-core kernel (tcgen05, operands
+ * copied by TMA, FP32 accumulator in tensor memory).  The exact FP32 and
+ * FP64 modes permute an operand into a column-major matrix unless it already
+ * is one (either orientation) and run a cuBLAS GEMM in pedantic math (no
+ * reduced-precision substitution).  C takes the GEMM's output directly when
+ * it is laid out as [free A labels, free B labels] or the reverse, else it is
  * permuted from a workspace with the beta update of Eq. 1.
  *
  *  ttc_contraction_plan     validate and plan (host only).  dtype: type of A,
@@ -312,9 +317,14 @@ ttc_status ttc_batch_set_direct_threshold(ttc_batch_t batch, int64_t min_element
  *                           inconsistent extents or a GEMM extent >= 2^31.
  *  ttc_contraction_execute  enqueue on `stream` (A, B, C device pointers;
  *                           C must not overlap A or B).  Workspaces (the
- *                           permuted operands and product) and the cuBLAS
- *                           handle are created on the first execution on a
- *                           device and owned by the contraction.
+ *                           permuted operands and product, an error word)
+ *                           and the cuBLAS handle are created on the first
+ *                           execution on a device and owned by the
+ *                           contraction.
+ *  ttc_contraction_check    synchronous: TTC_ERR_TIMEOUT (reported once) if
+ *                           a bounded wait of the tensor-core GEMM gave up
+ *                           since the last check (that execution's C is not
+ *                           valid), else TTC_OK.
  *  ttc_contraction_info     GEMM extents m, n, k and which tensors are
  *                           permuted (bit 0: A, bit 1: B, bit 2: C).
  *  ttc_contraction_destroy  release (no work using it may be queued).
@@ -326,6 +336,7 @@ ttc_status ttc_contraction_plan(ttc_contraction_t* out, int nA, const int* modes
                                 double beta);
 ttc_status ttc_contraction_execute(ttc_contraction_t c, const void* A, const void* B, void* C,
                                    ttc_stream_t stream);
+ttc_status ttc_contraction_check(ttc_contraction_t c);
 ttc_status ttc_contraction_info(ttc_contraction_t c, int64_t* m, int64_t* n, int64_t* k, int* transposes);
 ttc_status ttc_contraction_destroy(ttc_contraction_t c);
 

@@ -66,6 +66,14 @@ ttc_status ttc_debug_server_submit_delay(ttc_server_t server, int64_t microsecon
  */
 ttc_status ttc_debug_packed_gemm_skip_mma(ttc_packed_gemm_t g, int skip);
 
+/*
+ * A timed comparison for the BF16 contraction: with use != 0 the
+ * contraction's GEMM on the same K-major BF16 operands runs on cuBLAS
+ * instead of this library's tensor-core kernel (use = 0 restores it).  No
+ * effect on the FP32 and FP64 modes.
+ */
+ttc_status ttc_debug_contraction_use_cublas(ttc_contraction_t c, int use);
+
 #ifdef __cplusplus
 }
 #endif

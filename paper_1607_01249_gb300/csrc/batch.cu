@@ -1,17 +1,19 @@
-// batch.cu -- many permute-scale-adds in one persistent kernel launch
-// (include/ttc.h, ttc_batch_*).
+// batch.cu -- many permute-scale-adds in one kernel launch (include/ttc.h,
+// ttc_batch_*).
 //
-// Every problem of a batch is cut into tiles by its own plan.  A tile is
-// processed by one CTA with one of three bodies:
-//   BP_TILE -- the generic staged tile (flat walks, offset tables for both
-//              cross offsets), for problems whose perm moves index 0 (the
-//              warp-mapped walks of tile2_kernel measured slower here: the
-//              batch's small problems leave most of their lanes idle);
-//   BP_ROWS -- the multi-row copy (perm keeps index 0, short runs);
+// Every problem of a batch is cut into tiles by its own plan (the batch
+// body's schedules: tiles of at most half the single-plan kernels' volume).
+// A tile is processed by one CTA with one of three bodies:
+//   BP_TILE -- the packed-lane tile (problems whose perm moves index 0): lane
+//              groups of any width over the tile's rows, so the many small
+//              problems of a batch, whose runs are short and ragged, keep
+//              their lanes busy;
+//   BP_ROWS -- packed rows (perm keeps index 0, tiles of whole rows copied
+//              directly);
 //   BP_COPY -- one chunk of one long run (perm keeps index 0, long runs).
-// Resident CTAs claim tiles from one atomic counter (uneven problems balance
-// themselves); a per-tile map names the problem, whose descriptor (pointers,
-// tile parameters, epilogue) sits in one device arena owned by the batch.
+// The launch has one CTA per tile of the whole batch; a per-tile record names
+// the problem, whose descriptor (pointers, tile parameters, epilogue) sits in
+// one device arena owned by the batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,62 +26,22 @@
 
 #include "../../include/ttc.h"
 #include "batch_impl.h"
-#include "kernels.cuh"
+#include "kernels_impl.cuh"
 #include "launch.h"
 #include "plan_impl.h"
 #include "planner.h"
 
 namespace ttc {
 
-extern std::atomic<int64_t> g_launches;
-cudaError_t grid_for(const void* fn, int smem, int64_t work, int* grid);
-
 // --------------------------------------------------------------- device --
 
-template <int DIN, int DOUT, bool BNZ, bool TAB>
-__device__ __forceinline__ void batch_tile(const BatchDesc& d, const TileCoord& c, unsigned char* smem) {
-  using S = stage_t<DIN>;
-  using TO = store_t<DOUT>;
-  constexpr int K = batch_k_for(sizeof(S));
-  const WalkP p = walk_params(d.tp);      // registers, not shared-memory loads per element
-  const int t = threadIdx.x;
-  const store_t<DIN>* Ab = static_cast<const store_t<DIN>*>(d.A) + c.baseA;
-  TO* Bb = static_cast<TO*>(d.B) + c.baseB;
-  S v[K];
-  TO bo[K] = {};
-  if (d.path == BP_ROWS) {
-    walk_rows<K>(c, p, t, [&](int k, bool, int32_t offA, int32_t offB) {
-      v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + offA));
-      if constexpr (BNZ) bo[k] = Bb[offB];
-    });
-    walk_rows<K>(c, p, t, [&](int k, bool ok, int32_t, int32_t offB) {
-      if (ok) Bb[offB] = epilogue<DIN, DOUT>(v[k], bo[k], p.epi, 1.f);
-    });
-    return;
-  }
-  S* tile = reinterpret_cast<S*>(smem);
-  int u0, lb0, lc0, lbw0, la0;
-  flat_starts(p, t, u0, lb0, lc0, lbw0, la0);
-  walk_read<K, TAB>(c, p, p.tabA, u0, lb0,
-                    [&](int k, bool, int32_t off, int) { v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + off)); });
-  walk_read<K, TAB>(c, p, p.tabA, u0, lb0, [&](int k, bool ok, int32_t, int pos) {
-    if (ok) tile[pos] = v[k];
-  });
-  __syncthreads();
-  if constexpr (BNZ)
-    walk_write<K, TAB>(c, p, p.tabB, lc0, lbw0, la0, [&](int k, bool, int32_t off, int) { bo[k] = Bb[off]; });
-  walk_write<K, TAB>(c, p, p.tabB, lc0, lbw0, la0, [&](int k, bool ok, int32_t off, int pos) {
-    if (ok) Bb[off] = epilogue<DIN, DOUT>(tile[pos], bo[k], p.epi, 1.f);
-  });
-}
-
-template <int DIN, int DOUT, bool BNZ>
+template <int DIN, int DOUT, int EK>
 __device__ __forceinline__ void batch_copy(const BatchDesc& d, const RowCoord& rc) {
   using S = stage_t<DIN>;
   using TO = store_t<DOUT>;
   constexpr int K = kBatchCopyChunk / kThreads / (sizeof(S) == 8 ? 2 : 1);
   const int64_t sa0 = d.rp.sa0, sb0 = d.rp.sb0;
-  const Epilogue epi = d.rp.epi;
+  const Epilogue& epi = d.rp.epi;
   const int t = threadIdx.x;
   const store_t<DIN>* Ar = static_cast<const store_t<DIN>*>(d.A) + rc.offA;
   TO* Br = static_cast<TO*>(d.B) + rc.offB;
@@ -90,45 +52,35 @@ __device__ __forceinline__ void batch_copy(const BatchDesc& d, const RowCoord& r
     const int64_t x = rc.start + t + int64_t(k) * kThreads;
     const int64_t xs = x < rc.end ? x : rc.start;
     v[k] = to_stage<DIN>(ldg_elem<DIN>(Ar + xs * sa0));
-    if constexpr (BNZ) bo[k] = Br[xs * sb0];
+    if constexpr (ek_reads_b(EK)) bo[k] = Br[xs * sb0];
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int64_t x = rc.start + t + int64_t(k) * kThreads;
-    if (x < rc.end) Br[x * sb0] = epilogue<DIN, DOUT>(v[k], bo[k], epi, 1.f);
+    if (x < rc.end) Br[x * sb0] = epilogue_k<DIN, DOUT, EK>(v[k], bo[k], epi, 1.f);
   }
 }
 
-// one claimed tile of one problem
-template <int DIN, int DOUT>
-__device__ __noinline__ void batch_unit(const BatchDesc& d, const TileRec& r, unsigned char* smem) {
-  if (d.path == BP_COPY) {
+// One tile of one problem with the class's body: the packed-lane tile
+// (BP_TILE, J run chunks per thread), packed rows (BP_ROWS, J positions per
+// row) or a run chunk (BP_COPY); the epilogue's mode is read at run time, B is
+// read only for beta != 0 (EK_RT_B).
+template <int DIN, int DOUT, int EK, int PATH, int J>
+__device__ __forceinline__ void batch_unit_ek(const BatchDesc& d, const TileRec& r, unsigned char* smem) {
+  constexpr int K = batch_k_for(sizeof(stage_t<DIN>));
+  if constexpr (PATH == BP_COPY) {
     const RowCoord rc{r.baseA, r.baseB, int64_t(r.remA), int64_t(r.remA) + r.remB};
-    if (d.rp.epi.beta_nz) batch_copy<DIN, DOUT, true>(d, rc);
-    else batch_copy<DIN, DOUT, false>(d, rc);
+    batch_copy<DIN, DOUT, EK>(d, rc);
   } else {
     const TileCoord c{r.baseA, r.baseB, r.remA, r.remB};
-    // both cross offsets linear, or both from tables
-    if (d.tp.crossA_tab) {
-      if (d.tp.epi.beta_nz) batch_tile<DIN, DOUT, true, true>(d, c, smem);
-      else batch_tile<DIN, DOUT, false, true>(d, c, smem);
+    const store_t<DIN>* Ab = static_cast<const store_t<DIN>*>(d.A) + c.baseA;
+    store_t<DOUT>* Bb = static_cast<store_t<DOUT>*>(d.B) + c.baseB;
+    if constexpr (PATH == BP_ROWS) {
+      rowsp_tile<DIN, DOUT, (J <= K ? J : K), EK, K>(Ab, Bb, d.tp, c, 1.f);
     } else {
-      if (d.tp.epi.beta_nz) batch_tile<DIN, DOUT, true, false>(d, c, smem);
-      else batch_tile<DIN, DOUT, false, false>(d, c, smem);
+      stage_t<DIN>* tile = reinterpret_cast<stage_t<DIN>*>(smem);
+      tilep_tile<DIN, DOUT, J, J, EK, K>(Ab, Bb, d.tp, c, tile, 1.f);
     }
-  }
-}
-
-__device__ __forceinline__ void batch_dispatch(const BatchDesc& d, const TileRec& r, unsigned char* smem) {
-  switch (d.din * 4 + d.dout) {
-    case DT_F32 * 4 + DT_F32: batch_unit<DT_F32, DT_F32>(d, r, smem); break;
-    case DT_F32 * 4 + DT_F64: batch_unit<DT_F32, DT_F64>(d, r, smem); break;
-    case DT_F32 * 4 + DT_BF16: batch_unit<DT_F32, DT_BF16>(d, r, smem); break;
-    case DT_F64 * 4 + DT_F64: batch_unit<DT_F64, DT_F64>(d, r, smem); break;
-    case DT_F64 * 4 + DT_F32: batch_unit<DT_F64, DT_F32>(d, r, smem); break;
-    case DT_BF16 * 4 + DT_BF16: batch_unit<DT_BF16, DT_BF16>(d, r, smem); break;
-    case DT_BF16 * 4 + DT_F32: batch_unit<DT_BF16, DT_F32>(d, r, smem); break;
-    default: break;
   }
 }
 
@@ -166,68 +118,68 @@ __device__ __forceinline__ uint32_t find_problem(const uint32_t* __restrict__ ti
   return lo;
 }
 
-// Persistent: resident CTAs claim tiles from one counter (uneven problems
-// balance themselves).  The claim of the next tile is issued while the
-// current one is processed; the current problem's descriptor is kept in
-// shared memory and reloaded only when the problem changes.  A tile's record
-// comes either from the precomputed array `recs` (ttc_batch_*, built once and
-// replayed) or, when recs is null, from the problem's tile prefix `tile0`
-// and its tile parameters on the device (the server, whose epochs are built
-// per launch and should cost the host nothing per tile).
-__global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc* __restrict__ descs,
+// One CTA per tile (the paper's independent macro-tiles, section 2.2,
+// scheduled across thread blocks): the hardware block scheduler hands out the
+// tiles of all problems of one class (dtype pair, beta zero or not; one
+// launch per class, so that each launch has its types and epilogue fixed at
+// compile time), refilling an SM the moment one of its CTAs ends, which keeps
+// more bytes in flight than CTAs that claim tiles in a loop, and lets the
+// batch's side-stream kernels share the GPU.  Global tile g = first +
+// blockIdx.x.  A tile's record comes from the precomputed array `recs`
+// (ttc_batch_*, built once and replayed) or, when recs is null, from the
+// problems' tile prefix `tile0` (ascending over all nprob problems) and the
+// problem's tile parameters on the device (the server's epochs, built per
+// launch at no per-tile host cost).  The problem's descriptor is read from
+// global memory, where it stays cached for the problem's other tiles.
+template <int DIN, int DOUT, int EK, int PATH, int J>
+__global__ void __launch_bounds__(kThreads, EK == EK_RT_B ? 4 : 5) batch_kernel(const BatchDesc* __restrict__ descs,
                                                             const TileRec* __restrict__ recs,
                                                             const uint32_t* __restrict__ tile0, uint32_t nprob,
-                                                            uint32_t total, uint32_t* counter) {
+                                                            uint32_t first) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // the claimed tile, double-buffered: thread 0 records the next claim in the
-  // other buffer before the end-of-tile barrier, which then also publishes it
-  __shared__ uint32_t s_g[2], s_p[2];
-  __shared__ TileRec s_rec[2];
-  // raw storage: BatchDesc has member initializers, which a __shared__
-  // variable cannot run
-  __shared__ __align__(16) unsigned char s_desc_raw[sizeof(BatchDesc)];
-  BatchDesc& s_desc = *reinterpret_cast<BatchDesc*>(s_desc_raw);
-  constexpr int kWords = int(sizeof(BatchDesc) / sizeof(int4));
-  static_assert(sizeof(BatchDesc) % sizeof(int4) == 0, "descriptor copied as 16-byte words");
-  const int t = threadIdx.x;
-  uint32_t have = 0xffffffffu;
-  auto claim = [&](int b, uint32_t g) {   // thread 0: remember tile g and its problem in buffer b
-    s_g[b] = g;
-    if (g < total) {
-      if (recs) {
-        s_rec[b] = recs[g];
-        s_p[b] = s_rec[b].prob;
-      } else {
-        s_p[b] = find_problem(tile0, nprob, g);
-      }
+  __shared__ TileRec s_rec;
+  const uint32_t g = first + blockIdx.x;
+  if (threadIdx.x == 0) {
+    if (recs) {
+      s_rec = recs[g];
+    } else {
+      const uint32_t prob = find_problem(tile0, nprob, g);
+      s_rec = device_rec(descs[prob], prob, g - __ldg(tile0 + prob));
     }
-  };
-  if (t == 0) claim(0, atomicAdd(counter, 1u));
-  __syncthreads();
-  for (int b = 0;; b ^= 1) {
-    const uint32_t g = s_g[b];
-    if (g >= total) break;
-    const uint32_t prob = s_p[b];
-    uint32_t gn = 0;
-    if (t == 0) gn = atomicAdd(counter, 1u);
-    if (prob != have) {
-      const int4* src = reinterpret_cast<const int4*>(descs + prob);
-      int4* dst = reinterpret_cast<int4*>(&s_desc);
-      for (int i = t; i < kWords; i += kThreads) dst[i] = src[i];
-      have = prob;
-      __syncthreads();
-    }
-    if (!recs) {
-      if (t == 0) s_rec[b] = device_rec(s_desc, prob, g - __ldg(tile0 + prob));
-      __syncthreads();
-    }
-    const TileRec r = s_rec[b];
-    batch_dispatch(s_desc, r, smem);
-    // buffer b^1 was last read at the start of the previous tile, before the
-    // previous end-of-tile barrier, so thread 0 may overwrite it now
-    if (t == 0) claim(b ^ 1, gn);
-    __syncthreads();   // the tile buffer, the descriptor and buffer b^1
   }
+  __syncthreads();
+  const TileRec r = s_rec;
+  batch_unit_ek<DIN, DOUT, EK, PATH, J>(descs[r.prob], r, smem);
+}
+
+template <int DIN, int DOUT, int EK, int PATH, int J>
+cudaError_t launch_batch_body(const BatchDesc* d_descs, const TileRec* d_recs, const uint32_t* d_tile0,
+                              uint32_t nprob, uint32_t first, uint32_t count, int smem, cudaStream_t s) {
+  const void* fn = reinterpret_cast<const void*>(&batch_kernel<DIN, DOUT, EK, PATH, J>);
+  if (smem > 48 * 1024) {
+    int g = 0;
+    cudaError_t e = grid_for(fn, smem, 1, &g);
+    if (e != cudaSuccess) return e;
+  }
+  batch_kernel<DIN, DOUT, EK, PATH, J><<<count, kThreads, smem, s>>>(d_descs, d_recs, d_tile0, nprob, first);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+// the body variants of a class: packed-lane tiles with 1 or 2 chunks, packed
+// rows with 1 or K positions per row, run chunks
+template <int DIN, int DOUT, int EK>
+cudaError_t launch_batch_class(int path, int j, const BatchDesc* d_descs, const TileRec* d_recs,
+                               const uint32_t* d_tile0, uint32_t nprob, uint32_t first, uint32_t count, int smem,
+                               cudaStream_t s) {
+  constexpr int K = batch_k_for(sizeof(stage_t<DIN>));
+  if (path == BP_COPY)
+    return launch_batch_body<DIN, DOUT, EK, BP_COPY, 1>(d_descs, d_recs, d_tile0, nprob, first, count, smem, s);
+  if (path == BP_ROWS)
+    return j == 1 ? launch_batch_body<DIN, DOUT, EK, BP_ROWS, 1>(d_descs, d_recs, d_tile0, nprob, first, count, smem, s)
+                  : launch_batch_body<DIN, DOUT, EK, BP_ROWS, K>(d_descs, d_recs, d_tile0, nprob, first, count, smem, s);
+  return j == 1 ? launch_batch_body<DIN, DOUT, EK, BP_TILE, 1>(d_descs, d_recs, d_tile0, nprob, first, count, smem, s)
+                : launch_batch_body<DIN, DOUT, EK, BP_TILE, 2>(d_descs, d_recs, d_tile0, nprob, first, count, smem, s);
 }
 
 }  // namespace ttc
@@ -248,30 +200,21 @@ std::shared_ptr<const BatchTemplate> make_template(const ttc_plan_s* p) {
   // tiles for the batch body: the best schedule with at most its tile volume
   const std::vector<Candidate> bc =
       make_candidates(p->canon, p->din, p->dout, p->beta, 4, kThreads * batch_k_for(p->din == DT_F64 ? 8 : 4));
+  if (bc.empty()) return t;       // not batchable: the batch runs it as a single-plan kernel
   const Candidate& k = bc.front();
+  d->beta_nz = p->beta_nonzero() ? 1 : 0;
   if (k.variant == VAR_TILE) {
     std::vector<int32_t> ta, tb;
     int sm = 0;
     build_tile_params(p->canon, k, p->din, &d->tp, &ta, &tb, &sm);
-    d->path = k.rows ? BP_ROWS : BP_TILE;
-    if (d->path == BP_TILE && (d->tp.crossA_tab || d->tp.crossB_tab)) {
-      // the batch body has two walks: both cross offsets linear, or both
-      // from tables (a linear one is then written out as a table)
-      if (!d->tp.crossA_tab) {
-        ta.resize(d->tp.LB);
-        for (int i = 0; i < d->tp.LB; ++i) ta[i] = i * d->tp.crossA_lin;
-        d->tp.crossA_tab = 1;
-      }
-      if (!d->tp.crossB_tab) {
-        tb.resize(d->tp.LA);
-        for (int i = 0; i < d->tp.LA; ++i) tb[i] = i * d->tp.crossB_lin;
-        d->tp.crossB_tab = 1;
-      }
+    d->path = k.rj ? BP_ROWS : BP_TILE;
+    d->j = k.rj ? k.rj : k.ju;
+    if (d->tp.crossA_tab || d->tp.crossB_tab) {
       t->tabA_count = ta.size();
       t->tabs.insert(t->tabs.end(), ta.begin(), ta.end());
       t->tabs.insert(t->tabs.end(), tb.begin(), tb.end());
     }
-    if (d->path == BP_TILE) t->smem = d->tp.P * d->tp.LB * (p->din == DT_F64 ? 8 : 4);
+    if (d->path == BP_TILE) t->smem = d->tp.P * d->tp.LB * stage_bytes_of(p->din);
     d->ntiles = d->tp.ntiles;
     d->tp.epi = make_epilogue(p, nullptr);
   } else {
@@ -336,17 +279,37 @@ void batch_records(const BatchDesc& d, uint32_t prob, std::vector<TileRec>* recs
   }
 }
 
+int batch_class(const BatchDesc& d) {
+  const int body = d.path == BP_COPY ? 4 : (d.path == BP_ROWS ? 2 : 0) + (d.j == 1 ? 0 : 1);
+  return ((d.din * kNumDTypes + d.dout) * 2 + (d.beta_nz ? 1 : 0)) * 8 + body;
+}
+
+void batch_ranges(const std::vector<BatchDesc>& descs, std::vector<BatchRange>* ranges) {
+  ranges->clear();
+  for (const BatchDesc& d : descs) {
+    const int cls = batch_class(d);
+    if (ranges->empty() || ranges->back().cls != cls)
+      ranges->push_back({cls, d.din, d.dout, d.beta_nz, d.path, d.j, d.tile0, 0});
+    ranges->back().count += d.ntiles;
+  }
+}
+
 cudaError_t batch_launch(const BatchDesc* d_descs, const TileRec* d_recs, const uint32_t* d_tile0, uint32_t nprob,
-                         uint32_t total, uint32_t* d_counter, int smem, cudaStream_t s) {
-  if (total == 0) return cudaSuccess;
-  int grid = 0;
-  cudaError_t e = grid_for(reinterpret_cast<const void*>(&batch_kernel), smem, int64_t(total), &grid);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
-  batch_kernel<<<grid, kThreads, smem, s>>>(d_descs, d_recs, d_tile0, nprob, total, d_counter);
-  ++g_launches;
-  return cudaGetLastError();
+                         const std::vector<BatchRange>& ranges, int smem, cudaStream_t s) {
+  for (const BatchRange& r : ranges) {
+    if (r.count == 0) continue;
+    cudaError_t e = cudaErrorInvalidValue;
+#define TTC_BC(I, O)                                                                                     \
+  if (r.din == I && r.dout == O)                                                                          \
+    e = r.bnz ? launch_batch_class<I, O, EK_RT_B>(r.path, r.j, d_descs, d_recs, d_tile0, nprob, r.first, r.count, \
+                                                  smem, s)                                                        \
+              : launch_batch_class<I, O, EK_RT>(r.path, r.j, d_descs, d_recs, d_tile0, nprob, r.first, r.count, smem, s);
+    TTC_BC(DT_F32, DT_F32) TTC_BC(DT_F32, DT_F64) TTC_BC(DT_F32, DT_BF16) TTC_BC(DT_F64, DT_F64)
+    TTC_BC(DT_F64, DT_F32) TTC_BC(DT_BF16, DT_BF16) TTC_BC(DT_BF16, DT_F32)
+#undef TTC_BC
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace ttc
@@ -367,15 +330,15 @@ struct ttc_batch_s {
   size_t arena_bytes = 0;
   BatchDesc* d_descs = nullptr;
   TileRec* d_recs = nullptr;
-  uint32_t* d_counter = nullptr;
   uint32_t total = 0;
   int smem = 0;
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   // problems of at least direct_min elements run as their own single-plan
-  // kernels on a side stream, beside the persistent kernel
+  // kernels on a side stream, beside the batch kernel
   int64_t direct_min = int64_t(1) << 21;
   std::vector<Item> direct;
+  std::vector<BatchRange> ranges;   // the class launches of the batch kernel
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   ~ttc_batch_s() {
@@ -423,19 +386,48 @@ ttc_status batch_build(ttc_batch_s* b) {
     BatchDesc d;
     size_t na = 0;
     const size_t at = tabs.size();
-    if (!batch_describe(it.plan, it.A, it.B, &d, &tabs, &na, &smem)) continue;
-    d.tile0 = uint32_t(total);
-    total += d.ntiles;
-    if (total >= 0x7fffffffull) return fail(TTC_ERR_INVALID_SIZE, "batch has too many tiles");
+    if (!batch_describe(it.plan, it.A, it.B, &d, &tabs, &na, &smem)) {
+      // a problem the batch body cannot take runs as its own kernel
+      if (it.plan->canon.n > 0) {
+        DevRes* r = nullptr;
+        const ttc_status st = ensure_device(it.plan, dev, &r);
+        if (st != TTC_OK) return st;
+        b->direct.push_back(it);
+      }
+      continue;
+    }
     descs.push_back(d);
     tab_at.push_back(at);
     tab_na.push_back(na);
   }
-  // arena: descriptors | tables | tile records | counter
+  // problems ordered by class (one kernel launch per class), each class in
+  // the order the problems were added; then every problem's first tile
+  {
+    std::vector<size_t> idx(descs.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](size_t x, size_t y) { return batch_class(descs[x]) < batch_class(descs[y]); });
+    std::vector<BatchDesc> d2;
+    std::vector<size_t> at2, na2;
+    for (size_t i : idx) {
+      d2.push_back(descs[i]);
+      at2.push_back(tab_at[i]);
+      na2.push_back(tab_na[i]);
+    }
+    descs.swap(d2);
+    tab_at.swap(at2);
+    tab_na.swap(na2);
+  }
+  for (BatchDesc& d : descs) {
+    d.tile0 = uint32_t(total);
+    total += d.ntiles;
+    if (total >= 0x7fffffffull) return fail(TTC_ERR_INVALID_SIZE, "batch has too many tiles");
+  }
+  batch_ranges(descs, &b->ranges);
+  // arena: descriptors | tables | tile records
   const size_t off_tab = (descs.size() * sizeof(BatchDesc) + 255) & ~size_t(255);
   const size_t off_rec = (off_tab + tabs.size() * 4 + 255) & ~size_t(255);
-  const size_t off_cnt = (off_rec + total * sizeof(TileRec) + 255) & ~size_t(255);
-  const size_t bytes = off_cnt + 256;
+  const size_t bytes = (off_rec + total * sizeof(TileRec) + 255) & ~size_t(255);
   if (b->arena) {
     cudaFree(b->arena);
     b->arena = nullptr;
@@ -451,7 +443,7 @@ ttc_status batch_build(ttc_batch_s* b) {
   recs.reserve(total);
   for (size_t i = 0; i < descs.size(); ++i) {
     BatchDesc& d = descs[i];
-    if (d.path == BP_TILE) {
+    if (d.path != BP_COPY) {
       d.tp.tabA = d_tab + tab_at[i];
       d.tp.tabB = d_tab + tab_at[i] + tab_na[i];
     }
@@ -465,7 +457,6 @@ ttc_status batch_build(ttc_batch_s* b) {
   b->arena_bytes = bytes;
   b->d_descs = reinterpret_cast<BatchDesc*>(base);
   b->d_recs = reinterpret_cast<TileRec*>(base + off_rec);
-  b->d_counter = reinterpret_cast<uint32_t*>(base + off_cnt);
   b->total = uint32_t(total);
   b->smem = smem;
   b->dev = dev;
@@ -487,7 +478,7 @@ ttc_status batch_build(ttc_batch_s* b) {
   return TTC_OK;
 }
 
-// The persistent kernel on s; the direct problems one after another on the
+// The batch kernel on s; the direct problems one after another on the
 // side stream, forked from and joined back into s (so that a capture of s
 // records both branches).
 ttc_status batch_enqueue(ttc_batch_s* b, cudaStream_t s) {
@@ -505,7 +496,7 @@ ttc_status batch_enqueue(ttc_batch_s* b, cudaStream_t s) {
     if (e != cudaSuccess && st == TTC_OK) st = cuda_fail(e, "batch join");
   }
   if (b->total && st == TTC_OK) {
-    e = batch_launch(b->d_descs, b->d_recs, nullptr, 0, b->total, b->d_counter, b->smem, s);
+    e = batch_launch(b->d_descs, b->d_recs, nullptr, 0, b->ranges, b->smem, s);
     if (e != cudaSuccess) st = cuda_fail(e, "batch kernel launch");
   }
   if (!b->direct.empty()) {
@@ -593,7 +584,7 @@ ttc_status ttc_batch_graph_launch(ttc_batch_t b, ttc_stream_t stream) {
   }
   cudaError_t e = cudaGraphLaunch(b->gexec, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-  g_launches += (b->total ? 1 : 0) + int64_t(b->direct.size());
+  g_launches += int64_t(b->ranges.size()) + int64_t(b->direct.size());
   return TTC_OK;
 }
 

@@ -1,12 +1,16 @@
 // contract.cu -- tensor contractions by Transpose-Transpose-GEMM-Transpose
 // (TTGT), the use of tensor transpositions that motivates the paper
 // (section 1): each operand is permuted (and for the BF16 GEMM path
-// downcast) by this library's permute-scale-add kernels into a column-major
-// matrix, the contraction runs as one GEMM (cuBLAS: a plain library GEMM),
-// and the product is permuted into C with Eq. 1's beta update.  An operand
-// already laid out as a matrix in either order is passed to the GEMM as it
-// is (transposed or not), and a C laid out as [free A indices, free B
-// indices] or the reverse takes the GEMM's output directly.
+// downcast) by this library's permute-scale-add kernels into a matrix, the
+// contraction runs as one GEMM, and the product is permuted into C with
+// Eq. 1's beta update.  The BF16 mode permutes both operands into K-major
+// BF16 matrices (the contracted indices fastest, the row pitch padded to a
+// multiple of 8 elements) and runs this library's tensor-core GEMM
+// (gemm.cu); the exact FP32 and FP64 modes run a cuBLAS GEMM in pedantic
+// math (SIMT FP32/FP64, no reduced-precision substitution), with an operand
+// already laid out as a matrix in either order passed as it is.  A C laid out
+// as [free A indices, free B indices] or the reverse takes the GEMM's output
+// directly.
 #include <cublas_v2.h>
 #include <cuda_runtime.h>
 
@@ -19,6 +23,8 @@
 #include <vector>
 
 #include "../../include/ttc.h"
+#include "../../include/ttc_debug.h"
+#include "gemm.h"
 #include "plan_impl.h"
 
 using namespace ttc;
@@ -36,8 +42,9 @@ struct Operand {
 
 struct DevState {
   cublasHandle_t handle = nullptr;
-  void* ws = nullptr;          // A' | B' | C' workspaces
+  void* ws = nullptr;          // A' | B' | C' workspaces | error word of the tensor-core GEMM
   size_t bytes = 0;
+  int* err = nullptr;
 };
 
 }  // namespace
@@ -49,6 +56,9 @@ struct ttc_contraction_s {
   int64_t M = 1, N = 1, K = 1;
   bool swap = false;           // C is [free B, free A]: compute C^T = B'^T A'^T
   Operand opA, opB;
+  int64_t kpitch = 0;          // BF16 mode: row pitch of the K-major operands (K rounded up to 8)
+  std::vector<int64_t> offs;   // BF16 mode: C offsets of the GEMM's rows (M' entries), then columns (N')
+  bool use_cublas = false;     // testing hook: the BF16 mode's GEMM on cuBLAS (a timed comparison)
   ttc_plan_t planC = nullptr;  // C' -> C with beta, when C is not a GEMM output layout
   size_t wsC = 0;
   int64_t sizeA = 0, sizeB = 0, sizeC = 0;   // elements of each tensor
@@ -128,6 +138,50 @@ ttc_status setup_operand(const std::vector<int>& mx, const std::vector<int64_t>&
   return TTC_OK;
 }
 
+// BF16 mode: operand X (modes `mx`, sizes `sx`) as a K-major BF16 matrix:
+// for every free position (`frees`, column-major) the contracted indices
+// (`contracted`, column-major) at consecutive addresses, at a row pitch of
+// K rounded up to a multiple of 8 elements (the last contracted index's
+// outer extent is widened; the padding is never read).  rows = product of
+// the free extents.
+ttc_status setup_kmajor(const std::vector<int>& mx0, const std::vector<int64_t>& sx0,
+                        const std::vector<int>& contracted0, const std::vector<int>& frees,
+                        std::map<int, int64_t> ext, int64_t rows, int din, int64_t* kpitch, Operand* op) {
+  std::vector<int> mx(mx0), contracted(contracted0);
+  std::vector<int64_t> sx(sx0);
+  if (contracted.empty()) {
+    // an outer product (K = 1): a contracted index of extent 1 stands in,
+    // appended to the operand, so that the rows still have a pitch
+    int dummy = 0;
+    for (const auto& kv : ext) dummy = std::max(dummy, kv.first + 1);
+    mx.push_back(dummy);
+    sx.push_back(1);
+    contracted.push_back(dummy);
+    ext[dummy] = 1;
+  }
+  std::vector<int> order(contracted);
+  order.insert(order.end(), frees.begin(), frees.end());
+  const std::vector<int> p = perm_to(mx, order);
+  std::vector<int64_t> outer;
+  int64_t below = 1;   // product of the contracted extents before the last one
+  for (size_t i = 0; i < order.size(); ++i) outer.push_back(ext.at(order[i]));
+  for (size_t i = 0; i + 1 < contracted.size(); ++i) below *= ext.at(contracted[i]);
+  const int64_t last = ext.at(contracted.back());
+  int64_t o = last;
+  while ((below * o) % 8) ++o;
+  outer[contracted.size() - 1] = o;
+  ttc_plan_t plan = nullptr;
+  const ttc_status st = ttc_plan(&plan, int(mx.size()), p.data(), sx.data(), nullptr, outer.data(), ttc_dtype(din),
+                                 TTC_BF16, 1.0, 0.0);
+  if (st != TTC_OK) return st;
+  op->plan = plan;
+  op->trans = false;
+  op->ld = below * o;
+  op->ws_bytes = size_t(below * o) * size_t(std::max<int64_t>(rows, 1)) * 2;
+  *kpitch = below * o;
+  return TTC_OK;
+}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 ttc_status cublas_fail(cublasStatus_t s, const char* where) {
@@ -204,6 +258,60 @@ ttc_status ttc_contraction_plan(ttc_contraction_t* out, int nA, const int* modes
     return fail(TTC_ERR_INVALID_SIZE, "a GEMM extent exceeds 2^31 - 1");
   // C as the GEMM output: [freeA, freeB] directly, [freeB, freeA] by
   // computing the transpose; else through C' and a final transpose with beta
+  if (dg == DT_BF16) {
+    // Both operands K-major BF16 for the tensor-core GEMM, and C written by
+    // the GEMM's epilogue at offset rowoff[m] + coloff[n] in any layout (the
+    // transpose of the product folded into the stores): the GEMM's rows are
+    // the free labels of the operand that holds C's stride-1 label, so that
+    // consecutive rows are consecutive in C; each operand's free labels in
+    // C's order.  With an empty extent nothing is permuted.
+    const bool b_rows = !mC.empty() && where[mC[0]] == 6;
+    c->swap = b_rows;
+    c->kpitch = 8;
+    if (c->K > 0 && c->M > 0 && c->N > 0) {
+      st = setup_kmajor(mA, sA, contracted, freeA, ext, c->M, dt, &c->kpitch, &c->opA);
+      if (st == TTC_OK) st = setup_kmajor(mB, sB, contracted, freeB, ext, c->N, dt, &c->kpitch, &c->opB);
+      if (st != TTC_OK) return st;
+    }
+    std::map<int, int64_t> strideC;
+    int64_t acc = 1;
+    for (size_t i = 0; i < mC.size(); ++i) {
+      strideC[mC[i]] = acc;
+      acc *= sC[i];
+    }
+    auto offsets = [&](const std::vector<int>& labels) {
+      int64_t cnt = 1;
+      for (int l : labels) cnt *= ext[l];
+      for (int64_t i = 0; i < cnt; ++i) {
+        int64_t r = i, off = 0;
+        for (int l : labels) {
+          off += (r % ext[l]) * strideC[l];
+          r /= ext[l];
+        }
+        c->offs.push_back(off);
+      }
+    };
+    offsets(b_rows ? freeB : freeA);
+    offsets(b_rows ? freeA : freeB);
+    // the timed comparison on cuBLAS writes the product as a column-major
+    // matrix [rows, columns]; a C of another layout then takes it through a
+    // permute plan with beta (the unfused route)
+    const std::vector<int>& rl = b_rows ? freeB : freeA;
+    const std::vector<int>& cl = b_rows ? freeA : freeB;
+    std::vector<int> cp(rl);
+    cp.insert(cp.end(), cl.begin(), cl.end());
+    if (cp != mC && c->M > 0 && c->N > 0) {
+      std::vector<int64_t> scp;
+      for (int l : cp) scp.push_back(ext[l]);
+      const std::vector<int> p = perm_to(cp, mC);
+      st = ttc_plan(&c->planC, int(cp.size()), p.data(), scp.data(), nullptr, nullptr, ttc_dtype(dt), ttc_dtype(dt),
+                    1.0, beta);
+      if (st != TTC_OK) return st;
+      c->wsC = size_t(c->M) * size_t(c->N) * size_t(dtype_size(dt));
+    }
+    *out = c.release();
+    return TTC_OK;
+  }
   const bool direct = is_concat(mC, freeA, freeB);
   const bool swapped = !direct && is_concat(mC, freeB, freeA);
   std::vector<int> fa(freeA), fb(freeB);
@@ -255,7 +363,8 @@ ttc_status ttc_contraction_execute(ttc_contraction_t c, const void* A, const voi
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   DevState& ds = c->dev[dev];
-  const size_t need = align256(c->opA.ws_bytes) + align256(c->opB.ws_bytes) + align256(c->wsC);
+  const size_t need = align256(c->opA.ws_bytes) + align256(c->opB.ws_bytes) + align256(c->wsC) +
+                      align256(c->offs.size() * sizeof(int64_t)) + 256;
   if (!ds.handle) {
     cublasStatus_t cs = cublasCreate(&ds.handle);
     if (cs != CUBLAS_STATUS_SUCCESS) {
@@ -273,6 +382,15 @@ ttc_status ttc_contraction_execute(ttc_contraction_t c, const void* A, const voi
                                             : cuda_fail(e, "cudaMalloc");
     }
     ds.bytes = need;
+    ds.err = reinterpret_cast<int*>(static_cast<char*>(ds.ws) + need - 256);
+    e = cudaMemset(ds.err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    if (!c->offs.empty()) {
+      e = cudaMemcpy(static_cast<char*>(ds.ws) + align256(c->opA.ws_bytes) + align256(c->opB.ws_bytes) +
+                         align256(c->wsC),
+                     c->offs.data(), c->offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_fail(e, "offset table upload");
+    }
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ds.ws);
@@ -293,10 +411,25 @@ ttc_status ttc_contraction_execute(ttc_contraction_t c, const void* A, const voi
     if (st != TTC_OK) return st;
     gb = wb;
   }
-  cublasStatus_t cs = cublasSetStream(ds.handle, s);
-  if (cs != CUBLAS_STATUS_SUCCESS) return cublas_fail(cs, "cublasSetStream");
   void* gc = c->planC ? wc : C;
   const double beta_g = c->planC ? 0.0 : c->beta;
+  if (c->kpitch && !c->use_cublas) {
+    // the tensor-core GEMM on the K-major operands, rows from the operand
+    // holding C's stride-1 label, C written through the offset tables
+    if (c->M == 0 || c->N == 0) return TTC_OK;
+    const bool sw = c->swap;
+    const void* X = sw ? gb : ga;
+    const void* Y = sw ? ga : gb;
+    const int64_t m = sw ? c->N : c->M, n = sw ? c->M : c->N;
+    const int64_t* rows = reinterpret_cast<const int64_t*>(static_cast<char*>(wc) + align256(c->wsC));
+    if (const char* why = gemm_bf16_check(X, c->kpitch, Y, c->kpitch, m, n, c->K)) return fail(TTC_ERR_INVALID_SIZE, why);
+    e = gemm_bf16(X, c->kpitch, Y, c->kpitch, static_cast<float*>(C), rows, rows + m, m, n, c->K, float(c->alpha),
+                  float(c->beta), ds.err, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM launch");
+    return TTC_OK;
+  }
+  cublasStatus_t cs = cublasSetStream(ds.handle, s);
+  if (cs != CUBLAS_STATUS_SUCCESS) return cublas_fail(cs, "cublasSetStream");
   // column-major GEMM: C (M x N) = op(A') (M x K) op(B') (K x N); with swap,
   // C^T (N x M) = op(B')^T op(A')^T
   const bool sw = c->swap;
@@ -320,6 +453,14 @@ ttc_status ttc_contraction_execute(ttc_contraction_t c, const void* A, const voi
     const float al = float(c->alpha), be = float(beta_g);
     cs = cublasSgemm(ds.handle, tx, ty, m, n, k, &al, static_cast<const float*>(X), ldx,
                      static_cast<const float*>(Y), ldy, &be, static_cast<float*>(gc), ldc);
+  } else if (c->kpitch) {
+    // the timed comparison: the same K-major BF16 operands on cuBLAS, the
+    // product [rows, columns] into C or, for another layout, into C' and a
+    // permute plan
+    const float al = float(c->alpha), be = float(beta_g);
+    const int kp = int(c->kpitch);
+    cs = cublasGemmEx(ds.handle, CUBLAS_OP_T, CUBLAS_OP_N, m, n, k, &al, X, CUDA_R_16BF, kp, Y, CUDA_R_16BF, kp, &be,
+                      gc, CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
   } else {
     const float al = float(c->alpha), be = float(beta_g);
     cs = cublasGemmEx(ds.handle, tx, ty, m, n, k, &al, X, CUDA_R_16BF, ldx, Y, CUDA_R_16BF, ldy, &be, gc,
@@ -336,6 +477,30 @@ ttc_status ttc_contraction_info(ttc_contraction_t c, int64_t* m, int64_t* n, int
   if (n) *n = c->N;
   if (k) *k = c->K;
   if (transposes) *transposes = (c->opA.plan ? 1 : 0) + (c->opB.plan ? 2 : 0) + (c->planC ? 4 : 0);
+  return TTC_OK;
+}
+
+ttc_status ttc_contraction_check(ttc_contraction_t c) {
+  if (!c) return fail(TTC_ERR_INVALID_ARG, "contraction is NULL");
+  std::lock_guard<std::mutex> lk(c->mu);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  auto it = c->dev.find(dev);
+  if (it == c->dev.end() || !it->second.err) return TTC_OK;
+  int flag = 0;
+  e = cudaMemcpy(&flag, it->second.err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "error word read");
+  if (!flag) return TTC_OK;
+  e = cudaMemset(it->second.err, 0, sizeof(int));      // reported once
+  if (e != cudaSuccess) return cuda_fail(e, "error word reset");
+  return fail(TTC_ERR_TIMEOUT, "a tensor-core wait of the GEMM gave up");
+}
+
+ttc_status ttc_debug_contraction_use_cublas(ttc_contraction_t c, int use) {
+  if (!c) return fail(TTC_ERR_INVALID_ARG, "contraction is NULL");
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->use_cublas = use != 0;
   return TTC_OK;
 }
 

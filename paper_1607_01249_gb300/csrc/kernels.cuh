@@ -85,6 +85,24 @@ __device__ __forceinline__ float fp8_scale_of(const Epilogue& e) {
   return s == 0.f ? 1.f : s;
 }
 
+// The E4M3 code (RNE, satfinite) of fl32(v / s), s > 0 finite, without a
+// division per element.  q = fl32(v * fl32(1/s)) differs from fl32(v / s) by
+// at most 2.5 binary32 ulps (two roundings of relative size 2^-24 each, and
+// the quotient's own half ulp).  When the codes of q moved down and up by
+// 2^-20 of its magnitude (at least 4 ulps) agree with the code of q, no E4M3
+// rounding boundary lies within the band that holds both q and fl32(v / s),
+// so q's code is the quotient's; otherwise (near a boundary, infinities, a
+// reciprocal that overflows) the quotient is formed by an IEEE division.
+__device__ __forceinline__ uint8_t e4m3_of_quotient(float v, float s, float r) {
+  const float q = __fmul_rn(v, r);
+  const float d = __fmul_rn(fabsf(q), 0x1p-20f);
+  const __nv_fp8x2_storage_t lh =
+      __nv_cvt_float2_to_fp8x2(make_float2(__fsub_rn(q, d), __fadd_rn(q, d)), __NV_SATFINITE, __NV_E4M3);
+  const uint8_t c = uint8_t(__nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3));
+  if (uint8_t(lh & 0xffu) == c && uint8_t(lh >> 8) == c && r < __int_as_float(0x7f800000)) return c;
+  return uint8_t(__nv_cvt_float_to_fp8(__fdiv_rn(v, s), __NV_SATFINITE, __NV_E4M3));
+}
+
 // The alpha/beta update of Eq. 1 for one element, in the compute type, then
 // one rounding to B's type.  `b` is only meaningful when e.beta_nz.
 template <int DIN, int DOUT>
@@ -92,8 +110,7 @@ __device__ __forceinline__ store_t<DOUT> epilogue(stage_t<DIN> a, store_t<DOUT> 
                                                   float scale) {
   if constexpr (DOUT == DT_E4M3) {
     const float v = __fmul_rn(e.alpha_f, float(a));
-    const float q = __fdiv_rn(v, scale);
-    return store_t<DOUT>(__nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3));
+    return store_t<DOUT>(e4m3_of_quotient(v, scale, __frcp_rn(scale)));
   } else {
     if (e.mode == MODE_BITCOPY) {
       // same dtype in and out (the planner guarantees it)
@@ -117,7 +134,12 @@ __device__ __forceinline__ store_t<DOUT> epilogue(stage_t<DIN> a, store_t<DOUT> 
 // The update of Eq. 1 with the mode fixed at compile time (no per-element
 // branches): EK_COPY moves bits (alpha = 1, beta = 0, same type), EK_SCALE
 // r = alpha*a, EK_AXPBY r = fma(beta, b, alpha*a), EK_FP8 the scaled E4M3 code.
-enum EpiKind : int { EK_COPY = 0, EK_SCALE = 1, EK_AXPBY = 2, EK_FP8 = 3 };
+// EK_RT / EK_RT_B: the mode is read at run time (the batch body, one kernel
+// for every problem), without / with B read.
+enum EpiKind : int { EK_COPY = 0, EK_SCALE = 1, EK_AXPBY = 2, EK_FP8 = 3, EK_RT = 4, EK_RT_B = 5 };
+
+// whether an epilogue kind reads B
+constexpr bool ek_reads_b(int ek) { return ek == EK_AXPBY || ek == EK_RT_B; }
 
 // Complex update (the paper's c, z, cz, zc types), in double-complex when
 // either side is double-complex, else in single-complex, with this fixed
@@ -168,9 +190,11 @@ __device__ __forceinline__ store_t<DOUT> epilogue_complex(stage_t<DIN> a, store_
 template <int DIN, int DOUT, int EK>
 __device__ __forceinline__ store_t<DOUT> epilogue_k(stage_t<DIN> a, store_t<DOUT> b, const Epilogue& e,
                                                     float scale) {
-  if constexpr (EK == EK_FP8) {
+  if constexpr (EK == EK_RT || EK == EK_RT_B) {
+    return epilogue<DIN, DOUT>(a, b, e, scale);
+  } else if constexpr (EK == EK_FP8) {
     const float v = __fmul_rn(e.alpha_f, float(a));
-    return store_t<DOUT>(__nv_cvt_float_to_fp8(__fdiv_rn(v, scale), __NV_SATFINITE, __NV_E4M3));
+    return store_t<DOUT>(e4m3_of_quotient(v, scale, __frcp_rn(scale)));
   } else if constexpr (EK == EK_COPY) {
     if constexpr (DIN == DT_BF16 && DOUT == DT_BF16) return store_t<DOUT>(__float_as_uint(a) >> 16);
     else return a;
@@ -325,60 +349,64 @@ TTC_HD void walk_write(const TileCoord& c, const PT& p, const int32_t* tabB, int
 // Warp-mapped walks (tile2_kernel).  Read: lanes along u (JU chunks of 32),
 // warps along lb.  Write: lanes along v (JW chunks), warps along la.
 // FULL: an interior tile (no cut index is short).  f(k, ok, offset, smem
-// position) as for the flat walks; rows past the tile's end are skipped
-// (warp-uniform), lanes past a run's end get ok == false.
-template <int JU, int K, bool FULL, bool TAB, class PT, class F>
+// position): rows past the tile's end are skipped (warp-uniform); lanes past
+// a run's end get ok == false, and their offset and position are not
+// meaningful (callers predicate every access on ok, which keeps the loads and
+// stores branch-free).  UNIT: the runs have unit stride on both sides (the
+// planner only gives these kernels such tiles), so a lane's chunks sit at
+// constant distances from its row offset.
+template <int JU, int K, bool FULL, bool TAB, bool UNIT, class PT, class F>
 TTC_HD void walk2_read(const TileCoord& c, const PT& p, const int32_t* tabA, int lane, int warp,
                        F&& f) {
   constexpr int RR = K / JU;
   const int limU = FULL ? p.U : c.remA * p.LC;
   const int remB = FULL ? p.LB : c.remB;
+  const int32_t su = UNIT ? 1 : p.saU;
+  bool uok[JU];
+#pragma unroll
+  for (int j = 0; j < JU; ++j) uok[j] = lane + 32 * j < limU;
 #pragma unroll
   for (int i = 0; i < RR; ++i) {
     const int r = warp + 8 * i;
     if (r < remB) {
-      const int32_t row = TAB ? tabA[r] : r * p.crossA_lin;
-      const int pos = r * p.P;
+      const int32_t row = (TAB ? tabA[r] : r * p.crossA_lin) + lane * su;
+      const int pos = r * p.P + lane;
 #pragma unroll
-      for (int j = 0; j < JU; ++j) {
-        const int u = lane + 32 * j;
-        const bool ok = u < limU;
-        f(i * JU + j, ok, ok ? row + u * p.saU : 0, pos + u);
-      }
+      for (int j = 0; j < JU; ++j) f(i * JU + j, uok[j], row + 32 * j * su, pos + 32 * j);
     }
   }
 }
 
-// per-lane constants of the write walk: shared-memory offset and B offset of
-// the lane's run positions v = lane + 32 j
+// per-lane constants of the write walk: shared-memory offset of the lane's
+// run positions v = lane + 32 j
 template <int JW, class PT>
-TTC_HD void walk2_lane_consts(const PT& p, int lane, int (&spre)[JW], int32_t (&voff)[JW]) {
+TTC_HD void walk2_lane_consts(const PT& p, int lane, int (&spre)[JW]) {
 #pragma unroll
   for (int j = 0; j < JW; ++j) {
     const int vv = lane + 32 * j;
     const int q = int(fast_div(uint32_t(vv), p.divLC));
     spre[j] = q * p.P + (vv - q * p.LC);
-    voff[j] = vv * p.sbV;
   }
 }
 
-template <int JW, int K, bool FULL, bool TAB, class PT, class F>
+template <int JW, int K, bool FULL, bool TAB, bool UNIT, class PT, class F>
 TTC_HD void walk2_write(const TileCoord& c, const PT& p, const int32_t* tabB, int lane, int warp,
-                        const int (&spre)[JW], const int32_t (&voff)[JW], F&& f) {
+                        const int (&spre)[JW], F&& f) {
   constexpr int RW = K / JW;
   const int limV = FULL ? p.W : c.remB * p.LC;
   const int remA = FULL ? p.LA : c.remA;
+  const int32_t sv = UNIT ? 1 : p.sbV;
+  bool vok[JW];
+#pragma unroll
+  for (int j = 0; j < JW; ++j) vok[j] = lane + 32 * j < limV;
 #pragma unroll
   for (int i = 0; i < RW; ++i) {
     const int la = warp + 8 * i;
     if (la < remA) {
-      const int32_t row = TAB ? tabB[la] : la * p.crossB_lin;
+      const int32_t row = (TAB ? tabB[la] : la * p.crossB_lin) + lane * sv;
       const int spos = la * p.LC;
 #pragma unroll
-      for (int j = 0; j < JW; ++j) {
-        const bool ok = lane + 32 * j < limV;
-        f(i * JW + j, ok, ok ? row + voff[j] : 0, spre[j] + spos);
-      }
+      for (int j = 0; j < JW; ++j) f(i * JW + j, vok[j], row + 32 * j * sv, spre[j] + spos);
     }
   }
 }
@@ -394,8 +422,10 @@ TTC_HD void walk2_write(const TileCoord& c, const PT& p, const int32_t* tabB, in
 // idling at a run's end, and each thread's offsets advance by constants (one
 // add per element, the row's cross offset once per row).  tile2_kernel is
 // the case g = 32 with warps as the groups.  f(k, ok, offset in tile, smem
-// position): smem holds the tile as lb rows of pitch P in A order.
-template <int NT, int J, int K, bool TAB, class F>
+// position): smem holds the tile as lb rows of pitch P in A order; when ok is
+// false the offset and position are not meaningful (callers predicate on
+// ok).  UNIT as for the warp-mapped walks.
+template <int NT, int J, int K, bool TAB, bool UNIT, class F>
 TTC_HD void walkp_read(const TileCoord& c, const TileParams& p, const int32_t* tabA, int t, F&& f) {
   constexpr int R = K / J;
   // (the two layouts are selected field by field: indexing the parameter
@@ -405,13 +435,14 @@ TTC_HD void walkp_read(const TileCoord& c, const TileParams& p, const int32_t* t
   const int tr = int(fast_div(uint32_t(t), whole ? p.pkA[0].div : p.pkA[1].div));
   const int tu = t - tr * g;
   const bool active = tr < rows;
+  const int32_t su = UNIT ? 1 : p.saU;
   int32_t uoff[J];
   bool uok[J];
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     const int u = tu + g * j;
     uok[j] = active && u < c.remA;
-    uoff[j] = u * p.saU;
+    uoff[j] = u * su;
   }
 #pragma unroll
   for (int i = 0; i < R; ++i) {
@@ -420,14 +451,11 @@ TTC_HD void walkp_read(const TileCoord& c, const TileParams& p, const int32_t* t
     const int32_t cross = TAB ? (rok && active ? tabA[lb] : 0) : lb * p.crossA_lin;
     const int pos = lb * p.P + tu;
 #pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const bool ok = rok && uok[j];
-      f(i * J + j, ok, ok ? uoff[j] + cross : 0, pos + g * j);
-    }
+    for (int j = 0; j < J; ++j) f(i * J + j, rok && uok[j], uoff[j] + cross, pos + g * j);
   }
 }
 
-template <int NT, int J, int K, bool TAB, class F>
+template <int NT, int J, int K, bool TAB, bool UNIT, class F>
 TTC_HD void walkp_write(const TileCoord& c, const TileParams& p, const int32_t* tabB, int t, F&& f) {
   constexpr int R = K / J;
   const bool whole = c.remB == p.LB;
@@ -435,13 +463,14 @@ TTC_HD void walkp_write(const TileCoord& c, const TileParams& p, const int32_t* 
   const int tr = int(fast_div(uint32_t(t), whole ? p.pkB[0].div : p.pkB[1].div));
   const int tv = t - tr * g;
   const bool active = tr < rows;
+  const int32_t sv = UNIT ? 1 : p.sbV;
   int32_t voff[J];
   bool vok[J];
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     const int v = tv + g * j;
     vok[j] = active && v < c.remB;
-    voff[j] = v * p.sbV;
+    voff[j] = v * sv;
   }
 #pragma unroll
   for (int i = 0; i < R; ++i) {
@@ -450,10 +479,7 @@ TTC_HD void walkp_write(const TileCoord& c, const TileParams& p, const int32_t* 
     const int32_t cross = TAB ? (rok && active ? tabB[la] : 0) : la * p.crossB_lin;
     const int pos = tv * p.P + la;
 #pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const bool ok = rok && vok[j];
-      f(i * J + j, ok, ok ? voff[j] + cross : 0, pos + g * j * p.P);
-    }
+    for (int j = 0; j < J; ++j) f(i * J + j, rok && vok[j], voff[j] + cross, pos + g * j * p.P);
   }
 }
 

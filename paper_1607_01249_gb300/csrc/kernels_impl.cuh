@@ -244,22 +244,26 @@ __device__ __forceinline__ void tile2_body(const store_t<DIN>* __restrict__ Ab, 
   using TO = store_t<DOUT>;
   constexpr int K = tile_k_for(sizeof(S));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // every access is predicated on the walk's ok (no branches); the staged
+  // value of a lane with no element is read from position 0 and not stored
   S v[K];
-  walk2_read<JU, K, FULL, TA>(c, p, p.tabA, lane, warp,
-                              [&](int k, bool, int32_t off, int) { v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + off)); });
-  walk2_read<JU, K, FULL, TA>(c, p, p.tabA, lane, warp, [&](int k, bool ok, int32_t, int pos) {
+  walk2_read<JU, K, FULL, TA, true>(c, p, p.tabA, lane, warp, [&](int k, bool ok, int32_t off, int) {
+    if (ok) v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + off));
+  });
+  walk2_read<JU, K, FULL, TA, true>(c, p, p.tabA, lane, warp, [&](int k, bool ok, int32_t, int pos) {
     if (ok) tile[pos] = v[k];
   });
   __syncthreads();
   int spre[JW];
-  int32_t voff[JW];
-  walk2_lane_consts<JW>(p, lane, spre, voff);
+  walk2_lane_consts<JW>(p, lane, spre);
   TO bo[K] = {};
-  if constexpr (EK == EK_AXPBY)
-    walk2_write<JW, K, FULL, TB>(c, p, p.tabB, lane, warp, spre, voff,
-                                 [&](int k, bool, int32_t off, int) { bo[k] = Bb[off]; });
-  walk2_write<JW, K, FULL, TB>(c, p, p.tabB, lane, warp, spre, voff, [&](int k, bool ok, int32_t off, int pos) {
-    if (ok) Bb[off] = epilogue_k<DIN, DOUT, EK>(tile[pos], bo[k], p.epi, scale);
+  if constexpr (ek_reads_b(EK))
+    walk2_write<JW, K, FULL, TB, true>(c, p, p.tabB, lane, warp, spre, [&](int k, bool ok, int32_t off, int) {
+      if (ok) bo[k] = Bb[off];
+    });
+  walk2_write<JW, K, FULL, TB, true>(c, p, p.tabB, lane, warp, spre, [&](int k, bool ok, int32_t off, int pos) {
+    const TO y = epilogue_k<DIN, DOUT, EK>(tile[ok ? pos : 0], bo[k], p.epi, scale);
+    if (ok) Bb[off] = y;
   });
 }
 
@@ -293,57 +297,63 @@ __global__ void __launch_bounds__(kThreads, 6) tile2_kernel(const store_t<DIN>* 
 
 // --------------------------------------------------------- packed-lane tile --
 //
-// Tiles without a C index of any extents up to (threads x K) elements, on 256
-// or 512 threads (the thread count is the launch's; the walks only see the
-// host's layouts): the lanes of a warp are packed over the rows of each side
-// (walkp_read / walkp_write), so runs of any length, and the short runs of the
-// tiles at the tensor's edge, keep almost every lane busy, at the per-element
-// cost of the warp-mapped walk.  With 512 threads a tile holds 8192 four-byte
-// elements, which lets both sides' runs be longer than a 4096-element tile
-// allows.
+// Tiles without a C index of any extents up to 256 x K elements: the lanes of
+// a warp are packed over the rows of each side (walkp_read / walkp_write), so
+// runs of any length, and the short runs of the tiles at the tensor's edge,
+// keep almost every lane busy, at about the per-element cost of the
+// warp-mapped walk.
 
-constexpr int kPackMaxThreads = 512;
 
-template <int DIN, int DOUT, int JU, int JW, int EK, bool TA, bool TB>
+template <int DIN, int DOUT, int JU, int JW, int EK, bool TA, bool TB, int K = tile_k_for(sizeof(stage_t<DIN>))>
 __device__ __forceinline__ void tilep_body(const store_t<DIN>* __restrict__ Ab, store_t<DOUT>* __restrict__ Bb,
                                            const TileParams& p, const TileCoord& c, stage_t<DIN>* tile,
                                            float scale) {
   using S = stage_t<DIN>;
   using TO = store_t<DOUT>;
-  constexpr int K = tile_k_for(sizeof(S));
   const int t = threadIdx.x;
+  // accesses predicated on the walk's ok, as in tile2_body
   S v[K];
-  walkp_read<0, JU, K, TA>(c, p, p.tabA, t,
-                           [&](int k, bool, int32_t off, int) { v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + off)); });
-  walkp_read<0, JU, K, TA>(c, p, p.tabA, t, [&](int k, bool ok, int32_t, int pos) {
+  walkp_read<0, JU, K, TA, true>(c, p, p.tabA, t, [&](int k, bool ok, int32_t off, int) {
+    if (ok) v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + off));
+  });
+  walkp_read<0, JU, K, TA, true>(c, p, p.tabA, t, [&](int k, bool ok, int32_t, int pos) {
     if (ok) tile[pos] = v[k];
   });
   __syncthreads();
   TO bo[K] = {};
-  if constexpr (EK == EK_AXPBY)
-    walkp_write<0, JW, K, TB>(c, p, p.tabB, t, [&](int k, bool, int32_t off, int) { bo[k] = Bb[off]; });
-  walkp_write<0, JW, K, TB>(c, p, p.tabB, t, [&](int k, bool ok, int32_t off, int pos) {
-    if (ok) Bb[off] = epilogue_k<DIN, DOUT, EK>(tile[pos], bo[k], p.epi, scale);
+  if constexpr (ek_reads_b(EK))
+    walkp_write<0, JW, K, TB, true>(c, p, p.tabB, t, [&](int k, bool ok, int32_t off, int) {
+      if (ok) bo[k] = Bb[off];
+    });
+  walkp_write<0, JW, K, TB, true>(c, p, p.tabB, t, [&](int k, bool ok, int32_t off, int pos) {
+    const TO y = epilogue_k<DIN, DOUT, EK>(tile[ok ? pos : 0], bo[k], p.epi, scale);
+    if (ok) Bb[off] = y;
   });
 }
 
+// the packed-lane tile with its cross-offset kinds (linear or table) resolved
+template <int DIN, int DOUT, int JU, int JW, int EK, int KS = tile_k_for(sizeof(stage_t<DIN>))>
+__device__ __forceinline__ void tilep_tile(const store_t<DIN>* __restrict__ Ab, store_t<DOUT>* __restrict__ Bb,
+                                           const TileParams& p, const TileCoord& c, stage_t<DIN>* tile,
+                                           float scale) {
+  if (p.crossA_tab) {
+    if (p.crossB_tab) tilep_body<DIN, DOUT, JU, JW, EK, true, true, KS>(Ab, Bb, p, c, tile, scale);
+    else tilep_body<DIN, DOUT, JU, JW, EK, true, false, KS>(Ab, Bb, p, c, tile, scale);
+  } else {
+    if (p.crossB_tab) tilep_body<DIN, DOUT, JU, JW, EK, false, true, KS>(Ab, Bb, p, c, tile, scale);
+    else tilep_body<DIN, DOUT, JU, JW, EK, false, false, KS>(Ab, Bb, p, c, tile, scale);
+  }
+}
+
 template <int DIN, int DOUT, int JU, int JW, int EK>
-__global__ void __launch_bounds__(kPackMaxThreads, EK == EK_AXPBY ? 2 : 3) tilep_kernel(
+__global__ void __launch_bounds__(kThreads, EK == EK_AXPBY ? 4 : JU == 1 ? 5 : 6) tilep_kernel(
     const store_t<DIN>* __restrict__ A, store_t<DOUT>* __restrict__ B, const __grid_constant__ TileParams p) {
   using S = stage_t<DIN>;
   extern __shared__ __align__(16) unsigned char smem[];
   S* tile = reinterpret_cast<S*>(smem);
   const float scale = cta_fp8_scale<EK>(p.epi);
   const TileCoord c = cta_tile_coord(p);
-  const store_t<DIN>* Ab = A + c.baseA;
-  store_t<DOUT>* Bb = B + c.baseB;
-  if (p.crossA_tab) {
-    if (p.crossB_tab) tilep_body<DIN, DOUT, JU, JW, EK, true, true>(Ab, Bb, p, c, tile, scale);
-    else tilep_body<DIN, DOUT, JU, JW, EK, true, false>(Ab, Bb, p, c, tile, scale);
-  } else {
-    if (p.crossB_tab) tilep_body<DIN, DOUT, JU, JW, EK, false, true>(Ab, Bb, p, c, tile, scale);
-    else tilep_body<DIN, DOUT, JU, JW, EK, false, false>(Ab, Bb, p, c, tile, scale);
-  }
+  tilep_tile<DIN, DOUT, JU, JW, EK>(A + c.baseA, B + c.baseB, p, c, tile, scale);
 }
 
 // ------------------------------------------------------------- packed rows --
@@ -353,19 +363,18 @@ __global__ void __launch_bounds__(kPackMaxThreads, EK == EK_AXPBY ? 2 : 3) tilep
 // warp packed over the rows, so rows of any length keep almost every lane
 // busy and no shared memory is needed.
 
-template <int DIN, int DOUT, int J, int EK, bool TA, bool TB>
+template <int DIN, int DOUT, int J, int EK, bool TA, bool TB, int K>
 __device__ __forceinline__ void rowsp_body(const store_t<DIN>* __restrict__ Ab, store_t<DOUT>* __restrict__ Bb,
                                            const TileParams& p, const TileCoord& c, float scale) {
   using S = stage_t<DIN>;
   using TO = store_t<DOUT>;
-  constexpr int K = tile_k_for(sizeof(S));
   const int t = threadIdx.x;
   S v[K];
   TO bo[K] = {};
   int32_t ob[K];     // B offsets of one walk (-1: no element), kept for the stores
   walk_rowsp<J, K, TA, TB>(c, p, p.tabA, p.tabB, t, [&](int k, bool ok, int32_t offA, int32_t offB) {
     v[k] = to_stage<DIN>(ldg_elem<DIN>(Ab + offA));
-    if constexpr (EK == EK_AXPBY) bo[k] = Bb[offB];
+    if constexpr (ek_reads_b(EK)) bo[k] = Bb[offB];
     ob[k] = ok ? offB : -1;
   });
 #pragma unroll
@@ -373,20 +382,25 @@ __device__ __forceinline__ void rowsp_body(const store_t<DIN>* __restrict__ Ab, 
     if (ob[k] >= 0) Bb[ob[k]] = epilogue_k<DIN, DOUT, EK>(v[k], bo[k], p.epi, scale);
 }
 
+// the packed rows of one tile with the cross-offset kinds resolved
+template <int DIN, int DOUT, int J, int EK, int K = tile_k_for(sizeof(stage_t<DIN>))>
+__device__ __forceinline__ void rowsp_tile(const store_t<DIN>* __restrict__ Ab, store_t<DOUT>* __restrict__ Bb,
+                                           const TileParams& p, const TileCoord& c, float scale) {
+  if (p.crossA_tab) {
+    if (p.crossB_tab) rowsp_body<DIN, DOUT, J, EK, true, true, K>(Ab, Bb, p, c, scale);
+    else rowsp_body<DIN, DOUT, J, EK, true, false, K>(Ab, Bb, p, c, scale);
+  } else {
+    if (p.crossB_tab) rowsp_body<DIN, DOUT, J, EK, false, true, K>(Ab, Bb, p, c, scale);
+    else rowsp_body<DIN, DOUT, J, EK, false, false, K>(Ab, Bb, p, c, scale);
+  }
+}
+
 template <int DIN, int DOUT, int J, int EK>
 __global__ void __launch_bounds__(kThreads, EK == EK_AXPBY ? 3 : 4) rowsp_kernel(
     const store_t<DIN>* __restrict__ A, store_t<DOUT>* __restrict__ B, const __grid_constant__ TileParams p) {
   const float scale = cta_fp8_scale<EK>(p.epi);
   const TileCoord c = cta_tile_coord(p);
-  const store_t<DIN>* Ab = A + c.baseA;
-  store_t<DOUT>* Bb = B + c.baseB;
-  if (p.crossA_tab) {
-    if (p.crossB_tab) rowsp_body<DIN, DOUT, J, EK, true, true>(Ab, Bb, p, c, scale);
-    else rowsp_body<DIN, DOUT, J, EK, true, false>(Ab, Bb, p, c, scale);
-  } else {
-    if (p.crossB_tab) rowsp_body<DIN, DOUT, J, EK, false, true>(Ab, Bb, p, c, scale);
-    else rowsp_body<DIN, DOUT, J, EK, false, false>(Ab, Bb, p, c, scale);
-  }
+  rowsp_tile<DIN, DOUT, J, EK>(A + c.baseA, B + c.baseB, p, c, scale);
 }
 
 // ------------------------------------------------------------ multi-row copy --
@@ -686,7 +700,7 @@ cudaError_t launch_tile2_pair(int ju, int jw, const void* A, void* B, const Tile
 template <int DIN, int DOUT>
 cudaError_t launch_tilep_pair(int nt, int ju, int jw, const void* A, void* B, const TileParams& p, int smem,
                               cudaStream_t s) {
-  if (nt != 256 && nt != 512) return cudaErrorInvalidValue;
+  if (nt != kThreads) return cudaErrorInvalidValue;
 #define J(U_, W_)                                                                                           \
   if (ju == U_ && jw == W_)                                                                                 \
     return with_ek<DIN, DOUT, TilepL<DIN, DOUT, U_, W_>::template L>(p.epi.mode, p.epi.beta_nz, nt, A, B, p, smem, s);

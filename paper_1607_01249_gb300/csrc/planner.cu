@@ -405,7 +405,7 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
 
   // ---- multi-row copy: perm keeps index 0 with short runs; G consecutive
   // indices of A's next index make one contiguous block of A per tile
-  if (c.perm[0] == 0 && c.N >= 2 && c.sa[0] == 1 && c.sb[0] == 1 && c.sa[1] == c.s[0]) {
+  if (!flat && c.perm[0] == 0 && c.N >= 2 && c.sa[0] == 1 && c.sb[0] == 1 && c.sa[1] == c.s[0]) {
     const int Kt = tile_k_for(stage_bytes(din));
     const int64_t vcap = vmax > 0 ? std::min<int64_t>(vmax, int64_t(kThreads) * Kt) : int64_t(kThreads) * Kt;
     const int64_t cap = vcap / c.s[0];
@@ -449,14 +449,15 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
   const int c0 = hc ? 1 : 0;
   const int64_t LC = hc ? c.s[0] : 1;
   const int Kt = tile_k_for(stage_bytes(din));
-  // elements of one 256-thread tile; the packed-lane kernel (single-plan
-  // tiles without a C index) also runs tiles of twice that on 512 threads
+  // elements of one 256-thread tile (packed-lane tiles of twice that volume
+  // on 512 threads measured slower than 256-thread ones on every sweep case:
+  // fewer, larger CTAs hide the latency between their load and store phases
+  // less well)
   const int V1 = vmax > 0 ? std::min(vmax, kThreads * Kt) : kThreads * Kt;
-  // (512-thread packed tiles of twice the volume measured slower than the
-  // 256-thread ones on every sweep case: fewer, larger CTAs hide the
-  // latency between their load and store phases less well)
-  const bool pk_ok = vmax == 0 && !hc;
+  // the packed-lane kernel needs unit-stride runs on both sides
+  const bool pk_ok = !hc && c.sa[0] == 1 && c.sb[c.perm[0]] == 1;
   const int Vmax = V1;
+  const int Kp = flat ? vmax / kThreads : Kt;   // slots per thread of the packed kernels
   std::vector<Candidate> tiles;
   if (!(hc && c.N == 1) && LC * 2 <= Vmax) {
     // A-group index list: A order from c0, dense, never B's first index after C
@@ -541,7 +542,7 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
             k.order = grid_order(c, ext, 0);
             k.seg_a = run_length(c, ext, orderA, c.sa);
             k.seg_b = run_length(c, ext, orderB, c.sb);
-            if (V <= V1) {
+            if (!flat) {
               const double per_slot = 26.0 + (sh.ga.size() > 1 ? 3 : 0) + (sh.gb.size() > 1 ? 3 : 0) + (bnz ? 6 : 0);
               const double issue = ntiles * kTileK * kThreads * per_slot / kLaneInstrPerS;
               k.est_s = std::max(mem, issue) + 0.25 * std::min(mem, issue) + over + 3e-6;
@@ -560,6 +561,9 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
               // the warp-mapped kernel (single-plan only), when the shape fits
               // one of its lane layouts
               const int64_t U = LC * LA, W = LC * LB;
+              // (unit-stride runs on both sides: the warp-mapped walks step
+              // their lanes' chunks by constants)
+              const bool unit = c.sa[0] == 1 && c.sb[c.perm[0]] == 1;
               int ju = 0, jw = 0;
               for (int j : {1, 2, 4})
                 if (!ju && vmax == 0 && U <= 32 * j && LB <= 8 * Kt / j) ju = j;
@@ -568,7 +572,7 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
               // a run shorter than half a warp leaves most lanes idle: every
               // warp access then carries a few elements only (measured slower
               // than the flat walk in the batch body)
-              if (U < 16 || W < 16) ju = jw = 0;
+              if (U < 16 || W < 16 || !unit) ju = jw = 0;
               if (ju && jw) {
                 // lanes past a run's end idle, also in the short tiles at the
                 // tensor's edge: every tile costs the full tile's instructions
@@ -584,40 +588,52 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
                 tiles.push_back(k2);
               }
             }
-            if (hc && vmax == 0 && V >= 64) {
+            if (hc && (flat || V >= 64)) {
               // packed rows: the C run is contiguous on both sides, so rows
               // are copied directly (no staging); the fewest idle threads
-              // whose layout covers the tile's rows
+              // whose layout covers the tile's rows (the batch body has the
+              // layouts with 1 and Kp positions per row)
               const int nrows = int(LA * LB);
               int best_j = 0, best_active = 0;
               for (int j : {1, 2, 4, 8, 16}) {
-                if (j > Kt) break;
+                if (j > Kp) break;
+                if (flat && j != 1 && j != Kp) continue;
                 PackWalk w;
-                if (!pack_layout(int(LC), nrows, kThreads, Kt, j, &w)) continue;
+                if (!pack_layout(int(LC), nrows, kThreads, Kp, j, &w)) continue;
                 if (w.g * w.rows > best_active) {
                   best_active = w.g * w.rows;
                   best_j = j;
                 }
               }
               if (best_j) {
-                const double rows_per_thread = double(Kt / best_j);
+                const double rows_per_thread = double(Kp / best_j);
                 const double wi = rows_per_thread * (16.0 + best_j * (4.0 + (bnz ? 3.0 : 0.0))) + 20.0;
                 const double issuer = ntiles * kThreads * wi / kLaneInstrPerS;
                 Candidate kr = k;
                 kr.slots = 0;
                 kr.rj = best_j;
+                kr.kt = flat ? Kp : 0;
                 kr.est_s = std::max(mem, issuer) + 0.25 * std::min(mem, issuer) + over + 3e-6;
                 tiles.push_back(kr);
               }
             }
-            if (pk_ok && V >= 64) {
+            if (pk_ok && (flat || V >= 64)) {
               // the packed-lane kernel: lane groups of any width, so ragged
               // runs (and the short runs of the edge tiles) idle few lanes
-              const int nt = V <= V1 ? kThreads : 2 * kThreads;
-              const int ju = pack_chunks(int(LA), int(LB), nt, Kt), jw = pack_chunks(int(LB), int(LA), nt, Kt);
+              // (the batch body has the layouts with 1 or 2 chunks on both
+              // sides)
+              const int nt = kThreads;
+              int ju = pack_chunks(int(LA), int(LB), nt, Kp), jw = pack_chunks(int(LB), int(LA), nt, Kp);
+              if (flat) {
+                const int j = std::max(ju, jw);
+                ju = jw = (j == 1 || j == 2) && pack_layout(int(LA), int(LB), nt, Kp, j, nullptr) &&
+                                  pack_layout(int(LB), int(LA), nt, Kp, j, nullptr)
+                             ? j
+                             : 0;
+              }
               if (ju && jw) {
-                const double wi = (Kt / ju) * (ju * 3.0 + 6.0 + (sh.gb.size() > 1 ? 2 : 0)) +
-                                  (Kt / jw) * (jw * (4.0 + (bnz ? 3.0 : 0.0)) + 6.0 + (sh.ga.size() > 1 ? 2 : 0)) + 30.0;
+                const double wi = (Kp / ju) * (ju * 3.0 + 6.0 + (sh.gb.size() > 1 ? 2 : 0)) +
+                                  (Kp / jw) * (jw * (4.0 + (bnz ? 3.0 : 0.0)) + 6.0 + (sh.ga.size() > 1 ? 2 : 0)) + 30.0;
                 const double issuep = ntiles * nt * wi / kLaneInstrPerS;
                 const double overp = ntiles * nt * (60.0 + 10.0 * c.N) / kLaneInstrPerS;
                 Candidate kp = k;
@@ -625,6 +641,7 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
                 kp.ju = ju;
                 kp.jw = jw;
                 kp.pk = nt;
+                kp.kt = flat ? Kp : 0;
                 kp.est_s = std::max(mem, issuep) + 0.25 * std::min(mem, issuep) + overp + 3e-6;
                 tiles.push_back(kp);
               }
@@ -802,7 +819,7 @@ void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* 
   if (k.pk) {
     // packed-lane layouts of both sides, for a whole tile and for the tile a
     // cut index leaves short (remA = fullA * (s mod t), likewise remB)
-    const int Kt = tile_k_for(stage_bytes(din));
+    const int Kt = k.kt ? k.kt : tile_k_for(stage_bytes(din));
     int edgeA = LA, edgeB = LB;
     if (cutA >= 0 && ext[cutA] < c.s[cutA] && c.s[cutA] % ext[cutA]) edgeA = fullA * int(c.s[cutA] % ext[cutA]);
     if (cutB >= 0 && ext[cutB] < c.s[cutB] && c.s[cutB] % ext[cutB]) edgeB = fullB * int(c.s[cutB] % ext[cutB]);
@@ -814,7 +831,7 @@ void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* 
   if (k.rj) {
     // packed rows: g threads per row of LC elements, and the row counts of
     // a whole tile's A side and of the short last block's
-    const int Kt = tile_k_for(stage_bytes(din));
+    const int Kt = k.kt ? k.kt : tile_k_for(stage_bytes(din));
     int edgeA = LA;
     if (cutA >= 0 && ext[cutA] < c.s[cutA] && c.s[cutA] % ext[cutA]) edgeA = fullA * int(c.s[cutA] % ext[cutA]);
     pack_layout(LC, LA * LB, kThreads, Kt, k.rj, &p->pkA[0]);
@@ -823,6 +840,27 @@ void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* 
   }
   *smem_bytes = int(((tabA->size() + tabB->size()) * sizeof(int32_t) + 15) & ~size_t(15)) +
                 p->P * LB * stage_bytes(din);
+}
+
+void build_amax_rows(const Canon& c, RowParams* p) {
+  // the FP8 pre-pass reads A only: neighbouring indices that are dense in A
+  // merge whatever B's order (longer rows to stream)
+  Canon a = c;
+  int n = 0;
+  for (int k = 0; k < c.N; ++k) {
+    if (n > 0 && c.sa[k] == a.sa[n - 1] * a.s[n - 1]) {
+      a.s[n - 1] *= c.s[k];
+    } else {
+      a.s[n] = c.s[k];
+      a.sa[n] = c.sa[k];
+      a.sb[n] = c.sb[k];
+      ++n;
+    }
+  }
+  a.N = n;
+  // chunks of at most 1024 elements: a warp streams a few chunks at a time,
+  // and long rows still give every SM many warps' work
+  build_row_params(a, a.s[0] <= 1024 ? a.s[0] : 1024, p);
 }
 
 void build_row_params(const Canon& c, int64_t chunk, RowParams* p) {

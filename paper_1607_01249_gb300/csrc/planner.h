@@ -41,6 +41,7 @@ struct Candidate {
   int pk = 0;                  // >0: packed-lane tile kernel with pk (256 or 512) threads per CTA
   int swz = 0;                 // grouped grid order (TileParams::swz), 0: plain
   int rj = 0;                  // >0: packed rows (C tiles copied row by row), rj positions per thread and row
+  int kt = 0;                  // packed kernels: slots per thread their layouts assume (0: the single-plan kernels')
   // copy variant
   int64_t chunk = 0;
   int vec = 1;                 // vector width usable when pointers are aligned
@@ -56,7 +57,9 @@ int canonicalize(int ndim, const int* perm, const int64_t* sizes, const int64_t*
                  const int64_t* outerB, Canon* c, std::string* err);
 
 // Candidate schedules, best estimate first (at most max_keep).
-// vmax > 0 caps the tile volume (elements) below the single-plan kernels' cap.
+// vmax > 0: schedules of the batch body instead (tiles of at most vmax
+// elements, vmax / 256 slots per thread: packed-lane tiles, packed rows and
+// run chunks only).
 std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double beta, int max_keep, int vmax = 0);
 
 // Kernel parameters of a candidate.  Host tables (crossA, crossB) are
@@ -64,6 +67,9 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
 void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* p,
                        std::vector<int32_t>* tabA, std::vector<int32_t>* tabB, int* smem_bytes);
 void build_row_params(const Canon& c, int64_t chunk, RowParams* p);
+// Rows of the FP8 amax pre-pass over A's (sub-)tensor: A-dense neighbours
+// merged regardless of B (only A offsets are meaningful).
+void build_amax_rows(const Canon& c, RowParams* p);
 
 // Slot tables of a tile for tile_slots_kernel (layout: TileParams::slots);
 // `tabA`/`tabB` are the host cross tables of the same parameters.  Returns

@@ -133,23 +133,44 @@ ttc_status launch_batched(Lane& L, int slot, const std::vector<Req*>& small, int
     size_t na = 0;
     const size_t at = tabs.size();
     if (!batch_describe(r->plan, r->A, r->B, &d, &tabs, &na, &smem)) continue;
-    d.tile0 = uint32_t(total);
-    tile0.push_back(uint32_t(total));
-    total += d.ntiles;
     descs.push_back(d);
     tab_at.push_back(at);
     tab_na.push_back(na);
   }
+  // ordered by class (one kernel launch per class), then the first tiles
+  {
+    std::vector<size_t> idx(descs.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](size_t x, size_t y) { return batch_class(descs[x]) < batch_class(descs[y]); });
+    std::vector<BatchDesc> d2;
+    std::vector<size_t> at2, na2;
+    for (size_t i : idx) {
+      d2.push_back(descs[i]);
+      at2.push_back(tab_at[i]);
+      na2.push_back(tab_na[i]);
+    }
+    descs.swap(d2);
+    tab_at.swap(at2);
+    tab_na.swap(na2);
+  }
+  for (BatchDesc& d : descs) {
+    d.tile0 = uint32_t(total);
+    tile0.push_back(uint32_t(total));
+    total += d.ntiles;
+  }
+  std::vector<BatchRange> ranges;
+  batch_ranges(descs, &ranges);
   if (descs.empty()) return TTC_OK;
   const size_t off_tab = (descs.size() * sizeof(BatchDesc) + 255) & ~size_t(255);
   const size_t off_t0 = (off_tab + tabs.size() * 4 + 255) & ~size_t(255);
-  const size_t off_cnt = (off_t0 + tile0.size() * 4 + 255) & ~size_t(255);
+  const size_t off_cnt = (off_t0 + tile0.size() * 4 + 255) & ~size_t(255);   // end of the epoch's data
   if (off_cnt + 256 > kSlotBytes) return fail(TTC_ERR_INVALID_SIZE, "epoch exceeds the descriptor slot");
   char* hb = L.h_slots + size_t(slot) * kSlotBytes;
   char* db = L.d_slots + size_t(slot) * kSlotBytes;
   int32_t* d_tab = reinterpret_cast<int32_t*>(db + off_tab);
   for (size_t i = 0; i < descs.size(); ++i) {
-    if (descs[i].path == BP_TILE) {
+    if (descs[i].path != BP_COPY) {
       descs[i].tp.tabA = d_tab + tab_at[i];
       descs[i].tp.tabB = d_tab + tab_at[i] + tab_na[i];
     }
@@ -160,9 +181,9 @@ ttc_status launch_batched(Lane& L, int slot, const std::vector<Req*>& small, int
   cudaError_t e = cudaMemcpyAsync(db, hb, off_cnt, cudaMemcpyHostToDevice, L.s);
   if (e != cudaSuccess) return cuda_fail(e, "server descriptor upload");
   e = batch_launch(reinterpret_cast<BatchDesc*>(db), nullptr, reinterpret_cast<uint32_t*>(db + off_t0),
-                   uint32_t(descs.size()), uint32_t(total), reinterpret_cast<uint32_t*>(db + off_cnt), smem, L.s);
+                   uint32_t(descs.size()), ranges, smem, L.s);
   if (e != cudaSuccess) return cuda_fail(e, "server batch launch");
-  ++*launches;
+  *launches += int64_t(ranges.size());
   return TTC_OK;
 }
 

@@ -21,8 +21,8 @@ namespace {
 
 template <int JU, int K, bool FULL, class F>
 void read2j(const TileCoord& c, const TileParams& tp, const int32_t* tab, int ln, int wp, F&& f) {
-  if (tp.crossA_tab) walk2_read<JU, K, FULL, true>(c, tp, tab, ln, wp, f);
-  else walk2_read<JU, K, FULL, false>(c, tp, tab, ln, wp, f);
+  if (tp.crossA_tab) walk2_read<JU, K, FULL, true, true>(c, tp, tab, ln, wp, f);
+  else walk2_read<JU, K, FULL, false, true>(c, tp, tab, ln, wp, f);
 }
 
 template <int K, bool FULL, class F>
@@ -37,10 +37,9 @@ bool read2(int ju, const TileCoord& c, const TileParams& tp, const int32_t* tab,
 template <int JW, int K, bool FULL, class F>
 void write2j(const TileCoord& c, const TileParams& tp, const int32_t* tab, int ln, int wp, F&& f) {
   int sp[JW];
-  int32_t vo[JW];
-  walk2_lane_consts<JW>(tp, ln, sp, vo);
-  if (tp.crossB_tab) walk2_write<JW, K, FULL, true>(c, tp, tab, ln, wp, sp, vo, f);
-  else walk2_write<JW, K, FULL, false>(c, tp, tab, ln, wp, sp, vo, f);
+  walk2_lane_consts<JW>(tp, ln, sp);
+  if (tp.crossB_tab) walk2_write<JW, K, FULL, true, true>(c, tp, tab, ln, wp, sp, f);
+  else walk2_write<JW, K, FULL, false, true>(c, tp, tab, ln, wp, sp, f);
 }
 
 template <int K, bool FULL, class F>
@@ -133,6 +132,8 @@ struct Checker {
     build_tile_params(p->canon, k, p->din, &tp, &ta, &tb, &smem);
     if (smem > 200 * 1024) return fail("shared memory over budget", smem, 0);
     const int nthreads = k.pk ? k.pk : kThreads;
+    if ((k.pk || k.ju) && (tp.saU != 1 || tp.sbV != 1))
+      return fail("warp-mapped or packed-lane tile without unit-stride runs", tp.saU, tp.sbV);
     if (tp.V > nthreads * K) return fail("tile larger than the threads cover", tp.V, nthreads * K);
     std::vector<int32_t> slots;
     int sbytes = 0;
@@ -266,13 +267,13 @@ struct Checker {
   // tilep_kernel: every thread's load walk, then every thread's store walk
   template <int J, int K, class F>
   void packed_read(const TileCoord& c, const TileParams& tp, const std::vector<int32_t>& ta, int t, F& f) {
-    if (tp.crossA_tab) walkp_read<0, J, K, true>(c, tp, ta.data(), t, f);
-    else walkp_read<0, J, K, false>(c, tp, ta.data(), t, f);
+    if (tp.crossA_tab) walkp_read<0, J, K, true, true>(c, tp, ta.data(), t, f);
+    else walkp_read<0, J, K, false, true>(c, tp, ta.data(), t, f);
   }
   template <int J, int K, class F>
   void packed_write(const TileCoord& c, const TileParams& tp, const std::vector<int32_t>& tb, int t, F& f) {
-    if (tp.crossB_tab) walkp_write<0, J, K, true>(c, tp, tb.data(), t, f);
-    else walkp_write<0, J, K, false>(c, tp, tb.data(), t, f);
+    if (tp.crossB_tab) walkp_write<0, J, K, true, true>(c, tp, tb.data(), t, f);
+    else walkp_write<0, J, K, false, true>(c, tp, tb.data(), t, f);
   }
   template <int K, class FR, class FW>
   bool packed(int nt, int ju, int jw, const TileCoord& c, const TileParams& tp, const std::vector<int32_t>& ta,
@@ -346,8 +347,10 @@ extern "C" ttc_status ttc_debug_verify_schedule(ttc_plan_t plan, int candidate, 
   if (batch) {
     // the schedule the batch body (ttc_batch_*, the server) runs for this plan
     if (plan->dout == DT_E4M3 || is_complex(plan->din)) return TTC_OK;    // never batched
-    k = make_candidates(plan->canon, plan->din, plan->dout, plan->beta, 4,
-                        kThreads * batch_k_for(plan->din == DT_F64 ? 8 : 4)).front();
+    const std::vector<Candidate> bc = make_candidates(plan->canon, plan->din, plan->dout, plan->beta, 4,
+                                                      kThreads * batch_k_for(plan->din == DT_F64 ? 8 : 4));
+    if (bc.empty()) return TTC_OK;    // not batchable: the batch runs it as a single-plan kernel
+    k = bc.front();
     if (k.variant == VAR_COPY) k.chunk = kBatchCopyChunk / (plan->din == DT_F64 ? 2 : 1);
   } else {
     k = plan->cands[candidate];

@@ -89,6 +89,7 @@ SIGNATURES = {
                                             ctypes.POINTER(ctypes.c_int), _i64p, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_double]),
     "ttc_contraction_execute": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ttc_contraction_check": (ctypes.c_int, [_vp]),
     "ttc_contraction_info": (ctypes.c_int, [_vp, _i64p, _i64p, _i64p, ctypes.POINTER(ctypes.c_int)]),
     "ttc_contraction_destroy": (ctypes.c_int, [_vp]),
     "ttc_packed_gemm_plan": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i64p,
@@ -110,6 +111,7 @@ SIGNATURES = {
     "ttc_debug_slot_tables": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
                                              _i64p]),
     "ttc_debug_packed_gemm_skip_mma": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "ttc_debug_contraction_use_cublas": (ctypes.c_int, [_vp, ctypes.c_int]),
     "ttc_debug_server_set_watchdog": (ctypes.c_int, [_vp, ctypes.c_double]),
     "ttc_debug_server_submit_delay": (ctypes.c_int, [_vp, ctypes.c_int64, _i64p]),
 }
@@ -314,6 +316,16 @@ class Contraction:
         return C
 
     __call__ = execute
+
+    def check(self):
+        """ttc_contraction_check: raises TTCError(TTC_ERR_TIMEOUT) once after a
+        tensor-core wait of the BF16 GEMM gave up."""
+        _check(lib().ttc_contraction_check(self._h))
+
+    def use_cublas(self, use: bool = True):
+        """Testing hook: the BF16 GEMM on cuBLAS (a timed comparison)."""
+        _check(lib().ttc_debug_contraction_use_cublas(self._h, 1 if use else 0))
+        return self
 
     def info(self) -> dict:
         m, n, k, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()

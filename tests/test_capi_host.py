@@ -404,6 +404,15 @@ def test_contraction_plan_validation_and_layouts():
     # the BF16 GEMM path always packs (downcasts) both operands
     assert C((0, 1), (4, 5), (1, 2), (5, 6), (0, 2), (4, 6), "f32", "bf16").info()["permuted"] == {
         "A": True, "B": True, "C": False}
+    # BF16 plans of every layout kind, including an outer product (no
+    # contracted label: a unit contracted index stands in), an empty
+    # contracted extent and an empty free extent, are made on the host
+    for ma, sa, mb, sb, mc, sc in [((0, 1), (4, 6), (2, 3), (5, 7), (3, 0, 2, 1), (7, 4, 5, 6)),
+                                   ((5, 1, 0, 6), (3, 4, 5, 6), (6, 3, 1, 5), (6, 7, 4, 3), (3, 0), (7, 5)),
+                                   ((0, 1), (5, 0), (1, 2), (0, 6), (2, 0), (6, 5)),
+                                   ((0, 1), (0, 4), (1, 2), (4, 3), (0, 2), (0, 3))]:
+        inf = C(ma, sa, mb, sb, mc, sc, "f32", "bf16").info()
+        assert inf["m"] * inf["n"] == math.prod(sc)
 
 
 def test_packed_gemm_plan_on_the_host():

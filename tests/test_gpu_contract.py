@@ -143,3 +143,84 @@ def test_full_size_contraction_sampled(case):
         K = int(np.prod([ext[m] for m in contracted]))
         n = K + 2
         assert abs(float(got[off]) - exact) <= n * 2.0 ** -24 / (1 - n * 2.0 ** -24) * scale
+
+
+def test_bf16_gemm_tiles_and_edges():
+    """The tensor-core GEMM of the BF16 mode over several 128 x 256 tiles in
+    both directions, ragged M, N and K (K a multiple of 8 and not, so that
+    the operands' row pitch is padded), with beta, and with C taking the
+    GEMM's output directly, transposed, and through a workspace."""
+    for ext, mc, beta in (({0: 300, 1: 1000, 2: 600}, (0, 2), 0.5),      # M, N ragged; K % 64 != 0
+                          ({0: 129, 1: 77, 2: 257}, (2, 0), 0.0),        # K % 8 != 0: padded pitch
+                          ({0: 40, 1: 8, 2: 30}, (0, 2), -1.0)):         # one K stage
+        run_case((0, 1), (1, 2), mc, ext, "f32", "bf16", 1.25, beta, 20)
+    run_case((0, 3, 1, 4), (4, 2, 3), (1, 2, 0), {0: 37, 1: 29, 2: 71, 3: 13, 4: 11}, "f32", "bf16", 1.3, 0.5, 21)
+    con = run_case((5, 1, 0, 6), (6, 3, 1, 5), (3, 0), {0: 150, 1: 5, 3: 270, 5: 7, 6: 9}, "f32", "bf16", 1.0,
+                   0.0, 22)
+    con.check()
+
+
+def test_bf16_gemm_matches_cublas_on_the_same_operands():
+    """The same K-major BF16 operands through cuBLAS (the timed comparison):
+    both within the dot-product bound of the definition, and of each other."""
+    ext = {0: 260, 1: 520, 2: 390}
+    ours = run_case((0, 1), (1, 2), (0, 2), ext, "f32", "bf16", 1.0, 0.25, 23)
+    g = inputs.rng(23)
+    sa, sb, sc = (260, 520), (520, 390), (260, 390)
+    A = g.uniform(-1, 1, 260 * 520).astype(np.float32)
+    B = g.uniform(-1, 1, 520 * 390).astype(np.float32)
+    C0 = g.uniform(-1, 1, 260 * 390).astype(np.float32)
+    outs = []
+    for use in (False, True):
+        con = ttc.Contraction((0, 1), sa, (1, 2), sb, (0, 2), sc, "f32", "bf16", 1.0, 0.25).use_cublas(use)
+        dA, dB, dC = (torch.from_numpy(x.copy()).cuda() for x in (A, B, C0))
+        con.execute(dA, dB, dC)
+        torch.cuda.synchronize()
+        outs.append(dC.cpu().numpy().astype(np.float64))
+    scale = np.abs(A.reshape(sa, order="F")).astype(np.float64) @ np.abs(B.reshape(sb, order="F")).astype(np.float64)
+    n = 520 + 2
+    tol = 2 * n * 2.0 ** -24 / (1 - n * 2.0 ** -24) * (scale.ravel(order="F") + 0.25 * np.abs(C0))
+    assert np.all(np.abs(outs[0] - outs[1]) <= tol)
+    ours.check()
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_full_size_bf16_contraction_sampled(case):
+    """The bench's contractions at full size in the BF16 mode: sampled entries
+    of C against the definition on the operands rounded to BF16."""
+    from paper_1607_01249_gb300.inputs import contraction_cases
+    c = contraction_cases()[case]
+    ma, mb, mc, ext = c["modes_a"], c["modes_b"], c["modes_c"], c["extents"]
+    sa, sb, sc = (tuple(ext[m] for m in ms) for ms in (ma, mb, mc))
+    g = inputs.rng(700 + case)
+    A = g.uniform(-1, 1, int(np.prod(sa, dtype=np.int64))).astype(np.float32)
+    B = g.uniform(-1, 1, int(np.prod(sb, dtype=np.int64))).astype(np.float32)
+    con = ttc.Contraction(ma, sa, mb, sb, mc, sc, "f32", "bf16", 1.0, 0.0)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.zeros(int(np.prod(sc, dtype=np.int64)), device="cuda")
+    con.execute(dA, dB, dC)
+    torch.cuda.synchronize()
+    con.check()
+    got = dC.cpu().numpy()
+    Ar = oracle.bf16_from_f32(A).astype(np.uint32).__lshift__(16).view(np.float32)
+    Br = oracle.bf16_from_f32(B).astype(np.uint32).__lshift__(16).view(np.float32)
+    a = Ar.reshape(sa, order="F").astype(np.float64)
+    b = Br.reshape(sb, order="F").astype(np.float64)
+    contracted = [m for m in ma if m in mb]
+    K = int(np.prod([ext[m] for m in contracted]))
+    n = K + 2
+    for _ in range(64):
+        idx = {m: int(g.integers(0, ext[m])) for m in mc}
+        sl_a = tuple(idx[m] if m in idx else slice(None) for m in ma)
+        sl_b = tuple(idx[m] if m in idx else slice(None) for m in mb)
+        ra = [m for m in ma if m not in idx]
+        rb = [m for m in mb if m not in idx]
+        va = np.transpose(a[sl_a], [ra.index(m) for m in contracted])
+        vb = np.transpose(b[sl_b], [rb.index(m) for m in contracted])
+        exact = float(np.sum(va * vb))
+        scale = float(np.sum(np.abs(va) * np.abs(vb)))
+        off, st = 0, 1
+        for m, s in zip(mc, sc):
+            off += idx[m] * st
+            st *= s
+        assert abs(float(got[off]) - exact) <= n * 2.0 ** -24 / (1 - n * 2.0 ** -24) * scale
