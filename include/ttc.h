@@ -324,7 +324,11 @@ ttc_status ttc_batch_set_direct_threshold(ttc_batch_t batch, int64_t min_element
  *  ttc_contraction_check    synchronous: TTC_ERR_TIMEOUT (reported once) if
  *                           a bounded wait of the tensor-core GEMM gave up
  *                           since the last check (that execution's C is not
- *                           valid), else TTC_OK.
+ *                           valid), else TTC_OK.  Sticky (reported by every
+ *                           later check) if the MMAs in flight had not
+ *                           finished when the kernel released its tensor
+ *                           memory: tensor-core results of concurrent and
+ *                           later launches on that device may be corrupt.
  *  ttc_contraction_info     GEMM extents m, n, k and which tensors are
  *                           permuted (bit 0: A, bit 1: B, bit 2: C).
  *  ttc_contraction_destroy  release (no work using it may be queued).
@@ -366,7 +370,12 @@ ttc_status ttc_contraction_destroy(ttc_contraction_t c);
  *  ttc_packed_gemm_check    synchronous: TTC_ERR_TIMEOUT if a tensor-core
  *                           wait of an execution on the current device gave
  *                           up since the last check (that C is incomplete;
- *                           the error is reported once), else TTC_OK.
+ *                           the error is reported once), else TTC_OK.  If
+ *                           the MMAs in flight did not finish either before
+ *                           the kernel released its tensor memory, the
+ *                           error is sticky (reported by every later check):
+ *                           tensor-core results of concurrent and later
+ *                           launches on that device may be corrupt.
  *  ttc_packed_gemm_info     m, n, k.
  *  ttc_packed_gemm_destroy  release (no work using it may be queued).
  */

@@ -59,6 +59,8 @@ struct ttc_contraction_s {
   int64_t kpitch = 0;          // BF16 mode: row pitch of the K-major operands (K rounded up to 8)
   std::vector<int64_t> offs;   // BF16 mode: C offsets of the GEMM's rows (M' entries), then columns (N')
   bool use_cublas = false;     // testing hook: the BF16 mode's GEMM on cuBLAS (a timed comparison)
+  int gemm_variant = 0;        // testing hook: the tensor-core GEMM's tile shape (GemmVariant; 0 = pick)
+  int gemm_used = 0;           // the tile shape of the last execution
   ttc_plan_t planC = nullptr;  // C' -> C with beta, when C is not a GEMM output layout
   size_t wsC = 0;
   int64_t sizeA = 0, sizeB = 0, sizeC = 0;   // elements of each tensor
@@ -424,7 +426,7 @@ ttc_status ttc_contraction_execute(ttc_contraction_t c, const void* A, const voi
     const int64_t* rows = reinterpret_cast<const int64_t*>(static_cast<char*>(wc) + align256(c->wsC));
     if (const char* why = gemm_bf16_check(X, c->kpitch, Y, c->kpitch, m, n, c->K)) return fail(TTC_ERR_INVALID_SIZE, why);
     e = gemm_bf16(X, c->kpitch, Y, c->kpitch, static_cast<float*>(C), rows, rows + m, m, n, c->K, float(c->alpha),
-                  float(c->beta), ds.err, s);
+                  float(c->beta), ds.err, c->gemm_variant, &c->gemm_used, s);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM launch");
     return TTC_OK;
   }
@@ -492,6 +494,9 @@ ttc_status ttc_contraction_check(ttc_contraction_t c) {
   e = cudaMemcpy(&flag, it->second.err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "error word read");
   if (!flag) return TTC_OK;
+  if (flag == 2)   // sticky: not reset
+    return fail(TTC_ERR_TIMEOUT, "a CTA released its tensor memory with MMAs possibly still in flight: tensor-core "
+                                 "results on this device are unreliable from then on");
   e = cudaMemset(it->second.err, 0, sizeof(int));      // reported once
   if (e != cudaSuccess) return cuda_fail(e, "error word reset");
   return fail(TTC_ERR_TIMEOUT, "a tensor-core wait of the GEMM gave up");
@@ -501,6 +506,15 @@ ttc_status ttc_debug_contraction_use_cublas(ttc_contraction_t c, int use) {
   if (!c) return fail(TTC_ERR_INVALID_ARG, "contraction is NULL");
   std::lock_guard<std::mutex> lk(c->mu);
   c->use_cublas = use != 0;
+  return TTC_OK;
+}
+
+ttc_status ttc_debug_contraction_gemm_variant(ttc_contraction_t c, int variant, int* last_used) {
+  if (!c) return fail(TTC_ERR_INVALID_ARG, "contraction is NULL");
+  if (variant > 3) return fail(TTC_ERR_INVALID_ARG, "variant must be -1..3");
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (variant >= 0) c->gemm_variant = variant;
+  if (last_used) *last_used = c->gemm_used;
   return TTC_OK;
 }
 

@@ -22,13 +22,28 @@
 //              N 256, K 16) as each buffer fills, commits each stage to the
 //              buffer's "empty" barrier so the producer can refill it, and a
 //              finished tile to its accumulator's "full" barrier;
-//   warps 2-5 -- the epilogue: tcgen05.ld of one accumulator (each warp its
-//              32 TMEM lanes), alpha and beta applied, C written, then the
-//              accumulator handed back; meanwhile the MMAs of the next tile
-//              run in the other accumulator.
+//   warps 2-9 -- the epilogue: tcgen05.ld of one accumulator (each warp its
+//              32 TMEM lanes and half of the columns), alpha and beta
+//              applied, C written, then the accumulator handed back;
+//              meanwhile the MMAs of the next tile run in the other
+//              accumulator.  A warp stores one column of its 32 rows per
+//              instruction (consecutive m, one 128-byte line when rowoff is
+//              contiguous); the column offsets of each 32-column chunk are
+//              read once, one per lane, and broadcast by shuffles, so that no
+//              store waits on a load of its own address.
 // Every mbarrier wait is bounded; a wait that gives up records an error word
 // (reported by the caller as TTC_ERR_TIMEOUT), waits (bounded) for its own
-// copies and MMAs in flight and returns.
+// copies and MMAs in flight and returns.  If the MMAs in flight do not finish
+// within that last wait either, the tensor memory is released under them and
+// the error word is set to 2, which the caller never clears.
+//
+// The pair variant (gemm_bf16_pair_kernel) runs the same roles on a cluster
+// of two CTAs on neighbouring SMs that share one 256 x BN output tile
+// (tcgen05 with cta_group::2): each CTA copies its 128 rows of A and its
+// BN/2 rows of B, one thread of the even CTA issues MMAs of M = 256 that read
+// both CTAs' shared memory and write 128 accumulator rows into each CTA's
+// tensor memory.  Per output element each SM then streams half the B bytes
+// of the single-CTA tile, and the smaller stages make a deeper ring.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -47,7 +62,8 @@ namespace {
 
 constexpr int kGM = 128, kGN = 256, kGK = 64;        // CTA tile; one MMA is 128 x 256 x 16
 constexpr int kStages = 4;
-constexpr int kGThreads = 192;                        // 6 warps
+constexpr int kGEpiWarps = 8;                        // two per TMEM lane quarter, one per half of the columns
+constexpr int kGThreads = 64 + 32 * kGEpiWarps;       // producer warp, MMA warp, epilogue warps
 constexpr uint32_t kGTmemCols = 512;                  // two 256-column accumulators
 constexpr int kATile = kGM * kGK * 2;                 // 16 KiB
 constexpr int kBTile = kGN * kGK * 2;                 // 32 KiB
@@ -113,6 +129,274 @@ __device__ __forceinline__ void tile_of(int t, int ntm, int ntn, int* mb, int* n
   *nb = in / gsz;
 }
 
+// Epilogue of one accumulator (TMEM columns from tacc): warp (q, h) writes
+// rows m_base + 32 q + lane and columns n_base + [h BN/2, (h + 1) BN/2).
+// kzero: K = 0, the accumulator was never written and counts as zero.
+template <int BN>
+__device__ __forceinline__ void store_accumulator(uint32_t tacc, int q, int h, int lane, int m_base, int n_base,
+                                                  int M, int N, float* __restrict__ C,
+                                                  const int64_t* __restrict__ rowoff,
+                                                  const int64_t* __restrict__ coloff, float alpha, float beta,
+                                                  bool kzero) {
+  const int m = m_base + 32 * q + lane;
+  const bool mok = m < M;
+  const int64_t ro = mok ? __ldg(rowoff + m) : 0;
+#pragma unroll 1
+  for (int c = 0; c < BN / 64; ++c) {
+    const int col = (BN / 2) * h + 32 * c;
+    const int n0 = n_base + col;
+    const int64_t co = n0 + lane < N ? __ldg(coloff + n0 + lane) : 0;
+    uint32_t r[32];
+    const uint32_t taddr = tacc + (uint32_t(32 * q) << 16) + uint32_t(col);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+      const int64_t coe = __shfl_sync(0xffffffffu, co, e);   // every lane takes part
+      if (mok && n0 + e < N) {
+        float* cp = C + (ro + coe);
+        const float acc = kzero ? 0.f : __fmul_rn(alpha, __uint_as_float(r[e]));
+        *cp = beta != 0.f ? __fmaf_rn(beta, *cp, acc) : acc;
+      }
+    }
+  }
+}
+
+// --- CTA pairs (cluster of two) ------------------------------------------
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// the address of the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// bounded wait with cluster-scope acquire (arrivals from the peer CTA)
+__device__ __forceinline__ bool bar_wait_cluster(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kGWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// a TMA copy into this CTA's shared memory whose completion is counted on a
+// barrier of either CTA of the pair (bar: a cluster address)
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// commit of the pair's MMAs issued so far to the barrier at offset `bar` in
+// both CTAs
+__device__ __forceinline__ void commit_pair(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(uint16_t(3))
+      : "memory");
+}
+
+template <int BN>
+struct PairCfg {
+  static constexpr int kBHalf = BN / 2;                     // rows of B per CTA
+  static constexpr int kBTile = kBHalf * kGK * 2;
+  static constexpr int kStageBytes = kATile + kBTile;       // per CTA
+  static constexpr int kStages = BN == 256 ? 7 : 9;
+  static constexpr uint32_t kCols = 2 * BN;                 // two accumulators
+  static constexpr int kSmem = 1024 + kStages * kStageBytes + 256;
+};
+static_assert(PairCfg<256>::kSmem <= 232448 && PairCfg<128>::kSmem <= 232448, "shared memory");
+
+template <int BN>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGThreads, 1)
+    gemm_bf16_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                          float* __restrict__ C, const int64_t* __restrict__ rowoff,
+                          const int64_t* __restrict__ coloff, int M, int N, int K, float alpha, float beta,
+                          int* err) {
+  using P = PairCfg<BN>;
+  constexpr int S = P::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + S * kATile;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + S * P::kBTile);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 4);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * S;
+  const uint32_t afull0 = full0 + 16 * S, aempty0 = afull0 + 16;
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t rank = cluster_rank();
+  const int pair = int(blockIdx.x >> 1), npairs = int(gridDim.x >> 1);
+  const int nk = (K + kGK - 1) / kGK;
+  const int ntm = (M + 2 * kGM - 1) / (2 * kGM), ntn = (N + BN - 1) / BN, total = ntm * ntn;
+
+  if (t == 0) {
+    for (int s = 0; s < S; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * s) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * s) : "memory");
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(afull0 + 8 * b) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(aempty0 + 8 * b), "n"(2 * kGEpiWarps)
+                   : "memory");   // the epilogue warps of both CTAs
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+  }
+  if (warp == 1) {
+    // the same columns in both CTAs' tensor memory
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(P::kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  // both CTAs' barriers initialised and tensor memory allocated before any
+  // copy, MMA or arrival crosses between them
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  cluster_sync_all();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (t == 0) {
+      // producer (both CTAs): its own rows of A and B, counted on the even
+      // CTA's full barrier, which the even CTA arms with both CTAs' bytes
+      const uint32_t full_l = map_to_rank(full0, 0);
+      bool ok = true;
+      int it = 0;
+      for (int tile = pair; tile < total && ok; tile += npairs) {
+        int mb, nb;
+        tile_of(tile, ntm, ntn, &mb, &nb);
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = it % S;
+          if (it >= S && !bar_wait(empty0 + 8 * s, uint32_t((it / S - 1) & 1))) {
+            ok = false;
+            break;
+          }
+          if (rank == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full0 + 8 * s),
+                         "r"(2 * P::kStageBytes)
+                         : "memory");
+          tma_load_2d_pair(smem_u32(sA + s * kATile), &mapA, kt * kGK, mb * 2 * kGM + int(rank) * kGM, full_l + 8 * s);
+          tma_load_2d_pair(smem_u32(sB + s * P::kBTile), &mapB, kt * kGK, nb * BN + int(rank) * P::kBHalf,
+                           full_l + 8 * s);
+        }
+      }
+      if (!ok) {
+        atomicExch(err, 1);
+        // the copies already issued land in these CTAs' buffers: the even CTA
+        // waits (bounded) for the stages in flight before the pair may end
+        if (rank == 0)
+          for (int j = (it > S ? it - S : 0); j < it; ++j) bar_wait(full0 + 8 * (j % S), uint32_t((j / S) & 1));
+      }
+    }
+  } else if (warp == 1) {
+    if (t == 32 && rank == 0) {
+      // MMA issuer of the pair
+      bool ok = true;
+      int it = 0, ti = 0, committed = -1;
+      for (int tile = pair; tile < total && ok; tile += npairs, ++ti) {
+        const int b = ti & 1;
+        if (ti >= 2 && !bar_wait_cluster(aempty0 + 8 * b, uint32_t((ti / 2 - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc_tmem = tmem + uint32_t(BN * b);
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = it % S;
+          if (!bar_wait(full0 + 8 * s, uint32_t((it / S) & 1))) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(sA + s * kATile), b0 = smem_u32(sB + s * P::kBTile);
+#pragma unroll
+          for (int q = 0; q < kGK / 16; ++q) {
+            const uint64_t da = smem_desc(a0 + q * 32), db = smem_desc(b0 + q * 32);
+            const uint32_t accumulate = (kt > 0 || q > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_tmem),
+                "l"(da), "l"(db), "r"(mma_idesc(2 * kGM, BN)), "r"(accumulate)
+                : "memory");
+          }
+          commit_pair(empty0 + 8 * s);
+          committed = it;
+        }
+        if (!ok) break;
+        commit_pair(afull0 + 8 * b);
+      }
+      if (!ok) {
+        atomicExch(err, 1);
+        if (committed >= 0 && !bar_wait(empty0 + 8 * (committed % S), uint32_t((committed / S) & 1)))
+          atomicExch(err, 2);   // MMAs may outlive the pair's tensor memory: reported for good
+      }
+    }
+  } else {
+    // epilogue (both CTAs): this CTA's 128 rows of the pair's tile
+    const int q = warp & 3, h = (warp - 2) >> 2, lane = t & 31;
+    const uint32_t aempty_l = map_to_rank(aempty0, 0);
+    int ti = 0;
+    for (int tile = pair; tile < total; tile += npairs, ++ti) {
+      const int b = ti & 1;
+      // (the warp leaves together: the tensor-memory loads below are
+      // warp-collective)
+      if (!__all_sync(0xffffffffu, bar_wait(afull0 + 8 * b, uint32_t((ti / 2) & 1)))) {
+        if (lane == 0) atomicExch(err, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int mb, nb;
+      tile_of(tile, ntm, ntn, &mb, &nb);
+      store_accumulator<BN>(tmem + uint32_t(BN * b), q, h, lane, mb * 2 * kGM + int(rank) * kGM, nb * BN, M, N, C,
+                            rowoff, coloff, alpha, beta, false);
+      // this warp's reads of the accumulator are done: tell the issuer
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(aempty_l + 8 * b) : "memory");
+    }
+  }
+  // neither CTA frees its tensor memory or leaves while the pair's MMAs,
+  // copies or arrivals may still reach it
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  cluster_sync_all();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P::kCols) : "memory");
+}
+
 __global__ void __launch_bounds__(kGThreads, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                      float* __restrict__ C, const int64_t* __restrict__ rowoff, const int64_t* __restrict__ coloff,
@@ -138,7 +422,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(afull0 + 8 * b) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(aempty0 + 8 * b) : "memory");   // 4 epilogue warps
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(aempty0 + 8 * b), "n"(kGEpiWarps)
+                   : "memory");   // the epilogue warps
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
@@ -235,51 +520,27 @@ __global__ void __launch_bounds__(kGThreads, 1)
         atomicExch(err, 1);
         // the MMAs already issued still read the ring and write TMEM: wait
         // (bounded) for the last commit before the accumulators are released
-        if (committed >= 0) bar_wait(empty0 + 8 * (committed % kStages), uint32_t((committed / kStages) & 1));
+        if (committed >= 0 && !bar_wait(empty0 + 8 * (committed % kStages), uint32_t((committed / kStages) & 1)))
+          atomicExch(err, 2);   // MMAs may outlive the CTA's tensor memory: reported for good
       }
     }
   } else {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (accumulator rows)
-    const int q = warp & 3, lane = t & 31;
+    const int q = warp & 3, h = (warp - 2) >> 2, lane = t & 31;
     int ti = 0;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++ti) {
       const int b = ti & 1;
-      if (!bar_wait(afull0 + 8 * b, uint32_t((ti / 2) & 1))) {
+      // (the warp leaves together: the tensor-memory loads below are
+      // warp-collective)
+      if (!__all_sync(0xffffffffu, bar_wait(afull0 + 8 * b, uint32_t((ti / 2) & 1)))) {
         if (lane == 0) atomicExch(err, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       int mb, nb;
       tile_of(tile, ntm, ntn, &mb, &nb);
-      const int m = mb * kGM + 32 * q + lane;
-      const int64_t ro = m < M ? __ldg(rowoff + m) : 0;
-#pragma unroll 1
-      for (int c = 0; c < kGN / 32; ++c) {
-        uint32_t r[32];
-        const uint32_t taddr = tmem + uint32_t(256 * b) + (uint32_t(32 * q) << 16) + uint32_t(32 * c);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-              "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr)
-            : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (m < M) {
-#pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int n = nb * kGN + 32 * c + e;
-            if (n < N) {
-              float* cp = C + (ro + __ldg(coloff + n));
-              const float acc = K > 0 ? __fmul_rn(alpha, __uint_as_float(r[e])) : 0.f;
-              *cp = beta != 0.f ? __fmaf_rn(beta, *cp, acc) : acc;
-            }
-          }
-        }
-      }
+      store_accumulator<kGN>(tmem + uint32_t(256 * b), q, h, lane, mb * kGM, nb * kGN, M, N, C, rowoff, coloff,
+                             alpha, beta, K == 0);
       // this warp's TMEM reads are done: hand the accumulator back
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -328,7 +589,43 @@ bool make_map(CUtensorMap* map, const uint16_t* base, int64_t K, int64_t rows, i
 }
 
 std::mutex g_attr_mu;
-bool g_attr_set[64] = {};
+bool g_attr_set[64][3] = {};
+int g_pairs[64] = {};          // co-resident CTA pairs of the pair kernel (0: not yet known)
+
+template <class F>
+cudaError_t set_smem_attr(int dev, int which, F* fn, int bytes) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!g_attr_set[dev][which]) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    g_attr_set[dev][which] = true;
+  }
+  return cudaSuccess;
+}
+
+// clusters of two of the pair kernel that fit on the device at once
+int pairs_on(int dev, int sms) {
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (dev >= 0 && dev < 64 && g_pairs[dev]) return g_pairs[dev];
+  }
+  if (set_smem_attr(dev, 1, gemm_bf16_pair_kernel<256>, PairCfg<256>::kSmem) != cudaSuccess) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(2 * (sms / 2)));
+  cfg.blockDim = dim3(kGThreads);
+  cfg.dynamicSmemBytes = PairCfg<256>::kSmem;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, gemm_bf16_pair_kernel<256>, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    n = 0;
+  }
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (dev >= 0 && dev < 64) g_pairs[dev] = n;
+  return n;
+}
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 }  // namespace
 
@@ -343,34 +640,60 @@ const char* gemm_bf16_check(const void* A, int64_t lda, const void* B, int64_t l
   return nullptr;
 }
 
+int gemm_bf16_pick(int64_t M, int64_t N, int64_t K, int sms, int pairs) {
+  if (K == 0 || pairs < 1 || sms < 1) return GEMM_SINGLE;
+  // time ~ waves x (output columns per SM per tile) / relative rate, the
+  // rates of each tile shape measured on the 2304^3 and 4096^3 GEMMs
+  const double single = double(cdiv(cdiv(M, kGM) * cdiv(N, kGN), sms)) * 256 / 0.6;
+  const double p256 = double(cdiv(cdiv(M, 2 * kGM) * cdiv(N, 256), pairs)) * 256 / 1.0;
+  const double p128 = double(cdiv(cdiv(M, 2 * kGM) * cdiv(N, 128), pairs)) * 128 / 0.85;
+  if (single < p256 && single < p128) return GEMM_SINGLE;
+  return p128 < p256 ? GEMM_PAIR_128 : GEMM_PAIR_256;
+}
+
 cudaError_t gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, const int64_t* rowoff,
                       const int64_t* coloff, int64_t M, int64_t N, int64_t K, float alpha, float beta, int* err,
-                      cudaStream_t s) {
-  CUtensorMap ma, mb;
-  std::memset(&ma, 0, sizeof(ma));
-  std::memset(&mb, 0, sizeof(mb));
-  // (K = 0: no copies are issued and the maps stay unused)
-  if (K > 0 && (!make_map(&ma, static_cast<const uint16_t*>(A), K, M, lda, kGM) ||
-                !make_map(&mb, static_cast<const uint16_t*>(B), K, N, ldb, kGN)))
-    return cudaErrorInvalidValue;
+                      int variant, int* used, cudaStream_t s) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  {
-    std::lock_guard<std::mutex> lk(g_attr_mu);
-    if (dev >= 0 && dev < 64 && !g_attr_set[dev]) {
-      e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
+  const int pairs = K > 0 ? pairs_on(dev, sms) : 0;
+  int v = variant;
+  if (v == GEMM_AUTO || (v != GEMM_SINGLE && (K == 0 || pairs < 1))) v = gemm_bf16_pick(M, N, K, sms, pairs);
+  if (used) *used = v;
+  const int bn = v == GEMM_PAIR_128 ? 128 : 256;
+  CUtensorMap ma, mb;
+  std::memset(&ma, 0, sizeof(ma));
+  std::memset(&mb, 0, sizeof(mb));
+  // (K = 0: no copies are issued and the maps stay unused)
+  if (K > 0 && (!make_map(&ma, static_cast<const uint16_t*>(A), K, M, lda, kGM) ||
+                !make_map(&mb, static_cast<const uint16_t*>(B), K, N, ldb, v == GEMM_SINGLE ? kGN : bn / 2)))
+    return cudaErrorInvalidValue;
+  if (v == GEMM_SINGLE) {
+    e = set_smem_attr(dev, 0, gemm_bf16_kernel, kGSmem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = cdiv(M, kGM) * cdiv(N, kGN);
+    const unsigned grid = unsigned(std::min<int64_t>(tiles, sms));
+    gemm_bf16_kernel<<<grid, kGThreads, kGSmem, s>>>(ma, mb, C, rowoff, coloff, int(M), int(N), int(K), alpha,
+                                                     beta, err);
+  } else {
+    const int64_t tiles = cdiv(M, 2 * kGM) * cdiv(N, bn);
+    const unsigned grid = unsigned(2 * std::min<int64_t>(tiles, pairs));
+    if (bn == 256) {
+      e = set_smem_attr(dev, 1, gemm_bf16_pair_kernel<256>, PairCfg<256>::kSmem);
       if (e != cudaSuccess) return e;
-      g_attr_set[dev] = true;
+      gemm_bf16_pair_kernel<256><<<grid, kGThreads, PairCfg<256>::kSmem, s>>>(ma, mb, C, rowoff, coloff, int(M),
+                                                                               int(N), int(K), alpha, beta, err);
+    } else {
+      e = set_smem_attr(dev, 2, gemm_bf16_pair_kernel<128>, PairCfg<128>::kSmem);
+      if (e != cudaSuccess) return e;
+      gemm_bf16_pair_kernel<128><<<grid, kGThreads, PairCfg<128>::kSmem, s>>>(ma, mb, C, rowoff, coloff, int(M),
+                                                                               int(N), int(K), alpha, beta, err);
     }
   }
-  const int64_t tiles = ((M + kGM - 1) / kGM) * ((N + kGN - 1) / kGN);
-  const unsigned grid = unsigned(std::min<int64_t>(tiles, sms));
-  gemm_bf16_kernel<<<grid, kGThreads, kGSmem, s>>>(ma, mb, C, rowoff, coloff, int(M), int(N), int(K), alpha, beta,
-                                                   err);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -13,16 +13,28 @@ namespace ttc {
 const char* gemm_bf16_check(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
                             int64_t K);
 
+// Tile shapes of gemm_bf16: GEMM_SINGLE -- one CTA per 128 x 256 output
+// tile; GEMM_PAIR_256 / GEMM_PAIR_128 -- a cluster of two CTAs per 256 x 256
+// or 256 x 128 tile (tensor-core MMAs spanning both SMs); GEMM_AUTO picks by
+// gemm_bf16_pick.
+enum GemmVariant : int { GEMM_AUTO = 0, GEMM_SINGLE = 1, GEMM_PAIR_256 = 2, GEMM_PAIR_128 = 3 };
+
+// The tile shape GEMM_AUTO runs for M x N x K on `sms` SMs of which `pairs`
+// CTA pairs are co-resident: the one with the fewest tile rounds weighted by
+// the work per round and the shape's measured rate.
+int gemm_bf16_pick(int64_t M, int64_t N, int64_t K, int sms, int pairs);
+
 // C[rowoff[m] + coloff[n]] (FP32) = alpha * sum_k A[m, k] B[n, k] + beta *
 // the same, for m < M, n < N, where A and B are K-major BF16 matrices: row m
 // of A and row n of B each hold K consecutive elements, at pitches lda and
 // ldb; rowoff (M entries) and coloff (N entries) are device arrays of element
 // offsets (a column-major C with leading dimension ldc: rowoff[m] = m,
-// coloff[n] = n * ldc).  Asynchronous on s (one persistent launch).  A
-// tensor-core wait that gives up sets *err (device memory) to 1 and the
-// result is not valid.
+// coloff[n] = n * ldc).  Asynchronous on s (one persistent launch of the
+// tile shape `variant`; *used, if not null, receives the shape run: K = 0
+// always runs GEMM_SINGLE).  A tensor-core wait that gives up sets *err
+// (device memory) to 1 and the result is not valid.
 cudaError_t gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, const int64_t* rowoff,
                       const int64_t* coloff, int64_t M, int64_t N, int64_t K, float alpha, float beta, int* err,
-                      cudaStream_t s);
+                      int variant, int* used, cudaStream_t s);
 
 }  // namespace ttc

@@ -280,8 +280,10 @@ __global__ void __launch_bounds__(kPgThreads, 2)
   } else if (t == 0) {
     atomicExch(err, 1);
     // give the MMAs in flight a last bounded chance to finish before the
-    // accumulator is released
-    if (issued >= 0) barrier_wait(bar0 + 8 * (issued & 1), uint32_t(issued >> 1) & 1u, wait_limit);
+    // accumulator is released; if they still have not, the tensor memory is
+    // released under them, and the error word says so for good (2)
+    if (issued >= 0 && !barrier_wait(bar0 + 8 * (issued & 1), uint32_t(issued >> 1) & 1u, wait_limit))
+      atomicExch(err, 2);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -450,6 +452,9 @@ ttc_status ttc_packed_gemm_check(ttc_packed_gemm_t g) {
   e = cudaMemcpy(&flag, it->second.err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "error word read");
   if (!flag) return TTC_OK;
+  if (flag == 2)   // sticky: not reset
+    return fail(TTC_ERR_TIMEOUT, "a CTA released its tensor memory with MMAs possibly still in flight: tensor-core "
+                                 "results on this device are unreliable from then on");
   e = cudaMemset(it->second.err, 0, sizeof(int));      // reported once
   if (e != cudaSuccess) return cuda_fail(e, "error word reset");
   return fail(TTC_ERR_TIMEOUT, "a tensor-core wait gave up");

@@ -112,6 +112,7 @@ SIGNATURES = {
                                              _i64p]),
     "ttc_debug_packed_gemm_skip_mma": (ctypes.c_int, [_vp, ctypes.c_int]),
     "ttc_debug_contraction_use_cublas": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "ttc_debug_contraction_gemm_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ttc_debug_server_set_watchdog": (ctypes.c_int, [_vp, ctypes.c_double]),
     "ttc_debug_server_submit_delay": (ctypes.c_int, [_vp, ctypes.c_int64, _i64p]),
 }
@@ -326,6 +327,16 @@ class Contraction:
         """Testing hook: the BF16 GEMM on cuBLAS (a timed comparison)."""
         _check(lib().ttc_debug_contraction_use_cublas(self._h, 1 if use else 0))
         return self
+
+    GEMM_VARIANTS = {0: "auto", 1: "single 128x256", 2: "pair 256x256", 3: "pair 256x128"}
+
+    def gemm_variant(self, variant: int = -1) -> int:
+        """Testing hook: force the BF16 GEMM's tile shape (0 pick, 1 one CTA
+        per 128 x 256 tile, 2 / 3 a CTA pair per 256 x 256 / 256 x 128 tile;
+        -1 keeps it); returns the shape the last execution ran."""
+        used = ctypes.c_int()
+        _check(lib().ttc_debug_contraction_gemm_variant(self._h, int(variant), ctypes.byref(used)))
+        return used.value
 
     def info(self) -> dict:
         m, n, k, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()

@@ -39,7 +39,7 @@ LAYOUTS = [
 ]
 
 
-def run_case(ma, mb, mc, ext, dtype, gemm, alpha, beta, seed):
+def run_case(ma, mb, mc, ext, dtype, gemm, alpha, beta, seed, variant=None):
     sa, sb, sc = (tuple(ext[m] for m in ms) for ms in (ma, mb, mc))
     npdt = np.float32 if dtype == "f32" else np.float64
     g = inputs.rng(seed)
@@ -47,9 +47,13 @@ def run_case(ma, mb, mc, ext, dtype, gemm, alpha, beta, seed):
     B = g.uniform(-1, 1, int(np.prod(sb, dtype=np.int64))).astype(npdt)
     C0 = g.uniform(-1, 1, int(np.prod(sc, dtype=np.int64))).astype(npdt)
     con = ttc.Contraction(ma, sa, mb, sb, mc, sc, dtype, gemm, alpha, beta)
+    if variant is not None:
+        con.gemm_variant(variant)
     dA, dB, dC = (torch.from_numpy(x.copy()).cuda() for x in (A, B, C0))
     con.execute(dA, dB, dC)
     torch.cuda.synchronize()
+    if variant:
+        assert con.gemm_variant() == variant
     got = dC.cpu().numpy().astype(np.float64)
     Ar, Br = A, B
     if gemm == "bf16":
@@ -145,18 +149,23 @@ def test_full_size_contraction_sampled(case):
         assert abs(float(got[off]) - exact) <= n * 2.0 ** -24 / (1 - n * 2.0 ** -24) * scale
 
 
-def test_bf16_gemm_tiles_and_edges():
-    """The tensor-core GEMM of the BF16 mode over several 128 x 256 tiles in
-    both directions, ragged M, N and K (K a multiple of 8 and not, so that
-    the operands' row pitch is padded), with beta, and with C taking the
-    GEMM's output directly, transposed, and through a workspace."""
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_bf16_gemm_tiles_and_edges(variant):
+    """The tensor-core GEMM of the BF16 mode in each tile shape (one CTA per
+    128 x 256 tile; a CTA pair per 256 x 256 or 256 x 128 tile) over several
+    tiles in both directions, ragged M, N and K (K a multiple of 8 and not,
+    so that the operands' row pitch is padded), M within one CTA's half of a
+    pair tile, with beta, and with C taking the GEMM's output directly,
+    transposed, and through a workspace."""
     for ext, mc, beta in (({0: 300, 1: 1000, 2: 600}, (0, 2), 0.5),      # M, N ragged; K % 64 != 0
                           ({0: 129, 1: 77, 2: 257}, (2, 0), 0.0),        # K % 8 != 0: padded pitch
-                          ({0: 40, 1: 8, 2: 30}, (0, 2), -1.0)):         # one K stage
-        run_case((0, 1), (1, 2), mc, ext, "f32", "bf16", 1.25, beta, 20)
-    run_case((0, 3, 1, 4), (4, 2, 3), (1, 2, 0), {0: 37, 1: 29, 2: 71, 3: 13, 4: 11}, "f32", "bf16", 1.3, 0.5, 21)
+                          ({0: 40, 1: 8, 2: 30}, (0, 2), -1.0),          # one K stage, M < 128
+                          ({0: 520, 1: 4100, 2: 1030}, (0, 2), 0.0)):    # many K stages, ragged pair tiles
+        run_case((0, 1), (1, 2), mc, ext, "f32", "bf16", 1.25, beta, 20, variant)
+    run_case((0, 3, 1, 4), (4, 2, 3), (1, 2, 0), {0: 37, 1: 29, 2: 71, 3: 13, 4: 11}, "f32", "bf16", 1.3, 0.5, 21,
+             variant)
     con = run_case((5, 1, 0, 6), (6, 3, 1, 5), (3, 0), {0: 150, 1: 5, 3: 270, 5: 7, 6: 9}, "f32", "bf16", 1.0,
-                   0.0, 22)
+                   0.0, 22, variant)
     con.check()
 
 
@@ -184,10 +193,12 @@ def test_bf16_gemm_matches_cublas_on_the_same_operands():
     ours.check()
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("case", range(3))
-def test_full_size_bf16_contraction_sampled(case):
-    """The bench's contractions at full size in the BF16 mode: sampled entries
-    of C against the definition on the operands rounded to BF16."""
+def test_full_size_bf16_contraction_sampled(case, variant):
+    """The bench's contractions at full size in the BF16 mode, in the tile
+    shape the library picks and in each forced one: sampled entries of C
+    against the definition on the operands rounded to BF16."""
     from paper_1607_01249_gb300.inputs import contraction_cases
     c = contraction_cases()[case]
     ma, mb, mc, ext = c["modes_a"], c["modes_b"], c["modes_c"], c["extents"]
@@ -196,11 +207,13 @@ def test_full_size_bf16_contraction_sampled(case):
     A = g.uniform(-1, 1, int(np.prod(sa, dtype=np.int64))).astype(np.float32)
     B = g.uniform(-1, 1, int(np.prod(sb, dtype=np.int64))).astype(np.float32)
     con = ttc.Contraction(ma, sa, mb, sb, mc, sc, "f32", "bf16", 1.0, 0.0)
+    con.gemm_variant(variant)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     dC = torch.zeros(int(np.prod(sc, dtype=np.int64)), device="cuda")
     con.execute(dA, dB, dC)
     torch.cuda.synchronize()
     con.check()
+    assert con.gemm_variant() == variant or (variant == 0 and con.gemm_variant() in (1, 2, 3))
     got = dC.cpu().numpy()
     Ar = oracle.bf16_from_f32(A).astype(np.uint32).__lshift__(16).view(np.float32)
     Br = oracle.bf16_from_f32(B).astype(np.uint32).__lshift__(16).view(np.float32)

@@ -128,6 +128,33 @@ def test_fp8_caller_scale_and_degenerate_amax():
     assert scale == 1.0 and not got.any()
 
 
+@pytest.mark.parametrize("scale", [0.01, 0.7, 3.0, 0.25, 1.0e-6])
+def test_fp8_codes_at_and_around_rounding_boundaries(scale):
+    """FP8 codes of quotients at every E4M3 rounding boundary (the midpoints
+    between neighbouring codes, the subnormal ones included) and a few
+    binary32 ulps on either side, for several caller scales: the kernels'
+    reciprocal fast path must fall back to the exact division exactly where
+    it matters, so the codes equal the oracle's bit for bit."""
+    s32 = np.float32(scale)
+    codes = np.arange(0, 0x7F, dtype=np.uint8)                  # finite non-negative codes
+    vals = oracle.e4m3_to_f32(codes).astype(np.float64)
+    mids = (vals[:-1] + vals[1:]) / 2                              # exact in binary32
+    q = np.concatenate([mids, vals]).astype(np.float32)
+    steps = np.arange(-6, 7, dtype=np.int64)
+    qq = (q.view(np.int32)[:, None] + steps[None, :]).astype(np.int32).view(np.float32).ravel()
+    qq = qq[np.isfinite(qq) & (qq >= 0)]
+    a = np.concatenate([qq, -qq]).astype(np.float64) * np.float64(s32)   # alpha * a / scale ~ the quotients
+    A = a.astype(np.float32)
+    n = A.size
+    p = Problem(perm=(1, 0), sizes=(n // 2, 2), dtype_in="f32", dtype_out="e4m3")
+    dev_scale = torch.tensor([float(s32)], dtype=torch.float32, device="cuda")
+    got, sc = H.run_gpu(p, A, np.zeros(n, np.uint8), scale_dev=dev_scale)
+    assert sc == s32
+    want, _ = H.oracle_mirror(p, A, np.zeros(n, np.uint8), scale=float(s32))
+    ok, msg = H.compare_bits(got, want, "e4m3", nan_as_nan=True)
+    assert ok, msg
+
+
 def test_beta_zero_never_reads_B():
     for dt in ("f32", "f64", "bf16"):
         for perm, sizes in [((2, 0, 1), (40, 30, 20)), ((0, 2, 1), (200, 10, 30))]:
