@@ -772,6 +772,8 @@ def run_contraction(args, rank, world):
         row = {"case": c["tag"]}
         for gd in ("f32", "bf16"):
             con = ttc.Contraction(c["modes_a"], sa, c["modes_b"], sb, c["modes_c"], sc, "f32", gd, 1.0, 0.0)
+            if args.autotune > 0:
+                con.autotune(args.autotune, stream)     # the permute plans, before the first execution
             inf = con.info()
             flop = 2.0 * inf["m"] * inf["n"] * inf["k"]
             l0 = ttc.launch_count()
@@ -795,6 +797,8 @@ def run_contraction(args, rank, world):
                        "transpose_share": round(max(ms - ms_gemm, 0.0) / ms, 3),
                        "frac_of_peak": round(tf / world / peak, 3) if peak else None,
                        "gemm": "tcgen05 (this library)" if gd == "bf16" else "cuBLAS SIMT FP32 (pedantic)"}
+            if gd == "bf16":
+                row[gd]["gemm_tile"] = ttc.Contraction.GEMM_VARIANTS.get(con.gemm_variant(), "?")
             if ms_cublas:
                 row[gd]["with_cublas_gemm_ms"] = round(ms_cublas, 4)
                 row[gd]["speedup_vs_cublas_gemm"] = round(ms_cublas / ms, 3)

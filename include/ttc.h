@@ -331,6 +331,11 @@ ttc_status ttc_batch_set_direct_threshold(ttc_batch_t batch, int64_t min_element
  *                           later launches on that device may be corrupt.
  *  ttc_contraction_info     GEMM extents m, n, k and which tensors are
  *                           permuted (bit 0: A, bit 1: B, bit 2: C).
+ *  ttc_contraction_autotune ttc_plan_autotune (max_candidates, stream) on
+ *                           each of the contraction's permute plans; call
+ *                           it before the first execution on a device, or
+ *                           the permutes keep the schedules they started
+ *                           with.  Synchronises `stream`.
  *  ttc_contraction_destroy  release (no work using it may be queued).
  */
 typedef struct ttc_contraction_s* ttc_contraction_t;
@@ -342,6 +347,7 @@ ttc_status ttc_contraction_execute(ttc_contraction_t c, const void* A, const voi
                                    ttc_stream_t stream);
 ttc_status ttc_contraction_check(ttc_contraction_t c);
 ttc_status ttc_contraction_info(ttc_contraction_t c, int64_t* m, int64_t* n, int64_t* k, int* transposes);
+ttc_status ttc_contraction_autotune(ttc_contraction_t c, int max_candidates, ttc_stream_t stream);
 ttc_status ttc_contraction_destroy(ttc_contraction_t c);
 
 /*

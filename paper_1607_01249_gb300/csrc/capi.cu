@@ -291,7 +291,7 @@ ttc_status plan_create(ttc_plan_t* out, int ndim, const int* perm, const int64_t
   p->cands = make_candidates(p->canon, din, dout, p->beta_nonzero() ? 1.0 : 0.0, kPlanCandidates);
   if (p->cands.empty()) return fail(TTC_ERR_INVALID_SIZE, "no schedule fits this problem");
   if (p->canon.n > 0) {
-    build_amax_rows(p->canon, &p->amax_rows);
+    build_amax_rows(p->canon, dtype_size(p->din), &p->amax_rows);
     if (dout == DT_E4M3 && double(p->canon.n) / double(p->canon.s[0]) >= 2147483647.0)
       return fail(TTC_ERR_INVALID_SIZE, "too many rows for the FP8 amax pass");
   }

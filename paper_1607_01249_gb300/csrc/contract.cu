@@ -45,6 +45,10 @@ struct DevState {
   void* ws = nullptr;          // A' | B' | C' workspaces | error word of the tensor-core GEMM
   size_t bytes = 0;
   int* err = nullptr;
+  // the two operand permutes run side by side: B's on `side`, forked from
+  // and joined back into the caller's stream by the two events
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 }  // namespace
@@ -75,6 +79,9 @@ struct ttc_contraction_s {
       if (have) cudaSetDevice(kv.first);
       if (kv.second.handle) cublasDestroy(kv.second.handle);
       if (kv.second.ws) cudaFree(kv.second.ws);
+      if (kv.second.fork) cudaEventDestroy(kv.second.fork);
+      if (kv.second.join) cudaEventDestroy(kv.second.join);
+      if (kv.second.side) cudaStreamDestroy(kv.second.side);
     }
     if (have) cudaSetDevice(cur);
   }
@@ -385,6 +392,19 @@ ttc_status ttc_contraction_execute(ttc_contraction_t c, const void* A, const voi
     }
     ds.bytes = need;
     ds.err = reinterpret_cast<int*>(static_cast<char*>(ds.ws) + need - 256);
+    if (c->opA.plan && c->opB.plan) {
+      // (without them both permutes stay on the caller's stream)
+      if (cudaStreamCreateWithFlags(&ds.side, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ds.fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ds.join, cudaEventDisableTiming) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (ds.side) cudaStreamDestroy(ds.side);
+        if (ds.fork) cudaEventDestroy(ds.fork);
+        if (ds.join) cudaEventDestroy(ds.join);
+        ds.side = nullptr;
+        ds.fork = ds.join = nullptr;
+      }
+    }
     e = cudaMemset(ds.err, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
     if (!c->offs.empty()) {
@@ -403,15 +423,30 @@ ttc_status ttc_contraction_execute(ttc_contraction_t c, const void* A, const voi
   // handles k = 0 as a pure beta scaling)
   const void* ga = A;
   const void* gb = B;
-  if (c->opA.plan && c->K > 0 && c->M > 0) {
+  const bool permA = c->opA.plan && c->K > 0 && c->M > 0;
+  const bool permB = c->opB.plan && c->K > 0 && c->N > 0;
+  // both operands permuted: B's permute on the side stream, so that the two
+  // launches fill each other's ramp and tail
+  const bool side = permA && permB && ds.side;
+  if (side) {
+    e = cudaEventRecord(ds.fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ds.side, ds.fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "fork of the operand permutes");
+  }
+  if (permA) {
     ttc_status st = run_plan(c->opA.plan, A, wa, s);
     if (st != TTC_OK) return st;
     ga = wa;
   }
-  if (c->opB.plan && c->K > 0 && c->N > 0) {
-    ttc_status st = run_plan(c->opB.plan, B, wb, s);
+  if (permB) {
+    ttc_status st = run_plan(c->opB.plan, B, wb, side ? ds.side : s);
     if (st != TTC_OK) return st;
     gb = wb;
+  }
+  if (side) {
+    e = cudaEventRecord(ds.join, ds.side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ds.join, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "join of the operand permutes");
   }
   void* gc = c->planC ? wc : C;
   const double beta_g = c->planC ? 0.0 : c->beta;
@@ -482,6 +517,17 @@ ttc_status ttc_contraction_info(ttc_contraction_t c, int64_t* m, int64_t* n, int
   return TTC_OK;
 }
 
+ttc_status ttc_contraction_autotune(ttc_contraction_t c, int max_candidates, ttc_stream_t stream) {
+  if (!c) return fail(TTC_ERR_INVALID_ARG, "contraction is NULL");
+  std::lock_guard<std::mutex> lk(c->mu);
+  for (ttc_plan_t p : {c->opA.plan, c->opB.plan, c->planC}) {
+    if (!p) continue;
+    const ttc_status st = ttc_plan_autotune(p, max_candidates, stream, nullptr);
+    if (st != TTC_OK) return st;
+  }
+  return TTC_OK;
+}
+
 ttc_status ttc_contraction_check(ttc_contraction_t c) {
   if (!c) return fail(TTC_ERR_INVALID_ARG, "contraction is NULL");
   std::lock_guard<std::mutex> lk(c->mu);
@@ -511,7 +557,7 @@ ttc_status ttc_debug_contraction_use_cublas(ttc_contraction_t c, int use) {
 
 ttc_status ttc_debug_contraction_gemm_variant(ttc_contraction_t c, int variant, int* last_used) {
   if (!c) return fail(TTC_ERR_INVALID_ARG, "contraction is NULL");
-  if (variant > 3) return fail(TTC_ERR_INVALID_ARG, "variant must be -1..3");
+  if (variant > 5) return fail(TTC_ERR_INVALID_ARG, "variant must be -1..5");
   std::lock_guard<std::mutex> lk(c->mu);
   if (variant >= 0) c->gemm_variant = variant;
   if (last_used) *last_used = c->gemm_used;

@@ -60,18 +60,14 @@ extern std::atomic<int64_t> g_launches;
 
 namespace {
 
-constexpr int kGM = 128, kGN = 256, kGK = 64;        // CTA tile; one MMA is 128 x 256 x 16
-constexpr int kStages = 4;
+constexpr int kGM = 128, kGK = 64;                   // rows of A per CTA; K per stage (one MMA takes 16)
 constexpr int kGEpiWarps = 8;                        // two per TMEM lane quarter, one per half of the columns
 constexpr int kGThreads = 64 + 32 * kGEpiWarps;       // producer warp, MMA warp, epilogue warps
-constexpr uint32_t kGTmemCols = 512;                  // two 256-column accumulators
 constexpr int kATile = kGM * kGK * 2;                 // 16 KiB
-constexpr int kBTile = kGN * kGK * 2;                 // 32 KiB
 constexpr int kSBO = 8 * kGK * 2;                     // 1024-byte atoms of 8 rows of 128 bytes
 constexpr uint64_t kSwizzle128B = 2;
 constexpr int kGroupM = 16;                           // tiles visited in groups of 16 row blocks
-// dynamic shared memory: 1024-byte alignment slack, the ring, the barriers
-constexpr int kGSmem = 1024 + kStages * (kATile + kBTile) + 256;
+// (dynamic shared memory: 1024-byte alignment slack, the ring, the barriers)
 constexpr uint32_t kGWaitLimit = 1u << 24;            // polls of one barrier phase before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -129,45 +125,82 @@ __device__ __forceinline__ void tile_of(int t, int ntm, int ntn, int* mb, int* n
   *nb = in / gsz;
 }
 
-// Epilogue of one accumulator (TMEM columns from tacc): warp (q, h) writes
-// rows m_base + 32 q + lane and columns n_base + [h BN/2, (h + 1) BN/2).
+// Epilogue offsets of one tile, read before the accumulator is ready so that
+// their latency hides behind the MMAs: warp (q, h) writes rows m_base + 32 q
+// + lane and the BN/64 column chunks n_base + h BN/2 + 32 c + [0, 32).
+template <int BN>
+struct EpiOffsets {
+  int64_t ro;
+  int64_t co[BN / 64];   // lane's column offset in each chunk
+  bool mok;
+};
+
+template <int BN>
+__device__ __forceinline__ void load_offsets(EpiOffsets<BN>& o, int q, int h, int lane, int m_base, int n_base, int M,
+                                             int N, const int64_t* __restrict__ rowoff,
+                                             const int64_t* __restrict__ coloff) {
+  const int m = m_base + 32 * q + lane;
+  o.mok = m < M;
+  o.ro = o.mok ? __ldg(rowoff + m) : 0;
+#pragma unroll
+  for (int c = 0; c < BN / 64; ++c) {
+    const int n = n_base + (BN / 2) * h + 32 * c + lane;
+    o.co[c] = n < N ? __ldg(coloff + n) : 0;
+  }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+// one 32-column chunk: a store per column, lanes on consecutive rows; with
+// BETA false C is never read
+template <bool BETA>
+__device__ __forceinline__ void store_chunk(const uint32_t (&r)[32], int64_t co, bool mok, int64_t ro, int nleft,
+                                            float* __restrict__ C, float alpha, float beta, bool kzero) {
+#pragma unroll
+  for (int e = 0; e < 32; ++e) {
+    const int64_t coe = __shfl_sync(0xffffffffu, co, e);   // every lane takes part
+    if (mok && e < nleft) {
+      float* cp = C + (ro + coe);
+      const float acc = kzero ? 0.f : __fmul_rn(alpha, __uint_as_float(r[e]));
+      if (BETA)
+        *cp = __fmaf_rn(beta, *cp, acc);
+      else
+        *cp = acc;
+    }
+  }
+}
+
+// Epilogue of one accumulator (TMEM columns from tacc) with the offsets o:
+// the next chunk's tensor-memory load is in flight while a chunk is stored.
 // kzero: K = 0, the accumulator was never written and counts as zero.
 template <int BN>
-__device__ __forceinline__ void store_accumulator(uint32_t tacc, int q, int h, int lane, int m_base, int n_base,
-                                                  int M, int N, float* __restrict__ C,
-                                                  const int64_t* __restrict__ rowoff,
-                                                  const int64_t* __restrict__ coloff, float alpha, float beta,
+__device__ __forceinline__ void store_accumulator(uint32_t tacc, const EpiOffsets<BN>& o, int q, int h,
+                                                  int n_base, int N, float* __restrict__ C, float alpha, float beta,
                                                   bool kzero) {
-  const int m = m_base + 32 * q + lane;
-  const bool mok = m < M;
-  const int64_t ro = mok ? __ldg(rowoff + m) : 0;
-#pragma unroll 1
-  for (int c = 0; c < BN / 64; ++c) {
-    const int col = (BN / 2) * h + 32 * c;
-    const int n0 = n_base + col;
-    const int64_t co = n0 + lane < N ? __ldg(coloff + n0 + lane) : 0;
-    uint32_t r[32];
-    const uint32_t taddr = tacc + (uint32_t(32 * q) << 16) + uint32_t(col);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-          "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  constexpr int NC = BN / 64;
+  uint32_t r[2][32];
+  const uint32_t t0 = tacc + (uint32_t(32 * q) << 16) + uint32_t((BN / 2) * h);
+  tmem_ld32(t0, r[0]);
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int e = 0; e < 32; ++e) {
-      const int64_t coe = __shfl_sync(0xffffffffu, co, e);   // every lane takes part
-      if (mok && n0 + e < N) {
-        float* cp = C + (ro + coe);
-        const float acc = kzero ? 0.f : __fmul_rn(alpha, __uint_as_float(r[e]));
-        *cp = beta != 0.f ? __fmaf_rn(beta, *cp, acc) : acc;
-      }
-    }
+  for (int c = 0; c < NC; ++c) {
+    if (c + 1 < NC) tmem_ld32(t0 + uint32_t(32 * (c + 1)), r[(c + 1) & 1]);
+    const int nleft = N - (n_base + (BN / 2) * h + 32 * c);
+    if (beta != 0.f)
+      store_chunk<true>(r[c & 1], o.co[c], o.mok, o.ro, nleft, C, alpha, beta, kzero);
+    else
+      store_chunk<false>(r[c & 1], o.co[c], o.mok, o.ro, nleft, C, alpha, beta, kzero);
+    if (c + 1 < NC) asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
   }
 }
 
@@ -370,6 +403,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGThreads, 1)
     int ti = 0;
     for (int tile = pair; tile < total; tile += npairs, ++ti) {
       const int b = ti & 1;
+      int mb, nb;
+      tile_of(tile, ntm, ntn, &mb, &nb);
+      EpiOffsets<BN> o;
+      load_offsets<BN>(o, q, h, lane, mb * 2 * kGM + int(rank) * kGM, nb * BN, M, N, rowoff, coloff);
       // (the warp leaves together: the tensor-memory loads below are
       // warp-collective)
       if (!__all_sync(0xffffffffu, bar_wait(afull0 + 8 * b, uint32_t((ti / 2) & 1)))) {
@@ -377,10 +414,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      int mb, nb;
-      tile_of(tile, ntm, ntn, &mb, &nb);
-      store_accumulator<BN>(tmem + uint32_t(BN * b), q, h, lane, mb * 2 * kGM + int(rank) * kGM, nb * BN, M, N, C,
-                            rowoff, coloff, alpha, beta, false);
+      store_accumulator<BN>(tmem + uint32_t(BN * b), o, q, h, nb * BN, N, C, alpha, beta, false);
       // this warp's reads of the accumulator are done: tell the issuer
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -397,10 +431,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P::kCols) : "memory");
 }
 
+// single-CTA tiles 128 x BN (BN 256, 192 or 128): the ring takes what
+// shared memory allows, the two accumulators 2 BN TMEM columns (allocated
+// as the next power of two)
+template <int BN>
+struct SingleCfg {
+  static constexpr int kBTile = BN * kGK * 2;
+  static constexpr int kStages = BN == 256 ? 4 : BN == 192 ? 5 : 6;
+  static constexpr uint32_t kCols = BN == 128 ? 256 : 512;
+  static constexpr uint32_t kAccStride = BN == 128 ? 128 : 256;   // accumulator b at column b x this
+  static constexpr int kSmem = 1024 + kStages * (kATile + kBTile) + 256;
+};
+static_assert(SingleCfg<256>::kSmem <= 232448 && SingleCfg<192>::kSmem <= 232448 &&
+                  SingleCfg<128>::kSmem <= 232448, "shared memory");
+
+template <int BN>
 __global__ void __launch_bounds__(kGThreads, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                      float* __restrict__ C, const int64_t* __restrict__ rowoff, const int64_t* __restrict__ coloff,
                      int M, int N, int K, float alpha, float beta, int* err) {
+  using P = SingleCfg<BN>;
+  constexpr int kStages = P::kStages;
+  constexpr int kBTile = P::kBTile;
   extern __shared__ uint8_t smem_raw[];
   // the ring must start on a 1024-byte boundary (the swizzle atoms)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -413,7 +465,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
   const uint32_t afull0 = full0 + 16 * kStages, aempty0 = afull0 + 16;
   const int t = threadIdx.x, warp = t >> 5;
   const int nk = (K + kGK - 1) / kGK;
-  const int ntm = (M + kGM - 1) / kGM, ntn = (N + kGN - 1) / kGN, total = ntm * ntn;
+  const int ntm = (M + kGM - 1) / kGM, ntn = (N + BN - 1) / BN, total = ntm * ntn;
 
   if (t == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -431,7 +483,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kGTmemCols)
+                 "r"(P::kCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -460,7 +512,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
                        "r"(kATile + kBTile)
                        : "memory");
           tma_load_2d(smem_u32(sA + s * kATile), &mapA, kt * kGK, mb * kGM, full0 + 8 * s);
-          tma_load_2d(smem_u32(sB + s * kBTile), &mapB, kt * kGK, nb * kGN, full0 + 8 * s);
+          tma_load_2d(smem_u32(sB + s * kBTile), &mapB, kt * kGK, nb * BN, full0 + 8 * s);
         }
       }
       if (!ok) {
@@ -483,7 +535,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t acc_tmem = tmem + uint32_t(256 * b);
+        const uint32_t acc_tmem = tmem + P::kAccStride * uint32_t(b);
         for (int kt = 0; kt < nk; ++kt, ++it) {
           const int s = it % kStages;
           if (!bar_wait(full0 + 8 * s, uint32_t((it / kStages) & 1))) {
@@ -500,7 +552,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 "{\n\t.reg .pred p;\n\t"
                 "setp.ne.b32 p, %4, 0;\n\t"
                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_tmem),
-                "l"(da), "l"(db), "r"(mma_idesc(kGM, kGN)), "r"(accumulate)
+                "l"(da), "l"(db), "r"(mma_idesc(kGM, BN)), "r"(accumulate)
                 : "memory");
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -530,6 +582,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
     int ti = 0;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++ti) {
       const int b = ti & 1;
+      int mb, nb;
+      tile_of(tile, ntm, ntn, &mb, &nb);
+      EpiOffsets<BN> o;
+      load_offsets<BN>(o, q, h, lane, mb * kGM, nb * BN, M, N, rowoff, coloff);
       // (the warp leaves together: the tensor-memory loads below are
       // warp-collective)
       if (!__all_sync(0xffffffffu, bar_wait(afull0 + 8 * b, uint32_t((ti / 2) & 1)))) {
@@ -537,10 +593,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      int mb, nb;
-      tile_of(tile, ntm, ntn, &mb, &nb);
-      store_accumulator<kGN>(tmem + uint32_t(256 * b), q, h, lane, mb * kGM, nb * kGN, M, N, C, rowoff, coloff,
-                             alpha, beta, K == 0);
+      store_accumulator<BN>(tmem + P::kAccStride * uint32_t(b), o, q, h, nb * BN, N, C, alpha, beta, K == 0);
       // this warp's TMEM reads are done: hand the accumulator back
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -551,7 +604,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P::kCols) : "memory");
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry points (no link
@@ -589,7 +642,7 @@ bool make_map(CUtensorMap* map, const uint16_t* base, int64_t K, int64_t rows, i
 }
 
 std::mutex g_attr_mu;
-bool g_attr_set[64][3] = {};
+bool g_attr_set[64][6] = {};
 int g_pairs[64] = {};          // co-resident CTA pairs of the pair kernel (0: not yet known)
 
 template <class F>
@@ -610,7 +663,7 @@ int pairs_on(int dev, int sms) {
     std::lock_guard<std::mutex> lk(g_attr_mu);
     if (dev >= 0 && dev < 64 && g_pairs[dev]) return g_pairs[dev];
   }
-  if (set_smem_attr(dev, 1, gemm_bf16_pair_kernel<256>, PairCfg<256>::kSmem) != cudaSuccess) return 0;
+  if (set_smem_attr(dev, GEMM_PAIR_256, gemm_bf16_pair_kernel<256>, PairCfg<256>::kSmem) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(2 * (sms / 2)));
   cfg.blockDim = dim3(kGThreads);
@@ -627,12 +680,41 @@ int pairs_on(int dev, int sms) {
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+int tile_n_of(int v) { return v == GEMM_SINGLE_192 ? 192 : (v == GEMM_SINGLE_128 || v == GEMM_PAIR_128) ? 128 : 256; }
+bool is_pair(int v) { return v == GEMM_PAIR_256 || v == GEMM_PAIR_128; }
+
+template <int BN>
+cudaError_t launch_single(int dev, int which, int sms, const CUtensorMap& ma, const CUtensorMap& mb, float* C,
+                          const int64_t* rowoff, const int64_t* coloff, int64_t M, int64_t N, int64_t K,
+                          float alpha, float beta, int* err, cudaStream_t s) {
+  cudaError_t e = set_smem_attr(dev, which, gemm_bf16_kernel<BN>, SingleCfg<BN>::kSmem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = cdiv(M, kGM) * cdiv(N, BN);
+  const unsigned grid = unsigned(std::min<int64_t>(tiles, sms));
+  gemm_bf16_kernel<BN><<<grid, kGThreads, SingleCfg<BN>::kSmem, s>>>(ma, mb, C, rowoff, coloff, int(M), int(N),
+                                                                     int(K), alpha, beta, err);
+  return cudaSuccess;
+}
+
+template <int BN>
+cudaError_t launch_pair(int dev, int which, int pairs, const CUtensorMap& ma, const CUtensorMap& mb, float* C,
+                        const int64_t* rowoff, const int64_t* coloff, int64_t M, int64_t N, int64_t K, float alpha,
+                        float beta, int* err, cudaStream_t s) {
+  cudaError_t e = set_smem_attr(dev, which, gemm_bf16_pair_kernel<BN>, PairCfg<BN>::kSmem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = cdiv(M, 2 * kGM) * cdiv(N, BN);
+  const unsigned grid = unsigned(2 * std::min<int64_t>(tiles, pairs));
+  gemm_bf16_pair_kernel<BN><<<grid, kGThreads, PairCfg<BN>::kSmem, s>>>(ma, mb, C, rowoff, coloff, int(M), int(N),
+                                                                         int(K), alpha, beta, err);
+  return cudaSuccess;
+}
+
 }  // namespace
 
 const char* gemm_bf16_check(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N, int64_t K) {
   if (M < 1 || N < 1 || K < 0) return "empty GEMM";
   if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return "a GEMM extent exceeds 2^31 - 1";
-  if (((M + kGM - 1) / kGM) * ((N + kGN - 1) / kGN) > INT32_MAX) return "too many tiles";
+  if (cdiv(M, kGM) * cdiv(N, 128) > INT32_MAX) return "too many tiles";
   if (K == 0) return nullptr;   // the operands are not read
   if (lda < K || ldb < K || lda % 8 || ldb % 8) return "row pitches must be >= K and multiples of 8 elements";
   if (reinterpret_cast<uintptr_t>(A) % 16 || reinterpret_cast<uintptr_t>(B) % 16)
@@ -641,14 +723,32 @@ const char* gemm_bf16_check(const void* A, int64_t lda, const void* B, int64_t l
 }
 
 int gemm_bf16_pick(int64_t M, int64_t N, int64_t K, int sms, int pairs) {
-  if (K == 0 || pairs < 1 || sms < 1) return GEMM_SINGLE;
-  // time ~ waves x (output columns per SM per tile) / relative rate, the
-  // rates of each tile shape measured on the 2304^3 and 4096^3 GEMMs
-  const double single = double(cdiv(cdiv(M, kGM) * cdiv(N, kGN), sms)) * 256 / 0.6;
-  const double p256 = double(cdiv(cdiv(M, 2 * kGM) * cdiv(N, 256), pairs)) * 256 / 1.0;
-  const double p128 = double(cdiv(cdiv(M, 2 * kGM) * cdiv(N, 128), pairs)) * 128 / 0.85;
-  if (single < p256 && single < p128) return GEMM_SINGLE;
-  return p128 < p256 ? GEMM_PAIR_128 : GEMM_PAIR_256;
+  if (sms < 1) return GEMM_SINGLE;
+  // time ~ rounds of tiles x K x the shape's cost of one tile per unit of K,
+  // plus the last tile's epilogue, which nothing hides.  Costs relative to
+  // the 128 x 256 tile, measured on 2304^3 and 4096^3 GEMMs: 128 x 192 0.87,
+  // 128 x 128 0.78 (the tensor cores re-read the A slice for every MMA, so
+  // narrower tiles save less than their width), a pair's 256 x 256 0.95 per
+  // SM, a pair's 256 x 128 1.3; the epilogue about 500 units of K for 256
+  // columns.
+  const double kk = double(std::max<int64_t>(K, 1));
+  int best = GEMM_SINGLE;
+  double best_t = 1e300;
+  const int cand[5] = {GEMM_SINGLE, GEMM_SINGLE_192, GEMM_SINGLE_128, GEMM_PAIR_256, GEMM_PAIR_128};
+  const double cost[5] = {1.0, 0.87, 0.78, 0.95, 1.3};
+  for (int i = 0; i < 5; ++i) {
+    const int v = cand[i];
+    if (is_pair(v) && (K == 0 || pairs < 1)) continue;
+    const int bn = tile_n_of(v);
+    const int64_t tiles = is_pair(v) ? cdiv(M, 2 * kGM) * cdiv(N, bn) : cdiv(M, kGM) * cdiv(N, bn);
+    const int64_t rounds = cdiv(tiles, is_pair(v) ? pairs : sms);
+    const double t = double(rounds) * kk * cost[i] + 500.0 * bn / 256.0;
+    if (t < best_t * 0.999) {
+      best_t = t;
+      best = v;
+    }
+  }
+  return best;
 }
 
 cudaError_t gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, const int64_t* rowoff,
@@ -662,38 +762,35 @@ cudaError_t gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, fl
   if (e != cudaSuccess) return e;
   const int pairs = K > 0 ? pairs_on(dev, sms) : 0;
   int v = variant;
-  if (v == GEMM_AUTO || (v != GEMM_SINGLE && (K == 0 || pairs < 1))) v = gemm_bf16_pick(M, N, K, sms, pairs);
+  if (v < GEMM_AUTO || v > GEMM_SINGLE_128) return cudaErrorInvalidValue;
+  if (v == GEMM_AUTO) v = gemm_bf16_pick(M, N, K, sms, pairs);
+  if (is_pair(v) && (K == 0 || pairs < 1)) v = GEMM_SINGLE;
   if (used) *used = v;
-  const int bn = v == GEMM_PAIR_128 ? 128 : 256;
+  const int bn = tile_n_of(v);
   CUtensorMap ma, mb;
   std::memset(&ma, 0, sizeof(ma));
   std::memset(&mb, 0, sizeof(mb));
   // (K = 0: no copies are issued and the maps stay unused)
   if (K > 0 && (!make_map(&ma, static_cast<const uint16_t*>(A), K, M, lda, kGM) ||
-                !make_map(&mb, static_cast<const uint16_t*>(B), K, N, ldb, v == GEMM_SINGLE ? kGN : bn / 2)))
+                !make_map(&mb, static_cast<const uint16_t*>(B), K, N, ldb, is_pair(v) ? bn / 2 : bn)))
     return cudaErrorInvalidValue;
-  if (v == GEMM_SINGLE) {
-    e = set_smem_attr(dev, 0, gemm_bf16_kernel, kGSmem);
-    if (e != cudaSuccess) return e;
-    const int64_t tiles = cdiv(M, kGM) * cdiv(N, kGN);
-    const unsigned grid = unsigned(std::min<int64_t>(tiles, sms));
-    gemm_bf16_kernel<<<grid, kGThreads, kGSmem, s>>>(ma, mb, C, rowoff, coloff, int(M), int(N), int(K), alpha,
-                                                     beta, err);
-  } else {
-    const int64_t tiles = cdiv(M, 2 * kGM) * cdiv(N, bn);
-    const unsigned grid = unsigned(2 * std::min<int64_t>(tiles, pairs));
-    if (bn == 256) {
-      e = set_smem_attr(dev, 1, gemm_bf16_pair_kernel<256>, PairCfg<256>::kSmem);
-      if (e != cudaSuccess) return e;
-      gemm_bf16_pair_kernel<256><<<grid, kGThreads, PairCfg<256>::kSmem, s>>>(ma, mb, C, rowoff, coloff, int(M),
-                                                                               int(N), int(K), alpha, beta, err);
-    } else {
-      e = set_smem_attr(dev, 2, gemm_bf16_pair_kernel<128>, PairCfg<128>::kSmem);
-      if (e != cudaSuccess) return e;
-      gemm_bf16_pair_kernel<128><<<grid, kGThreads, PairCfg<128>::kSmem, s>>>(ma, mb, C, rowoff, coloff, int(M),
-                                                                               int(N), int(K), alpha, beta, err);
-    }
+  switch (v) {
+    case GEMM_SINGLE_192:
+      e = launch_single<192>(dev, v, sms, ma, mb, C, rowoff, coloff, M, N, K, alpha, beta, err, s);
+      break;
+    case GEMM_SINGLE_128:
+      e = launch_single<128>(dev, v, sms, ma, mb, C, rowoff, coloff, M, N, K, alpha, beta, err, s);
+      break;
+    case GEMM_PAIR_256:
+      e = launch_pair<256>(dev, v, pairs, ma, mb, C, rowoff, coloff, M, N, K, alpha, beta, err, s);
+      break;
+    case GEMM_PAIR_128:
+      e = launch_pair<128>(dev, v, pairs, ma, mb, C, rowoff, coloff, M, N, K, alpha, beta, err, s);
+      break;
+    default:
+      e = launch_single<256>(dev, v, sms, ma, mb, C, rowoff, coloff, M, N, K, alpha, beta, err, s);
   }
+  if (e != cudaSuccess) return e;
   ++g_launches;
   return cudaGetLastError();
 }

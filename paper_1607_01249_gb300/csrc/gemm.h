@@ -13,15 +13,22 @@ namespace ttc {
 const char* gemm_bf16_check(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
                             int64_t K);
 
-// Tile shapes of gemm_bf16: GEMM_SINGLE -- one CTA per 128 x 256 output
-// tile; GEMM_PAIR_256 / GEMM_PAIR_128 -- a cluster of two CTAs per 256 x 256
-// or 256 x 128 tile (tensor-core MMAs spanning both SMs); GEMM_AUTO picks by
-// gemm_bf16_pick.
-enum GemmVariant : int { GEMM_AUTO = 0, GEMM_SINGLE = 1, GEMM_PAIR_256 = 2, GEMM_PAIR_128 = 3 };
+// Tile shapes of gemm_bf16: GEMM_SINGLE / _192 / _128 -- one CTA per 128 x
+// 256, 128 x 192 or 128 x 128 output tile; GEMM_PAIR_256 / GEMM_PAIR_128 --
+// a cluster of two CTAs per 256 x 256 or 256 x 128 tile (tensor-core MMAs
+// spanning both SMs); GEMM_AUTO picks by gemm_bf16_pick.
+enum GemmVariant : int {
+  GEMM_AUTO = 0,
+  GEMM_SINGLE = 1,
+  GEMM_PAIR_256 = 2,
+  GEMM_PAIR_128 = 3,
+  GEMM_SINGLE_192 = 4,
+  GEMM_SINGLE_128 = 5
+};
 
 // The tile shape GEMM_AUTO runs for M x N x K on `sms` SMs of which `pairs`
-// CTA pairs are co-resident: the one with the fewest tile rounds weighted by
-// the work per round and the shape's measured rate.
+// CTA pairs are co-resident: the least rounds of tiles weighted by each
+// shape's measured cost per tile, plus the exposed last epilogue.
 int gemm_bf16_pick(int64_t M, int64_t N, int64_t K, int sms, int pairs);
 
 // C[rowoff[m] + coloff[n]] (FP32) = alpha * sum_k A[m, k] B[n, k] + beta *

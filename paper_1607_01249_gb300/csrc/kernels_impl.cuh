@@ -504,16 +504,48 @@ __global__ void __launch_bounds__(kThreads) copy_kernel(const store_t<DIN>* __re
 
 // ---------------------------------------------------------------- amax ----
 
-// A warp takes kAmaxItems consecutive row chunks of A's sub-tensor at a time
-// (their coordinates decomposed once per chunk, not per element) and keeps
-// kAmaxItems x kAmaxUnroll loads per lane in flight, so that short rows (a
-// packing panel's 48- or 256-element columns) still stream.  One CTA also
+// A warp takes kAmaxItems groups of consecutive row chunks of A's
+// sub-tensor at a time (their coordinates decomposed once per chunk, not per
+// element; a group is 32 / L chunks for chunks that L < 32 lanes cover) and
+// keeps kAmaxItems x kAmaxUnroll loads per lane in flight, so that short rows
+// (a packing panel's 48- or 256-element columns) still stream.  One CTA also
 // clears `clear_bits`, the word the next execution of the plan accumulates
 // into, so no separate reset is launched (two words alternate per plan).
 constexpr int kAmaxItems = 4;
 constexpr int kAmaxUnroll = 2;
 
-template <int DIN>
+// lanes of a warp per chunk of `chunk` elements read V at a time: the least
+// power of two that covers its loads, at most 32
+TTC_HD int amax_lanes_per_item(int64_t chunk, int V) {
+  const int64_t loads = (chunk + V - 1) / V;
+  int L = 32;
+  while (L > 1 && L / 2 >= loads) L >>= 1;
+  return L;
+}
+
+// V > 1: every chunk starts and ends on a 16-byte boundary (RowParams::vec)
+// and a lane loads V consecutive elements at a time.
+template <int DIN, int V>
+__device__ __forceinline__ void amax_load(const store_t<DIN>* __restrict__ A, int64_t i, float alpha_f, float (&v)[V]) {
+  if constexpr (V == 1) {
+    v[0] = fabsf(__fmul_rn(alpha_f, float(to_stage<DIN>(ldg_elem<DIN>(A + i)))));
+  } else {
+    static_assert(V * sizeof(store_t<DIN>) == 16, "16-byte loads");
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(A + i));
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      store_t<DIN> x;
+      if constexpr (V == 4)
+        x = __uint_as_float(u[k]);
+      else
+        x = store_t<DIN>(uint16_t(u[k / 2] >> (16 * (k & 1))));
+      v[k] = fabsf(__fmul_rn(alpha_f, float(to_stage<DIN>(x))));
+    }
+  }
+}
+
+template <int DIN, int V>
 __global__ void __launch_bounds__(kThreads) amax_kernel(const store_t<DIN>* __restrict__ A,
                                                         const __grid_constant__ RowParams p, float alpha_f,
                                                         uint32_t* amax_bits, uint32_t* clear_bits) {
@@ -521,31 +553,38 @@ __global__ void __launch_bounds__(kThreads) amax_kernel(const store_t<DIN>* __re
   if (blockIdx.x == 0 && t == 0 && clear_bits) *clear_bits = 0u;
   const uint32_t warp = (blockIdx.x * kThreads + t) >> 5;
   const uint32_t nwarps = (gridDim.x * kThreads) >> 5;
+  // short chunks share a warp: L lanes per chunk (a power of two covering
+  // its vectors), 32 / L chunks side by side
+  const int L = amax_lanes_per_item(p.chunk, V);
+  const int per = 32 / L, sub = lane / L, li = lane % L;
+  const uint64_t step = uint64_t(kAmaxItems) * per;
   float m = 0.f;
-  for (uint64_t i0 = uint64_t(warp) * kAmaxItems; i0 < p.nitems; i0 += uint64_t(nwarps) * kAmaxItems) {
+  for (uint64_t i0 = uint64_t(warp) * step; i0 < p.nitems; i0 += uint64_t(nwarps) * step) {
     RowCoord rc[kAmaxItems];
 #pragma unroll
     for (int j = 0; j < kAmaxItems; ++j) {
-      rc[j] = row_coord(uint32_t(i0 + j < p.nitems ? i0 + j : i0), p);
-      if (i0 + j >= p.nitems) rc[j].end = rc[j].start;     // no such chunk
+      const uint64_t it = i0 + uint64_t(j) * per + sub;
+      rc[j] = row_coord(uint32_t(it < p.nitems ? it : i0), p);
+      if (it >= p.nitems) rc[j].end = rc[j].start;     // no such chunk
     }
-    for (int64_t x0 = lane; x0 < p.chunk; x0 += 32 * kAmaxUnroll) {
-      float v[kAmaxItems][kAmaxUnroll];
+    for (int64_t x0 = int64_t(li) * V; x0 < p.chunk; x0 += int64_t(L) * kAmaxUnroll * V) {
+      float v[kAmaxItems][kAmaxUnroll][V];
       bool ok[kAmaxItems][kAmaxUnroll];
 #pragma unroll
       for (int j = 0; j < kAmaxItems; ++j)
 #pragma unroll
         for (int u = 0; u < kAmaxUnroll; ++u) {
-          const int64_t x = rc[j].start + x0 + 32 * u;
-          ok[j][u] = x < rc[j].end;
-          v[j][u] = fabsf(__fmul_rn(alpha_f, float(to_stage<DIN>(ldg_elem<DIN>(A + (ok[j][u] ? rc[j].offA + x * p.sa0
-                                                                                                 : int64_t(0)))))));
+          const int64_t x = rc[j].start + x0 + int64_t(L) * V * u;
+          ok[j][u] = x < rc[j].end;     // (V > 1: whole vectors only)
+          amax_load<DIN, V>(A, ok[j][u] ? rc[j].offA + x * p.sa0 : int64_t(0), alpha_f, v[j][u]);
         }
 #pragma unroll
       for (int j = 0; j < kAmaxItems; ++j)
 #pragma unroll
         for (int u = 0; u < kAmaxUnroll; ++u)
-          if (ok[j][u] && v[j][u] > m) m = v[j][u];     // NaN compares false: ignored
+#pragma unroll
+          for (int k = 0; k < V; ++k)
+            if (ok[j][u] && v[j][u][k] > m) m = v[j][u][k];     // NaN compares false: ignored
     }
   }
   for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -720,18 +759,28 @@ cudaError_t launch_rowsp_pair(int j, const void* A, void* B, const TileParams& p
   return cudaErrorInvalidValue;
 }
 
+template <int DIN, int V>
+cudaError_t launch_amax_v(const void* A, const RowParams& p, float alpha_f, uint32_t* amax_bits,
+                          uint32_t* clear_bits, cudaStream_t s) {
+  const void* fn = reinterpret_cast<const void*>(&amax_kernel<DIN, V>);
+  int grid = 0;
+  const int64_t step = int64_t(kAmaxItems) * (32 / amax_lanes_per_item(p.chunk, V));
+  const int64_t groups = (int64_t(p.nitems) + step - 1) / step;
+  cudaError_t err = grid_for(fn, 0, (groups + kThreads / 32 - 1) / (kThreads / 32), &grid);
+  if (err != cudaSuccess) return err;
+  amax_kernel<DIN, V><<<grid, kThreads, 0, s>>>(static_cast<const store_t<DIN>*>(A), p, alpha_f, amax_bits,
+                                                clear_bits);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
 template <int DIN>
 cudaError_t launch_amax_t(const void* A, const RowParams& p, float alpha_f, uint32_t* amax_bits,
                           uint32_t* clear_bits, cudaStream_t s) {
-  const void* fn = reinterpret_cast<const void*>(&amax_kernel<DIN>);
-  int grid = 0;
-  const int64_t groups = (int64_t(p.nitems) + kAmaxItems - 1) / kAmaxItems;
-  cudaError_t err = grid_for(fn, 0, (groups + kThreads / 32 - 1) / (kThreads / 32), &grid);
-  if (err != cudaSuccess) return err;
-  amax_kernel<DIN><<<grid, kThreads, 0, s>>>(static_cast<const store_t<DIN>*>(A), p, alpha_f, amax_bits,
-                                             clear_bits);
-  ++g_launches;
-  return cudaGetLastError();
+  constexpr int V = 16 / int(sizeof(store_t<DIN>));
+  if (p.vec == V && reinterpret_cast<uintptr_t>(A) % 16 == 0)
+    return launch_amax_v<DIN, V>(A, p, alpha_f, amax_bits, clear_bits, s);
+  return launch_amax_v<DIN, 1>(A, p, alpha_f, amax_bits, clear_bits, s);
 }
 
 }  // namespace ttc

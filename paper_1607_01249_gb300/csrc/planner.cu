@@ -842,7 +842,7 @@ void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* 
                 p->P * LB * stage_bytes(din);
 }
 
-void build_amax_rows(const Canon& c, RowParams* p) {
+void build_amax_rows(const Canon& c, int elem_bytes, RowParams* p) {
   // the FP8 pre-pass reads A only: neighbouring indices that are dense in A
   // merge whatever B's order (longer rows to stream)
   Canon a = c;
@@ -858,9 +858,15 @@ void build_amax_rows(const Canon& c, RowParams* p) {
     }
   }
   a.N = n;
-  // chunks of at most 1024 elements: a warp streams a few chunks at a time,
+  // chunks of at most 256 elements: a warp streams a few chunks at a time,
   // and long rows still give every SM many warps' work
-  build_row_params(a, a.s[0] <= 1024 ? a.s[0] : 1024, p);
+  build_row_params(a, a.s[0] <= 256 ? a.s[0] : 256, p);
+  // 16-byte loads where every chunk starts and ends on a 16-byte boundary
+  // (relative to A's base; the launch checks the base itself)
+  const int v = elem_bytes > 0 && elem_bytes < 16 ? 16 / elem_bytes : 1;
+  bool ok = v > 1 && p->sa0 == 1 && p->len % v == 0 && p->chunk % v == 0;
+  for (int i = 0; ok && i < p->nrd; ++i) ok = p->stA[i] % v == 0;
+  p->vec = ok ? v : 1;
 }
 
 void build_row_params(const Canon& c, int64_t chunk, RowParams* p) {
@@ -881,6 +887,7 @@ void build_row_params(const Canon& c, int64_t chunk, RowParams* p) {
     rows *= uint64_t(c.s[k]);
   }
   p->nitems = uint32_t(rows * uint64_t(nch));
+  p->vec = 1;
 }
 
 namespace {

@@ -68,8 +68,9 @@ void build_tile_params(const Canon& c, const Candidate& k, int din, TileParams* 
                        std::vector<int32_t>* tabA, std::vector<int32_t>* tabB, int* smem_bytes);
 void build_row_params(const Canon& c, int64_t chunk, RowParams* p);
 // Rows of the FP8 amax pre-pass over A's (sub-)tensor: A-dense neighbours
-// merged regardless of B (only A offsets are meaningful).
-void build_amax_rows(const Canon& c, RowParams* p);
+// merged regardless of B (only A offsets are meaningful), with the width
+// of its 16-byte loads (elem_bytes: the size of an A element).
+void build_amax_rows(const Canon& c, int elem_bytes, RowParams* p);
 
 // Slot tables of a tile for tile_slots_kernel (layout: TileParams::slots);
 // `tabA`/`tabB` are the host cross tables of the same parameters.  Returns

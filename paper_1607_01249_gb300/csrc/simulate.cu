@@ -312,6 +312,8 @@ struct Checker {
     int64_t visits = 0;
     for (uint32_t item = 0; item < rp.nitems; ++item) {
       const RowCoord rc = row_coord(item, rp);
+      if (rp.vec > 1 && (rp.sa0 != 1 || rc.offA % rp.vec || rc.start % rp.vec || rc.end % rp.vec))
+        return fail("amax: 16-byte load not aligned", item, rp.vec);
       for (int64_t x = rc.start; x < rc.end; ++x) {
         const int64_t a = rc.offA + x * rp.sa0;
         if (a < 0 || a >= spanA) return fail("amax: A access out of range", a, spanA);

@@ -182,6 +182,7 @@ struct RowParams {
   int64_t len;         // run length (elements)
   int64_t chunk;       // chunk length (elements)
   int64_t sa0, sb0;    // run strides
+  int vec;             // FP8 amax pre-pass: elements per 16-byte load (1: one element per load)
   Epilogue epi;
 };
 

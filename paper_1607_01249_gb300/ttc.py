@@ -91,6 +91,7 @@ SIGNATURES = {
     "ttc_contraction_execute": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "ttc_contraction_check": (ctypes.c_int, [_vp]),
     "ttc_contraction_info": (ctypes.c_int, [_vp, _i64p, _i64p, _i64p, ctypes.POINTER(ctypes.c_int)]),
+    "ttc_contraction_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "ttc_contraction_destroy": (ctypes.c_int, [_vp]),
     "ttc_packed_gemm_plan": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i64p,
                                             _i64p, ctypes.c_int, ctypes.c_int64, ctypes.c_double]),
@@ -328,12 +329,19 @@ class Contraction:
         _check(lib().ttc_debug_contraction_use_cublas(self._h, 1 if use else 0))
         return self
 
-    GEMM_VARIANTS = {0: "auto", 1: "single 128x256", 2: "pair 256x256", 3: "pair 256x128"}
+    def autotune(self, max_candidates=8, stream=None):
+        """Autotune the contraction's permute plans (before its first
+        execution on the device)."""
+        _check(lib().ttc_contraction_autotune(self._h, int(max_candidates), _stream(stream)))
+        return self
+
+    GEMM_VARIANTS = {0: "auto", 1: "single 128x256", 2: "pair 256x256", 3: "pair 256x128", 4: "single 128x192",
+                     5: "single 128x128"}
 
     def gemm_variant(self, variant: int = -1) -> int:
-        """Testing hook: force the BF16 GEMM's tile shape (0 pick, 1 one CTA
-        per 128 x 256 tile, 2 / 3 a CTA pair per 256 x 256 / 256 x 128 tile;
-        -1 keeps it); returns the shape the last execution ran."""
+        """Testing hook: force the BF16 GEMM's tile shape (GEMM_VARIANTS; 0
+        lets the library pick, -1 keeps the setting); returns the shape the
+        last execution ran."""
         used = ctypes.c_int()
         _check(lib().ttc_debug_contraction_gemm_variant(self._h, int(variant), ctypes.byref(used)))
         return used.value
