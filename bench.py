@@ -581,7 +581,7 @@ def run_batch(args, rank, world):
         "config": {"workload": f"batch of {len(probs)} transposes, N 2..5, 2^10..2^22 elements log-uniform, "
                                "f32/bf16 50/50, alpha=1, beta in {0,0.5}; one CUDA-graph launch per step",
                    "tiles": info["tiles"],
-                   "direct_problems": sum(p.n >= direct_min for p in probs),
+                   "direct_problems": sum(p.n >= direct_min for p in probs) if direct_min > 0 else 0,
                    "direct_threshold_elements": direct_min, "algorithmic_bytes_per_step": bytes_step,
                    "parallelism": f"replicas x{world}"},
         "batch": {"transposes_per_s": round(job_rate(len(probs), world, ms_b), 1), "ms": round(ms_b, 4),
@@ -592,7 +592,8 @@ def run_batch(args, rank, world):
         "speedup_vs_per_call": round(ms_c / ms_b, 3),
         "roofline": {"bound": "hbm", "achieved": round(bytes_step / (ms_b * 1e-3) / 1e9, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(bytes_step / (ms_b * 1e-3) / 1e9 / peak, 4),
-                     "kernel": "one graph launch: batch_kernel + the side stream's single-plan kernels",
+                     "kernel": "one graph launch: the batch_kernel launches (one per class)"
+                               + (" + the side stream's single-plan kernels" if direct_min > 0 else ""),
                      "traffic": (ncu_traffic("step", "batch") or {}).get("bytes_per_launch")
                      if args.batch_count == 4096 and direct_min == ttc.Batch.DIRECT_MIN_DEFAULT else None},
         "gpu_launches": launches_b * args.steps,

@@ -240,12 +240,13 @@ int64_t ttc_launch_count(void);
 
 /*
  * Batches: many independent permute-scale-adds (Eq. 1) -- different
- * permutations, sizes, dtypes, alpha/beta -- in ONE persistent kernel launch.
- * Every problem is cut into tiles (the paper's macro-tiles, section 2.2);
- * resident CTAs claim tiles through an atomic counter, so uneven problems
- * balance across the GPU, and each tile is processed with its own problem's
- * parameters.  This is the analogue of scheduling the macro-tiles of section
- * 2.2 across threadblocks, extended across problems.
+ * permutations, sizes, dtypes, alpha/beta -- launched together.  Every
+ * problem is cut into tiles (the paper's macro-tiles, section 2.2); the
+ * problems are grouped by class (dtype pair, beta zero or not, tile body) and
+ * each class is one kernel launch with one CTA per tile of all its problems,
+ * each tile processed with its own problem's parameters (a per-tile record
+ * names the problem).  This is the scheduling of the macro-tiles of section
+ * 2.2 across thread blocks, extended across problems.
  *
  *  ttc_batch_create   new empty batch (host only).
  *  ttc_batch_add      append (plan, A, B): the plan must stay alive and
@@ -253,10 +254,10 @@ int64_t ttc_launch_count(void);
  *                     pointers as for ttc_execute (checked the same way).
  *                     FP8 plans are rejected (TTC_ERR_UNSUPPORTED_DTYPE): their
  *                     scale needs a pre-pass of its own; so are complex plans
- *                     (the persistent kernel's epilogue covers the real pairs).
- *  ttc_batch_execute  enqueue the batch on `stream`: one counter reset and one
- *                     persistent kernel for the problems below the direct
- *                     threshold, and beside it, on a stream of the batch
+ *                     (the batch kernels' epilogue covers the real pairs).
+ *  ttc_batch_execute  enqueue the batch on `stream`: one launch per class
+ *                     for the problems below the direct threshold, and
+ *                     beside them, on a stream of the batch
  *                     forked from and joined back into `stream`, one
  *                     single-plan launch per problem at or above it.  The
  *                     first execution after an add builds and uploads the
@@ -267,8 +268,8 @@ int64_t ttc_launch_count(void);
  *                     first call (after the descriptors are uploaded), then
  *                     replayed with one cudaGraphLaunch per call.
  *  ttc_batch_set_direct_threshold  problems of at least min_elements
- *                     elements run as their own kernels (default 2^21); 0 or
- *                     less puts every problem in the persistent kernel.
+ *                     elements run as their own kernels; 0 or less (the
+ *                     default) puts every problem in the batch kernels.
  *  ttc_batch_destroy  release the batch (not the plans); no work using it may
  *                     be queued.
  *  ttc_batch_info     number of problems and of tiles of the batch.
@@ -400,7 +401,7 @@ ttc_status ttc_packed_gemm_destroy(ttc_packed_gemm_t g);
  * order while the bytes of admitted, unfinished requests (A's and B's
  * sub-tensor spans) stay within `budget_bytes`, groups what it admitted into
  * an epoch and launches it on a stream: consecutive requests of at most
- * `small_tiles` tiles go together into one batched persistent launch (see
+ * `small_tiles` tiles go together into one batched launch per class (see
  * ttc_batch_*), other requests (and every FP8 or complex request) get their
  * own launch.  Epochs on different
  * streams run concurrently, so requests that arrive while others are on the

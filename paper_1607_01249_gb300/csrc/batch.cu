@@ -334,9 +334,11 @@ struct ttc_batch_s {
   int smem = 0;
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
-  // problems of at least direct_min elements run as their own single-plan
-  // kernels on a side stream, beside the batch kernel
-  int64_t direct_min = int64_t(1) << 21;
+  // problems of at least direct_min elements (if > 0) run as their own
+  // single-plan kernels on a side stream, beside the batch kernels; off by
+  // default: with one CTA per tile the batch kernels move even the largest
+  // problems of a mixed batch faster than a stream of single-plan launches
+  int64_t direct_min = 0;
   std::vector<Item> direct;
   std::vector<BatchRange> ranges;   // the class launches of the batch kernel
   cudaStream_t side = nullptr;

@@ -6,8 +6,8 @@
 // launches it on a lane (a stream with a ring of descriptor slots in pinned
 // host and device memory); a completion thread queries the oldest epoch of
 // each lane (a stream completes its work in order), stamps latencies and
-// releases budget.  Several small requests of an epoch share one batched
-// persistent launch (batch_impl.h); a large request, or a small one that
+// releases budget.  Several small requests of an epoch share the batched
+// launches, one per class (batch_impl.h); a large request, or a small one that
 // arrived alone, gets the single-plan kernel.  Lanes run concurrently, so new
 // requests overlap on the device with work in flight, and the least-loaded
 // lane takes the next epoch, so small requests need not queue behind a large

@@ -412,8 +412,11 @@ class PackedGemm:
 
 
 class Batch:
-    """Many permute-scale-adds in one persistent kernel launch (ttc_batch_*).
-    The batch keeps references to its plans so that they outlive it."""
+    """Many permute-scale-adds launched together (ttc_batch_*): one kernel
+    launch per class of problems (dtype pair, beta, body), one CTA per tile,
+    with the large problems as their own kernels on a side stream; all of it
+    one CUDA graph with graph_launch.  The batch keeps references to its
+    plans so that they outlive it."""
 
     def __init__(self):
         h = ctypes.c_void_p()
@@ -437,11 +440,11 @@ class Batch:
         _check(lib().ttc_batch_info(self._h, ctypes.byref(p), ctypes.byref(t)))
         return {"problems": p.value, "tiles": t.value}
 
-    DIRECT_MIN_DEFAULT = 1 << 21
+    DIRECT_MIN_DEFAULT = 0     # off
 
     def set_direct_threshold(self, min_elements: int):
         """Problems of at least this many elements run as their own kernels
-        beside the persistent one (<= 0: none; DIRECT_MIN_DEFAULT unless set)."""
+        beside the batch kernels (<= 0: none, the default)."""
         _check(lib().ttc_batch_set_direct_threshold(self._h, int(min_elements)))
         return self
 
