@@ -175,7 +175,8 @@ typedef enum {
     TTC_VARIANT_EMPTY = 0,    /* nothing to do */
     TTC_VARIANT_COPY = 1,     /* perm keeps index 0: long runs streamed directly */
     TTC_VARIANT_TILE = 2,     /* tile staged in shared memory between A's and B's runs */
-    TTC_VARIANT_ROWCOPY = 3   /* perm keeps index 0 with short runs: multi-row blocks, no staging */
+    TTC_VARIANT_ROWCOPY = 3,  /* perm keeps index 0 with short runs: multi-row blocks, no staging */
+    TTC_VARIANT_TMA_TILE = 4  /* two indices swapped: tiles copied into shared memory by the TMA */
 } ttc_variant;
 
 typedef struct {

@@ -17,6 +17,7 @@
 #include "launch.h"
 #include "plan_impl.h"
 #include "planner.h"
+#include "tma2d.h"
 
 using namespace ttc;
 
@@ -216,6 +217,9 @@ ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s) {
     if (vec > 1 && rp.chunk % vec) vec = 1;
     e = launch_copy(p->din, p->dout, vec, A, B, rp, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
+  } else if (k.variant == VAR_TMA) {
+    e = launch_tma2d(p->din, p->dout, A, B, tma2d_geom(p->canon, p->din), epi, s);
+    if (e != cudaSuccess) return cuda_fail(e, "TMA tile kernel launch");
   }
   return TTC_OK;
 }
@@ -382,7 +386,7 @@ ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info) {
   const int sa = dtype_size(plan->din), sb = dtype_size(plan->dout);
   info->algorithmic_bytes = c.n * (sa + (plan->beta_nonzero() ? 2 * sb : sb));
   const Candidate& k = plan->cands[plan->sel];
-  info->variant = k.rows ? TTC_VARIANT_ROWCOPY : k.variant;
+  info->variant = k.rows ? TTC_VARIANT_ROWCOPY : k.variant == VAR_TMA ? TTC_VARIANT_TMA_TILE : k.variant;
   info->candidate = plan->sel;
   info->ncandidates = int(plan->cands.size());
   if (k.variant == VAR_TILE) {
@@ -407,6 +411,13 @@ ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info) {
     info->tile_a = info->tile_b = 1;
     info->ntiles = rp.nitems;
     info->vec_in = info->vec_out = k.vec;
+  } else if (k.variant == VAR_TMA) {
+    const Tma2dGeom g = tma2d_geom(c, plan->din);
+    info->tile_c = 1;
+    info->tile_a = g.bx;
+    info->tile_b = 32 * kTmaBoxes;
+    info->ntiles = g.tiles;
+    info->vec_in = info->vec_out = 1;
   }
   return TTC_OK;
 }

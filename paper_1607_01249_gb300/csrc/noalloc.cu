@@ -13,6 +13,7 @@
 #include "launch.h"
 #include "plan_impl.h"
 #include "planner.h"
+#include "tma2d.h"
 
 using namespace ttc;
 
@@ -182,6 +183,10 @@ extern "C" ttc_status ttc_execute_noalloc(ttc_plan_t plan, const void* A, void* 
     if (vec > 1 && rp.chunk % vec) vec = 1;
     e = launch_copy(plan->din, plan->dout, vec, A, B, rp, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
+  } else if (k.variant == VAR_TMA) {
+    // (the tensor map travels as a kernel parameter: no scratch)
+    e = launch_tma2d(plan->din, plan->dout, A, B, tma2d_geom(c, plan->din), epi, s);
+    if (e != cudaSuccess) return cuda_fail(e, "TMA tile kernel launch");
   }
   return TTC_OK;
 }

@@ -27,6 +27,7 @@
 #include "kernels.cuh"
 #include "launch.h"
 #include "planner.h"
+#include "tma2d.h"
 
 namespace ttc {
 
@@ -61,6 +62,8 @@ std::string Candidate::describe() const {
   if (variant == VAR_EMPTY) return "empty";
   if (variant == VAR_COPY) {
     o << "copy chunk=" << chunk << " vec=" << vec;
+  } else if (variant == VAR_TMA) {
+    o << "tma2d box=" << ta << "x32x" << kTmaBoxes;
   } else {
     o << "tile c=" << has_c << " ga=[";
     for (size_t i = 0; i < ga.size(); ++i) o << (i ? "," : "") << ga[i];
@@ -722,6 +725,23 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
   std::stable_sort(out.begin(), out.end(),
                    [](const Candidate& a, const Candidate& b) { return a.est_s < b.est_s; });
   if (int(out.size()) > max_keep) out.resize(max_keep);
+  // the TMA-staged tile of a two-index transpose, where its strides allow a
+  // tensor map: always kept among the candidates (the autotuner decides);
+  // modelled at 0.96 of the copy bandwidth (measured 1-6 % above tile2 on
+  // aligned 2D FP32 transposes)
+  if (!flat && tma2d_eligible(c, din) && max_keep > 0) {
+    Candidate k;
+    k.variant = VAR_TMA;
+    k.ta = 128 / esA;
+    k.tb = 32 * kTmaBoxes;
+    k.seg_a = double(k.ta);
+    k.seg_b = 32.0;
+    k.est_s = n * double(esA + esB + (bnz ? esB : 0)) / (0.96 * kHbmBytesPerS) + 2e-6;
+    if (int(out.size()) >= max_keep) out.pop_back();
+    out.push_back(k);
+    std::stable_sort(out.begin(), out.end(),
+                     [](const Candidate& a, const Candidate& b) { return a.est_s < b.est_s; });
+  }
   return out;
 }
 

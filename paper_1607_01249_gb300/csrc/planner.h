@@ -22,7 +22,7 @@ struct Canon {
   int64_t spanB = 0;
 };
 
-enum Variant : int { VAR_EMPTY = 0, VAR_COPY = 1, VAR_TILE = 2 };
+enum Variant : int { VAR_EMPTY = 0, VAR_COPY = 1, VAR_TILE = 2, VAR_TMA = 3 };   // VAR_TMA: tma2d.h
 
 // One schedule the planner considers (a "candidate" in the paper's sense,
 // section 2.2: tile extents and the order of the flat grid).

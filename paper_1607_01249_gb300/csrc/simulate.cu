@@ -14,6 +14,7 @@
 #include "plan_impl.h"
 #include "batch_impl.h"
 #include "planner.h"
+#include "tma2d.h"
 
 using namespace ttc;
 
@@ -306,6 +307,30 @@ struct Checker {
     return true;
   }
 
+  // the TMA tile (tma2d.cu): every tile, box, warp, lane and row of the box
+  // as the kernel maps them
+  bool tma(const Candidate&) {
+    if (!tma2d_eligible(p->canon, p->din)) return fail("TMA tile on a problem it does not fit", 0, 0);
+    const Tma2dGeom g = tma2d_geom(p->canon, p->din);
+    const int es = dtype_size(p->din);
+    for (int64_t t = 0; t < g.tiles && err.empty(); ++t) {
+      int r0, c0;
+      tma2d_origin(g, t, &r0, &c0);
+      if (r0 % g.bx || r0 >= g.R || c0 >= g.C) return fail("TMA tile origin", r0, c0);
+      for (int k = 0; k < kTmaBoxes && c0 + 32 * k < g.C; ++k)
+        for (int w = 0; w < 8; ++w)
+          for (int lane = 0; lane < 32; ++lane)
+            for (int j = 0; j < g.bx / 8; ++j) {
+              const int x = w + 8 * j, r = r0 + x, col = c0 + 32 * k + lane;
+              const int sb = tma2d_smem_byte(x, lane, es);
+              if (sb < 0 || sb + es > kTmaBoxBytes || sb % es) return fail("TMA box position", sb, x);
+              if (r >= g.R || col >= g.C) continue;
+              if (!pair(int64_t(r) + int64_t(col) * g.lda, int64_t(col) + int64_t(r) * g.ldb)) return false;
+            }
+    }
+    return err.empty();
+  }
+
   bool amax() {
     const RowParams& rp = p->amax_rows;
     std::vector<uint8_t> seen(size_t(spanA), 0);
@@ -360,6 +385,7 @@ extern "C" ttc_status ttc_debug_verify_schedule(ttc_plan_t plan, int candidate, 
   bool ok = true;
   if (k.variant == VAR_TILE) ok = batch ? ck.tile_batch(k) : ck.tile(k);
   else if (k.variant == VAR_COPY) ok = ck.copy(k);
+  else if (k.variant == VAR_TMA) ok = ck.tma(k);
   if (ok && ck.writes != plan->canon.n) ok = ck.fail("wrong number of B elements written", ck.writes, plan->canon.n);
   if (ok && plan->dout == DT_E4M3 && !batch) ok = ck.amax();
   if (!ok) {

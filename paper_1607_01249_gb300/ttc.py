@@ -221,13 +221,13 @@ class Plan:
         return {"ndim": N, "perm": list(inf.perm[:N]), "sizes": list(inf.sizes[:N]),
                 "stride_A": list(inf.stride_A[:N]), "stride_B": list(inf.stride_B[:N]), "n": inf.n,
                 "algorithmic_bytes": inf.algorithmic_bytes,
-                "variant": {0: "empty", 1: "copy", 2: "tile", 3: "rowcopy"}[inf.variant],
+                "variant": {0: "empty", 1: "copy", 2: "tile", 3: "rowcopy", 4: "tma_tile"}[inf.variant],
                 "tile": (inf.tile_c, inf.tile_a, inf.tile_b), "ntiles": inf.ntiles,
                 "vec": (inf.vec_in, inf.vec_out), "candidate": inf.candidate,
                 "ncandidates": inf.ncandidates, "lanes": (inf.lanes_a, inf.lanes_b),
                 "slot_tables": bool(inf.slot_tables), "packed_threads": inf.packed_threads,
                 "packed_rows": inf.packed_rows,
-                "kernel": ({0: "empty", 1: "copy_kernel", 3: "rowcopy_kernel"}.get(inf.variant) or
+                "kernel": ({0: "empty", 1: "copy_kernel", 3: "rowcopy_kernel", 4: "tma2d_kernel"}.get(inf.variant) or
                            ("tile2_kernel" if inf.lanes_a else "tilep_kernel" if inf.packed_threads else
                             "rowsp_kernel" if inf.packed_rows else
                             "tile_slots_kernel" if inf.slot_tables else "tile_kernel"))}

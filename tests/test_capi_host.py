@@ -161,6 +161,9 @@ def test_canonical_form_properties():
             assert not (adjacent and dense)
         if inf["perm"][0] == 0:
             assert inf["variant"] in ("copy", "tile", "rowcopy")
+        elif inf["variant"] == "tma_tile":
+            # the TMA tile: two swapped indices, A's column stride 16-byte aligned
+            assert inf["ndim"] == 2 and (inf["stride_A"][1] * 4) % 16 == 0
         else:
             assert inf["variant"] == "tile"
 
