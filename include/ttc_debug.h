@@ -67,6 +67,16 @@ ttc_status ttc_debug_server_submit_delay(ttc_server_t server, int64_t microsecon
 ttc_status ttc_debug_packed_gemm_skip_mma(ttc_packed_gemm_t g, int skip);
 
 /*
+ * The packed GEMM runs its warp-specialised kernel (Bm copied by TMA, the
+ * pack by warps of its own, a ring of stages) when the pack reads A 16 bytes
+ * at a time (k dense in A, A 16-byte aligned); with classic != 0 it runs the
+ * kernel whose threads stage both operands through registers instead (what
+ * it runs otherwise), so that tests can compare the two on the same
+ * operands.  classic = 0 restores the choice.
+ */
+ttc_status ttc_debug_packed_gemm_classic(ttc_packed_gemm_t g, int classic);
+
+/*
  * A timed comparison for the BF16 contraction: with use != 0 the
  * contraction's GEMM on the same K-major BF16 operands runs on cuBLAS
  * instead of this library's tensor-core kernel (use = 0 restores it).  No

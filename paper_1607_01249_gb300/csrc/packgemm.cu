@@ -12,12 +12,14 @@
 //
 // Every wait is bounded: a wait that gives up sets the plan's error word,
 // which ttc_packed_gemm_check reports, and the CTA still frees its TMEM.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -292,9 +294,310 @@ __global__ void __launch_bounds__(kPgThreads, 2)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised form (K a multiple of 8, so that Bm's rows have a 16-byte
+// pitch): a persistent CTA per SM walks 128 x 256 tiles of C (groups of 16
+// row blocks, so that the A slices in flight share L2) with four roles over
+// a ring of kWsStages (P slice, Bm slice) buffers:
+//   warp 0      -- one thread copies each stage's 256 x 64 slice of Bm with
+//                  TMA (a tensor map over this GPU's memory, 128-byte
+//                  swizzle) and arms the stage's "full" barrier with its bytes;
+//   warps 10-17 -- the pack: they gather the stage's 128 x 64 slice of P from
+//                  A through the offset tables, round it to BF16 into the
+//                  same swizzled layout, make it visible to the tensor cores
+//                  (fence.proxy.async) and arrive on "full" (one arrival a
+//                  warp);
+//   warp 1      -- one thread issues the MMAs (M 128, N 256, K 16) of each
+//                  full stage into one of two TMEM accumulators and commits
+//                  the stage to its "empty" barrier, the tile to its
+//                  accumulator's barrier;
+//   warps 2-9   -- the epilogue of the other accumulator: tcgen05.ld, alpha,
+//                  C written one column of 32 rows per instruction.
+// The pack then runs ahead of the tensor cores by up to kWsStages stages
+// instead of one, no thread holds a prefetch in registers, and the dense Bm
+// takes no gather at all.
+constexpr int kWsStages = 4;
+constexpr int kWsGatherWarps = 8;
+constexpr int kWsThreads = 64 + 32 * 8 + 32 * kWsGatherWarps;   // 576
+constexpr int kWsGroupM = 16;
+constexpr int kWsSmem = 1024 + kWsStages * kStage + 256;
+
+__device__ __forceinline__ void ws_tile_of(int t, int ntm, int ntn, int* mb, int* nb) {
+  const int per = kWsGroupM * ntn;
+  const int grp = t / per, in = t - grp * per;
+  const int first = grp * kWsGroupM;
+  const int gsz = ntm - first < kWsGroupM ? ntm - first : kWsGroupM;
+  *mb = first + in % gsz;
+  *nb = in / gsz;
+}
+
+// one stage's 128 x 64 slice of P, as 4 items of (row, 8 k) per thread
+template <bool KVEC>
+__device__ __forceinline__ void ws_pack_stage(int gt, int m0, int k0, const float* __restrict__ A,
+                                              const int32_t* __restrict__ rowoff,
+                                              const int32_t* __restrict__ coloff, int M, int K, uint8_t* sA) {
+  float v[4][8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i = gt + 32 * kWsGatherWarps * j;
+    const int r = KVEC ? i / (kBK / 8) : i % kBM, kg = KVEC ? i % (kBK / 8) : i / kBM;
+    const int m = m0 + r, kb = k0 + kg * 8;
+    if (KVEC) {
+      float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+      if (m < M && kb < K) {
+        const float4* p = reinterpret_cast<const float4*>(A + (int64_t(rowoff[m]) + coloff[kb]));
+        lo = __ldg(p);
+        hi = __ldg(p + 1);
+      }
+      v[j][0] = lo.x; v[j][1] = lo.y; v[j][2] = lo.z; v[j][3] = lo.w;
+      v[j][4] = hi.x; v[j][5] = hi.y; v[j][6] = hi.z; v[j][7] = hi.w;
+    } else {
+      const int32_t ro = m < M ? __ldg(rowoff + m) : 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = kb + e;
+        v[j][e] = (m < M && k < K) ? __ldg(A + (int64_t(ro) + __ldg(coloff + k))) : 0.f;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i = gt + 32 * kWsGatherWarps * j;
+    const int r = KVEC ? i / (kBK / 8) : i % kBM, kg = KVEC ? i % (kBK / 8) : i / kBM;
+    *reinterpret_cast<uint4*>(sA + tile_off(r, kg * 8)) =
+        make_uint4(pack_bf16x2(v[j][0], v[j][1]), pack_bf16x2(v[j][2], v[j][3]), pack_bf16x2(v[j][4], v[j][5]),
+                   pack_bf16x2(v[j][6], v[j][7]));
+  }
+}
+
+template <bool KVEC>
+__global__ void __launch_bounds__(kWsThreads, 1)
+    packgemm_ws_kernel(const __grid_constant__ CUtensorMap mapB, const float* __restrict__ A,
+                       const int32_t* __restrict__ rowoff, const int32_t* __restrict__ coloff,
+                       float* __restrict__ C, int M, int N, int K, float alpha, int* err, int skip_mma) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t wait_limit = skip_mma ? kTestWaitLimit : kWaitLimit;
+  constexpr int S = kWsStages;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * kStage);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 4);
+  const uint32_t full0 = smem_addr(bars), empty0 = full0 + 8 * S;
+  const uint32_t afull0 = full0 + 16 * S, aempty0 = afull0 + 16;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int nk = (K + kBK - 1) / kBK;
+  const int ntm = (M + kBM - 1) / kBM, ntn = (N + kBN - 1) / kBN, total = ntm * ntn;
+
+  if (t == 0) {
+    for (int s = 0; s < S; ++s) {
+      // full: the TMA thread's arrival (with the bytes) and one per pack warp
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * s), "n"(1 + kWsGatherWarps) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * s) : "memory");
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(afull0 + 8 * b) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(aempty0 + 8 * b) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                 "r"(2 * kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (t == 0) {
+      bool ok = true;
+      int it = 0;
+      for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+        int mb, nb;
+        ws_tile_of(tile, ntm, ntn, &mb, &nb);
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = it % S;
+          if (it >= S && !barrier_wait(empty0 + 8 * s, uint32_t((it / S - 1) & 1), wait_limit)) {
+            ok = false;
+            break;
+          }
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full0 + 8 * s), "r"(kTileB)
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+              "[%4];" ::"r"(smem_addr(smem + s * kStage + kTileA)),
+              "l"(reinterpret_cast<uint64_t>(&mapB)), "r"(kt * kBK), "r"(nb * kBN), "r"(full0 + 8 * s)
+              : "memory");
+        }
+      }
+      if (!ok) {
+        atomicExch(err, 1);
+        // the copies already issued land in this CTA's ring: wait (bounded)
+        // for the stages in flight before the CTA may end
+        for (int j = (it > S ? it - S : 0); j < it; ++j)
+          barrier_wait(full0 + 8 * (j % S), uint32_t((j / S) & 1), wait_limit);
+      }
+    }
+  } else if (warp >= 10) {
+    // the pack warps
+    const int gt = t - 320;
+    bool ok = true;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+      int mb, nb;
+      ws_tile_of(tile, ntm, ntn, &mb, &nb);
+      for (int kt = 0; kt < nk; ++kt, ++it) {
+        const int s = it % S;
+        if (it >= S && !__all_sync(0xffffffffu, barrier_wait(empty0 + 8 * s, uint32_t((it / S - 1) & 1), wait_limit))) {
+          ok = false;
+          break;
+        }
+        ws_pack_stage<KVEC>(gt, mb * kBM, kt * kBK, A, rowoff, coloff, M, K, smem + s * kStage);
+        // written by the generic proxy, read by the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(full0 + 8 * s) : "memory");
+      }
+    }
+    if (!ok && lane == 0) atomicExch(err, 1);
+  } else if (warp == 1) {
+    if (t == 32) {
+      bool ok = true;
+      int it = 0, ti = 0, committed = -1;
+      for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x, ++ti) {
+        const int b = ti & 1;
+        if (ti >= 2 && !barrier_wait(aempty0 + 8 * b, uint32_t((ti / 2 - 1) & 1), wait_limit)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + uint32_t(kTmemCols * b);
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = it % S;
+          if (!barrier_wait(full0 + 8 * s, uint32_t((it / S) & 1), wait_limit)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (skip_mma) continue;   // testing hook: nothing issued or committed
+          const uint32_t a0 = smem_addr(smem + s * kStage), b0 = a0 + kTileA;
+#pragma unroll
+          for (int q = 0; q < kBK / 16; ++q) {
+            const uint64_t da = smem_desc(a0 + q * 32), db = smem_desc(b0 + q * 32);
+            const uint32_t accumulate = (kt > 0 || q > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc),
+                "l"(da), "l"(db), "r"(mma_idesc(kBM, kBN)), "r"(accumulate)
+                : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           empty0 + 8 * s)
+                       : "memory");
+          committed = it;
+        }
+        if (!ok || skip_mma) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         afull0 + 8 * b)
+                     : "memory");
+      }
+      if (!ok || skip_mma) {
+        atomicExch(err, 1);
+        if (committed >= 0 &&
+            !barrier_wait(empty0 + 8 * (committed % S), uint32_t((committed / S) & 1), wait_limit))
+          atomicExch(err, 2);   // MMAs may outlive the CTA's tensor memory: reported for good
+      }
+    }
+  } else {
+    // epilogue: warp (q, h) writes rows 32 q + lane and columns h * 128 ..
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    int ti = 0;
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++ti) {
+      const int b = ti & 1;
+      int mb, nb;
+      ws_tile_of(tile, ntm, ntn, &mb, &nb);
+      if (!__all_sync(0xffffffffu, barrier_wait(afull0 + 8 * b, uint32_t((ti / 2) & 1), wait_limit))) {
+        if (lane == 0) atomicExch(err, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int m = mb * kBM + 32 * q + lane;
+#pragma unroll 1
+      for (int c = 0; c < kBN / 64; ++c) {
+        const int col = (kBN / 2) * h + 32 * c;
+        uint32_t r[32];
+        const uint32_t taddr = tmem + uint32_t(kTmemCols * b) + (uint32_t(32 * q) << 16) + uint32_t(col);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (m < M) {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int n = nb * kBN + col + e;
+            if (n < N) C[int64_t(n) * M + m] = __fmul_rn(alpha, __uint_as_float(r[e]));
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(aempty0 + 8 * b) : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols) : "memory");
+}
+
+using EncodeTiledPg = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledPg pg_encode_fn() {
+  static EncodeTiledPg fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledPg>(f);
+  });
+  return fn;
+}
+
+// Bm (N rows of K BF16 elements, pitch K) in boxes of 64 x 256, 128-byte
+// swizzle, zero fill past its edges; false if it cannot be described
+bool pg_map_b(CUtensorMap* map, const void* Bm, int64_t K, int64_t N) {
+  EncodeTiledPg fn = pg_encode_fn();
+  if (!fn || K % 8 || reinterpret_cast<uintptr_t>(Bm) % 16) return false;
+  const cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(N)};
+  const cuuint64_t strides[1] = {cuuint64_t(K) * 2};
+  const cuuint32_t box[2] = {cuuint32_t(kBK), cuuint32_t(kBN)};
+  const cuuint32_t el[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(Bm), dims, strides, box, el,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct PgDev {
   int32_t* tables = nullptr;   // rowoff[M] | coloff[K] | error word
   int* err = nullptr;
+  bool ws_attr = false;        // the warp-specialised kernels' shared-memory limit is set
 };
 
 }  // namespace
@@ -305,6 +608,7 @@ struct ttc_packed_gemm_s {
   float alpha = 1.f;
   bool kvec = false;   // every group of 8 k is 8 consecutive floats of A, 16-byte aligned relative to A
   int skip_mma = 0;    // testing hook (ttc_debug_packed_gemm_skip_mma)
+  bool force_classic = false;   // testing hook (ttc_debug_packed_gemm_classic)
   std::vector<int32_t> rowoff, coloff;
   std::map<int, PgDev> dev;
   ~ttc_packed_gemm_s() {
@@ -427,6 +731,31 @@ ttc_status ttc_packed_gemm_execute(ttc_packed_gemm_t g, const float* A, const vo
   const int32_t* rows = d.tables;
   const int32_t* cols = d.tables + g->rowoff.size();
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CUtensorMap mapB;
+  std::memset(&mapB, 0, sizeof(mapB));
+  const bool kvec = g->kvec && reinterpret_cast<uintptr_t>(A) % 16 == 0;
+  if (!g->force_classic && kvec && pg_map_b(&mapB, B, g->K, g->N)) {
+    // the warp-specialised kernel: Bm by TMA, the pack by its own warps.
+    // Only where the pack reads A 16 bytes at a time (k dense in A): with
+    // scalar loads its 8 warps keep too few bytes in flight to feed the
+    // tensor cores (measured 210 against 336 TFLOP/s for the register-staged
+    // kernel on a 4096 x 2048 sub-block; 505 against 447 with 16-byte loads)
+    if (!d.ws_attr) {
+      e = cudaFuncSetAttribute(packgemm_ws_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      d.ws_attr = true;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    const int64_t tiles = int64_t(grid.x) * int64_t(grid.y);
+    const unsigned pgrid = unsigned(std::min<int64_t>(tiles, sms));
+    packgemm_ws_kernel<true><<<pgrid, kWsThreads, kWsSmem, s>>>(mapB, A, rows, cols, C, int(g->M), int(g->N),
+                                                                int(g->K), g->alpha, d.err, g->skip_mma);
+    ++g_launches;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? TTC_OK : cuda_fail(e, "packed GEMM launch");
+  }
   if (g->kvec && reinterpret_cast<uintptr_t>(A) % 16 == 0)
     packgemm_kernel<true><<<grid, kPgThreads, kPgSmem, s>>>(A, rows, cols, static_cast<const uint16_t*>(B), C,
                                                              int(g->M), int(g->N), int(g->K), g->alpha, d.err,
@@ -465,6 +794,13 @@ ttc_status ttc_packed_gemm_info(ttc_packed_gemm_t g, int64_t* m, int64_t* n, int
   if (m) *m = g->M;
   if (n) *n = g->N;
   if (k) *k = g->K;
+  return TTC_OK;
+}
+
+ttc_status ttc_debug_packed_gemm_classic(ttc_packed_gemm_t g, int classic) {
+  if (!g) return fail(TTC_ERR_INVALID_ARG, "plan is NULL");
+  std::lock_guard<std::mutex> lk(g->mu);
+  g->force_classic = classic != 0;
   return TTC_OK;
 }
 

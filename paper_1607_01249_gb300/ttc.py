@@ -113,6 +113,7 @@ SIGNATURES = {
                                              _i64p]),
     "ttc_debug_packed_gemm_skip_mma": (ctypes.c_int, [_vp, ctypes.c_int]),
     "ttc_debug_contraction_use_cublas": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "ttc_debug_packed_gemm_classic": (ctypes.c_int, [_vp, ctypes.c_int]),
     "ttc_debug_contraction_gemm_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ttc_debug_server_set_watchdog": (ctypes.c_int, [_vp, ctypes.c_double]),
     "ttc_debug_server_submit_delay": (ctypes.c_int, [_vp, ctypes.c_int64, _i64p]),
@@ -393,6 +394,12 @@ class PackedGemm:
         """Testing hook: executions issue no MMA, so their bounded waits run
         out and check() reports TTC_ERR_TIMEOUT."""
         _check(lib().ttc_debug_packed_gemm_skip_mma(self._h, int(bool(skip))))
+
+    def classic(self, on: bool = True):
+        """Testing hook: run the register-staged kernel even when the
+        warp-specialised one applies (K a multiple of 8)."""
+        _check(lib().ttc_debug_packed_gemm_classic(self._h, 1 if on else 0))
+        return self
 
     def info(self) -> dict:
         m, n, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

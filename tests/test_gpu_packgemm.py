@@ -29,11 +29,12 @@ def bf16_to_f64(bits):
     return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
 
 
-def run(perm, sizes, rank_m, n, alpha=1.0, outer=None, seed=0):
+def run(perm, sizes, rank_m, n, alpha=1.0, outer=None, seed=0, classic=False):
     g = inputs.rng(seed)
     oa = outer or sizes
     A = g.uniform(-1, 1, int(np.prod(oa, dtype=np.int64))).astype(np.float32)
     gemm = ttc.PackedGemm(perm, sizes, rank_m, n, alpha, outer)
+    gemm.classic(classic)
     inf = gemm.info()
     M, K = inf["m"], inf["k"]
     Bm = oracle.bf16_from_f32(g.uniform(-1, 1, K * n).astype(np.float32))
@@ -60,28 +61,96 @@ def run(perm, sizes, rank_m, n, alpha=1.0, outer=None, seed=0):
     return gemm
 
 
-def test_packed_gemm_plain_matrix_one_tile():
-    run((0, 1), (128, 64), 1, 128, seed=1)
+# both kernels: the default (the warp-specialised one -- Bm by TMA, the
+# pack by its own warps -- where the pack loads 16 bytes at a time) and the
+# register-staged one
+KERNELS = [False, True]
 
 
-def test_packed_gemm_ragged_edges_and_transposed_operand():
+@pytest.mark.parametrize("classic", KERNELS)
+def test_packed_gemm_plain_matrix_one_tile(classic):
+    run((0, 1), (128, 64), 1, 128, seed=1, classic=classic)
+
+
+@pytest.mark.parametrize("classic", KERNELS)
+def test_packed_gemm_ragged_edges_and_transposed_operand(classic):
     # A stored K x M: the panel is its transpose; M, N and K all ragged
-    run((1, 0), (72, 200), 1, 150, alpha=1.5, seed=2)
+    run((1, 0), (72, 200), 1, 150, alpha=1.5, seed=2, classic=classic)
 
 
-def test_packed_gemm_permuted_4d_operand():
+@pytest.mark.parametrize("classic", KERNELS)
+def test_packed_gemm_permuted_4d_operand(classic):
     # A[a, e, b, f] contracted over (e, f): M = a * b, K = e * f (the TTGT layout)
-    run((0, 2, 1, 3), (20, 8, 13, 9), 2, 96, alpha=-0.75, seed=3)
+    run((0, 2, 1, 3), (20, 8, 13, 9), 2, 96, alpha=-0.75, seed=3, classic=classic)
 
 
-def test_packed_gemm_sub_block_with_outer_sizes():
+@pytest.mark.parametrize("classic", KERNELS)
+def test_packed_gemm_sub_block_with_outer_sizes(classic):
     # a 300 x 136 block of a larger 320 x 160 matrix (the packing of section 2.1, Fig. 2)
-    run((0, 1), (300, 136), 1, 257, outer=(320, 160), seed=4)
+    run((0, 1), (300, 136), 1, 257, outer=(320, 160), seed=4, classic=classic)
 
 
-def test_packed_gemm_several_k_stages_and_tiles():
-    run((1, 0, 2), (16, 40, 24), 2, 300, seed=5)          # M = 640, K = 24
-    run((2, 0, 1), (32, 24, 16), 1, 200, seed=6)          # M = 16, K = 768 (12 stages)
+@pytest.mark.parametrize("classic", KERNELS)
+def test_packed_gemm_several_k_stages_and_tiles(classic):
+    run((1, 0, 2), (16, 40, 24), 2, 300, seed=5, classic=classic)          # M = 640, K = 24
+    run((2, 0, 1), (32, 24, 16), 1, 200, seed=6, classic=classic)          # M = 16, K = 768 (12 stages)
+    run((1, 0), (520, 1000), 1, 700, seed=7, classic=classic)              # many tiles per CTA, ragged
+
+
+@pytest.mark.parametrize("case", inputs.packed_gemm_cases(), ids=lambda c: c["tag"])
+def test_packed_gemm_at_bench_size_sampled(case):
+    """The bench's packed GEMMs at full size (a 4096 x 2048 block of an
+    8192^2 matrix times 2048 x 4096, its transposed storage, the 48^4 TTGT
+    operand): 96 sampled entries of C against the definition on the
+    operands rounded to BF16, and the default kernel (the warp-specialised
+    one where the pack loads 16 bytes at a time) equal bit for bit to the
+    register-staged one."""
+    perm, sizes, outer, rank_m, n = case["perm"], case["sizes"], case["outer"], case["rank_m"], case["n"]
+    g = inputs.rng(41)
+    oa = outer or sizes
+    A = g.uniform(-1, 1, int(np.prod(oa, dtype=np.int64))).astype(np.float32)
+    outs = []
+    for classic in (False, True):
+        gemm = ttc.PackedGemm(perm, sizes, rank_m, n, 1.0, outer).classic(classic)
+        inf = gemm.info()
+        M, K = inf["m"], inf["k"]
+        if not outs:
+            Bm = oracle.bf16_from_f32(g.uniform(-1, 1, K * n).astype(np.float32))
+            dA = torch.from_numpy(A).cuda()
+            dB = torch.from_numpy(Bm.view(np.int16)).cuda()
+        dC = torch.full((M * n,), float("nan"), device="cuda")
+        gemm.execute(dA, dB, dC)
+        torch.cuda.synchronize()
+        gemm.check()
+        outs.append(dC.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    got = outs[0].astype(np.float64).reshape(n, M).T
+    # P[m, k]: the A element the packing maps to (row m, column k), rounded to BF16
+    sB = [sizes[p] for p in perm]
+    stA = np.cumprod((1,) + tuple(oa[:-1]))
+    Ar = bf16_to_f64(oracle.bf16_from_f32(A))
+    Bmm = bf16_to_f64(Bm).reshape(n, K).T
+    nm = rank_m
+
+    def a_offset(m, k):
+        # B order index (m's digits over the first rank_m B indices, k's over the rest) -> A offset
+        idx, off = [0] * len(sizes), 0
+        for d in range(nm):
+            idx[perm[d]] = m % sB[d]
+            m //= sB[d]
+        for d in range(nm, len(perm)):
+            idx[perm[d]] = k % sB[d]
+            k //= sB[d]
+        return int(sum(i * s for i, s in zip(idx, stA)))
+
+    u = 2.0 ** -23
+    gamma = (K + 1) * u / (1 - (K + 1) * u)
+    for _ in range(96):
+        m, j = int(g.integers(0, M)), int(g.integers(0, n))
+        row = np.array([Ar[a_offset(m, k)] for k in range(K)])
+        want = float(row @ Bmm[:, j])
+        scale = float(np.abs(row) @ np.abs(Bmm[:, j]))
+        assert abs(got[m, j] - want) <= gamma * scale + 1e-30, (case["tag"], m, j)
 
 
 def test_packed_gemm_host_checks():
