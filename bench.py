@@ -893,12 +893,29 @@ def run_packed_gemm(args, rank, world):
         ms_pack = timed(lambda: plan.execute(A, P, stream))
         flop = 2.0 * M * N * K
         tf = world * flop / (ms * 1e-3) / 1e12
-        cases.append({"case": c["tag"], "m": M, "n": N, "k": K, "fused_ms": round(ms, 4),
-                      "fused_TFLOP/s": round(tf, 1), "unfused_ms": round(ms_unfused, 4),
-                      "unfused_pack_ms": round(ms_pack, 4), "unfused_gemm_result": mm_out,
-                      "unfused_TFLOP/s": round(world * flop / (ms_unfused * 1e-3) / 1e12, 1),
-                      "speedup_vs_unfused": round(ms_unfused / ms, 3),
-                      "frac_of_bf16_peak": round(tf / world / peak, 3) if peak else None})
+        row = {"case": c["tag"], "m": M, "n": N, "k": K, "fused_ms": round(ms, 4),
+               "fused_TFLOP/s": round(tf, 1), "unfused_ms": round(ms_unfused, 4),
+               "unfused_pack_ms": round(ms_pack, 4), "unfused_gemm_result": mm_out,
+               "unfused_TFLOP/s": round(world * flop / (ms_unfused * 1e-3) / 1e12, 1),
+               "speedup_vs_unfused": round(ms_unfused / ms, 3),
+               "frac_of_bf16_peak": round(tf / world / peak, 3) if peak else None}
+        if K % 16 == 0:
+            # E4M3 operands (P packed as codes with a per-tensor scale, Bm as
+            # codes): kind::f8f6f4; its peak is the measured BF16 one times the
+            # nominal FP8/BF16 ratio (4.5 / 2.25)
+            B8 = torch.full((K * N,), 0x38, dtype=torch.uint8, device="cuda")
+            sp = torch.full((1,), 0.01, device="cuda")
+            sb = torch.full((1,), 0.5, device="cuda")
+            gemm.set_fp8(sp, sb)
+            ms8 = timed(lambda: gemm.execute(A, B8, C, stream))
+            gemm.check()
+            gemm.set_fp8(None, None)
+            tf8 = world * flop / (ms8 * 1e-3) / 1e12
+            row["fp8"] = {"fused_ms": round(ms8, 4), "fused_TFLOP/s": round(tf8, 1),
+                          "frac_of_fp8_peak": round(tf8 / world / (2 * peak), 3) if peak else None,
+                          "fp8_peak_source": "2 x MEASURED_PEAKS.json bf16_tflops (nominal 4.5 / 2.25)"}
+            del B8
+        cases.append(row)
         tot_flop += flop
         tot_ms += ms
         del A, B, C, P

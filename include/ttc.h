@@ -385,6 +385,17 @@ ttc_status ttc_contraction_destroy(ttc_contraction_t c);
  *                           tensor-core results of concurrent and later
  *                           launches on that device may be corrupt.
  *  ttc_packed_gemm_info     m, n, k.
+ *  ttc_packed_gemm_set_fp8  E4M3 operands (scale_p, scale_b: device floats,
+ *                           read at execution; both NULL restore BF16): P is
+ *                           packed as the E4M3 codes (RNE, satfinite) of
+ *                           alpha * a / *scale_p -- the codes ttc_plan with an
+ *                           E4M3 output and that scale writes -- Bm is read as
+ *                           E4M3 codes (K x N bytes, column-major) standing for
+ *                           *scale_b * code, and C = *scale_p * *scale_b *
+ *                           P Bm, FP32 accumulation (tcgen05.mma
+ *                           kind::f8f6f4).  Scales must be positive and
+ *                           finite.  TTC_ERR_INVALID_SIZE unless K is a
+ *                           multiple of 16.
  *  ttc_packed_gemm_destroy  release (no work using it may be queued).
  */
 typedef struct ttc_packed_gemm_s* ttc_packed_gemm_t;
@@ -394,6 +405,7 @@ ttc_status ttc_packed_gemm_execute(ttc_packed_gemm_t g, const float* A, const vo
                                    ttc_stream_t stream);
 ttc_status ttc_packed_gemm_check(ttc_packed_gemm_t g);
 ttc_status ttc_packed_gemm_info(ttc_packed_gemm_t g, int64_t* m, int64_t* n, int64_t* k);
+ttc_status ttc_packed_gemm_set_fp8(ttc_packed_gemm_t g, const float* scale_p, const float* scale_b);
 ttc_status ttc_packed_gemm_destroy(ttc_packed_gemm_t g);
 
 /*

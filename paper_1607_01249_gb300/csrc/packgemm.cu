@@ -28,6 +28,7 @@
 
 #include "../../include/ttc.h"
 #include "../../include/ttc_debug.h"
+#include "kernels.cuh"
 #include "plan_impl.h"
 
 using namespace ttc;
@@ -331,6 +332,47 @@ __device__ __forceinline__ void ws_tile_of(int t, int ntm, int ntn, int* mb, int
   *nb = in / gsz;
 }
 
+// one stage's 128 x 128 slice of P as E4M3 codes of alpha * a / scale (the
+// codes of the FP8 permute), as 4 items of (row, 16 k) per thread
+template <bool KVEC>
+__device__ __forceinline__ void ws_pack_stage_fp8(int gt, int m0, int k0, const float* __restrict__ A,
+                                                  const int32_t* __restrict__ rowoff,
+                                                  const int32_t* __restrict__ coloff, int M, int K, float alpha,
+                                                  float scale, float rcp, uint8_t* sA) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i = gt + 32 * kWsGatherWarps * j;
+    const int r = KVEC ? i / 8 : i % kBM, kg = KVEC ? i % 8 : i / kBM;
+    const int m = m0 + r, kb = k0 + kg * 16;
+    float v[16];
+    if (KVEC) {
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m < M && kb < K) q = __ldg(reinterpret_cast<const float4*>(A + (int64_t(rowoff[m]) + coloff[kb])) + h);
+        v[4 * h] = q.x; v[4 * h + 1] = q.y; v[4 * h + 2] = q.z; v[4 * h + 3] = q.w;
+      }
+    } else {
+      const int32_t ro = m < M ? __ldg(rowoff + m) : 0;
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int k = kb + e;
+        v[e] = (m < M && k < K) ? __ldg(A + (int64_t(ro) + __ldg(coloff + k))) : 0.f;
+      }
+    }
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      w[q] = 0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        w[q] |= uint32_t(e4m3_of_quotient(__fmul_rn(alpha, v[4 * q + e]), scale, rcp)) << (8 * e);
+    }
+    // chunk kg of row r: 16 codes (the same 16-byte chunk layout as 8 BF16)
+    *reinterpret_cast<uint4*>(sA + tile_off(r, kg * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
 // one stage's 128 x 64 slice of P, as 4 items of (row, 8 k) per thread
 template <bool KVEC>
 __device__ __forceinline__ void ws_pack_stage(int gt, int m0, int k0, const float* __restrict__ A,
@@ -370,11 +412,19 @@ __device__ __forceinline__ void ws_pack_stage(int gt, int m0, int k0, const floa
   }
 }
 
-template <bool KVEC>
+// FP8: P packed as E4M3 codes of alpha * a / *scale_p, Bm read as E4M3
+// codes, MMAs of kind::f8f6f4 (K 32), C = *scale_p * *scale_b * P Bm;
+// 128 k per stage (still 128-byte rows)
+template <bool KVEC, bool FP8>
 __global__ void __launch_bounds__(kWsThreads, 1)
     packgemm_ws_kernel(const __grid_constant__ CUtensorMap mapB, const float* __restrict__ A,
                        const int32_t* __restrict__ rowoff, const int32_t* __restrict__ coloff,
-                       float* __restrict__ C, int M, int N, int K, float alpha, int* err, int skip_mma) {
+                       float* __restrict__ C, int M, int N, int K, float alpha, const float* __restrict__ scale_p,
+                       const float* __restrict__ scale_b, int* err, int skip_mma) {
+  constexpr int KB = FP8 ? 128 : kBK;                 // k per stage
+  // kind::f8f6f4 with E4M3 A and B (format 0), FP32 accumulator
+  constexpr uint32_t kIdesc = FP8 ? ((1u << 4) | (uint32_t(kBN >> 3) << 17) | (uint32_t(kBM >> 4) << 24))
+                                  : mma_idesc(kBM, kBN);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t wait_limit = skip_mma ? kTestWaitLimit : kWaitLimit;
@@ -384,7 +434,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   const uint32_t full0 = smem_addr(bars), empty0 = full0 + 8 * S;
   const uint32_t afull0 = full0 + 16 * S, aempty0 = afull0 + 16;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int nk = (K + kBK - 1) / kBK;
+  const int nk = (K + KB - 1) / KB;
   const int ntm = (M + kBM - 1) / kBM, ntn = (N + kBN - 1) / kBN, total = ntm * ntn;
 
   if (t == 0) {
@@ -429,7 +479,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           asm volatile(
               "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
               "[%4];" ::"r"(smem_addr(smem + s * kStage + kTileA)),
-              "l"(reinterpret_cast<uint64_t>(&mapB)), "r"(kt * kBK), "r"(nb * kBN), "r"(full0 + 8 * s)
+              "l"(reinterpret_cast<uint64_t>(&mapB)), "r"(kt * KB), "r"(nb * kBN), "r"(full0 + 8 * s)
               : "memory");
         }
       }
@@ -444,6 +494,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   } else if (warp >= 10) {
     // the pack warps
     const int gt = t - 320;
+    const float sp = FP8 ? *scale_p : 1.f, rp = FP8 ? __frcp_rn(sp) : 1.f;
     bool ok = true;
     int it = 0;
     for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
@@ -455,7 +506,10 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           ok = false;
           break;
         }
-        ws_pack_stage<KVEC>(gt, mb * kBM, kt * kBK, A, rowoff, coloff, M, K, smem + s * kStage);
+        if constexpr (FP8)
+          ws_pack_stage_fp8<KVEC>(gt, mb * kBM, kt * KB, A, rowoff, coloff, M, K, alpha, sp, rp, smem + s * kStage);
+        else
+          ws_pack_stage<KVEC>(gt, mb * kBM, kt * KB, A, rowoff, coloff, M, K, smem + s * kStage);
         // written by the generic proxy, read by the tensor cores
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
@@ -485,15 +539,23 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           if (skip_mma) continue;   // testing hook: nothing issued or committed
           const uint32_t a0 = smem_addr(smem + s * kStage), b0 = a0 + kTileA;
 #pragma unroll
-          for (int q = 0; q < kBK / 16; ++q) {
+          for (int q = 0; q < 4; ++q) {   // 32 bytes of every row per MMA: K 16 (BF16) or 32 (E4M3)
             const uint64_t da = smem_desc(a0 + q * 32), db = smem_desc(b0 + q * 32);
             const uint32_t accumulate = (kt > 0 || q > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "setp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc),
-                "l"(da), "l"(db), "r"(mma_idesc(kBM, kBN)), "r"(accumulate)
-                : "memory");
+            if constexpr (FP8)
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\t"
+                  "setp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc),
+                  "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate)
+                  : "memory");
+            else
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\t"
+                  "setp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc),
+                  "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate)
+                  : "memory");
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            empty0 + 8 * s)
@@ -515,6 +577,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   } else {
     // epilogue: warp (q, h) writes rows 32 q + lane and columns h * 128 ..
     const int q = warp & 3, h = (warp - 2) >> 2;
+    // FP8: the product of the codes times both scales (alpha is in P's codes)
+    const float outscale = FP8 ? __fmul_rn(*scale_p, *scale_b) : alpha;
     int ti = 0;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++ti) {
       const int b = ti & 1;
@@ -546,7 +610,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
             const int n = nb * kBN + col + e;
-            if (n < N) C[int64_t(n) * M + m] = __fmul_rn(alpha, __uint_as_float(r[e]));
+            if (n < N) C[int64_t(n) * M + m] = __fmul_rn(outscale, __uint_as_float(r[e]));
           }
         }
       }
@@ -582,14 +646,16 @@ EncodeTiledPg pg_encode_fn() {
 
 // Bm (N rows of K BF16 elements, pitch K) in boxes of 64 x 256, 128-byte
 // swizzle, zero fill past its edges; false if it cannot be described
-bool pg_map_b(CUtensorMap* map, const void* Bm, int64_t K, int64_t N) {
+bool pg_map_b(CUtensorMap* map, const void* Bm, int64_t K, int64_t N, bool fp8) {
   EncodeTiledPg fn = pg_encode_fn();
-  if (!fn || K % 8 || reinterpret_cast<uintptr_t>(Bm) % 16) return false;
+  const int es = fp8 ? 1 : 2;
+  if (!fn || (K * es) % 16 || reinterpret_cast<uintptr_t>(Bm) % 16) return false;
   const cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(N)};
-  const cuuint64_t strides[1] = {cuuint64_t(K) * 2};
-  const cuuint32_t box[2] = {cuuint32_t(kBK), cuuint32_t(kBN)};
+  const cuuint64_t strides[1] = {cuuint64_t(K) * cuuint64_t(es)};
+  const cuuint32_t box[2] = {cuuint32_t(128 / es), cuuint32_t(kBN)};
   const cuuint32_t el[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(Bm), dims, strides, box, el,
+  return fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(Bm),
+            dims, strides, box, el,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -598,6 +664,7 @@ struct PgDev {
   int32_t* tables = nullptr;   // rowoff[M] | coloff[K] | error word
   int* err = nullptr;
   bool ws_attr = false;        // the warp-specialised kernels' shared-memory limit is set
+  bool ws_fp8_attr = false;
 };
 
 }  // namespace
@@ -609,6 +676,9 @@ struct ttc_packed_gemm_s {
   bool kvec = false;   // every group of 8 k is 8 consecutive floats of A, 16-byte aligned relative to A
   int skip_mma = 0;    // testing hook (ttc_debug_packed_gemm_skip_mma)
   bool force_classic = false;   // testing hook (ttc_debug_packed_gemm_classic)
+  bool kvec16 = false;          // every group of 16 k is 16 consecutive floats of A, 16-byte aligned relative to A
+  const float* scale_p = nullptr;   // FP8 operands (ttc_packed_gemm_set_fp8): device scales of P and Bm
+  const float* scale_b = nullptr;
   std::vector<int32_t> rowoff, coloff;
   std::map<int, PgDev> dev;
   ~ttc_packed_gemm_s() {
@@ -685,6 +755,9 @@ ttc_status ttc_packed_gemm_plan(ttc_packed_gemm_t* out, int ndim, const int* per
   }
   for (int64_t m = 0; m < g->M && g->kvec; ++m)
     if (g->rowoff[size_t(m)] % 4) g->kvec = false;
+  g->kvec16 = g->kvec && g->K % 16 == 0;
+  for (int64_t k = 0; k < g->K && g->kvec16; k += 16)
+    if (g->coloff[size_t(k + 8)] != g->coloff[size_t(k)] + 8) g->kvec16 = false;
   *out = g.release();
   return TTC_OK;
 }
@@ -699,7 +772,8 @@ ttc_status ttc_packed_gemm_execute(ttc_packed_gemm_t g, const float* A, const vo
   const uintptr_t a = reinterpret_cast<uintptr_t>(A), c = reinterpret_cast<uintptr_t>(C);
   const uintptr_t b = reinterpret_cast<uintptr_t>(B);
   const size_t bytesC = size_t(g->M) * size_t(g->N) * 4, bytesA = size_t(g->spanA) * 4;
-  const size_t bytesB = size_t(g->K) * size_t(g->N) * 2;
+  const bool fp8 = g->scale_p != nullptr;
+  const size_t bytesB = size_t(g->K) * size_t(g->N) * (fp8 ? 1 : 2);
   if ((c < a + bytesA && a < c + bytesC) || (c < b + bytesB && b < c + bytesC))
     return fail(TTC_ERR_ALIAS, "C overlaps A or B");
   std::lock_guard<std::mutex> lk(g->mu);
@@ -734,14 +808,41 @@ ttc_status ttc_packed_gemm_execute(ttc_packed_gemm_t g, const float* A, const vo
   CUtensorMap mapB;
   std::memset(&mapB, 0, sizeof(mapB));
   const bool kvec = g->kvec && reinterpret_cast<uintptr_t>(A) % 16 == 0;
-  if (!g->force_classic && kvec && pg_map_b(&mapB, B, g->K, g->N)) {
+  if (fp8) {
+    // E4M3 operands: the warp-specialised kernel only (kind::f8f6f4)
+    if (!pg_map_b(&mapB, B, g->K, g->N, true)) return fail(TTC_ERR_INVALID_ARG, "cannot describe Bm for TMA");
+    if (!d.ws_fp8_attr) {
+      e = cudaFuncSetAttribute(packgemm_ws_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(packgemm_ws_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kWsSmem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      d.ws_fp8_attr = true;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    const unsigned pgrid = unsigned(std::min<int64_t>(int64_t(grid.x) * int64_t(grid.y), sms));
+    if (g->kvec16 && reinterpret_cast<uintptr_t>(A) % 16 == 0)
+      packgemm_ws_kernel<true, true><<<pgrid, kWsThreads, kWsSmem, s>>>(mapB, A, rows, cols, C, int(g->M),
+                                                                        int(g->N), int(g->K), g->alpha, g->scale_p,
+                                                                        g->scale_b, d.err, g->skip_mma);
+    else
+      packgemm_ws_kernel<false, true><<<pgrid, kWsThreads, kWsSmem, s>>>(mapB, A, rows, cols, C, int(g->M),
+                                                                         int(g->N), int(g->K), g->alpha, g->scale_p,
+                                                                         g->scale_b, d.err, g->skip_mma);
+    ++g_launches;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? TTC_OK : cuda_fail(e, "packed GEMM launch");
+  }
+  if (!g->force_classic && kvec && pg_map_b(&mapB, B, g->K, g->N, false)) {
     // the warp-specialised kernel: Bm by TMA, the pack by its own warps.
     // Only where the pack reads A 16 bytes at a time (k dense in A): with
     // scalar loads its 8 warps keep too few bytes in flight to feed the
     // tensor cores (measured 210 against 336 TFLOP/s for the register-staged
     // kernel on a 4096 x 2048 sub-block; 505 against 447 with 16-byte loads)
     if (!d.ws_attr) {
-      e = cudaFuncSetAttribute(packgemm_ws_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem);
+      e = cudaFuncSetAttribute(packgemm_ws_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
       d.ws_attr = true;
     }
@@ -750,8 +851,9 @@ ttc_status ttc_packed_gemm_execute(ttc_packed_gemm_t g, const float* A, const vo
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     const int64_t tiles = int64_t(grid.x) * int64_t(grid.y);
     const unsigned pgrid = unsigned(std::min<int64_t>(tiles, sms));
-    packgemm_ws_kernel<true><<<pgrid, kWsThreads, kWsSmem, s>>>(mapB, A, rows, cols, C, int(g->M), int(g->N),
-                                                                int(g->K), g->alpha, d.err, g->skip_mma);
+    packgemm_ws_kernel<true, false><<<pgrid, kWsThreads, kWsSmem, s>>>(mapB, A, rows, cols, C, int(g->M),
+                                                                       int(g->N), int(g->K), g->alpha, nullptr,
+                                                                       nullptr, d.err, g->skip_mma);
     ++g_launches;
     e = cudaGetLastError();
     return e == cudaSuccess ? TTC_OK : cuda_fail(e, "packed GEMM launch");
@@ -794,6 +896,18 @@ ttc_status ttc_packed_gemm_info(ttc_packed_gemm_t g, int64_t* m, int64_t* n, int
   if (m) *m = g->M;
   if (n) *n = g->N;
   if (k) *k = g->K;
+  return TTC_OK;
+}
+
+ttc_status ttc_packed_gemm_set_fp8(ttc_packed_gemm_t g, const float* scale_p, const float* scale_b) {
+  if (!g) return fail(TTC_ERR_INVALID_ARG, "plan is NULL");
+  if ((scale_p == nullptr) != (scale_b == nullptr)) return fail(TTC_ERR_INVALID_ARG, "give both scales or neither");
+  if (scale_p && g->K % 16) return fail(TTC_ERR_INVALID_SIZE, "E4M3 operands need K a multiple of 16");
+  if ((scale_p && reinterpret_cast<uintptr_t>(scale_p) % 4) || (scale_b && reinterpret_cast<uintptr_t>(scale_b) % 4))
+    return fail(TTC_ERR_ALIGN, "scales need 4-byte alignment");
+  std::lock_guard<std::mutex> lk(g->mu);
+  g->scale_p = scale_p;
+  g->scale_b = scale_b;
   return TTC_OK;
 }
 

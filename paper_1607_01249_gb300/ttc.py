@@ -114,6 +114,7 @@ SIGNATURES = {
     "ttc_debug_packed_gemm_skip_mma": (ctypes.c_int, [_vp, ctypes.c_int]),
     "ttc_debug_contraction_use_cublas": (ctypes.c_int, [_vp, ctypes.c_int]),
     "ttc_debug_packed_gemm_classic": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "ttc_packed_gemm_set_fp8": (ctypes.c_int, [_vp, _vp, _vp]),
     "ttc_debug_contraction_gemm_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ttc_debug_server_set_watchdog": (ctypes.c_int, [_vp, ctypes.c_double]),
     "ttc_debug_server_submit_delay": (ctypes.c_int, [_vp, ctypes.c_int64, _i64p]),
@@ -394,6 +395,15 @@ class PackedGemm:
         """Testing hook: executions issue no MMA, so their bounded waits run
         out and check() reports TTC_ERR_TIMEOUT."""
         _check(lib().ttc_debug_packed_gemm_skip_mma(self._h, int(bool(skip))))
+
+    def set_fp8(self, scale_p=None, scale_b=None):
+        """E4M3 operands: P packed as codes of alpha * a / scale_p, Bm given
+        as E4M3 codes standing for scale_b * code (device float tensors of
+        one element; None for both restores BF16)."""
+        _check(lib().ttc_packed_gemm_set_fp8(self._h, _ptr(scale_p) if scale_p is not None else None,
+                                             _ptr(scale_b) if scale_b is not None else None))
+        self._scales = (scale_p, scale_b)
+        return self
 
     def classic(self, on: bool = True):
         """Testing hook: run the register-staged kernel even when the

@@ -191,3 +191,85 @@ def test_packed_gemm_wait_limit_reports_timeout_and_keeps_the_context():
     g.check()
     assert bool((C == 0.0).all())                             # Bm = 0
     run((0, 1), (128, 192), 1, 256, seed=7)                  # and a fresh plan matches the oracle
+
+
+def run_fp8(perm, sizes, rank_m, n, alpha=1.0, outer=None, seed=0, identity=False):
+    """E4M3 operands: P's codes against the oracle's FP8 permutation with the
+    same scale (bit for bit, through an identity Bm) or C against the exact
+    product of the decoded codes (random Bm codes)."""
+    g = inputs.rng(seed)
+    oa = outer or sizes
+    A = g.normal(0, 1, int(np.prod(oa, dtype=np.int64))).astype(np.float32)
+    gemm = ttc.PackedGemm(perm, sizes, rank_m, n, alpha, outer)
+    inf = gemm.info()
+    M, K = inf["m"], inf["k"]
+    sp, _ = oracle.fp8_scale(sizes, A, alpha, oracle.F32, outer)
+    sp = float(np.float32(sp))
+    sb = 0.03125 if not identity else 1.0
+    if identity:
+        assert n == K
+        Bcodes = np.zeros(K * n, np.uint8)
+        Bcodes[np.arange(K) * (K + 1)] = oracle.e4m3_from_f32(np.ones(1, np.float32))[0]
+    else:
+        Bcodes = oracle.e4m3_from_f32(g.uniform(-1, 1, K * n).astype(np.float32))
+    dsp = torch.tensor([sp], dtype=torch.float32, device="cuda")
+    dsb = torch.tensor([sb], dtype=torch.float32, device="cuda")
+    gemm.set_fp8(dsp, dsb)
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(Bcodes).cuda()
+    dC = torch.full((M * n,), float("nan"), device="cuda")
+    gemm.execute(dA, dB, dC)
+    torch.cuda.synchronize()
+    gemm.check()
+    got = dC.cpu().numpy().reshape(n, M).T
+    sB = [sizes[p] for p in perm]
+    Pc = np.zeros(int(np.prod(sB, dtype=np.int64)), np.uint8)
+    oracle.permute(perm, sizes, A, Pc, alpha, 0.0, oracle.F32, oracle.E4M3, outer, None, fp8_scale=sp)
+    P = oracle.e4m3_to_f32(Pc).astype(np.float64).reshape(K, M).T
+    if identity:
+        want = (np.float32(sp) * P.astype(np.float32))
+        assert np.array_equal(got, want), (perm, sizes, int((got != want).sum()))
+        return
+    Bv = oracle.e4m3_to_f32(Bcodes).astype(np.float64).reshape(n, K).T
+    s = np.float64(np.float32(np.float32(sp) * np.float32(sb)))
+    want = s * (P @ Bv)
+    scale = s * (np.abs(P) @ np.abs(Bv))
+    u = 2.0 ** -23
+    gamma = (K + 2) * u / (1 - (K + 2) * u)
+    err = np.abs(got.astype(np.float64) - want)
+    bad = ~(err <= gamma * scale + 1e-30)
+    assert not bad.any(), (perm, sizes, int(bad.sum()), float(np.nanmax(err)))
+
+
+@pytest.mark.parametrize("perm,sizes,rank_m,outer", [
+    ((0, 1), (128, 64), 1, None),                # one tile, m dense in A (scalar pack)
+    ((1, 0), (80, 200), 1, None),                # A stored K x M: k dense (16-byte pack loads)
+    ((0, 1), (300, 144), 1, (320, 160)),         # a sub-block, ragged M
+    ((0, 2, 1, 3), (20, 8, 13, 8), 2, None),     # the TTGT layout
+])
+def test_packed_gemm_fp8_codes_are_the_fp8_permutation(perm, sizes, rank_m, outer):
+    sB = [sizes[p] for p in perm]
+    K = int(np.prod(sB[rank_m:]))
+    run_fp8(perm, sizes, rank_m, K, alpha=1.25, outer=outer, seed=11, identity=True)
+
+
+@pytest.mark.parametrize("perm,sizes,rank_m,n,outer", [
+    ((0, 1), (128, 64), 1, 256, None),
+    ((1, 0), (160, 520), 1, 300, None),          # several k stages (128 per stage), ragged N
+    ((0, 1), (300, 144), 1, 257, (320, 160)),
+    ((0, 2, 1, 3), (20, 16, 13, 16), 2, 96, None),
+])
+def test_packed_gemm_fp8_product_within_bound(perm, sizes, rank_m, n, outer):
+    run_fp8(perm, sizes, rank_m, n, alpha=-0.5, outer=outer, seed=12)
+
+
+def test_packed_gemm_fp8_host_checks():
+    g = ttc.PackedGemm((0, 1), (64, 24), 1, 64)          # K = 24: BF16 fine, E4M3 needs K % 16 == 0
+    s = torch.ones(1, device="cuda")
+    with pytest.raises(ttc.TTCError) as ei:
+        g.set_fp8(s, s)
+    assert ei.value.name == "TTC_ERR_INVALID_SIZE"
+    g2 = ttc.PackedGemm((0, 1), (64, 32), 1, 64)
+    with pytest.raises(ttc.TTCError) as ei:
+        g2.set_fp8(s, None)
+    assert ei.value.name == "TTC_ERR_INVALID_ARG"
