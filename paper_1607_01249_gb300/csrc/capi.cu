@@ -17,6 +17,7 @@
 #include "launch.h"
 #include "plan_impl.h"
 #include "planner.h"
+#include "rowvec.h"
 #include "tma2d.h"
 
 using namespace ttc;
@@ -201,7 +202,7 @@ ttc_status run_plan(ttc_plan_s* p, const void* A, void* B, cudaStream_t s) {
   if (k.variant == VAR_TILE) {
     TileParams tp = r->tp;
     tp.epi = epi;
-    e = k.rows ? launch_rowcopy(p->din, p->dout, A, B, tp, s)
+    e = k.rows ? (k.vec > 1 ? launch_rowcopy_vec(p->din, p->dout, A, B, tp, s) : launch_rowcopy(p->din, p->dout, A, B, tp, s))
         : k.rj ? launch_rowsp(p->din, p->dout, k.rj, A, B, tp, s)
         : k.pk ? launch_tilep(p->din, p->dout, k.pk, k.ju, k.jw, A, B, tp, r->smem, s)
         : k.ju ? launch_tile2(p->din, p->dout, k.ju, k.jw, A, B, tp, r->smem, s)
@@ -398,7 +399,7 @@ ttc_status ttc_plan_get_info(ttc_plan_t plan, ttc_plan_info* info) {
     info->tile_a = tp.LA;
     info->tile_b = tp.LB;
     info->ntiles = tp.ntiles;
-    info->vec_in = info->vec_out = 1;
+    info->vec_in = info->vec_out = k.rows ? k.vec : 1;
     info->lanes_a = k.pk ? 0 : 32 * k.ju;
     info->lanes_b = k.pk ? 0 : 32 * k.jw;
     info->slot_tables = k.slots;

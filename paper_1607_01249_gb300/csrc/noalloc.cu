@@ -13,6 +13,7 @@
 #include "launch.h"
 #include "plan_impl.h"
 #include "planner.h"
+#include "rowvec.h"
 #include "tma2d.h"
 
 using namespace ttc;
@@ -170,7 +171,8 @@ extern "C" ttc_status ttc_execute_noalloc(ttc_plan_t plan, const void* A, void* 
     tp.tabA = tables;
     tp.tabB = tables + ta.size();
     tp.epi = epi;
-    e = k.rows ? launch_rowcopy(plan->din, plan->dout, A, B, tp, s)
+    e = k.rows ? (k.vec > 1 ? launch_rowcopy_vec(plan->din, plan->dout, A, B, tp, s)
+                            : launch_rowcopy(plan->din, plan->dout, A, B, tp, s))
         : k.rj ? launch_rowsp(plan->din, plan->dout, k.rj, A, B, tp, s)
         : k.pk ? launch_tilep(plan->din, plan->dout, k.pk, k.ju, k.jw, A, B, tp, smem, s)
         : k.ju ? launch_tile2(plan->din, plan->dout, k.ju, k.jw, A, B, tp, smem, s)

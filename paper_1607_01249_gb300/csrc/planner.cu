@@ -27,6 +27,7 @@
 #include "kernels.cuh"
 #include "launch.h"
 #include "planner.h"
+#include "rowvec.h"
 #include "tma2d.h"
 
 namespace ttc {
@@ -69,7 +70,9 @@ std::string Candidate::describe() const {
     for (size_t i = 0; i < ga.size(); ++i) o << (i ? "," : "") << ga[i];
     o << "]/" << ta << " gb=[";
     for (size_t i = 0; i < gb.size(); ++i) o << (i ? "," : "") << gb[i];
-    o << "]/" << tb << " j=" << ju << "," << jw << (rows ? " rows" : "") << (slots ? " slots" : "");
+    o << "]/" << tb << " j=" << ju << "," << jw << (rows ? " rows" : "") << (rows && vec > 1 ? " vec=" : "");
+    if (rows && vec > 1) o << vec;
+    o << (slots ? " slots" : "");
     if (pk) o << " pk=" << pk;
     if (swz) o << " swz=" << swz;
     if (rj) o << " rj=" << rj;
@@ -447,6 +450,49 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
     }
   }
 
+  // ---- multi-row copy with 16-byte accesses (rowvec.cu): rows a multiple
+  // of the vector, every A and B stride too, so that each thread's vectors
+  // are aligned relative to both bases; twice the bytes per thread and a
+  // quarter of the instructions of the element-wise copy
+  const int V = rowvec_width(din);
+  bool vec_rows = !flat && V > 1 && c.perm[0] == 0 && c.N >= 2 && c.sa[0] == 1 && c.sb[0] == 1 &&
+                  c.sa[1] == c.s[0] && c.s[0] % V == 0;
+  for (int i = 1; vec_rows && i < c.N; ++i) vec_rows = c.sa[i] % V == 0 && c.sb[i] % V == 0;
+  if (vec_rows) {
+    const int64_t vcap = int64_t(kThreads) * kRowVecK * V;
+    const int64_t cap = vcap / c.s[0];
+    if (cap >= 2) {
+      for (int G : cut_options(c.s[1], cap)) {
+        Candidate k;
+        k.variant = VAR_TILE;
+        k.rows = 1;
+        k.vec = V;
+        k.has_c = 1;
+        k.ga = {1};
+        k.ta = G;
+        int64_t ext[kMaxDim];
+        TileShape sh{1, k.ga, {}, G, 1};
+        tile_extents(c, sh, ext);
+        double ntiles = 1;
+        for (int q = 0; q < c.N; ++q) ntiles *= std::ceil(double(c.s[q]) / double(ext[q]));
+        if (ntiles >= 2147483647.0) continue;
+        k.order = grid_order(c, ext, 0);
+        const double ra = run_length(c, ext, orderA, c.sa), rb = run_length(c, ext, orderB, c.sb);
+        k.seg_a = ra;
+        k.seg_b = rb;
+        const double mem = (n * esA / run_efficiency(ra * esA, false, flat) +
+                            n * esB / run_efficiency(rb * esB, true, flat) +
+                            (bnz ? n * esB / run_efficiency(rb * esB, false, flat) : 0.0)) / kHbmBytesPerS;
+        const double issue = ntiles * kThreads * kRowVecK * (12.0 + (bnz ? 3 * V : 0)) / kLaneInstrPerS;
+        const double over = ntiles * kThreads * (40.0 + 10.0 * c.N) / kLaneInstrPerS;
+        const double fill = double(c.s[0]) * G / double(vcap);
+        const double rows_beta = bnz ? 1.5 : 1.0;
+        k.est_s = (std::max(mem, issue / std::max(fill, 0.05)) + 0.1 * std::min(mem, issue)) * rows_beta + over + 3e-6;
+        out.push_back(k);
+      }
+    }
+  }
+
   // ---- staged tile
   const bool hc = c.perm[0] == 0;
   const int c0 = hc ? 1 : 0;
@@ -717,14 +763,25 @@ std::vector<Candidate> make_candidates(const Canon& c, int din, int dout, double
   std::stable_sort(out.begin(), out.end(),
                    [](const Candidate& a, const Candidate& b) { return a.est_s < b.est_s; });
   std::vector<Candidate> rows_keep;
-  int nrows = 0;
+  int nrows = 0, nvrows = 0;
   for (const auto& q : out)
-    if (!q.rows || nrows++ < 3) rows_keep.push_back(q);
+    if (!q.rows || (q.vec > 1 ? nvrows++ < 2 : nrows++ < 3)) rows_keep.push_back(q);
   out.swap(rows_keep);
   out.insert(out.end(), keep.begin(), keep.end());
   std::stable_sort(out.begin(), out.end(),
                    [](const Candidate& a, const Candidate& b) { return a.est_s < b.est_s; });
+  // the best vector multi-row copy stays among the candidates even when the
+  // model ranks it below the cut (the autotuner decides)
+  Candidate best_vrow;
+  bool have_vrow = false, kept_vrow = false;
+  for (size_t i = 0; i < out.size(); ++i)
+    if (out[i].rows && out[i].vec > 1) {
+      if (!have_vrow) best_vrow = out[i];
+      have_vrow = true;
+      kept_vrow = kept_vrow || int(i) < max_keep;
+    }
   if (int(out.size()) > max_keep) out.resize(max_keep);
+  if (have_vrow && !kept_vrow && max_keep > 1) out.back() = best_vrow;
   // the TMA-staged tile of a two-index transpose, where its strides allow a
   // tensor map: always kept among the candidates (the autotuner decides);
   // modelled at 0.96 of the copy bandwidth (measured 1-6 % above tile2 on

@@ -14,6 +14,7 @@
 #include "plan_impl.h"
 #include "batch_impl.h"
 #include "planner.h"
+#include "rowvec.h"
 #include "tma2d.h"
 
 using namespace ttc;
@@ -135,7 +136,8 @@ struct Checker {
     const int nthreads = k.pk ? k.pk : kThreads;
     if ((k.pk || k.ju) && (tp.saU != 1 || tp.sbV != 1))
       return fail("warp-mapped or packed-lane tile without unit-stride runs", tp.saU, tp.sbV);
-    if (tp.V > nthreads * K) return fail("tile larger than the threads cover", tp.V, nthreads * K);
+    const int cover = (k.rows && k.vec > 1) ? kThreads * kRowVecK * k.vec : nthreads * K;
+    if (tp.V > cover) return fail("tile larger than the threads cover", tp.V, cover);
     std::vector<int32_t> slots;
     int sbytes = 0;
     if (k.slots) sbytes = build_slot_tables(tp, p->din, ta, tb, &slots);
@@ -171,6 +173,24 @@ struct Checker {
           };
           if (!rowsp_walk<K>(k.rj, c, tp, ta, tb, t, on_pair)) ok = fail("unknown packed-row layout", k.rj, 0);
         }
+        if (!ok) return false;
+        continue;
+      }
+      if (k.rows && k.vec > 1) {
+        // the vector multi-row copy (rowvec.cu): vectors of V elements, each
+        // inside one row, 16-byte aligned relative to A's base and V-aligned
+        // relative to B's
+        const int V = k.vec;
+        if (tp.LC % V) return fail("vector row copy: row length not a multiple of the vector", tp.LC, V);
+        for (int t = 0; t < kThreads && ok; ++t)
+          walk_rows_vec(c, tp, V, t, [&](int, bool valid, int32_t offA, int32_t offB) {
+            if (!ok || !valid) return;
+            if ((c.baseA + offA) % V || (c.baseB + offB) % V) {
+              ok = fail("vector row copy: unaligned vector", c.baseA + offA, c.baseB + offB);
+              return;
+            }
+            for (int i = 0; i < V && ok; ++i) ok = pair(c.baseA + offA + i, c.baseB + offB + i);
+          });
         if (!ok) return false;
         continue;
       }

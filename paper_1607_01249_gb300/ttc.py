@@ -229,7 +229,8 @@ class Plan:
                 "ncandidates": inf.ncandidates, "lanes": (inf.lanes_a, inf.lanes_b),
                 "slot_tables": bool(inf.slot_tables), "packed_threads": inf.packed_threads,
                 "packed_rows": inf.packed_rows,
-                "kernel": ({0: "empty", 1: "copy_kernel", 3: "rowcopy_kernel", 4: "tma2d_kernel"}.get(inf.variant) or
+                "kernel": ({0: "empty", 1: "copy_kernel", 3: "rowcopy_vec_kernel" if inf.vec_in > 1 else "rowcopy_kernel",
+                            4: "tma2d_kernel"}.get(inf.variant) or
                            ("tile2_kernel" if inf.lanes_a else "tilep_kernel" if inf.packed_threads else
                             "rowsp_kernel" if inf.packed_rows else
                             "tile_slots_kernel" if inf.slot_tables else "tile_kernel"))}

@@ -385,3 +385,41 @@ def test_autotune_choice_is_remembered_for_new_plans(tmp_path):
     b = ttc.Plan(p.perm, p.sizes, alpha=p.alpha)
     H.full_check(p, seed=3, plan=b)              # first execution applies the cache
     assert a.describe(chosen).split(" est_us")[0] == b.describe().split(" est_us")[0]
+
+
+ROWVEC_CASES = [
+    ((0, 2, 1), (256, 16, 64), "f32", "bf16", 1.0, 0.0),
+    ((0, 2, 1), (36, 10, 7), "f32", "f32", 1.5, 0.5),
+    ((0, 2, 1), (64, 30, 20), "f64", "f64", -0.75, 0.25),
+    ((0, 2, 1, 3), (64, 8, 12, 5), "bf16", "f32", 1.0, 0.5),
+    ((0, 2, 1), (128, 9, 40), "f32", "e4m3", 1.0, 0.0),
+    ((0, 2, 1), (370, 37, 48), "f64", "f64", 1.7, 0.4),   # a tile wider than the element-wise copy's
+]
+
+
+@pytest.mark.parametrize("perm,sizes,din,dout,alpha,beta", ROWVEC_CASES)
+def test_vector_row_copy_matches_oracle(perm, sizes, din, dout, alpha, beta):
+    """The multi-row copy with 16-byte accesses (every candidate of that
+    kind) against the oracle, bit for bit, with aligned bases and with A and
+    B offset by one element (element accesses, the same walk)."""
+    p = Problem(perm=perm, sizes=sizes, dtype_in=din, dtype_out=dout, alpha=alpha, beta=beta)
+    plan = ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta)
+    idx = [i for i in range(plan.info()["ncandidates"])
+           if "rows vec=" in plan.describe(i)]
+    assert idx, "a vector row copy should be a candidate here"
+    A, B0 = H.make_inputs(p, 33)
+    want, _ = H.oracle_mirror(p, A, B0)
+    for i in idx:
+        plan.select(i)
+        assert plan.info()["kernel"] == "rowcopy_vec_kernel"
+        assert plan.verify_schedule() == ""
+        got, _ = H.run_gpu(p, A, B0, plan=plan)
+        ok, msg = H.compare_bits(got, want, dout, nan_as_nan=True)
+        assert ok, (i, msg)
+        # misaligned bases: one element past a fresh allocation
+        dA = H.to_device(np.concatenate([A[:1], A]), din)[1:]
+        dB = H.to_device(np.concatenate([B0[:1], B0]), dout)[1:]
+        plan.execute(dA, dB)
+        torch.cuda.synchronize()
+        ok, msg = H.compare_bits(H.to_host(dB, dout), want, dout, nan_as_nan=True)
+        assert ok, (i, "misaligned", msg)
