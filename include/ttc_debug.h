@@ -87,9 +87,10 @@ ttc_status ttc_debug_contraction_use_cublas(ttc_contraction_t c, int use);
 /*
  * The tile shape of the BF16 contraction's tensor-core GEMM: variant 0 lets
  * the library pick (the default); 1, 4 and 5 force one CTA per 128 x 256,
- * 128 x 192 or 128 x 128 output tile; 2 and 3 a pair of CTAs on neighbouring
- * SMs per 256 x 256 or 256 x 128 tile; -1 leaves the setting as it is.
- * *last_used (if not NULL) receives the shape the last execution ran (1..5;
+ * 128 x 192 or 128 x 128 output tile; 2, 6 and 3 a pair of CTAs on
+ * neighbouring SMs per 256 x 256, 256 x 192 or 256 x 128 tile; -1 leaves the
+ * setting as it is.  Other values return TTC_ERR_INVALID_ARG.
+ * *last_used (if not NULL) receives the shape the last execution ran (1..6;
  * 0 before the first).  A pair shape falls back to 1 when K = 0 or the
  * device runs no CTA pairs.
  */

@@ -132,7 +132,7 @@ __device__ __forceinline__ uint32_t find_problem(const uint32_t* __restrict__ ti
 // launch at no per-tile host cost).  The problem's descriptor is read from
 // global memory, where it stays cached for the problem's other tiles.
 template <int DIN, int DOUT, int EK, int PATH, int J>
-__global__ void __launch_bounds__(kThreads, EK == EK_RT_B ? 5 : 6) batch_kernel(const BatchDesc* __restrict__ descs,
+__global__ void __launch_bounds__(kThreads, 8) batch_kernel(const BatchDesc* __restrict__ descs,
                                                             const TileRec* __restrict__ recs,
                                                             const uint32_t* __restrict__ tile0, uint32_t nprob,
                                                             uint32_t first) {

@@ -557,7 +557,7 @@ ttc_status ttc_debug_contraction_use_cublas(ttc_contraction_t c, int use) {
 
 ttc_status ttc_debug_contraction_gemm_variant(ttc_contraction_t c, int variant, int* last_used) {
   if (!c) return fail(TTC_ERR_INVALID_ARG, "contraction is NULL");
-  if (variant > 5) return fail(TTC_ERR_INVALID_ARG, "variant must be -1..5");
+  if (variant > 6) return fail(TTC_ERR_INVALID_ARG, "variant must be -1..6");
   std::lock_guard<std::mutex> lk(c->mu);
   if (variant >= 0) c->gemm_variant = variant;
   if (last_used) *last_used = c->gemm_used;

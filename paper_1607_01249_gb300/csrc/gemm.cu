@@ -263,11 +263,13 @@ struct PairCfg {
   static constexpr int kBHalf = BN / 2;                     // rows of B per CTA
   static constexpr int kBTile = kBHalf * kGK * 2;
   static constexpr int kStageBytes = kATile + kBTile;       // per CTA
-  static constexpr int kStages = BN == 256 ? 7 : 9;
-  static constexpr uint32_t kCols = 2 * BN;                 // two accumulators
+  static constexpr int kStages = BN == 256 ? 7 : BN == 192 ? 8 : 9;
+  static constexpr uint32_t kCols = BN == 128 ? 256 : 512;  // two accumulators (a power of two)
+  static constexpr uint32_t kAccStride = kCols / 2;         // accumulator b at column b x this
   static constexpr int kSmem = 1024 + kStages * kStageBytes + 256;
 };
-static_assert(PairCfg<256>::kSmem <= 232448 && PairCfg<128>::kSmem <= 232448, "shared memory");
+static_assert(PairCfg<256>::kSmem <= 232448 && PairCfg<192>::kSmem <= 232448 && PairCfg<128>::kSmem <= 232448,
+              "shared memory");
 
 template <int BN>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGThreads, 1)
@@ -364,7 +366,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGThreads, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t acc_tmem = tmem + uint32_t(BN * b);
+        const uint32_t acc_tmem = tmem + P::kAccStride * uint32_t(b);
         for (int kt = 0; kt < nk; ++kt, ++it) {
           const int s = it % S;
           if (!bar_wait(full0 + 8 * s, uint32_t((it / S) & 1))) {
@@ -414,7 +416,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      store_accumulator<BN>(tmem + uint32_t(BN * b), o, q, h, nb * BN, N, C, alpha, beta, false);
+      store_accumulator<BN>(tmem + P::kAccStride * uint32_t(b), o, q, h, nb * BN, N, C, alpha, beta, false);
       // this warp's reads of the accumulator are done: tell the issuer
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -642,7 +644,7 @@ bool make_map(CUtensorMap* map, const uint16_t* base, int64_t K, int64_t rows, i
 }
 
 std::mutex g_attr_mu;
-bool g_attr_set[64][6] = {};
+bool g_attr_set[64][7] = {};   // per device and GemmVariant
 int g_pairs[64] = {};          // co-resident CTA pairs of the pair kernel (0: not yet known)
 
 template <class F>
@@ -680,8 +682,10 @@ int pairs_on(int dev, int sms) {
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-int tile_n_of(int v) { return v == GEMM_SINGLE_192 ? 192 : (v == GEMM_SINGLE_128 || v == GEMM_PAIR_128) ? 128 : 256; }
-bool is_pair(int v) { return v == GEMM_PAIR_256 || v == GEMM_PAIR_128; }
+int tile_n_of(int v) {
+  return (v == GEMM_SINGLE_192 || v == GEMM_PAIR_192) ? 192 : (v == GEMM_SINGLE_128 || v == GEMM_PAIR_128) ? 128 : 256;
+}
+bool is_pair(int v) { return v == GEMM_PAIR_256 || v == GEMM_PAIR_192 || v == GEMM_PAIR_128; }
 
 template <int BN>
 cudaError_t launch_single(int dev, int which, int sms, const CUtensorMap& ma, const CUtensorMap& mb, float* C,
@@ -729,14 +733,16 @@ int gemm_bf16_pick(int64_t M, int64_t N, int64_t K, int sms, int pairs) {
   // the 128 x 256 tile, measured on 2304^3 and 4096^3 GEMMs: 128 x 192 0.87,
   // 128 x 128 0.78 (the tensor cores re-read the A slice for every MMA, so
   // narrower tiles save less than their width), a pair's 256 x 256 0.95 per
-  // SM, a pair's 256 x 128 1.3; the epilogue about 500 units of K for 256
-  // columns.
+  // SM, a pair's 256 x 192 0.90 (the same work per SM as 128 x 192 with a
+  // third less B per SM, and no faster: the operand stream from L2 is not
+  // what limits these tiles), a pair's 256 x 128 1.3; the epilogue about 500
+  // units of K for 256 columns.
   const double kk = double(std::max<int64_t>(K, 1));
   int best = GEMM_SINGLE;
   double best_t = 1e300;
-  const int cand[5] = {GEMM_SINGLE, GEMM_SINGLE_192, GEMM_SINGLE_128, GEMM_PAIR_256, GEMM_PAIR_128};
-  const double cost[5] = {1.0, 0.87, 0.78, 0.95, 1.3};
-  for (int i = 0; i < 5; ++i) {
+  const int cand[6] = {GEMM_SINGLE, GEMM_SINGLE_192, GEMM_SINGLE_128, GEMM_PAIR_256, GEMM_PAIR_192, GEMM_PAIR_128};
+  const double cost[6] = {1.0, 0.87, 0.78, 0.95, 0.90, 1.3};
+  for (int i = 0; i < 6; ++i) {
     const int v = cand[i];
     if (is_pair(v) && (K == 0 || pairs < 1)) continue;
     const int bn = tile_n_of(v);
@@ -762,7 +768,7 @@ cudaError_t gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, fl
   if (e != cudaSuccess) return e;
   const int pairs = K > 0 ? pairs_on(dev, sms) : 0;
   int v = variant;
-  if (v < GEMM_AUTO || v > GEMM_SINGLE_128) return cudaErrorInvalidValue;
+  if (v < GEMM_AUTO || v > GEMM_PAIR_192) return cudaErrorInvalidValue;
   if (v == GEMM_AUTO) v = gemm_bf16_pick(M, N, K, sms, pairs);
   if (is_pair(v) && (K == 0 || pairs < 1)) v = GEMM_SINGLE;
   if (used) *used = v;
@@ -783,6 +789,9 @@ cudaError_t gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, fl
       break;
     case GEMM_PAIR_256:
       e = launch_pair<256>(dev, v, pairs, ma, mb, C, rowoff, coloff, M, N, K, alpha, beta, err, s);
+      break;
+    case GEMM_PAIR_192:
+      e = launch_pair<192>(dev, v, pairs, ma, mb, C, rowoff, coloff, M, N, K, alpha, beta, err, s);
       break;
     case GEMM_PAIR_128:
       e = launch_pair<128>(dev, v, pairs, ma, mb, C, rowoff, coloff, M, N, K, alpha, beta, err, s);

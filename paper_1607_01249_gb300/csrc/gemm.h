@@ -14,16 +14,17 @@ const char* gemm_bf16_check(const void* A, int64_t lda, const void* B, int64_t l
                             int64_t K);
 
 // Tile shapes of gemm_bf16: GEMM_SINGLE / _192 / _128 -- one CTA per 128 x
-// 256, 128 x 192 or 128 x 128 output tile; GEMM_PAIR_256 / GEMM_PAIR_128 --
-// a cluster of two CTAs per 256 x 256 or 256 x 128 tile (tensor-core MMAs
-// spanning both SMs); GEMM_AUTO picks by gemm_bf16_pick.
+// 256, 128 x 192 or 128 x 128 output tile; GEMM_PAIR_256 / _192 / _128 --
+// a cluster of two CTAs per 256 x 256, 256 x 192 or 256 x 128 tile
+// (tensor-core MMAs spanning both SMs); GEMM_AUTO picks by gemm_bf16_pick.
 enum GemmVariant : int {
   GEMM_AUTO = 0,
   GEMM_SINGLE = 1,
   GEMM_PAIR_256 = 2,
   GEMM_PAIR_128 = 3,
   GEMM_SINGLE_192 = 4,
-  GEMM_SINGLE_128 = 5
+  GEMM_SINGLE_128 = 5,
+  GEMM_PAIR_192 = 6
 };
 
 // The tile shape GEMM_AUTO runs for M x N x K on `sms` SMs of which `pairs`

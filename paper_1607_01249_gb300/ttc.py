@@ -339,7 +339,7 @@ class Contraction:
         return self
 
     GEMM_VARIANTS = {0: "auto", 1: "single 128x256", 2: "pair 256x256", 3: "pair 256x128", 4: "single 128x192",
-                     5: "single 128x128"}
+                     5: "single 128x128", 6: "pair 256x192"}
 
     def gemm_variant(self, variant: int = -1) -> int:
         """Testing hook: force the BF16 GEMM's tile shape (GEMM_VARIANTS; 0
