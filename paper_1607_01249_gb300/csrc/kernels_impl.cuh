@@ -217,7 +217,7 @@ __device__ __forceinline__ void slots_body(const store_t<DIN>* __restrict__ Ab, 
 }
 
 template <int DIN, int DOUT, int EK>
-__global__ void __launch_bounds__(kThreads, EK == EK_AXPBY ? 4 : 5) tile_slots_kernel(const store_t<DIN>* __restrict__ A,
+__global__ void __launch_bounds__(kThreads, sizeof(stage_t<DIN>) == 4 ? (EK == EK_AXPBY ? 4 : 5) : (EK == EK_AXPBY ? 5 : 8)) tile_slots_kernel(const store_t<DIN>* __restrict__ A,
                                                                  store_t<DOUT>* __restrict__ B,
                                                                  const __grid_constant__ TileParams p) {
   using S = stage_t<DIN>;
@@ -281,7 +281,7 @@ __device__ __forceinline__ void tile2_tabs(const store_t<DIN>* __restrict__ Ab, 
 }
 
 template <int DIN, int DOUT, int JU, int JW, int EK>
-__global__ void __launch_bounds__(kThreads, 6) tile2_kernel(const store_t<DIN>* __restrict__ A,
+__global__ void __launch_bounds__(kThreads, EK == EK_AXPBY && JW == 4 ? 6 : 8) tile2_kernel(const store_t<DIN>* __restrict__ A,
                                                             store_t<DOUT>* __restrict__ B,
                                                             const __grid_constant__ TileParams p) {
   using S = stage_t<DIN>;
@@ -346,7 +346,7 @@ __device__ __forceinline__ void tilep_tile(const store_t<DIN>* __restrict__ Ab, 
 }
 
 template <int DIN, int DOUT, int JU, int JW, int EK>
-__global__ void __launch_bounds__(kThreads, EK == EK_AXPBY ? 4 : JU == 1 ? 5 : 6) tilep_kernel(
+__global__ void __launch_bounds__(kThreads, EK == EK_AXPBY ? 5 : JU == 1 ? 5 : 8) tilep_kernel(
     const store_t<DIN>* __restrict__ A, store_t<DOUT>* __restrict__ B, const __grid_constant__ TileParams p) {
   using S = stage_t<DIN>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -396,7 +396,7 @@ __device__ __forceinline__ void rowsp_tile(const store_t<DIN>* __restrict__ Ab, 
 }
 
 template <int DIN, int DOUT, int J, int EK>
-__global__ void __launch_bounds__(kThreads, EK == EK_AXPBY ? 3 : 4) rowsp_kernel(
+__global__ void __launch_bounds__(kThreads, sizeof(stage_t<DIN>) == 4 ? (EK == EK_AXPBY ? 3 : 4) : (EK == EK_AXPBY ? 5 : 6)) rowsp_kernel(
     const store_t<DIN>* __restrict__ A, store_t<DOUT>* __restrict__ B, const __grid_constant__ TileParams p) {
   const float scale = cta_fp8_scale<EK>(p.epi);
   const TileCoord c = cta_tile_coord(p);

@@ -43,7 +43,7 @@ __device__ __forceinline__ void load_vec(const T* __restrict__ p, T (&v)[V]) {
 }
 
 template <int DIN, int DOUT, int EK, bool VIO>
-__global__ void __launch_bounds__(kThreads) rowcopy_vec_kernel(const store_t<DIN>* __restrict__ A,
+__global__ void __launch_bounds__(kThreads, EK == EK_FP8 ? 4 : 1) rowcopy_vec_kernel(const store_t<DIN>* __restrict__ A,
                                                                store_t<DOUT>* __restrict__ B,
                                                                const __grid_constant__ TileParams p) {
   using TI = store_t<DIN>;
