@@ -565,6 +565,20 @@ def run_batch(args, rank, world):
         for pl, a, b in zip(plans, pa, pb):
             pl.execute(a, b, stream)
 
+    # the cost model's batch-body schedules, then (unless --autotune 0) the
+    # timed choice among each plan's best few (ttc_batch_autotune, outside
+    # the timed region), which the reported step uses
+    tune = None
+    if args.autotune > 0:
+        ms_cm, _ = timed(lambda: batch.graph_launch(stream), max(1, args.steps // 2))
+        ncand = min(args.autotune, 4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        retuned = batch.autotune(ncand, stream)
+        torch.cuda.synchronize()
+        tune = {"candidates_timed_per_plan": ncand, "plans": len(plans), "plans_retuned": retuned,
+                "tuning_wall_s": round(time.perf_counter() - t0, 2),
+                "cost_model_GB/s": round(job_rate(bytes_step, world, ms_cm) / 1e9, 2)}
     clk = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if clk:
         clk.start()
@@ -590,6 +604,7 @@ def run_batch(args, rank, world):
                      "GB/s": round(job_rate(bytes_step, world, ms_c) / 1e9, 2),
                      "kernel_launches_per_step": launches_c},
         "speedup_vs_per_call": round(ms_c / ms_b, 3),
+        "schedule": tune if tune else "cost model (--autotune 0)",
         "roofline": {"bound": "hbm", "achieved": round(bytes_step / (ms_b * 1e-3) / 1e9, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(bytes_step / (ms_b * 1e-3) / 1e9 / peak, 4),
                      "kernel": "one graph launch: the batch_kernel launches (one per class)"
@@ -1244,7 +1259,8 @@ def main():
                                 "transposes_per_s": b["batch"]["transposes_per_s"],
                                 "per_call_transposes_per_s": b["per_call"]["transposes_per_s"],
                                 "speedup_vs_per_call": b["speedup_vs_per_call"], "ms_per_step": b["ms_per_step"],
-                                "roofline_frac": b["roofline"]["frac"], "timing": "CUDA events"}
+                                "roofline_frac": b["roofline"]["frac"], "schedule": b["schedule"],
+                                "timing": "CUDA events"}
             if not args.no_serving:
                 sub.steps = min(args.steps, 3)
                 sv = run_serving(sub, rank, world)

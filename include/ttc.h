@@ -271,6 +271,21 @@ int64_t ttc_launch_count(void);
  *  ttc_batch_set_direct_threshold  problems of at least min_elements
  *                     elements run as their own kernels; 0 or less (the
  *                     default) puts every problem in the batch kernels.
+ *  ttc_batch_autotune  the timed search of section 2.1 stages 4-6 for the
+ *                     batch body: for every distinct plan in the batch below
+ *                     the direct threshold, time up to max_candidates of the
+ *                     plan's batch-body schedules (tile shape, lane layout,
+ *                     rows or chunks; the cost model's order, its first
+ *                     choice included) as a one-problem launch of the batch
+ *                     kernel on temporary tensors (the caller's are not
+ *                     touched), and keep the fastest in the plan, where
+ *                     every batch and server that takes the plan afterwards
+ *                     finds it.  Synchronises `stream`, allocates and frees
+ *                     its own device memory, and marks the batch for a
+ *                     rebuild (the next execution or graph launch uploads the
+ *                     new descriptors and captures a new graph).  *retuned
+ *                     (may be NULL) receives how many plans changed schedule.
+ *                     max_candidates < 1 returns TTC_ERR_INVALID_ARG.
  *  ttc_batch_destroy  release the batch (not the plans); no work using it may
  *                     be queued.
  *  ttc_batch_info     number of problems and of tiles of the batch.
@@ -285,6 +300,7 @@ ttc_status ttc_batch_graph_launch(ttc_batch_t batch, ttc_stream_t stream);
 ttc_status ttc_batch_destroy(ttc_batch_t batch);
 ttc_status ttc_batch_info(ttc_batch_t batch, int64_t* problems, int64_t* tiles);
 ttc_status ttc_batch_set_direct_threshold(ttc_batch_t batch, int64_t min_elements);
+ttc_status ttc_batch_autotune(ttc_batch_t batch, int max_candidates, ttc_stream_t stream, int64_t* retuned);
 
 /*
  * Tensor contraction by Transpose-Transpose-GEMM-Transpose (TTGT; the use of

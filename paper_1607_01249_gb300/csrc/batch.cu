@@ -21,6 +21,7 @@
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -190,18 +191,20 @@ namespace ttc {
 
 namespace {
 
-std::shared_ptr<const BatchTemplate> make_template(const ttc_plan_s* p) {
+// the batch body's candidate schedules of a plan, best first by the cost
+// model (tiles of at most the batch body's volume)
+std::vector<Candidate> batch_candidates(const ttc_plan_s* p, int keep) {
+  return make_candidates(p->canon, p->din, p->dout, p->beta, keep, kThreads * batch_k_for(p->din == DT_F64 ? 8 : 4));
+}
+
+// the batch template of a plan with schedule k
+std::shared_ptr<const BatchTemplate> make_template_for(const ttc_plan_s* p, const Candidate& k) {
   auto t = std::make_shared<BatchTemplate>();
   if (p->canon.n == 0 || p->dout == DT_E4M3 || is_complex(p->din)) return t;
   BatchDesc* d = &t->d;
   std::memset(d, 0, sizeof(*d));
   d->din = p->din;
   d->dout = p->dout;
-  // tiles for the batch body: the best schedule with at most its tile volume
-  const std::vector<Candidate> bc =
-      make_candidates(p->canon, p->din, p->dout, p->beta, 4, kThreads * batch_k_for(p->din == DT_F64 ? 8 : 4));
-  if (bc.empty()) return t;       // not batchable: the batch runs it as a single-plan kernel
-  const Candidate& k = bc.front();
   d->beta_nz = p->beta_nonzero() ? 1 : 0;
   if (k.variant == VAR_TILE) {
     std::vector<int32_t> ta, tb;
@@ -225,6 +228,14 @@ std::shared_ptr<const BatchTemplate> make_template(const ttc_plan_s* p) {
   }
   t->ok = true;
   return t;
+}
+
+// the cost model's choice (the template a plan starts with)
+std::shared_ptr<const BatchTemplate> make_template(const ttc_plan_s* p) {
+  if (p->canon.n == 0 || p->dout == DT_E4M3 || is_complex(p->din)) return std::make_shared<BatchTemplate>();
+  const std::vector<Candidate> bc = batch_candidates(p, 4);
+  if (bc.empty()) return std::make_shared<BatchTemplate>();   // the batch runs it as a single-plan kernel
+  return make_template_for(p, bc.front());
 }
 
 }  // namespace
@@ -596,6 +607,127 @@ ttc_status ttc_batch_set_direct_threshold(ttc_batch_t b, int64_t min_elements) {
   b->direct_min = min_elements;
   b->dirty = true;
   return TTC_OK;
+}
+
+ttc_status ttc_batch_autotune(ttc_batch_t b, int max_candidates, ttc_stream_t stream, int64_t* retuned) {
+  if (!b) return fail(TTC_ERR_INVALID_ARG, "batch is NULL");
+  if (max_candidates < 1) return fail(TTC_ERR_INVALID_ARG, "max_candidates must be >= 1");
+  std::lock_guard<std::mutex> lk(b->mu);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (retuned) *retuned = 0;
+  // the distinct plans that run in the batch body
+  std::vector<ttc_plan_s*> plans;
+  std::set<ttc_plan_s*> seen;
+  size_t maxA = 16, maxB = 16;
+  for (auto& it : b->items) {
+    ttc_plan_s* p = it.plan;
+    if (p->canon.n == 0 || (b->direct_min > 0 && p->canon.n >= b->direct_min)) continue;
+    if (!seen.insert(p).second) continue;
+    plans.push_back(p);
+    maxA = std::max(maxA, size_t(p->canon.spanA) * dtype_size(p->din));
+    maxB = std::max(maxB, size_t(p->canon.spanB) * dtype_size(p->dout));
+  }
+  if (plans.empty()) return TTC_OK;
+  // temporary tensors (the caller's are not touched) and one problem's
+  // descriptor, tables and records, grown as needed
+  void *dA = nullptr, *dB = nullptr, *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&dA, maxA);
+  if (e == cudaSuccess) e = cudaMalloc(&dB, maxB);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dA, 0, maxA, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dB, 0, maxB, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  ttc_status st = e == cudaSuccess ? TTC_OK : fail(TTC_ERR_OOM, "batch autotune buffers");
+  constexpr int kReps = 3;
+  for (size_t pi = 0; pi < plans.size() && st == TTC_OK; ++pi) {
+    ttc_plan_s* p = plans[pi];
+    const std::vector<Candidate> bc = batch_candidates(p, std::max(4, max_candidates));
+    const int n = std::min<int>(max_candidates, int(bc.size()));
+    if (n < 2) continue;   // nothing to choose between
+    std::shared_ptr<const BatchTemplate> best;
+    float best_ms = 0.f;
+    int best_i = -1;
+    for (int i = 0; i < n && st == TTC_OK; ++i) {
+      std::shared_ptr<const BatchTemplate> t = make_template_for(p, bc[size_t(i)]);
+      if (!t->ok || t->d.ntiles == 0) continue;
+      BatchDesc d = t->d;
+      d.A = dA;
+      d.B = dB;
+      d.tile0 = 0;
+      std::vector<TileRec> recs;
+      batch_records(d, 0, &recs);
+      const size_t off_tab = (sizeof(BatchDesc) + 255) & ~size_t(255);
+      const size_t off_rec = (off_tab + t->tabs.size() * 4 + 255) & ~size_t(255);
+      const size_t bytes = off_rec + recs.size() * sizeof(TileRec);
+      if (bytes > scratch_bytes) {
+        // the previous scratch may still be read by queued launches
+        if (scratch) {
+          e = cudaStreamSynchronize(s);
+          if (e == cudaSuccess) e = cudaFree(scratch);
+          scratch = nullptr;
+          scratch_bytes = 0;
+          if (e != cudaSuccess) {
+            st = cuda_fail(e, "batch autotune scratch");
+            break;
+          }
+        }
+        if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
+          scratch = nullptr;
+          st = fail(TTC_ERR_OOM, "batch autotune scratch allocation failed");
+          break;
+        }
+        scratch_bytes = bytes;
+      }
+      char* base = static_cast<char*>(scratch);
+      if (d.path != BP_COPY) {
+        d.tp.tabA = reinterpret_cast<int32_t*>(base + off_tab);
+        d.tp.tabB = d.tp.tabA + t->tabA_count;
+      }
+      // (synchronous copies: the previous candidate's launches have ended
+      // before this one's descriptor replaces theirs)
+      e = cudaStreamSynchronize(s);
+      if (e == cudaSuccess) e = cudaMemcpy(base, &d, sizeof(BatchDesc), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && !t->tabs.empty())
+        e = cudaMemcpy(base + off_tab, t->tabs.data(), t->tabs.size() * 4, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(base + off_rec, recs.data(), recs.size() * sizeof(TileRec), cudaMemcpyHostToDevice);
+      std::vector<BatchRange> ranges;
+      batch_ranges(std::vector<BatchDesc>{d}, &ranges);
+      const BatchDesc* dd = reinterpret_cast<const BatchDesc*>(base);
+      const TileRec* dr = reinterpret_cast<const TileRec*>(base + off_rec);
+      if (e == cudaSuccess) e = batch_launch(dd, dr, nullptr, 0, ranges, t->smem, s);   // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = batch_launch(dd, dr, nullptr, 0, ranges, t->smem, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "batch autotune timing");
+        break;
+      }
+      if (!best || ms < best_ms) {
+        best = t;
+        best_ms = ms;
+        best_i = i;
+      }
+    }
+    if (st == TTC_OK && best) {
+      std::lock_guard<std::mutex> pl(p->batch_mu);
+      p->batch_tmpl = best;
+      if (retuned && best_i != 0) ++*retuned;
+    }
+  }
+  if (dA || dB || scratch) cudaStreamSynchronize(s);
+  if (scratch) cudaFree(scratch);
+  if (dA) cudaFree(dA);
+  if (dB) cudaFree(dB);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  b->dirty = true;   // the next launch takes the chosen templates
+  return st;
 }
 
 ttc_status ttc_batch_destroy(ttc_batch_t b) {

@@ -84,6 +84,7 @@ SIGNATURES = {
     "ttc_batch_destroy": (ctypes.c_int, [_vp]),
     "ttc_batch_info": (ctypes.c_int, [_vp, _i64p, _i64p]),
     "ttc_batch_set_direct_threshold": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "ttc_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int64)]),
     "ttc_contraction_plan": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i64p,
                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i64p, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int), _i64p, ctypes.c_int, ctypes.c_int,
@@ -465,6 +466,14 @@ class Batch:
         beside the batch kernels (<= 0: none, the default)."""
         _check(lib().ttc_batch_set_direct_threshold(self._h, int(min_elements)))
         return self
+
+    def autotune(self, max_candidates: int = 4, stream=None) -> int:
+        """Time up to max_candidates batch-body schedules of each distinct
+        plan and keep the fastest (ttc_batch_autotune); returns how many
+        plans changed schedule."""
+        n = ctypes.c_int64(0)
+        _check(lib().ttc_batch_autotune(self._h, int(max_candidates), _stream(stream), ctypes.byref(n)))
+        return n.value
 
     def close(self):
         if getattr(self, "_h", None):

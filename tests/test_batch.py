@@ -84,6 +84,52 @@ def test_batch_matches_oracle_and_single_calls():
         assert H.compare_bits(single, H.to_host(dB, p.dtype_out), p.dtype_out, True)[0]
 
 
+def test_batch_autotune_argument_checks_on_the_host():
+    b = ttc.Batch()
+    with pytest.raises(ttc.TTCError) as ei:
+        b.autotune(0)
+    assert ei.value.name == "TTC_ERR_INVALID_ARG"
+    assert b.autotune(4) == 0          # an empty batch has nothing to time
+
+
+@pytest.mark.gpu
+def test_autotuned_batch_matches_oracle_and_leaves_tensors_alone():
+    """ttc_batch_autotune times each plan's batch-body schedules on its own
+    buffers: the caller's tensors are unchanged by it, and the batch built
+    from the chosen schedules (executed and replayed as a graph) still gives
+    the oracle's result for every problem."""
+    torch = pytest.importorskip("torch")
+    from tests import gpu_helpers as H
+    probs = [p for p in mixed_problems(40, 21) if p.beta == 0.0]
+    b = ttc.Batch()
+    data = []
+    for i, p in enumerate(probs):
+        plan = ttc.Plan(p.perm, p.sizes, p.dtype_in, p.dtype_out, p.alpha, p.beta, p.outer_a, p.outer_b)
+        A, B0 = H.make_inputs(p, 700 + i, "normal")
+        dA, dB = H.to_device(A, p.dtype_in), H.to_device(B0, p.dtype_out)
+        b.add(plan, dA, dB)
+        data.append((p, A, B0, dA, dB))
+    b.execute()                          # the cost model's schedules first
+    torch.cuda.synchronize()
+    before = [H.to_host(dB, p.dtype_out).copy() for p, A, B0, dA, dB in data]
+    changed = b.autotune(4)
+    torch.cuda.synchronize()
+    assert 0 <= changed <= len(probs)
+    for (p, A, B0, dA, dB), got in zip(data, before):
+        assert np.array_equal(H.to_host(dB, p.dtype_out).view(np.uint8), got.view(np.uint8)), p
+        assert np.array_equal(H.to_host(dA, p.dtype_in).view(np.uint8), A.view(np.uint8)), p
+    for launch in ("execute", "graph_launch"):
+        for p, A, B0, dA, dB in data:
+            dB.zero_()
+        getattr(b, launch)()
+        torch.cuda.synchronize()
+        for p, A, B0, dA, dB in data:
+            want, _ = H.oracle_mirror(p, A, np.zeros_like(B0))
+            bitcopy = p.alpha == 1.0 and p.dtype_in == p.dtype_out
+            ok, msg = H.compare_bits(H.to_host(dB, p.dtype_out), want, p.dtype_out, nan_as_nan=not bitcopy)
+            assert ok, (launch, p, msg)
+
+
 @pytest.mark.gpu
 def test_batch_graph_replay():
     torch = pytest.importorskip("torch")
