@@ -354,6 +354,11 @@ struct ttc_batch_s {
   std::vector<BatchRange> ranges;   // the class launches of the batch kernel
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  // every other class launch runs on this stream, forked from and joined
+  // back into the caller's, so that one class's last wave overlaps the next
+  // class's first
+  cudaStream_t lane2 = nullptr;
+  cudaEvent_t fork2 = nullptr, join2 = nullptr;
   ~ttc_batch_s() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
@@ -364,6 +369,12 @@ struct ttc_batch_s {
     }
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
+    if (lane2) {
+      cudaStreamSynchronize(lane2);
+      cudaStreamDestroy(lane2);
+    }
+    if (fork2) cudaEventDestroy(fork2);
+    if (join2) cudaEventDestroy(join2);
   }
 };
 
@@ -479,6 +490,12 @@ ttc_status batch_build(ttc_batch_s* b) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "batch side stream");
   }
+  if (b->ranges.size() > 1 && !b->lane2) {
+    e = cudaStreamCreateWithFlags(&b->lane2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join2, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "batch second class stream");
+  }
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
@@ -509,8 +526,24 @@ ttc_status batch_enqueue(ttc_batch_s* b, cudaStream_t s) {
     if (e != cudaSuccess && st == TTC_OK) st = cuda_fail(e, "batch join");
   }
   if (b->total && st == TTC_OK) {
-    e = batch_launch(b->d_descs, b->d_recs, nullptr, 0, b->ranges, b->smem, s);
-    if (e != cudaSuccess) st = cuda_fail(e, "batch kernel launch");
+    if (b->ranges.size() > 1 && b->lane2) {
+      // classes alternate between s and the batch's second stream
+      std::vector<BatchRange> even, odd;
+      for (size_t i = 0; i < b->ranges.size(); ++i) (i % 2 ? odd : even).push_back(b->ranges[i]);
+      e = cudaEventRecord(b->fork2, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->lane2, b->fork2, 0);
+      if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+      cudaError_t e1 = batch_launch(b->d_descs, b->d_recs, nullptr, 0, odd, b->smem, b->lane2);
+      e = cudaEventRecord(b->join2, b->lane2);
+      if (e == cudaSuccess && e1 == cudaSuccess)
+        e1 = batch_launch(b->d_descs, b->d_recs, nullptr, 0, even, b->smem, s);
+      const cudaError_t e2 = cudaStreamWaitEvent(s, b->join2, 0);   // always join, so a capture can end
+      if (e1 != cudaSuccess) st = cuda_fail(e1, "batch kernel launch");
+      else if (e != cudaSuccess || e2 != cudaSuccess) st = cuda_fail(e != cudaSuccess ? e : e2, "batch join");
+    } else {
+      e = batch_launch(b->d_descs, b->d_recs, nullptr, 0, b->ranges, b->smem, s);
+      if (e != cudaSuccess) st = cuda_fail(e, "batch kernel launch");
+    }
   }
   if (!b->direct.empty()) {
     e = cudaStreamWaitEvent(s, b->join, 0);      // always join, so a capture can end
