@@ -88,18 +88,20 @@ __device__ __forceinline__ float fp8_scale_of(const Epilogue& e) {
 // The E4M3 code (RNE, satfinite) of fl32(v / s), s > 0 finite, without a
 // division per element.  q = fl32(v * fl32(1/s)) differs from fl32(v / s) by
 // at most 2.5 binary32 ulps (two roundings of relative size 2^-24 each, and
-// the quotient's own half ulp).  When the codes of q moved down and up by
-// 2^-20 of its magnitude (at least 4 ulps) agree with the code of q, no E4M3
-// rounding boundary lies within the band that holds both q and fl32(v / s),
-// so q's code is the quotient's; otherwise (near a boundary, infinities, a
-// reciprocal that overflows) the quotient is formed by an IEEE division.
+// the quotient's own half ulp).  Take q moved down and up by 2^-20 of its
+// magnitude (at least 4 ulps; both ends keep q's sign): when the two ends
+// have the same code, no E4M3 rounding boundary lies between them, and since
+// rounding to nearest with saturation is monotonic, every value in the band
+// (q and fl32(v / s) among them) has that code.  Otherwise (near a boundary,
+// a zero of negative sign, infinities, NaN, a reciprocal that overflows) the
+// quotient is formed by an IEEE division.  One paired conversion per element.
 __device__ __forceinline__ uint8_t e4m3_of_quotient(float v, float s, float r) {
   const float q = __fmul_rn(v, r);
   const float d = __fmul_rn(fabsf(q), 0x1p-20f);
   const __nv_fp8x2_storage_t lh =
       __nv_cvt_float2_to_fp8x2(make_float2(__fsub_rn(q, d), __fadd_rn(q, d)), __NV_SATFINITE, __NV_E4M3);
-  const uint8_t c = uint8_t(__nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3));
-  if (uint8_t(lh & 0xffu) == c && uint8_t(lh >> 8) == c && r < __int_as_float(0x7f800000)) return c;
+  const uint8_t lo = uint8_t(lh & 0xffu);
+  if (lo == uint8_t(lh >> 8) && q == q && r < __int_as_float(0x7f800000)) return lo;
   return uint8_t(__nv_cvt_float_to_fp8(__fdiv_rn(v, s), __NV_SATFINITE, __NV_E4M3));
 }
 
