@@ -257,10 +257,13 @@ int64_t ttc_launch_count(void);
  *                     scale needs a pre-pass of its own; so are complex plans
  *                     (the batch kernels' epilogue covers the real pairs).
  *  ttc_batch_execute  enqueue the batch on `stream`: one launch per class
- *                     for the problems below the direct threshold, and
- *                     beside them, on a stream of the batch
- *                     forked from and joined back into `stream`, one
- *                     single-plan launch per problem at or above it.  The
+ *                     for the problems below the direct threshold (every
+ *                     other class on a second stream of the batch, forked
+ *                     from and joined back into `stream`, so that one
+ *                     class's last wave overlaps the next class's first),
+ *                     and beside them, on a third stream of the batch
+ *                     forked and joined the same way, one single-plan
+ *                     launch per problem at or above it.  The
  *                     first execution after an add builds and uploads the
  *                     descriptors and sets up the direct problems' plans
  *                     (synchronous, allocates device memory owned by the batch
