@@ -353,10 +353,15 @@ ttc_status ttc_batch_autotune(ttc_batch_t batch, int max_candidates, ttc_stream_
  *  ttc_contraction_info     GEMM extents m, n, k and which tensors are
  *                           permuted (bit 0: A, bit 1: B, bit 2: C).
  *  ttc_contraction_autotune ttc_plan_autotune (max_candidates, stream) on
- *                           each of the contraction's permute plans; call
- *                           it before the first execution on a device, or
- *                           the permutes keep the schedules they started
- *                           with.  Synchronises `stream`.
+ *                           each of the contraction's permute plans; in the
+ *                           BF16 mode, before the first execution, it also
+ *                           times the two operand permutes with the
+ *                           contracted labels in B's order instead of A's
+ *                           (both operands share the order) and keeps the
+ *                           faster pair.  Call it before the first
+ *                           execution on a device, or the permutes keep the
+ *                           schedules they started with.  Synchronises
+ *                           `stream`.
  *  ttc_contraction_destroy  release (no work using it may be queued).
  */
 typedef struct ttc_contraction_s* ttc_contraction_t;

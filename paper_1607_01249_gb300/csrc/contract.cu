@@ -68,6 +68,13 @@ struct ttc_contraction_s {
   ttc_plan_t planC = nullptr;  // C' -> C with beta, when C is not a GEMM output layout
   size_t wsC = 0;
   int64_t sizeA = 0, sizeB = 0, sizeC = 0;   // elements of each tensor
+  // BF16 mode: what the K-major operands are built from, and the other
+  // order of the contracted labels (B's, when it differs from A's) that the
+  // autotuner may take instead (both operands share the order; the GEMM and
+  // C's offsets do not depend on it)
+  std::vector<int> mA, mB, freeA, freeB, kalt;
+  std::vector<int64_t> sA, sB;
+  std::map<int, int64_t> ext;
   std::map<int, DevState> dev;
   ~ttc_contraction_s() {
     if (opA.plan) ttc_plan_destroy(opA.plan);
@@ -281,6 +288,19 @@ ttc_status ttc_contraction_plan(ttc_contraction_t* out, int nA, const int* modes
       st = setup_kmajor(mA, sA, contracted, freeA, ext, c->M, dt, &c->kpitch, &c->opA);
       if (st == TTC_OK) st = setup_kmajor(mB, sB, contracted, freeB, ext, c->N, dt, &c->kpitch, &c->opB);
       if (st != TTC_OK) return st;
+      std::vector<int> kB;
+      for (int m : mB)
+        if (where[m] == 3) kB.push_back(m);
+      if (kB != contracted) {
+        c->kalt = kB;
+        c->mA = mA;
+        c->mB = mB;
+        c->sA = sA;
+        c->sB = sB;
+        c->freeA = freeA;
+        c->freeB = freeB;
+        c->ext = ext;
+      }
     }
     std::map<int, int64_t> strideC;
     int64_t acc = 1;
@@ -520,6 +540,31 @@ ttc_status ttc_contraction_info(ttc_contraction_t c, int64_t* m, int64_t* n, int
 ttc_status ttc_contraction_autotune(ttc_contraction_t c, int max_candidates, ttc_stream_t stream) {
   if (!c) return fail(TTC_ERR_INVALID_ARG, "contraction is NULL");
   std::lock_guard<std::mutex> lk(c->mu);
+  if (!c->kalt.empty() && c->dev.empty() && c->opA.plan && c->opB.plan) {
+    // BF16 mode before its first execution: the contracted labels in A's
+    // order or in B's, whichever pair of operand permutes times faster
+    float ta = 0.f, tb = 0.f, ta2 = 0.f, tb2 = 0.f;
+    ttc_status st = ttc_plan_autotune(c->opA.plan, max_candidates, stream, &ta);
+    if (st == TTC_OK) st = ttc_plan_autotune(c->opB.plan, max_candidates, stream, &tb);
+    if (st != TTC_OK) return st;
+    Operand a2, b2;
+    int64_t kp2 = 8;
+    st = setup_kmajor(c->mA, c->sA, c->kalt, c->freeA, c->ext, c->M, c->dtype, &kp2, &a2);
+    if (st == TTC_OK) st = setup_kmajor(c->mB, c->sB, c->kalt, c->freeB, c->ext, c->N, c->dtype, &kp2, &b2);
+    if (st == TTC_OK) st = ttc_plan_autotune(a2.plan, max_candidates, stream, &ta2);
+    if (st == TTC_OK) st = ttc_plan_autotune(b2.plan, max_candidates, stream, &tb2);
+    if (st == TTC_OK && ta2 + tb2 < 0.98f * (ta + tb)) {
+      std::swap(c->opA, a2);
+      std::swap(c->opB, b2);
+      c->kpitch = kp2;
+    }
+    if (a2.plan) ttc_plan_destroy(a2.plan);
+    if (b2.plan) ttc_plan_destroy(b2.plan);
+    if (st != TTC_OK) return st;
+    c->kalt.clear();   // decided
+    if (c->planC) return ttc_plan_autotune(c->planC, max_candidates, stream, nullptr);
+    return TTC_OK;
+  }
   for (ttc_plan_t p : {c->opA.plan, c->opB.plan, c->planC}) {
     if (!p) continue;
     const ttc_status st = ttc_plan_autotune(p, max_candidates, stream, nullptr);

@@ -39,7 +39,7 @@ LAYOUTS = [
 ]
 
 
-def run_case(ma, mb, mc, ext, dtype, gemm, alpha, beta, seed, variant=None):
+def run_case(ma, mb, mc, ext, dtype, gemm, alpha, beta, seed, variant=None, autotune=0):
     sa, sb, sc = (tuple(ext[m] for m in ms) for ms in (ma, mb, mc))
     npdt = np.float32 if dtype == "f32" else np.float64
     g = inputs.rng(seed)
@@ -49,6 +49,8 @@ def run_case(ma, mb, mc, ext, dtype, gemm, alpha, beta, seed, variant=None):
     con = ttc.Contraction(ma, sa, mb, sb, mc, sc, dtype, gemm, alpha, beta)
     if variant is not None:
         con.gemm_variant(variant)
+    if autotune:
+        con.autotune(autotune)
     dA, dB, dC = (torch.from_numpy(x.copy()).cuda() for x in (A, B, C0))
     con.execute(dA, dB, dC)
     torch.cuda.synchronize()
@@ -83,6 +85,21 @@ def test_contraction_matches_definition(dtype, gemm, layout):
     ext = {m: int(g.integers(3, 19)) for m in labels}
     for alpha, beta in ((1.0, 0.0), (0.75, -1.25)):
         run_case(ma, mb, mc, ext, dtype, gemm, alpha, beta, 500 + layout)
+
+
+@pytest.mark.parametrize("layout", [((0, 3, 1, 4), (4, 2, 3), (2, 1, 0)),
+                                    ((0, 4, 1, 5), (5, 2, 4, 3), (0, 1, 2, 3)),
+                                    ((5, 1, 0, 6), (6, 3, 1, 5), (3, 0))])
+def test_autotuned_bf16_contraction_matches_definition(layout):
+    """The BF16 mode's autotuner also tries the contracted labels in B's
+    order (these layouts order them differently in A and B) and keeps the
+    faster pair of operand permutes; either way the result is the
+    definition's."""
+    ma, mb, mc = layout
+    g = inputs.rng(900)
+    ext = {m: int(g.integers(5, 17)) for m in set(ma) | set(mb) | set(mc)}
+    for alpha, beta in ((1.0, 0.0), (0.75, -1.25)):
+        run_case(ma, mb, mc, ext, "f32", "bf16", alpha, beta, 910, autotune=8)
 
 
 def test_contraction_larger_ragged_and_degenerate():
