@@ -20,10 +20,13 @@ extern "C" {
  * outer sizes as given to ttc_plan, (4) shared-memory positions stay inside
  * the tile buffer, each written once and read once, and (5) the FP8 amax
  * pre-pass visits every element of A's sub-tensor once.  Cost is linear in
- * the number of elements.  candidate = -1 checks the schedule the batched
- * body (ttc_batch_*, ttc_server_*) runs for the plan instead.  Returns TTC_OK
- * or TTC_ERR_INVALID_ARG with a description of the first violation in msg
- * (NUL-terminated, msglen bytes).
+ * the number of elements.  candidate = -1 - j checks instead the batched
+ * body's schedule j (ttc_batch_*, ttc_server_*): j = 0 is the one it runs by
+ * default, j = 1, 2, ... the further candidates ttc_batch_autotune may
+ * choose; a j beyond the plan's batch candidates returns TTC_ERR_INVALID_ARG
+ * with "no such batch candidate".  Returns TTC_OK or TTC_ERR_INVALID_ARG
+ * with a description of the first violation in msg (NUL-terminated, msglen
+ * bytes).
  */
 ttc_status ttc_debug_verify_schedule(ttc_plan_t plan, int candidate, char* msg, int msglen);
 

@@ -3,6 +3,7 @@
 // Runs the kernels' own index walks (kernels.cuh, compiled for the host) for
 // every tile / row chunk and every thread, and checks bounds, coverage and
 // the element mapping of Eq. 1 against the problem as given to ttc_plan.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -382,7 +383,7 @@ extern "C" ttc_status ttc_debug_verify_schedule(ttc_plan_t plan, int candidate, 
       std::snprintf(msg, size_t(msglen), "%s", s.c_str());
     }
   };
-  if (!plan || candidate < -1 || candidate >= int(plan->cands.size())) {
+  if (!plan || candidate >= int(plan->cands.size())) {
     say("bad plan or candidate");
     return TTC_ERR_INVALID_ARG;
   }
@@ -390,14 +391,21 @@ extern "C" ttc_status ttc_debug_verify_schedule(ttc_plan_t plan, int candidate, 
   if (plan->canon.n == 0) return TTC_OK;
   Checker ck(plan);
   Candidate k;
-  bool batch = candidate == -1;
+  bool batch = candidate < 0;
   if (batch) {
-    // the schedule the batch body (ttc_batch_*, the server) runs for this plan
+    // batch-body schedule j = -1 - candidate (ttc_batch_*, the server): 0 is
+    // the cost model's choice, the others those ttc_batch_autotune times
     if (plan->dout == DT_E4M3 || is_complex(plan->din)) return TTC_OK;    // never batched
-    const std::vector<Candidate> bc = make_candidates(plan->canon, plan->din, plan->dout, plan->beta, 4,
+    const int j = -1 - candidate;
+    const std::vector<Candidate> bc = make_candidates(plan->canon, plan->din, plan->dout, plan->beta,
+                                                      std::max(4, j + 1),
                                                       kThreads * batch_k_for(plan->din == DT_F64 ? 8 : 4));
     if (bc.empty()) return TTC_OK;    // not batchable: the batch runs it as a single-plan kernel
-    k = bc.front();
+    if (j >= int(bc.size())) {
+      say("no such batch candidate");
+      return TTC_ERR_INVALID_ARG;
+    }
+    k = bc[size_t(j)];
     if (k.variant == VAR_COPY) k.chunk = kBatchCopyChunk / (plan->din == DT_F64 ? 2 : 1);
   } else {
     k = plan->cands[candidate];

@@ -244,7 +244,8 @@ class Plan:
     def verify_schedule(self, candidate=None) -> str:
         """Host-side check of a schedule's index arithmetic (no GPU); returns
         "" when it is sound, else a description of the first violation.
-        candidate=-1 checks the batched body's schedule for this plan."""
+        candidate=-1-j checks the batched body's schedule j for this plan (0:
+        its default, then the candidates the batch autotuner may pick)."""
         if candidate is None:
             candidate = self.info()["candidate"]
         buf = ctypes.create_string_buffer(512)

@@ -322,8 +322,11 @@ def _verify_all(plan, label):
     for i in range(plan.info()["ncandidates"]):
         msg = plan.verify_schedule(i)
         assert msg == "", f"{label} candidate {i}: {msg}"
-    msg = plan.verify_schedule(-1)            # the batched body's schedule
-    assert msg == "", f"{label} batch schedule: {msg}"
+    for j in range(4):                        # the batched body's schedules (default and autotuned)
+        msg = plan.verify_schedule(-1 - j)
+        if msg == "no such batch candidate":
+            break
+        assert msg == "", f"{label} batch schedule {j}: {msg}"
 
 
 def test_schedules_are_sound_on_random_problems():
